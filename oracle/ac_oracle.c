@@ -1,0 +1,688 @@
+/*
+ * ac_oracle.c -- plain FP64 CPU restatement of the Godunov-type scheme for the
+ * 2D inviscid variable-density artificial-compressibility (AC) equations of
+ * Leakey, Glenis & Hewett, "Riemann solvers and pressure gradients in
+ * Godunov-type schemes for variable density incompressible flows"
+ * (arXiv 2108.08769).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is
+ * checked against.  Only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline load it.  It shares no code, header, table or helper with the
+ * CUDA library, and it never calls it.
+ *
+ * It is deliberately slow and literal: every step is a plain loop over a
+ * ghost-padded array, in the order the paper gives them, with no blocking or
+ * fusion.  Where the paper gives a matrix (the Jacobian, the eigenvector
+ * matrices R_x and L_x, the face rotation R) the oracle builds that matrix and
+ * multiplies by it, even where a cheaper closed form exists.
+ *
+ * Readings of points the paper leaves open (each is also listed in the design doc):
+ *  R1  beta is in pressure units (Sec. 2.1.3: c = sqrt(u^2 + 4 beta/rho)).
+ *  R2  MUSCL one-sided differences are divided by dx (the printed "dx/2" would
+ *      double every slope), and the face sits at x_i +- dx/2 (Eqs. muscl1-2,
+ *      whose "W_f - W_i" is read as x_f - x_i).
+ *  R3  Osher: the quadrature sum multiplies the jump from the left,
+ *      (1/2) sum_j w_j |A_j| (Q_R - Q_L)  (Sec. 2.4.3).
+ *  R4  RK coefficients alpha_s = 1/(s_max - s + 1); the paper fixes only the
+ *      last two (Sec. 2.2.2).                                    [parity unpinned]
+ *  R5  alpha_PI = 1 + B0 alpha_s dtau_i / dt scales the whole bracket,
+ *      pressure row included (Alg. 1, Eq. RK2, Eq. point_implicit).  An option
+ *      leaves the pressure row unscaled.
+ *  R6  dtau_i is computed once per pseudo-iteration from Q^{m} (Sec. 2.2.3).
+ *  R7  The y spectral radius uses c_y = sqrt(v^2 + 4 beta/rho).  Both
+ *      directions always contribute, also on grids one cell wide (the paper
+ *      runs its 1D tests on such 2D grids; Sec. 3.2 is stable at CFL 0.98 only
+ *      with the y term present).
+ *  R8  Residual: RMS over interior cells of the stage-1 bracket (the unsteady
+ *      residual at Q^{m}); pressure row in Pa/s (times beta).  Converged when
+ *      every field has R_k <= max(tol*R0_k, abs_tol_k), R0 being the first
+ *      iteration's norm.  tol < 0 disables the test.         [parity unpinned]
+ *  R9  The stored state holds p; the Riemann solvers use p/beta as the fifth
+ *      conserved component (Sec. 2.1.2).
+ *  R10 Ghost cells: two layers.  A wall ghost mirrors the interior cell at the
+ *      same distance from the wall: rho and p copied, normal velocity negated,
+ *      tangential velocity copied (slip) or negated (no-slip).  Transmissive
+ *      copies the boundary cell; periodic wraps.  Corners compose the x and y
+ *      rules.  The frozen real-time term follows the momentum rule.  Gravity
+ *      is reversed in wall ghosts when the pressure gradient is formed
+ *      (Sec. 2.5).                                  [corner order unpinned]
+ *  R11 Limiter G(a, b) with a the forward and b the backward difference,
+ *      s = sgn(b), sgn(0) = 0 (Sec. 2.3.1).  The new pressure gradient is not
+ *      limited (Sec. 2.3.2).
+ *  R12 The new pressure gradient uses rho, u, v of the cell at stage s-1, the
+ *      limited gradients of that stage, and the frozen real-time term.
+ *  R13 Bassi sampling at the interface: x/tau <= S_L -> left state,
+ *      <= u* -> left star, <= S_R -> right star, else right state.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ac_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Physics: flux, Jacobian, eigenstructure (Sec. 2.1.2, 2.1.3)               */
+/* ------------------------------------------------------------------------ */
+
+/* x-direction inviscid flux F_x,inv of the compact form (Sec. 2.1.2).
+ * Q = (rho, rho u, rho v, rho w, p/beta). */
+void orc_flux_x(const double Q[5], double beta, double F[5])
+{
+    double rho = Q[0];
+    double u = Q[1] / rho, v = Q[2] / rho, w = Q[3] / rho;
+    double p = beta * Q[4];
+    F[0] = rho * u;
+    F[1] = rho * u * u + p;
+    F[2] = rho * u * v;
+    F[3] = rho * u * w;
+    F[4] = u;
+}
+
+/* Jacobian A_x = dF_x,inv/dQ as printed in Sec. 2.1.3 (row-major 5x5). */
+void orc_jacobian_x(const double Q[5], double beta, double A[25])
+{
+    double rho = Q[0];
+    double u = Q[1] / rho, v = Q[2] / rho, w = Q[3] / rho;
+    double M[25] = {
+        0.0,        1.0,        0.0, 0.0, 0.0,
+        -u * u,     2.0 * u,    0.0, 0.0, beta,
+        -u * v,     v,          u,   0.0, 0.0,
+        -u * w,     w,          0.0, u,   0.0,
+        -u / rho,   1.0 / rho,  0.0, 0.0, 0.0,
+    };
+    memcpy(A, M, sizeof(M));
+}
+
+/* Eigenvalues and right/left eigenvector matrices R_x, L_x (Sec. 2.1.3). */
+void orc_eigen_x(const double Q[5], double beta, double lam[5], double R[25], double L[25])
+{
+    double rho = Q[0];
+    double u = Q[1] / rho, v = Q[2] / rho, w = Q[3] / rho;
+    double c = sqrt(u * u + 4.0 * beta / rho);
+    double l4 = 0.5 * (u + c), l5 = 0.5 * (u - c);
+    lam[0] = u; lam[1] = u; lam[2] = u; lam[3] = l4; lam[4] = l5;
+    double Rm[25] = {
+        1.0, 0.0, 0.0, l4,                   l5,
+        u,   0.0, 0.0, u * l4 + beta / rho,  u * l5 + beta / rho,
+        0.0, 1.0, 0.0, v * l4,               v * l5,
+        0.0, 0.0, 1.0, w * l4,               w * l5,
+        0.0, 0.0, 0.0, -l5 / rho,            -l4 / rho,
+    };
+    double bc = beta * c;
+    double Lm[25] = {
+        1.0 + u * u * rho / beta, -rho * u / beta,     0.0, 0.0, -rho,
+        u * u * v * rho / beta,   -u * v * rho / beta, 1.0, 0.0, -rho * v,
+        u * u * w * rho / beta,   -u * w * rho / beta, 0.0, 1.0, -rho * w,
+        -u * l4 * rho / bc,       l4 * rho / bc,       0.0, 0.0, rho / c,
+        u * l5 * rho / bc,        -l5 * rho / bc,      0.0, 0.0, -rho / c,
+    };
+    memcpy(R, Rm, sizeof(Rm));
+    memcpy(L, Lm, sizeof(Lm));
+}
+
+/* |A_x| = R_x |Lambda_x| L_x evaluated at Q (Sec. 2.4.3). */
+static void abs_jacobian_x(const double Q[5], double beta, double absA[25])
+{
+    double lam[5], R[25], L[25];
+    orc_eigen_x(Q, beta, lam, R, L);
+    for (int r = 0; r < 5; ++r)
+        for (int c = 0; c < 5; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 5; ++k)
+                s += R[r * 5 + k] * fabs(lam[k]) * L[k * 5 + c];
+            absA[r * 5 + c] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Riemann solvers (Sec. 2.4.1 - 2.4.3)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Osher flux with the Dumbser-Toro straight path and 3-point Gauss-Legendre
+ * quadrature (Sec. 2.4.3):
+ *   F = 1/2 (F(Q_L) + F(Q_R)) - 1/2 * [1/2 sum_j w_j |A(Q_j)|] (Q_R - Q_L),
+ *   Q_j = Q_L + (Q_R - Q_L) (xi_j + 1)/2.                                     */
+void orc_osher_x(const double QL[5], const double QR[5], double beta, double F[5])
+{
+    const double xi[3] = { -sqrt(3.0 / 5.0), 0.0, sqrt(3.0 / 5.0) };
+    const double wq[3] = { 5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0 };
+    double FL[5], FR[5], dQ[5], S[25];
+    orc_flux_x(QL, beta, FL);
+    orc_flux_x(QR, beta, FR);
+    for (int k = 0; k < 5; ++k) dQ[k] = QR[k] - QL[k];
+    for (int k = 0; k < 25; ++k) S[k] = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        double Qj[5], Aj[25];
+        double t = 0.5 * (xi[j] + 1.0);
+        for (int k = 0; k < 5; ++k) Qj[k] = QL[k] + dQ[k] * t;
+        abs_jacobian_x(Qj, beta, Aj);
+        for (int k = 0; k < 25; ++k) S[k] += wq[j] * Aj[k];
+    }
+    for (int r = 0; r < 5; ++r) {
+        double d = 0.0;
+        for (int c = 0; c < 5; ++c) d += 0.5 * S[r * 5 + c] * dQ[c];
+        F[r] = 0.5 * (FL[r] + FR[r]) - 0.5 * d;
+    }
+}
+
+/* Roe flux with the Roe averages of Sec. 2.4.2 (no entropy fix). */
+void orc_roe_x(const double QL[5], const double QR[5], double beta, double F[5])
+{
+    double FL[5], FR[5], dQ[5], A[25];
+    orc_flux_x(QL, beta, FL);
+    orc_flux_x(QR, beta, FR);
+    double rL = QL[0], rR = QR[0];
+    double sL = sqrt(rL), sR = sqrt(rR);
+    double uL = QL[1] / rL, uR = QR[1] / rR;
+    double vL = QL[2] / rL, vR = QR[2] / rR;
+    double wL = QL[3] / rL, wR = QR[3] / rR;
+    double rt = sqrt(rL * rR);
+    double ut = (sL * uL + sR * uR) / (sL + sR);
+    double vt = (sL * vL + sR * vR) / (sL + sR);
+    double wt = (sL * wL + sR * wR) / (sL + sR);
+    double Qt[5] = { rt, rt * ut, rt * vt, rt * wt, 0.0 };
+    abs_jacobian_x(Qt, beta, A);
+    for (int k = 0; k < 5; ++k) dQ[k] = QR[k] - QL[k];
+    for (int r = 0; r < 5; ++r) {
+        double d = 0.0;
+        for (int c = 0; c < 5; ++c) d += A[r * 5 + c] * dQ[c];
+        F[r] = 0.5 * (FL[r] + FR[r] - d);
+    }
+}
+
+/* Exact (non-iterative) star region of Bassi et al. (Sec. 2.4.1).
+ * W = (rho, u, v, p).  out = (S_L, S_R, u*, p*, rho*_L, rho*_R). */
+void orc_bassi_star(const double WL[4], const double WR[4], double beta, double out[6])
+{
+    double rL = WL[0], uL = WL[1], pL = WL[3];
+    double rR = WR[0], uR = WR[1], pR = WR[3];
+    double cL = sqrt(uL * uL + 4.0 * beta / rL);
+    double cR = sqrt(uR * uR + 4.0 * beta / rR);
+    double l4L = 0.5 * (uL + cL), l5L = 0.5 * (uL - cL);
+    double l4R = 0.5 * (uR + cR), l5R = 0.5 * (uR - cR);
+    double SL = 0.5 * (uL - cL);
+    double SR = 0.5 * (uR + cR);
+    double us = (pR - pL + rR * uR * l5R - rL * uL * l4L) / (rR * l5R - rL * l4L);
+    double ps = pR + rR * l5R * (uR - us);
+    double rsL = rL * l4L / (us - l5L);
+    double rsR = rR * l5R / (us - l4R);
+    out[0] = SL; out[1] = SR; out[2] = us; out[3] = ps; out[4] = rsL; out[5] = rsR;
+}
+
+/* Exact solution sampled at x/tau = xi (reading R13).  W = (rho, u, v, p). */
+void orc_bassi_sample(const double WL[4], const double WR[4], double beta, double xi, double W[4])
+{
+    double st[6];
+    orc_bassi_star(WL, WR, beta, st);
+    if (xi <= st[0]) {
+        memcpy(W, WL, 4 * sizeof(double));
+    } else if (xi <= st[2]) {
+        W[0] = st[4]; W[1] = st[2]; W[2] = WL[2]; W[3] = st[3];
+    } else if (xi <= st[1]) {
+        W[0] = st[5]; W[1] = st[2]; W[2] = WR[2]; W[3] = st[3];
+    } else {
+        memcpy(W, WR, 4 * sizeof(double));
+    }
+}
+
+/* Bassi flux: F_x,inv of the exact solution at the interface (Sec. 2.4.1). */
+void orc_bassi_x(const double QL[5], const double QR[5], double beta, double F[5])
+{
+    double WL[4] = { QL[0], QL[1] / QL[0], QL[2] / QL[0], beta * QL[4] };
+    double WR[4] = { QR[0], QR[1] / QR[0], QR[2] / QR[0], beta * QR[4] };
+    double W[4];
+    orc_bassi_sample(WL, WR, beta, 0.0, W);
+    /* the w component is carried like v (only the contact changes it) */
+    double st[6];
+    orc_bassi_star(WL, WR, beta, st);
+    double ww = (0.0 <= st[2]) ? QL[3] / QL[0] : QR[3] / QR[0];
+    double Q[5] = { W[0], W[0] * W[1], W[0] * W[2], W[0] * ww, W[3] / beta };
+    orc_flux_x(Q, beta, F);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Face rotation (Sec. 2.4, Alg. 2)                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Build the 5x5 rotation R = diag(1, [n; t1; t2], 1) with t1, t2 from Alg. 2. */
+void orc_rotation(const double n[3], double Rm[25])
+{
+    double t1[3], t2[3];
+    if (n[0] == 0.0) {
+        t1[0] = 1.0; t1[1] = 0.0; t1[2] = 0.0;
+    } else if (n[1] == 0.0) {
+        t1[0] = 0.0; t1[1] = 1.0; t1[2] = 0.0;
+    } else {
+        double h = sqrt(n[0] * n[0] + n[1] * n[1]);
+        t1[0] = n[1] / h; t1[1] = -n[0] / h; t1[2] = 0.0;
+    }
+    t2[0] = n[1] * t1[2] - n[2] * t1[1];
+    t2[1] = n[2] * t1[0] - n[0] * t1[2];
+    t2[2] = n[0] * t1[1] - n[1] * t1[0];
+    for (int k = 0; k < 25; ++k) Rm[k] = 0.0;
+    Rm[0] = 1.0;
+    Rm[24] = 1.0;
+    for (int c = 0; c < 3; ++c) {
+        Rm[1 * 5 + 1 + c] = n[c];
+        Rm[2 * 5 + 1 + c] = t1[c];
+        Rm[3 * 5 + 1 + c] = t2[c];
+    }
+}
+
+/* F = R^T F_x(R Q_a, R Q_b), n pointing out of a into b (Sec. 2.4). */
+void orc_face_flux(const double Qa[5], const double Qb[5], const double n[3], double beta,
+                   int riemann, double F[5])
+{
+    double Rm[25], QL[5], QR[5], Fx[5];
+    orc_rotation(n, Rm);
+    for (int r = 0; r < 5; ++r) {
+        QL[r] = 0.0; QR[r] = 0.0;
+        for (int c = 0; c < 5; ++c) {
+            QL[r] += Rm[r * 5 + c] * Qa[c];
+            QR[r] += Rm[r * 5 + c] * Qb[c];
+        }
+    }
+    if (riemann == ORC_RIEMANN_BASSI)
+        orc_bassi_x(QL, QR, beta, Fx);
+    else if (riemann == ORC_RIEMANN_ROE)
+        orc_roe_x(QL, QR, beta, Fx);
+    else
+        orc_osher_x(QL, QR, beta, Fx);
+    for (int r = 0; r < 5; ++r) {
+        F[r] = 0.0;
+        for (int c = 0; c < 5; ++c) F[r] += Rm[c * 5 + r] * Fx[c];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction (Sec. 2.3)                                                  */
+/* ------------------------------------------------------------------------ */
+
+static double sgn(double x) { return (x > 0.0) ? 1.0 : ((x < 0.0) ? -1.0 : 0.0); }
+
+/* k-limiter G(a, b) = s max(0, min(k|b|, s a), min(|b|, k s a)), s = sgn(b). */
+double orc_limiter(double a, double b, double k)
+{
+    double s = sgn(b);
+    double m1 = fmin(k * fabs(b), s * a);
+    double m2 = fmin(fabs(b), k * s * a);
+    return s * fmax(0.0, fmax(m1, m2));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ghost cells (Sec. 2.5, reading R10)                                        */
+/* ------------------------------------------------------------------------ */
+
+#define NG 2
+
+typedef struct {
+    int nx, ny, nxp, nyp;
+} padded_dims;
+
+static int pidx(const padded_dims *d, int i, int j) { return (j + NG) * d->nxp + (i + NG); }
+
+static int is_wall(int bc) { return bc == ORC_BC_WALL_SLIP || bc == ORC_BC_WALL_NOSLIP; }
+
+/* Map a (possibly ghost) index along one axis onto the interior cell it
+ * copies, counting the wall reflections (normal flips) and the no-slip
+ * reflections (tangential flips) on the way. */
+static int map_axis(int i, int n, int bc_lo, int bc_hi, int *nflip, int *tflip)
+{
+    *nflip = 0; *tflip = 0;
+    for (int guard = 0; guard < 64 && (i < 0 || i >= n); ++guard) {
+        if (i < 0) {
+            if (bc_lo == ORC_BC_PERIODIC) i += n;
+            else if (bc_lo == ORC_BC_TRANSMISSIVE) i = 0;
+            else { i = -1 - i; (*nflip)++; if (bc_lo == ORC_BC_WALL_NOSLIP) (*tflip)++; }
+        } else {
+            if (bc_hi == ORC_BC_PERIODIC) i -= n;
+            else if (bc_hi == ORC_BC_TRANSMISSIVE) i = n - 1;
+            else { i = 2 * n - 1 - i; (*nflip)++; if (bc_hi == ORC_BC_WALL_NOSLIP) (*tflip)++; }
+        }
+    }
+    return i;
+}
+
+/* Fill a padded 4-component array from interior arrays.  Component roles:
+ * 0 scalar, 1 x-momentum, 2 y-momentum, 3 scalar. */
+static void fill_padded(const orc_problem *pb, const padded_dims *d,
+                        const double *in0, const double *in1, const double *in2, const double *in3,
+                        double *P[4])
+{
+    for (int j = -NG; j < d->ny + NG; ++j)
+        for (int i = -NG; i < d->nx + NG; ++i) {
+            int nfx, tfx, nfy, tfy;
+            int si = map_axis(i, d->nx, pb->bc[0], pb->bc[1], &nfx, &tfx);
+            int sj = map_axis(j, d->ny, pb->bc[2], pb->bc[3], &nfy, &tfy);
+            int s = sj * d->nx + si;
+            double sx = ((nfx + tfy) % 2) ? -1.0 : 1.0; /* x-momentum: x-normal, y-tangential */
+            double sy = ((nfy + tfx) % 2) ? -1.0 : 1.0; /* y-momentum: y-normal, x-tangential */
+            int q = pidx(d, i, j);
+            P[0][q] = in0 ? in0[s] : 0.0;
+            P[1][q] = in1 ? sx * in1[s] : 0.0;
+            P[2][q] = in2 ? sy * in2[s] : 0.0;
+            P[3][q] = in3 ? in3[s] : 0.0;
+        }
+}
+
+/* +1 for interior cells, -1 for ghosts beyond a wall (gravity reversed). */
+static double gravity_sign(const orc_problem *pb, int i, int j)
+{
+    int wall = 0;
+    if (i < 0 && is_wall(pb->bc[0])) wall = 1;
+    if (i >= pb->nx && is_wall(pb->bc[1])) wall = 1;
+    if (j < 0 && is_wall(pb->bc[2])) wall = 1;
+    if (j >= pb->ny && is_wall(pb->bc[3])) wall = 1;
+    return wall ? -1.0 : 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial operator: the bracket of Eq. RK2                                   */
+/* ------------------------------------------------------------------------ */
+
+/* bracket = -(1/|Omega|) sum_f F_f.S_f - I_C RT + B for every interior cell
+ * (Sec. 2.2.1, Eq. RK2).  q: the stage s-1 state (rho, rho u, rho v, p);
+ * rt: the frozen real-time term for rho, rho u, rho v (may be NULL = 0);
+ * rho0: the stage-0 density for the body force.  br receives the bracket of
+ * rho, rho u, rho v and of the fifth component p/beta. */
+void orc_bracket(const orc_problem *pb, const double *const q[4], const double *const rt[3],
+                 const double *rho0, double *br[4])
+{
+    padded_dims d = { pb->nx, pb->ny, pb->nx + 2 * NG, pb->ny + 2 * NG };
+    size_t np = (size_t)d.nxp * d.nyp;
+    double dx = pb->dx, dy = pb->dy, beta = pb->beta;
+    double *buf = (double *)calloc(np * 20, sizeof(double));
+    double *P[4] = { buf, buf + np, buf + 2 * np, buf + 3 * np };         /* rho, rho u, rho v, p */
+    double *T[4] = { buf + 4 * np, buf + 5 * np, buf + 6 * np, buf + 7 * np }; /* RT (rho, rho u, rho v, -) */
+    double *U = buf + 8 * np, *V = buf + 9 * np;                           /* primitive velocities */
+    double *rx = buf + 10 * np, *ry = buf + 11 * np;                       /* limited gradients */
+    double *ux = buf + 12 * np, *uy = buf + 13 * np;
+    double *vx = buf + 14 * np, *vy = buf + 15 * np;
+    double *px = buf + 16 * np, *py = buf + 17 * np;
+
+    fill_padded(pb, &d, q[0], q[1], q[2], q[3], P);
+    if (rt) fill_padded(pb, &d, rt[0], rt[1], rt[2], NULL, T);
+
+    /* primitive variables W = (rho, u, v, p) */
+    for (size_t k = 0; k < np; ++k) {
+        U[k] = P[1][k] / P[0][k];
+        V[k] = P[2][k] / P[0][k];
+    }
+
+    double k_lim = (double)pb->limiter_k;
+    double k_p = (pb->gradp == ORC_GRADP_SUPERBEE || pb->gradp == ORC_GRADP_SPLIT_SUPERBEE) ? 2.0 : 1.0;
+
+    /* limited gradients on the interior plus the first ghost ring (Sec. 2.3.1) */
+    for (int j = -1; j <= d.ny; ++j)
+        for (int i = -1; i <= d.nx; ++i) {
+            int c = pidx(&d, i, j);
+            int e = pidx(&d, i + 1, j), w = pidx(&d, i - 1, j);
+            int n = pidx(&d, i, j + 1), s = pidx(&d, i, j - 1);
+            rx[c] = orc_limiter((P[0][e] - P[0][c]) / dx, (P[0][c] - P[0][w]) / dx, k_lim);
+            ry[c] = orc_limiter((P[0][n] - P[0][c]) / dy, (P[0][c] - P[0][s]) / dy, k_lim);
+            ux[c] = orc_limiter((U[e] - U[c]) / dx, (U[c] - U[w]) / dx, k_lim);
+            uy[c] = orc_limiter((U[n] - U[c]) / dy, (U[c] - U[s]) / dy, k_lim);
+            vx[c] = orc_limiter((V[e] - V[c]) / dx, (V[c] - V[w]) / dx, k_lim);
+            vy[c] = orc_limiter((V[n] - V[c]) / dy, (V[c] - V[s]) / dy, k_lim);
+        }
+
+    /* pressure gradient (Sec. 2.3.2) */
+    for (int j = -1; j <= d.ny; ++j)
+        for (int i = -1; i <= d.nx; ++i) {
+            int c = pidx(&d, i, j);
+            int e = pidx(&d, i + 1, j), w = pidx(&d, i - 1, j);
+            int n = pidx(&d, i, j + 1), s = pidx(&d, i, j - 1);
+            double gsg = gravity_sign(pb, i, j);
+            double gx = gsg * pb->gx, gy = gsg * pb->gy;
+            if (pb->gradp == ORC_GRADP_NEW) {
+                /* Eq. new_gradp with the product-rule expansions, x and y */
+                double rho = P[0][c], u = U[c], v = V[c];
+                double rtx = T[1][c], rty = T[2][c];
+                px[c] = -rtx
+                        - (u * u * rx[c] + 2.0 * rho * u * ux[c])
+                        - (u * v * ry[c] + rho * u * vy[c] + rho * v * uy[c])
+                        + rho * gx;
+                py[c] = -rty
+                        - (v * v * ry[c] + 2.0 * rho * v * vy[c])
+                        - (u * v * rx[c] + rho * v * ux[c] + rho * u * vx[c])
+                        + rho * gy;
+            } else if (pb->gradp == ORC_GRADP_SPLIT_MINMOD || pb->gradp == ORC_GRADP_SPLIT_SUPERBEE) {
+                /* Qian et al. hydrostatic/kinematic split (Sec. 2.3.2) */
+                double kinRx = (P[3][e] - P[3][c]) / dx - 0.5 * (P[0][c] + P[0][e]) * gx;
+                double kinLx = (P[3][c] - P[3][w]) / dx - 0.5 * (P[0][w] + P[0][c]) * gx;
+                double kinRy = (P[3][n] - P[3][c]) / dy - 0.5 * (P[0][c] + P[0][n]) * gy;
+                double kinLy = (P[3][c] - P[3][s]) / dy - 0.5 * (P[0][s] + P[0][c]) * gy;
+                px[c] = orc_limiter(kinRx, kinLx, k_p) + P[0][c] * gx;
+                py[c] = orc_limiter(kinRy, kinLy, k_p) + P[0][c] * gy;
+            } else {
+                /* standard limiter applied to p */
+                px[c] = orc_limiter((P[3][e] - P[3][c]) / dx, (P[3][c] - P[3][w]) / dx, k_p);
+                py[c] = orc_limiter((P[3][n] - P[3][c]) / dy, (P[3][c] - P[3][s]) / dy, k_p);
+            }
+        }
+
+    /* face fluxes: x-faces (i-1/2, j) for i = 0..nx, y-faces (i, j-1/2) for j = 0..ny */
+    int nxf = d.nx + 1, nyf = d.ny + 1;
+    double *FX = (double *)calloc((size_t)nxf * d.ny * 5, sizeof(double));
+    double *FY = (double *)calloc((size_t)d.nx * nyf * 5, sizeof(double));
+    const double nxv[3] = { 1.0, 0.0, 0.0 }, nyv[3] = { 0.0, 1.0, 0.0 };
+    for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i <= d.nx; ++i) {
+            int a = pidx(&d, i - 1, j), b = pidx(&d, i, j);
+            /* Eqs. muscl1-2 with x_f - x_a = +dx/2, x_f - x_b = -dx/2 */
+            double rL = P[0][a] + 0.5 * dx * rx[a], rR = P[0][b] - 0.5 * dx * rx[b];
+            double uL = U[a] + 0.5 * dx * ux[a], uR = U[b] - 0.5 * dx * ux[b];
+            double vL = V[a] + 0.5 * dx * vx[a], vR = V[b] - 0.5 * dx * vx[b];
+            double pL = P[3][a] + 0.5 * dx * px[a], pR = P[3][b] - 0.5 * dx * px[b];
+            double Qa[5] = { rL, rL * uL, rL * vL, 0.0, pL / beta };
+            double Qb[5] = { rR, rR * uR, rR * vR, 0.0, pR / beta };
+            orc_face_flux(Qa, Qb, nxv, beta, pb->riemann, &FX[((size_t)j * nxf + i) * 5]);
+        }
+    for (int j = 0; j <= d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+            int a = pidx(&d, i, j - 1), b = pidx(&d, i, j);
+            double rL = P[0][a] + 0.5 * dy * ry[a], rR = P[0][b] - 0.5 * dy * ry[b];
+            double uL = U[a] + 0.5 * dy * uy[a], uR = U[b] - 0.5 * dy * uy[b];
+            double vL = V[a] + 0.5 * dy * vy[a], vR = V[b] - 0.5 * dy * vy[b];
+            double pL = P[3][a] + 0.5 * dy * py[a], pR = P[3][b] - 0.5 * dy * py[b];
+            double Qa[5] = { rL, rL * uL, rL * vL, 0.0, pL / beta };
+            double Qb[5] = { rR, rR * uR, rR * vR, 0.0, pR / beta };
+            orc_face_flux(Qa, Qb, nyv, beta, pb->riemann, &FY[((size_t)j * d.nx + i) * 5]);
+        }
+
+    /* divergence, real-time term and body force (Sec. 2.2.1, Eq. RK2) */
+    double area = dx * dy;
+    for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+            const double *Fw = &FX[((size_t)j * nxf + i) * 5];
+            const double *Fe = &FX[((size_t)j * nxf + i + 1) * 5];
+            const double *Fs = &FY[((size_t)j * d.nx + i) * 5];
+            const double *Fn = &FY[((size_t)(j + 1) * d.nx + i) * 5];
+            double B[5] = { 0.0, rho0[j * d.nx + i] * pb->gx, rho0[j * d.nx + i] * pb->gy, 0.0, 0.0 };
+            double RT[5] = { 0.0, 0.0, 0.0, 0.0, 0.0 };
+            if (rt) {
+                RT[0] = rt[0][j * d.nx + i];
+                RT[1] = rt[1][j * d.nx + i];
+                RT[2] = rt[2][j * d.nx + i];
+            }
+            double out[5];
+            for (int k = 0; k < 5; ++k) {
+                double sumFS = Fe[k] * dy - Fw[k] * dy + Fn[k] * dx - Fs[k] * dx;
+                double IC = (k == 4) ? 0.0 : 1.0;
+                out[k] = -sumFS / area - IC * RT[k] + B[k];
+            }
+            br[0][j * d.nx + i] = out[0];
+            br[1][j * d.nx + i] = out[1];
+            br[2][j * d.nx + i] = out[2];
+            br[3][j * d.nx + i] = out[4];
+        }
+    free(FX);
+    free(FY);
+    free(buf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pseudo-time step sizes (Sec. 2.2.3)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Local pseudo-time step dtau_i = CFL |Omega| / (Lx + Ly), Lx = 1/2(|u|+c_x) dS_x,
+ * dS_x = 1/2 sum_f |S_x|_f = dy (reading R7).  Global: the minimum over cells. */
+void orc_dtau(const orc_problem *pb, const double *const q[4], double *dtau)
+{
+    int N = pb->nx * pb->ny;
+    double dSx = 0.5 * (pb->dy + pb->dy);
+    double dSy = 0.5 * (pb->dx + pb->dx);
+    double area = pb->dx * pb->dy;
+    double mn = INFINITY;
+    for (int k = 0; k < N; ++k) {
+        double rho = q[0][k], u = q[1][k] / rho, v = q[2][k] / rho;
+        double cx = sqrt(u * u + 4.0 * pb->beta / rho);
+        double cy = sqrt(v * v + 4.0 * pb->beta / rho);
+        double Lx = 0.5 * (fabs(u) + cx) * dSx;
+        double Ly = 0.5 * (fabs(v) + cy) * dSy;
+        dtau[k] = pb->cfl_tau * area / (Lx + Ly);
+        if (dtau[k] < mn) mn = dtau[k];
+    }
+    if (!pb->local_dtau)
+        for (int k = 0; k < N; ++k) dtau[k] = mn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dual time stepping (Alg. 1, Eqs. RK1-RK2, bdf, point_implicit)             */
+/* ------------------------------------------------------------------------ */
+
+static const double BDF[4][4] = {
+    { 0.0, 0.0, 0.0, 0.0 },
+    { 1.0, -1.0, 0.0, 0.0 },                    /* Backward-Euler */
+    { 1.5, -2.0, 0.5, 0.0 },                    /* BDF2 */
+    { 11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0 },      /* BDF3 */
+};
+
+/* One pseudo-iteration: Q^{m} -> Q^{m+1} in place; R receives the residual
+ * norms at Q^{m} (reading R8).  lev[0..2] hold Q^n, Q^{n-1}, Q^{n-2} for
+ * rho, rho u, rho v.  dtau_cap > 0 clips the pseudo-time step. */
+static void pseudo_iteration(const orc_problem *pb, double *q[4], const double *const lev[3][3],
+                             int order, double dt, double dtau_cap, double R[4])
+{
+    int N = pb->nx * pb->ny;
+    double *mem = (double *)malloc((size_t)N * 16 * sizeof(double));
+    double *q0[4] = { mem, mem + N, mem + 2 * N, mem + 3 * N };
+    double *rt[3] = { mem + 4 * N, mem + 5 * N, mem + 6 * N };
+    double *br[4] = { mem + 7 * N, mem + 8 * N, mem + 9 * N, mem + 10 * N };
+    double *dtau = mem + 11 * N;
+    double *qs[4] = { mem + 12 * N, mem + 13 * N, mem + 14 * N, mem + 15 * N };
+
+    /* Q^{m+1,0} <- Q^{m}  (Eq. RK1) */
+    for (int f = 0; f < 4; ++f) memcpy(q0[f], q[f], (size_t)N * sizeof(double));
+
+    /* frozen real-time term and pseudo-time step (Alg. 1; Eq. bdf) */
+    double B0 = pb->realtime ? BDF[order][0] : 0.0;
+    for (int f = 0; f < 3; ++f)
+        for (int k = 0; k < N; ++k) {
+            if (!pb->realtime) { rt[f][k] = 0.0; continue; }
+            double s = BDF[order][0] * q0[f][k];
+            for (int l = 0; l < order; ++l) s += BDF[order][l + 1] * lev[l][f][k];
+            rt[f][k] = s / dt;
+        }
+    orc_dtau(pb, (const double *const *)q0, dtau);
+    if (dtau_cap > 0.0)
+        for (int k = 0; k < N; ++k) if (dtau[k] > dtau_cap) dtau[k] = dtau_cap;
+
+    /* Runge-Kutta stages (Eq. RK2) */
+    for (int s = 1; s <= pb->s_max; ++s) {
+        double alpha = 1.0 / (double)(pb->s_max - s + 1);   /* reading R4 */
+        const double *qin[4];
+        for (int f = 0; f < 4; ++f) qin[f] = (s == 1) ? q0[f] : qs[f];
+        orc_bracket(pb, qin, (const double *const *)rt, q0[0], br);
+        if (s == 1) {
+            for (int f = 0; f < 4; ++f) {
+                double acc = 0.0, scale = (f == 3) ? pb->beta : 1.0;
+                for (int k = 0; k < N; ++k) acc += (scale * br[f][k]) * (scale * br[f][k]);
+                R[f] = sqrt(acc / (double)N);
+            }
+        }
+        for (int k = 0; k < N; ++k) {
+            double api = 1.0 + B0 * alpha * dtau[k] / dt;   /* Eq. point_implicit */
+            double coef = alpha * dtau[k] / api;
+            double coef_p = pb->alpha_pi_p_row ? coef : alpha * dtau[k];
+            qs[0][k] = q0[0][k] + coef * br[0][k];
+            qs[1][k] = q0[1][k] + coef * br[1][k];
+            qs[2][k] = q0[2][k] + coef * br[2][k];
+            qs[3][k] = q0[3][k] + pb->beta * coef_p * br[3][k];   /* p = beta (p/beta) */
+        }
+    }
+    for (int f = 0; f < 4; ++f) memcpy(q[f], qs[f], (size_t)N * sizeof(double));
+    free(mem);
+}
+
+static int finite4(const double R[4])
+{
+    for (int k = 0; k < 4; ++k) if (!isfinite(R[k])) return 0;
+    return 1;
+}
+
+int orc_physical_step(const orc_problem *pb, double *q[4], const double *const hist[2][3],
+                      double dt, double tol, int max_iters, int *iters, double R[4], double R0[4])
+{
+    int N = pb->nx * pb->ny;
+    int order = pb->bdf_order < 1 ? 1 : (pb->bdf_order > 3 ? 3 : pb->bdf_order);
+    if (order >= 2 && (!hist || !hist[0][0])) order = 1;
+    if (order >= 3 && !hist[1][0]) order = 2;
+    double *qn = (double *)malloc((size_t)N * 3 * sizeof(double));
+    const double *lev[3][3];
+    /* Q^n <- Q  (Alg. 1) */
+    for (int f = 0; f < 3; ++f) {
+        memcpy(qn + (size_t)f * N, q[f], (size_t)N * sizeof(double));
+        lev[0][f] = qn + (size_t)f * N;
+        lev[1][f] = (order >= 2) ? hist[0][f] : NULL;
+        lev[2][f] = (order >= 3) ? hist[1][f] : NULL;
+    }
+    int m = 0, status = ORC_NOT_CONVERGED;
+    double r0[4] = { 0, 0, 0, 0 }, r[4] = { 0, 0, 0, 0 };
+    while (m < max_iters) {
+        pseudo_iteration(pb, q, lev, order, dt, 0.0, r);
+        m++;
+        if (m == 1) memcpy(r0, r, sizeof(r));
+        if (!finite4(r)) { status = ORC_ERR_NONFINITE; break; }
+        if (tol >= 0.0) {
+            int ok = 1;
+            for (int k = 0; k < 4; ++k) {
+                double thr = fmax(tol * r0[k], pb->abs_tol[k]);
+                if (!(r[k] <= thr)) ok = 0;
+            }
+            if (ok) { status = ORC_OK; break; }
+        }
+    }
+    if (tol < 0.0 && status == ORC_NOT_CONVERGED && m == max_iters) status = ORC_OK;
+    if (iters) *iters = m;
+    if (R) memcpy(R, r, sizeof(r));
+    if (R0) memcpy(R0, r0, sizeof(r0));
+    free(qn);
+    return status;
+}
+
+/* Pure pseudo-time evolution (real-time term off, global dtau), stopped at
+ * pseudo-time tau_end by clipping the last step (Sec. 3.1 set-up). */
+int orc_pseudo_time_run(const orc_problem *pb, double *q[4], double tau_end, int max_iters, int *iters)
+{
+    orc_problem p = *pb;
+    p.realtime = 0;
+    p.local_dtau = 0;
+    int N = p.nx * p.ny;
+    double *dtau = (double *)malloc((size_t)N * sizeof(double));
+    double tau = 0.0, r[4];
+    int m = 0;
+    const double *lev[3][3] = { { NULL, NULL, NULL }, { NULL, NULL, NULL }, { NULL, NULL, NULL } };
+    while (tau < tau_end && m < max_iters) {
+        orc_dtau(&p, (const double *const *)q, dtau);
+        double step = dtau[0];
+        if (tau + step > tau_end) step = tau_end - tau;
+        pseudo_iteration(&p, q, lev, 1, 1.0, step, r);
+        tau += step;
+        m++;
+        if (!finite4(r)) { free(dtau); if (iters) *iters = m; return ORC_ERR_NONFINITE; }
+    }
+    free(dtau);
+    if (iters) *iters = m;
+    return ORC_OK;
+}

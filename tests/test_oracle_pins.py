@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests re-types an oracle formula.  Each checks the oracle
+against something independent of it: a finite-difference Jacobian, numpy's
+eigen-decomposition and Gauss-Legendre nodes, the Rankine-Hugoniot relations,
+the paper's printed tables (tests/golden/), closed forms of special cases,
+conservation, symmetry and well-balance invariants, and convergence to the
+exact Riemann solution.  Each test names the plausible mistakes it catches.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_08769_gb300 import workloads as W
+from conftest import load_golden
+
+RNG = np.random.default_rng(7)
+
+
+def rand_state(beta_range=(0.5, 3.0)):
+    rho = RNG.uniform(0.3, 3.0)
+    u, v = RNG.uniform(-1.0, 1.0, 2)
+    beta = RNG.uniform(*beta_range)
+    p = RNG.uniform(-1.0, 1.0)
+    return np.array([rho, rho * u, rho * v, 0.0, p / beta]), beta
+
+
+def fd_jacobian(Q, beta, h=1e-6):
+    cols = []
+    for e in np.eye(5):
+        cols.append((oracle.flux_x(Q + h * e, beta) - oracle.flux_x(Q - h * e, beta)) / (2 * h))
+    return np.array(cols).T
+
+
+# ----------------------------------------------------------------- eigenstructure
+
+def test_golden_tables_match_workloads():
+    rows = load_golden("riemann_problems.txt")
+    for r in rows:
+        assert tuple(r[1:]) == W.RIEMANN_TABLE[int(r[0])]
+
+
+def test_jacobian_is_derivative_of_flux():
+    """A_x (Sec. 2.1.3) equals the finite-difference Jacobian of F_x,inv.
+    Catches a wrong Jacobian entry or a wrong flux component."""
+    for _ in range(20):
+        Q, beta = rand_state()
+        Q[3] = RNG.uniform(-1, 1) * Q[0]  # exercise the w row too
+        A = oracle.jacobian_x(Q, beta)
+        J = fd_jacobian(Q, beta)
+        assert np.allclose(A, J, rtol=1e-7, atol=1e-7)
+
+
+def test_eigenvectors_diagonalise_jacobian():
+    """R_x Lambda L_x = A_x and L_x R_x = I (Sec. 2.1.3) against the FD Jacobian.
+    Catches sign/index slips in the printed R_x, L_x."""
+    for _ in range(20):
+        Q, beta = rand_state()
+        Q[3] = RNG.uniform(-1, 1) * Q[0]
+        lam, R, L = oracle.eigen_x(Q, beta)
+        J = fd_jacobian(Q, beta)
+        assert np.allclose(L @ R, np.eye(5), atol=1e-12)
+        assert np.allclose(R @ np.diag(lam) @ L, J, rtol=1e-7, atol=1e-7)
+        ev = np.sort(np.linalg.eigvals(J).real)
+        assert np.allclose(np.sort(lam), ev, rtol=1e-6, atol=1e-6)
+
+
+# ----------------------------------------------------------------- Riemann fluxes
+
+def test_gauss_legendre_golden_matches_numpy():
+    rows = load_golden("gauss_legendre.txt")
+    x, w = np.polynomial.legendre.leggauss(3)
+    assert np.allclose([r[1] for r in rows], x, atol=1e-15)
+    assert np.allclose([r[2] for r in rows], w, atol=1e-15)
+
+
+def test_osher_equals_numpy_path_quadrature():
+    """Osher (Sec. 2.4.3) against the same path integral built from numpy:
+    |A| from np.linalg.eig of the finite-difference Jacobian, nodes/weights
+    from leggauss, straight path in Q.  Catches a wrong 1/2 factor, wrong
+    nodes or weights, or a wrong matrix-vector order."""
+    x, w = np.polynomial.legendre.leggauss(3)
+    for _ in range(20):
+        QL, beta = rand_state()
+        QR, _ = rand_state()
+        dQ = QR - QL
+        S = np.zeros((5, 5))
+        for xj, wj in zip(x, w):
+            Qj = QL + dQ * 0.5 * (xj + 1.0)
+            # exact Jacobian from FD with tight step, then |A| by eigen-decomposition
+            J = fd_jacobian(Qj, beta, h=1e-7)
+            ev, V = np.linalg.eig(J)
+            S += wj * (V @ np.diag(np.abs(ev)) @ np.linalg.inv(V)).real
+        expect = 0.5 * (oracle.flux_x(QL, beta) + oracle.flux_x(QR, beta)) - 0.5 * (0.5 * S @ dQ)
+        got = oracle.riemann_flux("osher", QL, QR, beta)
+        assert np.allclose(got, expect, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("kind", ["osher", "roe", "bassi"])
+def test_flux_consistency(kind):
+    """F(Q, Q) = F_x,inv(Q) for every solver."""
+    for _ in range(10):
+        Q, beta = rand_state()
+        assert np.allclose(oracle.riemann_flux(kind, Q, Q, beta), oracle.flux_x(Q, beta),
+                           rtol=1e-13, atol=1e-13)
+
+
+def _rh(WL, WR, beta):
+    """Star states of the exact solver and Rankine-Hugoniot residuals of
+    the x-split conservation law across all three waves."""
+    SL, SR, us, ps, rsL, rsR = oracle.bassi_star(WL, WR, beta)
+
+    def Q(W):
+        r, u, v, p = W
+        return np.array([r, r * u, r * v, 0.0, p / beta])
+
+    QL, QR = Q(WL), Q(WR)
+    QsL = Q([rsL, us, WL[2], ps])
+    QsR = Q([rsR, us, WR[2], ps])
+    F = lambda q: oracle.flux_x(q, beta)
+    res = [F(QsL) - F(QL) - SL * (QsL - QL),
+           F(QR) - F(QsR) - SR * (QR - QsR),
+           F(QsR) - F(QsL) - us * (QsR - QsL)]
+    scale = max(np.abs(F(QL)).max(), np.abs(F(QR)).max(), abs(SL * QL).max(), 1.0)
+    return (SL, SR, us, ps, rsL, rsR), max(np.abs(r).max() for r in res) / scale
+
+
+def test_bassi_star_satisfies_rankine_hugoniot_on_table():
+    """The exact solver's star region (Sec. 2.4.1) satisfies the jump
+    conditions of the flux (Sec. 2.1.2) on all five problems of the paper's
+    table, with the contact between the acoustic waves.  Catches a wrong
+    term in u*, p*, rho*, or in the flux."""
+    for r in load_golden("riemann_problems.txt"):
+        _, rL, rR, uL, uR, pL, pR, beta, _ = r
+        st, res = _rh([rL, uL, 0.0, pL], [rR, uR, 0.0, pR], beta)
+        SL, SR, us, *_ = st
+        assert res < 1e-12, (r, res)
+        assert SL < us < SR
+
+
+def test_bassi_star_rankine_hugoniot_random():
+    for _ in range(50):
+        WL = [RNG.uniform(0.01, 3), RNG.uniform(-1, 1), RNG.uniform(-1, 1), RNG.uniform(-1, 1)]
+        WR = [RNG.uniform(0.01, 3), RNG.uniform(-1, 1), RNG.uniform(-1, 1), RNG.uniform(-1, 1)]
+        st, res = _rh(WL, WR, RNG.uniform(0.5, 3))
+        assert res < 1e-11
+
+
+# ------------------------------------------------------------------ limiter / rotation
+
+def test_limiter_is_textbook_minmod_and_superbee():
+    """G(a,b) with k=1 is minmod, k=2 superbee written as b*phi(a/b),
+    phi(r) = max(0, min(2r,1), min(r,2)) (Sweby).  Catches a swapped argument
+    or a wrong sign rule."""
+    vals = np.concatenate([np.linspace(-3, 3, 25), [0.0, 1e-300, -1e-300]])
+    for a in vals:
+        for b in vals:
+            mm = 0.0 if a * b <= 0 else math.copysign(min(abs(a), abs(b)), a)
+            assert oracle.limiter(a, b, 1) == pytest.approx(mm, abs=1e-300)
+            if b == 0.0:
+                sb = 0.0
+            else:
+                r = a / b
+                sb = b * max(0.0, min(2 * r, 1.0), min(r, 2.0))
+            assert oracle.limiter(a, b, 2) == pytest.approx(sb, rel=1e-14, abs=1e-300)
+
+
+def test_rotation_is_orthonormal_and_swaps_for_y_faces():
+    """Alg. 2: x-face rotation is the identity; y-face rotation sends the
+    normal velocity to the first velocity slot; R is orthonormal."""
+    Rx = oracle.rotation([1.0, 0.0, 0.0])
+    Ry = oracle.rotation([0.0, 1.0, 0.0])
+    assert np.allclose(Rx, np.eye(5))
+    for R in (Rx, Ry, oracle.rotation([0.6, 0.8, 0.0])):
+        assert np.allclose(R @ R.T, np.eye(5), atol=1e-15)
+    q = np.array([2.0, 0.3, -0.7, 0.0, 0.1])
+    assert np.allclose((Ry @ q)[:3], [2.0, -0.7, 0.3])
+    # y-flux of a state == x-flux of the transposed state, transposed back
+    for _ in range(10):
+        QL, beta = rand_state()
+        QR, _ = rand_state()
+        Fy = oracle.face_flux(QL, QR, [0, 1, 0], beta)
+        sw = lambda q: np.array([q[0], q[2], q[1], q[3], q[4]])
+        Fx = oracle.face_flux(sw(QL), sw(QR), [1, 0, 0], beta)
+        assert np.allclose(Fy, sw(Fx), rtol=1e-14, atol=1e-14)
+
+
+# ------------------------------------------------------------------ scheme invariants
+
+def _uniform_case(nx, ny, u, v, bc=("periodic",) * 4):
+    rho = np.full((ny, nx), 1.7)
+    return W.Case("uniform", nx, ny, 1.0, ny / nx, 0.0, 0.0, 3.0, bc, rho, rho * u, rho * v,
+                  np.full((ny, nx), 0.25), dt=1e-2, steps=1, tol=-1.0, max_iters=5)
+
+
+def test_free_stream_preserved():
+    """A uniform moving state in a periodic box stays uniform (bracket zero
+    to round-off) and keeps its values over a physical step."""
+    c = _uniform_case(12, 9, 0.3, -0.2)
+    br = oracle.bracket(c, c.state())
+    for b in br:
+        assert np.abs(b).max() < 1e-12
+    st, status, its, R, R0 = oracle.physical_step(c, c.state())
+    for a, b in zip(st, c.state()):
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_hydrostatic_tank_is_well_balanced():
+    """Sec. 2.3.2 and 2.5: with the new pressure gradient and reversed
+    gravity in wall ghosts, the discrete hydrostatic two-fluid state is a
+    steady state to round-off; p keeps its kink (slope ratio = density
+    ratio).  Catches a dropped gravity term, a wrong sign of g in the ghost
+    or in the source, or a wrong face offset."""
+    c = W.hydrostatic_tank(32)
+    st, info = oracle.run(c, steps=4, tol=-1.0, max_iters=15)
+    assert np.abs(st[1]).max() < 1e-10 and np.abs(st[2]).max() < 1e-10
+    assert np.abs(st[3] - c.p).max() < 1e-9 * np.abs(c.p).max()
+    R0 = info[0][3]
+    assert R0[2] < 1e-9 * 1000 * 9.81
+    col = st[3][:, 5]
+    slopes = np.diff(col) / c.dy
+    water, air = slopes[2], slopes[-3]
+    assert water / air == pytest.approx(1000.0, rel=1e-9)
+
+
+@pytest.mark.parametrize("gradp,expect_balanced", [("minmod", False), ("superbee", False),
+                                                   ("split_minmod", True), ("split_superbee", True)])
+def test_hydrostatic_negative_controls(gradp, expect_balanced):
+    """Sec. 3.2: standard limiters on p are not well-balanced; the split
+    limiters are (on a hydrostatic state given as input)."""
+    c = W.hydrostatic_tank(16)
+    c.options.gradp = gradp
+    st, info = oracle.run(c, steps=2, tol=-1.0, max_iters=10)
+    vmax = np.abs(st[2]).max() / c.rho.max()
+    if expect_balanced:
+        assert vmax < 1e-10
+    else:
+        assert vmax > 1e-3
+
+
+def test_hydrostatic_column_from_rest_converges():
+    """Sec. 3.2 set-up (20x1, walls, g=(9.81,0), p=0, beta=2000, dt=0.05,
+    CFL 0.98 local, until the rho u residual < 1e-5): the pressure settles to
+    hydrostatic, so its cell-to-cell slope equals the mean weight of the two
+    cells, with the kink at the interface."""
+    c = W.hydrostatic_column_1d()
+    st, status, its, R, R0 = oracle.physical_step(c, c.state())
+    assert status == oracle.OK and R[1] <= 1e-5
+    p = st[3][0]
+    rho = st[0][0]
+    slope = np.diff(p) / c.dx
+    expect = 0.5 * (rho[1:] + rho[:-1]) * c.gx
+    assert np.allclose(slope, expect, rtol=2e-3, atol=2e-3 * 9.81)
+    assert np.abs(st[1]).max() < 1e-3
+
+
+def test_mass_and_pressure_conserved_in_closed_box():
+    """Global pseudo-time step, real-time term off, slip walls: the fluxes
+    telescope and the wall mass and p/beta fluxes vanish, so sum(rho) and
+    sum(p) are constant to round-off.  Catches a sign or index slip in the
+    divergence or in the wall ghosts."""
+    c = W.random_two_fluid(20, 14, ratio=50.0, c0=5.0)
+    c.options.local_dtau = False
+    c.options.realtime = False
+    c.options.cfl_tau = 0.3
+    st = c.state()
+    m0, p0 = st[0].sum(), st[3].sum()
+    for _ in range(3):
+        st, *_ = oracle.physical_step(c, st, tol=-1.0, max_iters=3)
+    assert abs(st[0].sum() - m0) < 1e-12 * abs(m0)
+    assert abs(st[3].sum() - p0) < 1e-11 * np.abs(c.p).sum()
+    assert np.abs(st[0] - c.rho).max() > 1e-6  # something did happen
+
+
+def test_telescoping_in_periodic_box():
+    c = W.random_two_fluid(16, 10, ratio=20.0, bc=("periodic",) * 4, gy=0.0, c0=3.0)
+    br = oracle.bracket(c, c.state())
+    for f in range(4):
+        assert abs(br[f].sum()) < 1e-10 * np.abs(br[f]).sum()
+
+
+def _mirror_x(state):
+    r, ru, rv, p = state
+    return (r[:, ::-1], -ru[:, ::-1], rv[:, ::-1], p[:, ::-1])
+
+
+def test_mirror_symmetry_preserved():
+    """A state symmetric under x -> -x stays symmetric (Sec. 2.4 rotation,
+    Sec. 2.5 walls).  Catches left/right index slips."""
+    c = W.random_two_fluid(12, 10, ratio=100.0, c0=5.0, bc=("noslip", "noslip", "slip", "slip"))
+    s = c.state()
+    half = [a[:, :6] for a in s]
+    sym = (np.concatenate([half[0], half[0][:, ::-1]], 1),
+           np.concatenate([half[1], -half[1][:, ::-1]], 1),
+           np.concatenate([half[2], half[2][:, ::-1]], 1),
+           np.concatenate([half[3], half[3][:, ::-1]], 1))
+    out, *_ = oracle.physical_step(c, sym, tol=-1.0, max_iters=4)
+    mir = _mirror_x(out)
+    for a, b in zip(out, mir):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(a).max(), 1.0)
+
+
+def test_transpose_symmetry():
+    """Swapping x and y (grid, velocities, gravity, sides) transposes the
+    result: pins the y pressure gradient and the y-face treatment against
+    the x ones."""
+    c = W.random_two_fluid(11, 7, ratio=30.0, c0=4.0, gx=2.0, gy=-9.81,
+                           bc=("slip", "transmissive", "noslip", "slip"))
+    out, st, its, R, _ = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=3)
+    t = W.Case("t", c.ny, c.nx, c.ly, c.lx, c.gy, c.gx, c.beta, (c.bc[2], c.bc[3], c.bc[0], c.bc[1]),
+               c.rho.T.copy(), c.rhov.T.copy(), c.rhou.T.copy(), c.p.T.copy(), dt=c.dt,
+               options=c.options)
+    outT, *_ = oracle.physical_step(t, t.state(), tol=-1.0, max_iters=3)
+    pairs = [(out[0], outT[0].T), (out[1], outT[2].T), (out[2], outT[1].T), (out[3], outT[3].T)]
+    for a, b in pairs:
+        assert np.abs(a - b).max() <= 1e-11 * max(np.abs(a).max(), 1.0)
+
+
+# ------------------------------------------------------------------ time stepping
+
+def test_point_implicit_iteration_closed_form():
+    """Spatially uniform periodic box with gravity: the flux divergence is
+    zero, so each pseudo-iteration is x <- x + a (rho g - (x - x_n)/dt) with
+    a = dtau/(1 + dtau/dt) (Eqs. RK2, bdf with Backward-Euler,
+    point_implicit; only the last stage, alpha = 1, survives), converging to
+    x_n + dt rho g.  Catches a wrong alpha_PI, a wrong sign of the real-time term
+    or of the body force."""
+    c = _uniform_case(4, 4, 0.0, 0.0)
+    c.gx, c.gy = 0.7, -0.3
+    c.dt = 0.05
+    rho = 1.7
+    x = {1: 0.0, 2: 0.0}
+    for m in (1, 2, 3, 4, 5):
+        # dtau depends on the velocity reached so far (taken from the pinned dtau)
+        cur = (np.full((4, 4), rho), np.full((4, 4), x[1]), np.full((4, 4), x[2]), np.full((4, 4), 0.25))
+        dtau = oracle.dtau(c, cur)[0, 0]
+        a = dtau / (1.0 + dtau / c.dt)
+        for f, g in ((1, c.gx), (2, c.gy)):
+            x[f] = x[f] + a * (rho * g - (x[f] - 0.0) / c.dt)
+        st, status, its, R, R0 = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=m)
+        for f in (1, 2):
+            assert st[f][0, 0] == pytest.approx(x[f], rel=1e-12)
+        assert np.allclose(st[0], rho, rtol=0, atol=1e-14)
+    # and the fixed point is the Backward-Euler step of d(rho u)/dt = rho g
+    st, *_ = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=300)
+    assert st[1][0, 0] == pytest.approx(c.dt * rho * c.gx, rel=1e-12)
+
+
+def test_dtau_is_the_acoustic_cfl_limit():
+    """Sec. 2.2.3: the local pseudo-time step makes the fastest x and y waves
+    together cross CFL_tau cells, dtau (rho(A_x)/dx + rho(A_y)/dy) = CFL_tau,
+    with the spectral radii taken by numpy from finite-difference Jacobians
+    of the flux (the y one through the swapped state)."""
+    c = W.random_two_fluid(6, 5, ratio=10.0, c0=2.0, velocity=0.5)
+    s = c.state()
+    d = oracle.dtau(c, s)
+    for j in range(c.ny):
+        for i in range(c.nx):
+            r, ru, rv, p = (a[j, i] for a in s)
+            Qx = np.array([r, ru, rv, 0.0, p / c.beta])
+            Qy = np.array([r, rv, ru, 0.0, p / c.beta])
+            sx = np.abs(np.linalg.eigvals(fd_jacobian(Qx, c.beta))).max()
+            sy = np.abs(np.linalg.eigvals(fd_jacobian(Qy, c.beta))).max()
+            assert d[j, i] * (sx / c.dx + sy / c.dy) == pytest.approx(c.options.cfl_tau, rel=1e-6)
+    c.options.local_dtau = False
+    assert np.allclose(oracle.dtau(c, s), d.min(), rtol=0)
+
+
+def test_bdf_fixed_point_matches_paper_table():
+    """A uniform box at rest with no gravity has zero flux, so the converged
+    pseudo-iteration solves sum_s B_s Q^{n+1-s} = 0 with the paper's BDF
+    coefficients (Table BDF)."""
+    table = {int(r[0]): r[1:] for r in load_golden("bdf_coefficients.txt")}
+    for order in (1, 2, 3):
+        c = _uniform_case(4, 3, 0.0, 0.0)
+        c.options.bdf_order = order
+        rho_n, rho_n1, rho_n2 = 1.7, 1.1, 0.8
+        hist = [(np.full((3, 4), rho_n1), np.zeros((3, 4)), np.zeros((3, 4))),
+                (np.full((3, 4), rho_n2), np.zeros((3, 4)), np.zeros((3, 4)))]
+        st, status, its, R, R0 = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=400,
+                                                       history=hist)
+        B = table[order]
+        expect = -(B[1] * rho_n + B[2] * rho_n1 + B[3] * rho_n2) / B[0]
+        assert st[0][0, 0] == pytest.approx(expect, rel=1e-10)
+
+
+# ------------------------------------------------------------------ Riemann problems
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_riemann_problems_converge_to_exact_solution(k):
+    """Sec. 3.1 set-up (global dtau, CFL 0.98, 3 stages, minmod on p, real
+    time off): Osher's L1 error against the exact (Bassi) solution falls
+    under refinement 100 -> 200 -> 400 cells for rho, u and p."""
+    rL, rR, uL, uR, pL, pR, beta, tau = W.RIEMANN_TABLE[k]
+    errs = []
+    for nx in (100, 200, 400):
+        rp = W.riemann_problem(k, nx)
+        q, status, its = oracle.pseudo_time_run(rp, rp.state(), rp.tau_end)
+        assert status == oracle.OK
+        ex = np.array([oracle.bassi_sample([rL, uL, 0, pL], [rR, uR, 0, pR], beta, x / tau) for x in rp.x])
+        scale = np.abs(ex).max(axis=0) + 1e-30
+        e = [np.abs(q[0][0] - ex[:, 0]).mean() / scale[0],
+             np.abs(q[1][0] / q[0][0] - ex[:, 1]).mean() / max(scale[1], 1e-3),
+             np.abs(q[3][0] - ex[:, 3]).mean() / scale[3]]
+        errs.append(e)
+    errs = np.array(errs)
+    for f in range(3):
+        if errs[0, f] < 1e-12:
+            assert errs[2, f] < 1e-12   # exactly resolved (stationary contact)
+            continue
+        assert errs[1, f] < errs[0, f] and errs[2, f] < errs[1, f], errs
+        assert errs[2, f] < 0.15
+
+
+def test_riemann_problem_along_y_equals_along_x():
+    rx = W.riemann_problem(5, 60)
+    ry = W.riemann_problem(5, 60, along="y")
+    qx, *_ = oracle.pseudo_time_run(rx, rx.state(), rx.tau_end)
+    qy, *_ = oracle.pseudo_time_run(ry, ry.state(), ry.tau_end)
+    assert np.allclose(qx[0][0], qy[0][:, 0], rtol=1e-12)
+    assert np.allclose(qx[1][0], qy[2][:, 0], rtol=1e-12, atol=1e-14)
+    assert np.allclose(qx[3][0], qy[3][:, 0], rtol=1e-12, atol=1e-14)
