@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the pseudo-time residual sweep.
+
+Metric: cell pseudo-iterations per second = sum over tanks of (interior
+cells x pseudo-iterations completed) / time of the ac_physical_step calls.
+One pseudo-iteration = s_max = 3 fused stage sweeps + the residual test.
+
+Default workload: the hydrostatic two-fluid tank, 256 x 256 cells, FP64,
+each step one physical step (dt = 1e-3 s) iterated to a 1e-8 residual drop
+or 500 pseudo-iterations.  The state stays resident in HBM; L2 is flushed
+(256 MiB write) between timed steps, outside the event pairs.
+
+Extra objects on the JSON line:
+  roofline      the stage sweep's own event-timed duration against its
+                arithmetic roof (FP64 is ALU-bound on this part)
+  e2e           the same metric through the public API with host buffers:
+                ac_set_state from pinned host memory + the step +
+                ac_get_state into pinned host memory, every step
+  cpu_baseline  the FP64 oracle on the host cores, bounded sample
+
+``--impl reference`` times the FP64 oracle itself on the host cores (the
+project's reference implementation), on the same workload and metric.
+Under torchrun every rank runs its own replica of the workload (replicas
+only: one tank does not shard across GPUs here); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell pseudo-iterations/sec"
+UNIT = "cell-iter/s"
+# FP64 peak of the part (recipe's nominal dense FP64 rate, FLOP/s); the
+# stage sweep is bound by it, not by HBM
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="hydrostatic_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_case(name):
+    from paper_2108_08769_gb300 import workloads as W
+    if name == "hydrostatic_256":
+        c = W.hydrostatic_tank(256)
+        desc = ("hydrostatic two-fluid tank 256x256, closed 1x1 m box, water 1000 below y=0.5, air 1 above, "
+                "at rest, discrete hydrostatic p, g=-9.81, c0=20 m/s (beta=4e5 Pa), dt=1e-3 s, "
+                "pseudo-iterations to a 1e-8 residual drop or 500, FP64")
+        return c, desc
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("AC_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.proc = None
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline_sample(case, iters=10):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample:
+    one physical step of the same tank with a fixed number of iterations."""
+    import oracle
+    oracle.build()
+    state = case.state()
+    t0 = time.perf_counter()
+    _, st, its, _, _ = oracle.physical_step(case, state, tol=-1.0, max_iters=iters)
+    dt = time.perf_counter() - t0
+    return {"value": case.cells * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 physical step x {its} pseudo-iterations on the full {case.nx}x{case.ny} tank "
+                      f"({dt:.1f} s, FP64 C oracle, 1 thread)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    case, desc = make_case(args.workload)
+    import oracle
+    oracle.build()
+    iters = 3
+    for _ in range(args.warmup):
+        oracle.physical_step(case, case.state(), tol=-1.0, max_iters=iters)
+    tot, cells_iters = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, st, its, _, _ = oracle.physical_step(case, case.state(), tol=-1.0, max_iters=iters)
+        tot += time.perf_counter() - t0
+        cells_iters += case.cells * its
+    v = cells_iters / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "cells": case.cells,
+                                            "pseudo_iters_per_step": iters},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 1 physical step x {iters} pseudo-iterations of the full "
+                                       f"{case.nx}x{case.ny} tank, FP64 C oracle, 1 thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2108_08769_gb300 import ac
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case, desc = make_case(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    tank = ac.Tank.from_case(case)
+    tank.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    dt, tol, max_iters = case.dt, case.tol, case.max_iters
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        tank.physical_step(dt, tol, max_iters)
+
+    # ---- timed region: state resident in HBM ----
+    tank.set_state(*case.state())
+    launches0 = tank.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters = []
+    barrier()
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            rc, its = tank.physical_step(dt, tol, max_iters)
+            evs[k][1].record(stream)
+            iters.append(its)
+        barrier()
+        wall = time.perf_counter() - wall0
+    torch.cuda.synchronize(dev)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = tank.kernel_launches() - launches0
+    t_max = dev_ms
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    cell_iters = case.cells * sum(iters)
+    value = ws * cell_iters / (t_max * 1e-3)
+
+    # ---- e2e: host buffers through the public API ----
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.state()]
+    outs = [torch.empty(case.cells, dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_in = [p.numpy().reshape(-1) for p in pinned]
+    host_out = [o.numpy() for o in outs]
+    e_iters = []
+    barrier()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        tank.set_state(*host_in)
+        rc, its = tank.physical_step(dt, tol, max_iters)
+        tank.get_state_into(*host_out)
+        e_iters.append(its)
+    barrier()
+    e_wall = time.perf_counter() - e0
+    e2e = {"value": ws * case.cells * sum(e_iters) / e_wall, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * case.cells * 8, "d2h_bytes_per_step": 4 * case.cells * 8}
+
+    # ---- roofline: event-timed stage sweeps of the same steps ----
+    tank.set_state(*case.state())
+    tank.set_profiling(True)
+    for k in range(min(args.steps, 3)):
+        tank.physical_step(dt, tol, max_iters)
+    stage_ms, stage_n = tank.stage_kernel_time()
+    tank.set_profiling(False)
+    per_launch_s = stage_ms * 1e-3 / max(stage_n, 1)
+    flops = FP64_FLOPS_PER_CELL_STAGE * case.cells
+    achieved = flops / per_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "stage_kernel<double,32,8>", "launch_ms": per_launch_s * 1e3,
+                "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
+                "hbm_frac_of_measured": (BYTES_PER_CELL_ITER_F64 / 3.0) * case.cells / per_launch_s / 1e9
+                / measured_hbm_gbs(),
+                "peak_source": "nominal FP64 rate of the part (profiling recipe), not measured"}
+    tank.close()
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "cells": case.cells, "rk_stages": case.options.s_max,
+                       "pseudo_iters_per_step": statistics.mean(iters), "tol": tol, "max_iters": max_iters,
+                       "l2": "flushed between timed steps (256 MiB write outside the event pairs)",
+                       "parallelism": f"replicas x{ws}"},
+            "wall_s": wall, "gpu_launches": launches, "roofline": roofline, "e2e": e2e,
+            "clocks": clk.summary()}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(case)
+    print(json.dumps(line), flush=True)
+
+
+# FP64 operations of one stage sweep per cell ("roofline")
+FP64_FLOPS_PER_CELL_STAGE = 1500.0
+# algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3)
+BYTES_PER_CELL_ITER_F64 = 328.0
+
+
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

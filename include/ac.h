@@ -1,0 +1,173 @@
+/*
+ * ac.h -- C ABI of the GB300 pseudo-time residual sweep for the 2D inviscid
+ * variable-density artificial-compressibility (AC) equations.
+ *
+ * Method: Leakey, Glenis & Hewett, "Riemann solvers and pressure gradients
+ * in Godunov-type schemes for variable density incompressible flows"
+ * (arXiv 2108.08769).  Equation and section numbers below refer to it.
+ *
+ *   governing equations        Sec. 2.1.1 (Eqs. AC_start - AC_end)
+ *   compact form, Q = (rho, rho u, rho v, p/beta)           Sec. 2.1.2
+ *   dual time stepping, RK stages, point-implicit scaling   Sec. 2.2, Alg. 1,
+ *                                         Eqs. RK1, RK2, bdf, point_implicit
+ *   local pseudo-time step                                  Sec. 2.2.3
+ *   MUSCL + k-limiter, new pressure gradient                Sec. 2.3, Eq. new_gradp
+ *   face rotation, Osher / Bassi / Roe fluxes               Sec. 2.4, Alg. 2
+ *   ghost-cell boundaries, reversed gravity in wall ghosts  Sec. 2.5
+ *
+ * Conventions (all entry points):
+ *  - Grids are uniform, cell-centred, nx * ny interior cells.  Host field
+ *    arrays are caller-owned, nx*ny doubles, row-major with x fastest
+ *    (index j*nx + i), interior cells only.  Every call copies; no host
+ *    pointer is retained after a call returns.
+ *  - The library owns all device memory of a context.  Device work runs on
+ *    the context's stream (default stream unless ac_set_stream was called).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Return codes: AC_OK (0) on success, AC_NOT_CONVERGED (1) when a
+ *    physical step hit max_iters (the state is advanced), negative values
+ *    for errors.  After an error the state is the one before the call, and
+ *    ac_last_error() describes the failure.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AC_OK 0
+#define AC_NOT_CONVERGED 1
+#define AC_ERR_ARG (-1)       /* invalid argument (sizes, kinds, NULL, beta <= 0, ...) */
+#define AC_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define AC_ERR_NONFINITE (-3) /* a residual norm or an input became NaN/Inf */
+#define AC_ERR_TIMEOUT (-4)   /* a bounded device wait gave up */
+#define AC_ERR_OOM (-5)       /* device allocation failed */
+#define AC_ERR_STATE (-6)     /* call out of order (e.g. a step before ac_set_state) */
+
+/* ---- boundary kinds (Sec. 2.5) ---------------------------------------- */
+#define AC_BC_WALL_SLIP 0      /* mirror: rho, p copied; normal velocity negated */
+#define AC_BC_WALL_NOSLIP 1    /* as slip, tangential velocity negated too */
+#define AC_BC_TRANSMISSIVE 2   /* zero gradient: boundary cell copied */
+#define AC_BC_PERIODIC 3       /* wrap; must be set on both sides of an axis */
+
+/* ---- pressure-gradient methods (Sec. 2.3.2) --------------------------- */
+#define AC_GRADP_NEW 0         /* rearranged momentum equation (Eq. new_gradp), default */
+#define AC_GRADP_MINMOD 1      /* standard k-limiter on p, k = 1 */
+#define AC_GRADP_SUPERBEE 2    /* standard k-limiter on p, k = 2 */
+
+/* ---- Riemann solvers (Sec. 2.4) ---------------------------------------- */
+#define AC_RIEMANN_OSHER 0     /* Dumbser-Toro Osher flux, 3-point Gauss path (default) */
+
+/* ---- arithmetic -------------------------------------------------------- */
+#define AC_PREC_FP64 0         /* every step in FP64 */
+#define AC_PREC_MIXED 1        /* FP32 sweep; FP64 time levels, reference pressure, norms */
+
+typedef struct {
+    int nx, ny;        /* interior cells, >= 1 each */
+    double lx, ly;     /* domain extent (m); dx = lx/nx, dy = ly/ny */
+    double gx, gy;     /* gravity (m/s^2), body force rho g (Sec. 2.1.2) */
+} ac_grid;
+
+typedef struct {
+    double rho_heavy;  /* densest fluid present (kg/m^3) */
+    double rho_light;  /* lightest fluid present (kg/m^3) */
+} ac_fluids;
+
+typedef struct {
+    int xlo, xhi, ylo, yhi;   /* AC_BC_* per side */
+} ac_bc;
+
+typedef struct {
+    int rk_stages;       /* s_max, 1..4 (default 3); alpha_s = 1/(s_max - s + 1) */
+    int riemann;         /* AC_RIEMANN_* (default Osher) */
+    int gradp;           /* AC_GRADP_* (default AC_GRADP_NEW) */
+    int limiter_k;       /* k of the limiter on rho, u, v: 1 minmod (default), 2 superbee */
+    int local_dtau;      /* 1: local pseudo-time step (default); 0: global minimum */
+    int realtime;        /* 1: real-time term on (default); 0: pure pseudo-time */
+    int alpha_pi_p_row;  /* 1: alpha_PI also scales the pressure row (default) */
+    int precision;       /* AC_PREC_* (default AC_PREC_FP64) */
+    double cfl_tau;      /* pseudo-time Courant number (default 0.45) */
+    double abs_tol[4];   /* absolute residual floors for rho, rho u, rho v, p (default 0) */
+} ac_options;
+
+typedef struct ac_ctx ac_ctx;
+
+/* Fill *opt with the defaults listed above.  Returns AC_OK, or AC_ERR_ARG
+ * for NULL. */
+int ac_default_options(ac_options *opt);
+
+/* beta (Pa) that gives the fluid of density rho_ref the artificial sound
+ * speed sqrt(4 beta/rho_ref)/2 = c0 at rest, i.e. beta = rho_ref * c0^2
+ * (Sec. 2.1.3: c = sqrt(u^2 + 4 beta/rho), acoustic speeds (u +- c)/2). */
+double ac_beta_from_speed(double c0, double rho_ref);
+
+/* Create a context for one tank.  grid, bc must be non-NULL; fluids may be
+ * NULL (when given, ac_set_state rejects densities outside
+ * [rho_light/2, 2 rho_heavy]); opt may be NULL (defaults).  beta > 0 in Pa
+ * (Eq. AC_end).  Allocates the device state on the current device.
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.  *out is NULL on error. */
+int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const ac_bc *bc,
+              const ac_options *opt, ac_ctx **out);
+
+/* Release all device and host memory of ctx (NULL is ignored). */
+void ac_destroy(ac_ctx *ctx);
+
+/* Run the context's device work on `stream` (a cudaStream_t passed as
+ * void*; NULL = default stream).  Captured graphs are rebuilt lazily. */
+int ac_set_stream(ac_ctx *ctx, void *stream);
+
+/* Set the state Q = (rho, rho u, rho v, p) from host arrays (nx*ny doubles
+ * each).  Also sets the real-time level Q^n := Q and clears the older
+ * levels.  rho must be finite and > 0; all values finite
+ * (AC_ERR_NONFINITE otherwise, AC_ERR_ARG for rho <= 0). */
+int ac_set_state(ac_ctx *ctx, const double *rho, const double *rhou, const double *rhov,
+                 const double *p);
+
+/* Copy the current state to host arrays (nx*ny doubles each; any pointer
+ * may be NULL to skip that field).  Synchronises the context's stream. */
+int ac_get_state(const ac_ctx *ctx, double *rho, double *rhou, double *rhov, double *p);
+
+/* One real-time step of dual time stepping (Alg. 1): Q^n <- Q, then
+ * pseudo-iterations of s_max Runge-Kutta stages (Eqs. RK1-RK2) until every
+ * field's residual norm R_k <= max(tol * R0_k, abs_tol_k) or max_iters
+ * iterations have run.  R_k is the RMS over cells of the stage-1 bracket of
+ * Eq. RK2 (pressure row in Pa/s); R0 is the first iteration's norm.  tol < 0
+ * runs exactly max_iters iterations.  dt > 0 (ignored when the real-time
+ * term is off), max_iters >= 1.
+ * Returns AC_OK (converged, or tol < 0), AC_NOT_CONVERGED, or an error;
+ * *iters_out (may be NULL) receives the iterations completed.  On
+ * AC_ERR_NONFINITE the state is restored to its value before the call. */
+int ac_physical_step(ac_ctx *ctx, double dt, double tol, int max_iters, int *iters_out);
+
+/* Residual norms of the last physical step: out[4] = final R (rho, rho u,
+ * rho v, p), out0[4] (may be NULL) = first-iteration R0. */
+int ac_residual_norms(const ac_ctx *ctx, double out[4], double out0[4]);
+
+/* Real-time level Q^n (rho, rho u, rho v) of the last physical step, for
+ * checkpointing; ac_set_levels restores it (same layout as ac_set_state). */
+int ac_get_levels(const ac_ctx *ctx, double *rho_n, double *rhou_n, double *rhov_n);
+int ac_set_levels(ac_ctx *ctx, const double *rho_n, const double *rhou_n, const double *rhov_n);
+
+/* Number of kernels this context has launched since creation (device work
+ * inside captured graphs is counted per replay). */
+long long ac_kernel_launches(const ac_ctx *ctx);
+
+/* Per-kernel timing.  With profiling on, ac_physical_step launches each
+ * pseudo-iteration's kernels from the host (no captured graph, one host
+ * wait per iteration) and brackets every stage-sweep launch with a pair of
+ * CUDA events on the context's stream; the numerical result is the same.
+ * ac_stage_kernel_time returns the summed event time (ms) and the number
+ * of stage-sweep launches measured since profiling was switched on. */
+int ac_set_profiling(ac_ctx *ctx, int on);
+int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launches);
+
+/* Message describing the last error on this thread ("" if none). */
+const char *ac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

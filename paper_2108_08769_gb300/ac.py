@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in ``include/ac.h`` (same names).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library
+``libacgb300.so``.  There is no CPU fallback; loading fails loudly when the
+library is missing or cannot be built.
+
+``Tank`` wraps one ``ac_ctx`` for Python callers; the module-level
+``ac_*`` functions mirror the C entry points one to one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+AC_OK = 0
+AC_NOT_CONVERGED = 1
+AC_ERR_ARG = -1
+AC_ERR_CUDA = -2
+AC_ERR_NONFINITE = -3
+AC_ERR_TIMEOUT = -4
+AC_ERR_OOM = -5
+AC_ERR_STATE = -6
+
+BC = {"slip": 0, "noslip": 1, "transmissive": 2, "periodic": 3}
+GRADP = {"new": 0, "minmod": 1, "superbee": 2}
+RIEMANN = {"osher": 0}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+# every entry point include/ac.h declares
+EXPORTS = (
+    "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
+    "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_levels",
+    "ac_set_levels", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
+)
+
+
+class ac_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double)]
+
+
+class ac_fluids(C.Structure):
+    _fields_ = [("rho_heavy", C.c_double), ("rho_light", C.c_double)]
+
+
+class ac_bc(C.Structure):
+    _fields_ = [("xlo", C.c_int), ("xhi", C.c_int), ("ylo", C.c_int), ("yhi", C.c_int)]
+
+
+class ac_options(C.Structure):
+    _fields_ = [("rk_stages", C.c_int), ("riemann", C.c_int), ("gradp", C.c_int), ("limiter_k", C.c_int),
+                ("local_dtau", C.c_int), ("realtime", C.c_int), ("alpha_pi_p_row", C.c_int),
+                ("precision", C.c_int), ("cfl_tau", C.c_double), ("abs_tol", C.c_double * 4)]
+
+
+_D = C.POINTER(C.c_double)
+_lib = None
+
+
+class ACError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libacgb300.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    L.ac_default_options.argtypes = [C.POINTER(ac_options)]
+    L.ac_beta_from_speed.argtypes = [C.c_double, C.c_double]
+    L.ac_beta_from_speed.restype = C.c_double
+    L.ac_create.argtypes = [C.POINTER(ac_grid), C.POINTER(ac_fluids), C.c_double, C.POINTER(ac_bc),
+                            C.POINTER(ac_options), C.POINTER(C.c_void_p)]
+    L.ac_destroy.argtypes = [C.c_void_p]
+    L.ac_destroy.restype = None
+    L.ac_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.ac_set_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
+    L.ac_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
+    L.ac_physical_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
+    L.ac_residual_norms.argtypes = [C.c_void_p, _D, _D]
+    L.ac_get_levels.argtypes = [C.c_void_p, _D, _D, _D]
+    L.ac_set_levels.argtypes = [C.c_void_p, _D, _D, _D]
+    L.ac_kernel_launches.argtypes = [C.c_void_p]
+    L.ac_kernel_launches.restype = C.c_longlong
+    L.ac_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    L.ac_stage_kernel_time.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
+    L.ac_last_error.argtypes = []
+    L.ac_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def ac_last_error() -> str:
+    return load().ac_last_error().decode()
+
+
+def _check(rc: int, allow=(AC_OK,)) -> int:
+    if rc not in allow:
+        raise ACError(rc, ac_last_error())
+    return rc
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+def _host(a, n) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def ac_default_options() -> ac_options:
+    o = ac_options()
+    _check(load().ac_default_options(C.byref(o)))
+    return o
+
+
+def ac_beta_from_speed(c0: float, rho_ref: float) -> float:
+    return load().ac_beta_from_speed(c0, rho_ref)
+
+
+def options_from(case_options, precision: str = "fp64") -> ac_options:
+    """ac_options from a workloads.Options."""
+    o = ac_default_options()
+    o.rk_stages = case_options.s_max
+    o.riemann = RIEMANN[case_options.riemann]
+    o.gradp = GRADP[case_options.gradp]
+    o.limiter_k = case_options.limiter_k
+    o.local_dtau = int(case_options.local_dtau)
+    o.realtime = int(case_options.realtime)
+    o.alpha_pi_p_row = int(case_options.alpha_pi_p_row)
+    o.precision = PRECISION[precision]
+    o.cfl_tau = case_options.cfl_tau
+    for k in range(4):
+        o.abs_tol[k] = case_options.abs_tol[k]
+    return o
+
+
+class Tank:
+    """One simulated tank: an ``ac_ctx`` with its state on the GPU."""
+
+    def __init__(self, nx: int, ny: int, lx: float, ly: float, gx: float, gy: float, beta: float,
+                 bc: Sequence[str], options: Optional[ac_options] = None,
+                 fluids: Optional[Tuple[float, float]] = None):
+        L = load()
+        self.nx, self.ny = nx, ny
+        g = ac_grid(nx, ny, lx, ly, gx, gy)
+        b = ac_bc(*[BC[s] for s in bc])
+        fl = ac_fluids(fluids[0], fluids[1]) if fluids else None
+        h = C.c_void_p()
+        _check(L.ac_create(C.byref(g), C.byref(fl) if fl else None, beta, C.byref(b),
+                           C.byref(options) if options is not None else None, C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_case(cls, case, precision: str = "fp64", fluids=None) -> "Tank":
+        t = cls(case.nx, case.ny, case.lx, case.ly, case.gx, case.gy, case.beta, case.bc,
+                options_from(case.options, precision), fluids)
+        t.set_state(*case.state())
+        return t
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ac_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr: int):
+        _check(load().ac_set_stream(self._h, C.c_void_p(stream_ptr)))
+
+    def set_state(self, rho, rhou, rhov, p):
+        n = self.nx * self.ny
+        arrs = [_host(a, n) for a in (rho, rhou, rhov, p)]
+        _check(load().ac_set_state(self._h, *[_ptr(a) for a in arrs]))
+
+    def get_state(self) -> Tuple[np.ndarray, ...]:
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(load().ac_get_state(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def get_state_into(self, rho, rhou, rhov, p):
+        """Copy the state into caller-provided (e.g. pinned) float64 arrays."""
+        _check(load().ac_get_state(self._h, _ptr(rho), _ptr(rhou), _ptr(rhov), _ptr(p)))
+
+    def physical_step(self, dt: float, tol: float, max_iters: int) -> Tuple[int, int]:
+        its = C.c_int(0)
+        rc = load().ac_physical_step(self._h, dt, tol, max_iters, C.byref(its))
+        _check(rc, (AC_OK, AC_NOT_CONVERGED))
+        return rc, its.value
+
+    def residual_norms(self) -> Tuple[np.ndarray, np.ndarray]:
+        R = np.zeros(4)
+        R0 = np.zeros(4)
+        _check(load().ac_residual_norms(self._h, _ptr(R), _ptr(R0)))
+        return R, R0
+
+    def kernel_launches(self) -> int:
+        return load().ac_kernel_launches(self._h)
+
+    def set_profiling(self, on: bool):
+        _check(load().ac_set_profiling(self._h, int(on)))
+
+    def stage_kernel_time(self) -> Tuple[float, int]:
+        ms = C.c_double(0.0)
+        n = C.c_longlong(0)
+        _check(load().ac_stage_kernel_time(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value

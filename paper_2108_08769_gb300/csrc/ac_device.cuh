@@ -1,0 +1,144 @@
+// ac_device.cuh -- device-side building blocks of the fused pseudo-time stage
+// sweep: boundary mapping, k-limiter, the rank-2 Osher flux, pseudo-time step.
+//
+// Method: Leakey, Glenis & Hewett (arXiv 2108.08769).  Everything here is
+// written for GB300 (sm_103a): one thread per cell, tiles staged in shared
+// memory, no library calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace acgb {
+
+enum BcKind { kSlip = 0, kNoSlip = 1, kTransmissive = 2, kPeriodic = 3 };
+enum GradP { kGradNew = 0, kGradMinmod = 1, kGradSuperbee = 2 };
+
+// ---------------------------------------------------------------------------
+// Arithmetic traits.  FP64 uses IEEE division and square root; FP32 uses
+// the fast reciprocal / reciprocal-square-root instructions (about 1 ulp),
+// which is far below the FP32 rounding of the stored state.
+// ---------------------------------------------------------------------------
+template <typename T> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    // returns sqrt(x) and 1/sqrt(x)
+    static __device__ __forceinline__ void sqrt_rsqrt(double x, double &s, double &rs) {
+        s = sqrt(x);
+        rs = 1.0 / s;
+    }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ void sqrt_rsqrt(float x, float &s, float &rs) {
+        rs = rsqrtf(x);
+        s = x * rs;
+    }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+};
+
+// ---------------------------------------------------------------------------
+// Ghost cells (Sec. 2.5).  A ghost index along one axis is folded back onto
+// the interior cell it copies; every wall reflection flips the normal
+// momentum, a no-slip reflection also the tangential one.  Indices reach at
+// most a few cells past the domain, so the loop is short; the final clamp
+// keeps every access in bounds whatever the input.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fold_axis(int i, int n, int lo, int hi, int &nflip, int &tflip) {
+    nflip = 0;
+    tflip = 0;
+#pragma unroll 1
+    for (int g = 0; g < 8 && (i < 0 || i >= n); ++g) {
+        if (i < 0) {
+            if (lo == kPeriodic) i += n;
+            else if (lo == kTransmissive) i = 0;
+            else { i = -1 - i; ++nflip; tflip += (lo == kNoSlip); }
+        } else {
+            if (hi == kPeriodic) i -= n;
+            else if (hi == kTransmissive) i = n - 1;
+            else { i = 2 * n - 1 - i; ++nflip; tflip += (hi == kNoSlip); }
+        }
+    }
+    return min(max(i, 0), n - 1);
+}
+
+__device__ __forceinline__ bool is_wall(int bc) { return bc == kSlip || bc == kNoSlip; }
+
+// ---------------------------------------------------------------------------
+// k-limiter G(a, b) = s max(0, min(k|b|, s a), min(|b|, k s a)), s = sgn(b)
+// (Sec. 2.3.1); a forward, b backward difference.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T limiter(T a, T b, T k) {
+    T s = (b > T(0)) ? T(1) : ((b < T(0)) ? T(-1) : T(0));
+    T t = s * a;
+    T ab = fabs(b);
+    T m = fmax(fmin(k * ab, t), fmin(ab, k * t));
+    return s * fmax(T(0), m);
+}
+
+// minmod fast form (k = 1): the k-limiter reduces to s * max(0, min(|b|, s a)).
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+    T s = (b > T(0)) ? T(1) : ((b < T(0)) ? T(-1) : T(0));
+    return s * fmax(T(0), fmin(fabs(b), s * a));
+}
+
+// ---------------------------------------------------------------------------
+// Osher flux of Dumbser & Toro along the straight path in Q, 3-point
+// Gauss-Legendre (Sec. 2.4.3), in the face-normal frame.  States are given
+// as primitive (rho, un, ut, p); Q = (rho, rho un, rho ut, p/beta).
+//
+// |A| has the triple eigenvalue u and the acoustic pair (u +- c)/2, so with
+// sum_k r_k l_k = I it collapses to the exact rank-2 form
+//   |A| dQ = |u| dQ + (|l4| - |u|) r4 (l4.dQ) + (|l5| - |u|) r5 (l5.dQ),
+// with r4, r5, l4, l5 the acoustic columns/rows of R_x, L_x (Sec. 2.1.3).
+// Writing a = (d(rho un) - un d(rho))/beta and dq = d(p/beta):
+//   l4.dQ =  (rho/c)(l4 a + dq),   l5.dQ = -(rho/c)(l5 a + dq),
+// and since l4 > 0 > l5: |l4| - |u| = l4 - |u|, |l5| - |u| = -l5 - |u|.
+// Output F = (mass, normal momentum, tangential momentum, p/beta flux).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR,
+                                           T beta, T inv_beta, T F[4]) {
+    const T mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
+    const T mR = rR * uR, nR = rR * vR, qR = pR * inv_beta;
+    const T dr = rR - rL, dm = mR - mL, dn = nR - nL, dq = qR - qL;
+    const T four_beta = T(4) * beta;
+    // Gauss-Legendre points mapped to [0,1]: (xi + 1)/2, weights w/2
+    const T tq[3] = {T(0.11270166537925831148), T(0.5), T(0.88729833462074168852)};
+    const T wq[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+    T D0 = T(0), D1 = T(0), D2 = T(0), D3 = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T r = rL + tq[j] * dr;
+        const T m = mL + tq[j] * dm;
+        const T n = nL + tq[j] * dn;
+        const T ir = Ar<T>::rcp(r);
+        const T u = m * ir, v = n * ir;
+        const T c2 = u * u + four_beta * ir;
+        T c, ic;
+        Ar<T>::sqrt_rsqrt(c2, c, ic);
+        const T l4 = T(0.5) * (u + c), l5 = T(0.5) * (u - c);
+        const T au = fabs(u);
+        const T a = (dm - u * dr) * inv_beta;
+        const T k = r * ic;
+        const T g4 = (l4 - au) * k * (l4 * a + dq);
+        const T g5 = (l5 + au) * k * (l5 * a + dq);
+        const T e = g4 * l4 + g5 * l5;
+        const T w = wq[j];
+        D0 += w * (au * dr + e);
+        D1 += w * (au * dm + u * e + beta * ir * (g4 + g5));
+        D2 += w * (au * dn + v * e);
+        D3 += w * (au * dq - (g4 * l5 + g5 * l4) * ir);
+    }
+    // central part 1/2 (F(Q_L) + F(Q_R)); dissipation 1/2 * D (D already
+    // carries the 1/2 of the [0,1] quadrature)
+    F[0] = T(0.5) * (mL + mR) - T(0.5) * D0;
+    F[1] = T(0.5) * (mL * uL + pL + mR * uR + pR) - T(0.5) * D1;
+    F[2] = T(0.5) * (mL * vL + mR * vR) - T(0.5) * D2;
+    F[3] = T(0.5) * (uL + uR) - T(0.5) * D3;
+}
+
+}  // namespace acgb

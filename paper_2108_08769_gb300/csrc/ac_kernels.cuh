@@ -1,0 +1,387 @@
+// ac_kernels.cuh -- the fused pseudo-time stage sweep and its control kernels.
+//
+// One launch of stage_kernel performs Runge-Kutta stage s of one
+// pseudo-iteration (Alg. 1, Eq. RK2) over the whole grid:
+//   ghost synthesis (Sec. 2.5) -> limited gradients of rho, u, v (Sec. 2.3.1)
+//   -> pressure gradient (Eq. new_gradp, or a limiter on p) -> MUSCL face
+//   states (Eqs. muscl1-2) -> Osher flux on every x- and y-face (Sec. 2.4.3,
+//   y-faces through the rotation of Alg. 2) -> flux divergence + real-time
+//   term + body force (Sec. 2.2.1) -> point-implicit stage update
+//   (Eqs. RK2, point_implicit) -> stage-1 residual partial sums.
+// Each CTA owns a TX x TY tile; the tile plus a two-cell halo is staged in
+// shared memory, so every field of every cell is read from HBM once per
+// stage (halo re-reads hit L2).
+//
+// Which of the three state buffers holds Q^{m}, the stage inputs and the
+// stage outputs is decided on the device from ctl->cur, so one captured
+// graph serves every pseudo-iteration.
+#pragma once
+
+#include "ac_device.cuh"
+
+namespace acgb {
+
+// Device-resident control block of one physical step.
+struct Ctl {
+    int iter;        // pseudo-iterations completed
+    int done;        // 1: stop iterating
+    int cur;         // buffer index (0..2) holding Q^{m}
+    int status;      // 0 converged / 1 not converged / -3 non-finite
+    int max_iters;
+    int fixed;       // 1: tol < 0, run exactly max_iters
+    double tol;
+    double dt, inv_dt;
+    double R[4], R0[4];
+    double abs_tol[4];
+    unsigned long long dtau_bits;  // global pseudo-time step (bit pattern of a positive double)
+};
+
+template <typename T>
+struct SweepArgs {
+    int nx, ny;
+    int bc[4];
+    int gradp, limiter_k, realtime, local_dtau, alpha_pi_p_row;
+    int stage, s_max;
+    T alpha;                       // alpha_s of this stage
+    T dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
+    T beta, inv_beta, gx, gy;
+    T cfl_area;                    // CFL_tau * |Omega|
+    T *buf[3][4];                  // three state buffers: rho, rho u, rho v, p
+    T *lev[4];                     // real-time level Q^n (rho, rho u, rho v, p)
+    double *partials;              // per-CTA residual partial sums [nblocks][4]
+    Ctl *ctl;
+};
+
+// Buffer roles within a pseudo-iteration: stage s reads `in` and writes
+// `out`; Q^{m} (stage 0) stays in `cur` until the iteration ends.
+__device__ __forceinline__ void stage_buffers(int cur, int s, int &in, int &out) {
+    const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
+    out = (s & 1) ? o1 : o2;
+    in = (s == 1) ? cur : (((s - 1) & 1) ? o1 : o2);
+}
+__host__ __device__ __forceinline__ int final_buffer(int cur, int s_max) {
+    return (s_max & 1) ? (cur + 1) % 3 : (cur + 2) % 3;
+}
+
+template <typename T>
+__device__ __forceinline__ T wall_ghost_sign(int gi, int gj, int nx, int ny, const int bc[4]) {
+    const bool w = (gi < 0 && is_wall(bc[0])) || (gi >= nx && is_wall(bc[1])) ||
+                   (gj < 0 && is_wall(bc[2])) || (gj >= ny && is_wall(bc[3]));
+    return w ? T(-1) : T(1);
+}
+
+template <typename T, int TX, int TY>
+struct StageSmem {
+    static constexpr int RW = TX + 4, RH = TY + 4;   // tile + 2-cell halo
+    static constexpr int GW = TX + 2, GH = TY + 2;   // tile + 1-cell ring
+    static constexpr int NXF = (TX + 1) * TY;        // x-faces
+    static constexpr int NYF = TX * (TY + 1);        // y-faces
+    T w[4][RW * RH];      // rho, u, v, p
+    T rt[2][GW * GH];     // frozen real-time term of rho u, rho v on the ring
+    T gx[4][GW * GH];     // half slopes along x: rho, u, v, p (times dx/2 for p)
+    T gy[4][GW * GH];     // half slopes along y
+    T fx[4][NXF];         // x-face fluxes: mass, x-mom, y-mom, p/beta
+    T fy[4][NYF];         // y-face fluxes
+    double red[4][TX * TY / 32];
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+stage_kernel(const SweepArgs<T> a) {
+    using S = StageSmem<T, TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    constexpr int NT = TX * TY;
+    constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
+
+    const Ctl *ctl = a.ctl;
+    if (ctl->done) return;
+    int in, out;
+    const int cur = ctl->cur;
+    stage_buffers(cur, a.stage, in, out);
+    const T *const *qin = a.buf[in];
+    const T *const *q0 = a.buf[cur];
+    T *const *qout = a.buf[out];
+    const T inv_dt = a.realtime ? T(ctl->inv_dt) : T(0);
+
+    const int nx = a.nx, ny = a.ny;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+    // ---- 1. stage Q^{s-1} (+ two-cell halo, ghosts synthesised) as W ----
+    for (int k = tid; k < RW * RH; k += NT) {
+        const int gi = x0 + (k % RW) - 2, gj = y0 + (k / RW) - 2;
+        int nfx, tfx, nfy, tfy;
+        const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
+        const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
+        const size_t s = (size_t)sj * nx + si;
+        const T r = qin[0][s];
+        T m = qin[1][s], n = qin[2][s];
+        if ((nfx + tfy) & 1) m = -m;
+        if ((nfy + tfx) & 1) n = -n;
+        const T ir = Ar<T>::rcp(r);
+        sm.w[0][k] = r;
+        sm.w[1][k] = m * ir;
+        sm.w[2][k] = n * ir;
+        sm.w[3][k] = qin[3][s];
+    }
+    // ---- frozen real-time term of the momenta on the ring (Eq. bdf, BE) ----
+    const bool need_rt = (a.gradp == kGradNew) && a.realtime;
+    if (need_rt) {
+        for (int k = tid; k < GW * GH; k += NT) {
+            const int gi = x0 + (k % GW) - 1, gj = y0 + (k / GW) - 1;
+            int nfx, tfx, nfy, tfy;
+            const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
+            const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
+            const size_t s = (size_t)sj * nx + si;
+            T rx = (q0[1][s] - a.lev[1][s]) * inv_dt;
+            T ry = (q0[2][s] - a.lev[2][s]) * inv_dt;
+            if ((nfx + tfy) & 1) rx = -rx;
+            if ((nfy + tfx) & 1) ry = -ry;
+            sm.rt[0][k] = rx;
+            sm.rt[1][k] = ry;
+        }
+    }
+    __syncthreads();
+
+    // ---- 2. limited half slopes and pressure gradient on the ring ----
+    const T klim = T(a.limiter_k);
+    const T kp = (a.gradp == kGradSuperbee) ? T(2) : T(1);
+    for (int k = tid; k < GW * GH; k += NT) {
+        const int li = k % GW, lj = k / GW;            // ring coords (cell li-1, lj-1)
+        const int c = (lj + 1) * RW + (li + 1);
+        const int e = c + 1, wv = c - 1, nn = c + RW, ss = c - RW;
+        const T *R = sm.w[0], *U = sm.w[1], *V = sm.w[2], *P = sm.w[3];
+        T hrx, hry, hux, huy, hvx, hvy;
+        if (a.limiter_k == 1) {
+            hrx = T(0.5) * minmod(R[e] - R[c], R[c] - R[wv]);
+            hry = T(0.5) * minmod(R[nn] - R[c], R[c] - R[ss]);
+            hux = T(0.5) * minmod(U[e] - U[c], U[c] - U[wv]);
+            huy = T(0.5) * minmod(U[nn] - U[c], U[c] - U[ss]);
+            hvx = T(0.5) * minmod(V[e] - V[c], V[c] - V[wv]);
+            hvy = T(0.5) * minmod(V[nn] - V[c], V[c] - V[ss]);
+        } else {
+            hrx = T(0.5) * limiter(R[e] - R[c], R[c] - R[wv], klim);
+            hry = T(0.5) * limiter(R[nn] - R[c], R[c] - R[ss], klim);
+            hux = T(0.5) * limiter(U[e] - U[c], U[c] - U[wv], klim);
+            huy = T(0.5) * limiter(U[nn] - U[c], U[c] - U[ss], klim);
+            hvx = T(0.5) * limiter(V[e] - V[c], V[c] - V[wv], klim);
+            hvy = T(0.5) * limiter(V[nn] - V[c], V[c] - V[ss], klim);
+        }
+        T hpx, hpy;
+        if (a.gradp == kGradNew) {
+            // Eq. new_gradp times dx/2, with dx/2 * d_x rho = hrx etc.
+            const int gi = x0 + li - 1, gj = y0 + lj - 1;
+            const T sg = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc);
+            const T rho = R[c], u = U[c], v = V[c];
+            const T rtx = need_rt ? sm.rt[0][k] : T(0);
+            const T rty = need_rt ? sm.rt[1][k] : T(0);
+            const T ru = rho * u, rv = rho * v, uv = u * v;
+            hpx = -a.half_dx * rtx - (u * u * hrx + T(2) * ru * hux) -
+                  a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
+            hpy = -a.half_dy * rty - (v * v * hry + T(2) * rv * hvy) -
+                  a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * rho * a.gy * sg;
+        } else {
+            hpx = T(0.5) * limiter(P[e] - P[c], P[c] - P[wv], kp);
+            hpy = T(0.5) * limiter(P[nn] - P[c], P[c] - P[ss], kp);
+        }
+        sm.gx[0][k] = hrx; sm.gx[1][k] = hux; sm.gx[2][k] = hvx; sm.gx[3][k] = hpx;
+        sm.gy[0][k] = hry; sm.gy[1][k] = huy; sm.gy[2][k] = hvy; sm.gy[3][k] = hpy;
+    }
+    __syncthreads();
+
+    // ---- 3. face states and Osher fluxes ----
+    for (int k = tid; k < S::NXF + S::NYF; k += NT) {
+        T F[4];
+        if (k < S::NXF) {
+            const int fi = k % (TX + 1), fj = k / (TX + 1);  // face between cells fi-1 and fi
+            const int ga = (fj + 1) * GW + fi, gb = ga + 1;
+            const int ca = (fj + 2) * RW + fi + 1, cb = ca + 1;
+            const T rL = sm.w[0][ca] + sm.gx[0][ga], rR = sm.w[0][cb] - sm.gx[0][gb];
+            const T uL = sm.w[1][ca] + sm.gx[1][ga], uR = sm.w[1][cb] - sm.gx[1][gb];
+            const T vL = sm.w[2][ca] + sm.gx[2][ga], vR = sm.w[2][cb] - sm.gx[2][gb];
+            const T pL = sm.w[3][ca] + sm.gx[3][ga], pR = sm.w[3][cb] - sm.gx[3][gb];
+            osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
+            sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
+        } else {
+            const int kk = k - S::NXF;
+            const int fi = kk % TX, fj = kk / TX;            // face between cells fj-1 and fj
+            const int ga = fj * GW + fi + 1, gb = ga + GW;
+            const int ca = (fj + 1) * RW + fi + 2, cb = ca + RW;
+            const T rL = sm.w[0][ca] + sm.gy[0][ga], rR = sm.w[0][cb] - sm.gy[0][gb];
+            const T uL = sm.w[1][ca] + sm.gy[1][ga], uR = sm.w[1][cb] - sm.gy[1][gb];
+            const T vL = sm.w[2][ca] + sm.gy[2][ga], vR = sm.w[2][cb] - sm.gy[2][gb];
+            const T pL = sm.w[3][ca] + sm.gy[3][ga], pR = sm.w[3][cb] - sm.gy[3][gb];
+            // rotation (Alg. 2, n = y): normal velocity v, tangential u
+            osher_flux<T>(rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
+            sm.fy[0][kk] = F[0]; sm.fy[1][kk] = F[2]; sm.fy[2][kk] = F[1]; sm.fy[3][kk] = F[3];
+        }
+    }
+    __syncthreads();
+
+    // ---- 4. divergence + sources + point-implicit stage update ----
+    const int li = tid % TX, lj = tid / TX;
+    const int gi = x0 + li, gj = y0 + lj;
+    const bool inside = (gi < nx) && (gj < ny);
+    double sq[4] = {0.0, 0.0, 0.0, 0.0};
+    if (inside) {
+        const size_t g = (size_t)gj * nx + gi;
+        const int fw = lj * (TX + 1) + li, fe = fw + 1;
+        const int fs = lj * TX + li, fn = fs + TX;
+        T div[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+            div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * a.inv_dx + (sm.fy[f][fn] - sm.fy[f][fs]) * a.inv_dy;
+        const T r0 = q0[0][g], m0 = q0[1][g], n0 = q0[2][g], p0 = q0[3][g];
+        T rt0 = T(0), rt1 = T(0), rt2 = T(0);
+        if (a.realtime) {
+            rt0 = (r0 - a.lev[0][g]) * inv_dt;
+            rt1 = (m0 - a.lev[1][g]) * inv_dt;
+            rt2 = (n0 - a.lev[2][g]) * inv_dt;
+        }
+        const T b0 = -div[0] - rt0;
+        const T b1 = -div[1] - rt1 + r0 * a.gx;
+        const T b2 = -div[2] - rt2 + r0 * a.gy;
+        const T b3 = -div[3];
+        // pseudo-time step from Q^{m} (Sec. 2.2.3)
+        T dtau;
+        if (a.local_dtau) {
+            const T ir = Ar<T>::rcp(r0);
+            const T u = m0 * ir, v = n0 * ir, fb = T(4) * a.beta * ir;
+            const T cx = Ar<T>::sqrt_(u * u + fb), cy = Ar<T>::sqrt_(v * v + fb);
+            const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
+            dtau = a.cfl_area / den;
+        } else {
+            dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
+        }
+        const T api = T(1) + a.alpha * dtau * inv_dt;      // Eq. point_implicit, B0 = 1
+        const T coef = a.alpha * dtau / api;
+        const T coef_p = a.alpha_pi_p_row ? coef : a.alpha * dtau;
+        qout[0][g] = r0 + coef * b0;
+        qout[1][g] = m0 + coef * b1;
+        qout[2][g] = n0 + coef * b2;
+        qout[3][g] = p0 + a.beta * coef_p * b3;
+        if (a.stage == 1) {
+            const double pb = double(a.beta) * double(b3);
+            sq[0] = double(b0) * double(b0);
+            sq[1] = double(b1) * double(b1);
+            sq[2] = double(b2) * double(b2);
+            sq[3] = pb * pb;
+        }
+    }
+    if (a.stage == 1) {
+        // deterministic block reduction of the squared bracket (FP64)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            double v = sq[f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((tid & 31) == 0) sm.red[f][tid >> 5] = v;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += sm.red[tid][w];
+            a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = s;
+        }
+    }
+}
+
+// Global pseudo-time step option: min over cells of the local step
+// (Sec. 2.2.3), from Q^{m}.  Positive doubles order like their bit patterns.
+template <typename T>
+__global__ void dtau_min_kernel(const SweepArgs<T> a) {
+    const Ctl *ctl = a.ctl;
+    if (ctl->done) return;
+    const T *const *q = a.buf[ctl->cur];
+    const size_t N = (size_t)a.nx * a.ny;
+    double mn = INFINITY;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        const T r0 = q[0][g];
+        const T ir = Ar<T>::rcp(r0);
+        const T u = q[1][g] * ir, v = q[2][g] * ir, fb = T(4) * a.beta * ir;
+        const T cx = Ar<T>::sqrt_(u * u + fb), cy = Ar<T>::sqrt_(v * v + fb);
+        const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
+        mn = fmin(mn, double(a.cfl_area / den));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMin(&a.ctl->dtau_bits, (unsigned long long)__double_as_longlong(mn));
+}
+
+// Start of a physical step: Q^n <- Q (Alg. 1) and reset of the control block.
+template <typename T>
+__global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, int max_iters) {
+    Ctl *ctl = a.ctl;
+    const int cur = ctl->cur;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) a.lev[f][g] = a.buf[cur][f][g];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->iter = 0;
+        ctl->done = 0;
+        ctl->status = 1;
+        ctl->max_iters = max_iters;
+        ctl->fixed = tol < 0.0;
+        ctl->tol = tol;
+        ctl->dt = dt;
+        ctl->inv_dt = 1.0 / dt;
+        ctl->dtau_bits = 0x7ff0000000000000ull;  // +inf
+    }
+}
+
+// End of a pseudo-iteration: residual norms from the stage-1 partials (fixed
+// summation order), the stopping test (Alg. 1), and the buffer rotation.
+// Sets the graph's while-condition when launched inside a captured loop.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+end_iteration_kernel(Ctl *ctl, const double *partials, int nblocks, double inv_cells, int s_max,
+                     unsigned long long cond_handle, int use_cond) {
+    __shared__ double red[4][NT];
+    const int tid = threadIdx.x;
+    if (ctl->done) {
+        if (use_cond && tid == 0) cudaGraphSetConditional(cond_handle, 0);
+        return;
+    }
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nblocks; b += NT) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s[f] += partials[(size_t)b * 4 + f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) red[f][tid] = s[f];
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) red[f][tid] += red[f][tid + w];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int it = ctl->iter + 1;
+        ctl->iter = it;
+        bool finite = true, conv = true;
+        for (int f = 0; f < 4; ++f) {
+            const double R = sqrt(red[f][0] * inv_cells);
+            ctl->R[f] = R;
+            if (it == 1) ctl->R0[f] = R;
+            if (!isfinite(R)) finite = false;
+            const double thr = fmax(ctl->tol * ctl->R0[f], ctl->abs_tol[f]);
+            if (!(R <= thr)) conv = false;
+        }
+        ctl->cur = final_buffer(ctl->cur, s_max);
+        int done = 0;
+        if (!finite) { ctl->status = -3; done = 1; }
+        else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
+        else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
+        ctl->done = done;
+        ctl->dtau_bits = 0x7ff0000000000000ull;
+        if (use_cond) cudaGraphSetConditional(cond_handle, done ? 0u : 1u);
+    }
+}
+
+}  // namespace acgb

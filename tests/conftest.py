@@ -23,3 +23,34 @@ def load_golden(name):
                 continue
             rows.append([float(x) for x in line.split()])
     return rows
+
+
+def field_scales(state):
+    """Per-field scale for relative errors: max |field|, with the momenta
+    floored by max(rho) * 1e-3 m/s so that fields at rest (round-off
+    values) are compared against a physical scale rather than noise."""
+    import numpy as np
+    rho = np.abs(state[0]).max()
+    sc = []
+    for k, a in enumerate(state):
+        m = float(np.abs(a).max())
+        if k in (1, 2):
+            m = max(m, 1e-3 * rho)
+        if k == 3:
+            m = max(m, 1e-12)
+        sc.append(m)
+    return sc
+
+
+def rel_errors(got, ref):
+    import numpy as np
+    sc = field_scales(ref)
+    return [float(np.abs(np.asarray(g) - np.asarray(r)).max() / s) for g, r, s in zip(got, ref, sc)]
+
+
+def cuda_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

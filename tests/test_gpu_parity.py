@@ -1,0 +1,225 @@
+"""GPU FP64 sweep vs the FP64 oracle, element by element, through the C ABI.
+
+Bar: relative L-infinity error <= 1e-11 per field after one physical step
+from an identical input state (momenta scaled by max(rho) * 1e-3 m/s at
+least), and identical pseudo-iteration counts when the stopping test ends
+the step.  Sizes span several 32x8 tiles with ragged tails; options cover
+every boundary kind, pressure-gradient method, limiter, stage count and
+pseudo-time-step mode.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_errors
+from paper_2108_08769_gb300 import ac
+from paper_2108_08769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def run_both(case, steps=1, tol=None, max_iters=None):
+    """Advance GPU and oracle from the same state, one physical step at a
+    time; each step starts both from the oracle's previous state."""
+    t = ac.Tank.from_case(case)
+    state = case.state()
+    out = []
+    for _ in range(steps):
+        t.set_state(*state)
+        rc, its = t.physical_step(case.dt, case.tol if tol is None else tol,
+                                  case.max_iters if max_iters is None else max_iters)
+        got = t.get_state()
+        R, R0 = t.residual_norms()
+        ref, st, oits, oR, oR0 = oracle.physical_step(case, state, tol=tol, max_iters=max_iters)
+        out.append((got, ref, rc, its, st, oits, R, oR))
+        state = ref
+    t.close()
+    return out
+
+
+def assert_parity(res, tol=TOL, check_iters=True):
+    for got, ref, rc, its, st, oits, R, oR in res:
+        errs = rel_errors(got, ref)
+        assert max(errs) <= tol, errs
+        if check_iters:
+            assert its == oits, (its, oits)
+            assert rc == st, (rc, st)
+        assert np.allclose(R, oR, rtol=1e-9, atol=1e-300), (R, oR)
+
+
+def test_riemann_200x4_converged_steps():
+    """1D density-discontinuity Riemann problem (200x4, periodic in y,
+    transmissive in x): two physical steps ending on the 1e-8 residual drop."""
+    case = W.riemann_tank()
+    assert_parity(run_both(case, steps=2))
+
+
+def test_hydrostatic_tank_64_fixed_iterations():
+    case = W.hydrostatic_tank(64)
+    res = run_both(case, steps=1, tol=-1.0, max_iters=12)
+    assert_parity(res)
+    got = res[0][0]
+    assert np.abs(got[2]).max() < 1e-10
+
+
+def test_hydrostatic_tank_256_full_size():
+    """The benchmarked 256x256 workload in the benchmark's launch
+    configuration, a few pseudo-iterations, against the oracle on every cell."""
+    case = W.hydrostatic_tank(256)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3))
+
+
+def test_water_column_1024x512_full_size_one_iteration():
+    case = W.water_column(1024, 512)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=1))
+
+
+BCS = [("slip",) * 4,
+       ("noslip",) * 4,
+       ("transmissive", "slip", "noslip", "transmissive"),
+       ("periodic", "periodic", "slip", "slip"),
+       ("slip", "noslip", "periodic", "periodic"),
+       ("periodic",) * 4]
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("nx,ny", [(37, 19), (70, 9), (5, 3)])
+def test_boundary_kinds_ragged_grids(bc, nx, ny):
+    case = W.random_two_fluid(nx, ny, ratio=500.0, c0=8.0, bc=bc, gx=1.5,
+                              gy=0.0 if bc[2] == "periodic" else -9.81)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=4))
+
+
+OPTION_SETS = [
+    dict(gradp="minmod"),
+    dict(gradp="superbee"),
+    dict(limiter_k=2),
+    dict(s_max=1, cfl_tau=0.3),
+    dict(s_max=2),
+    dict(s_max=4),
+    dict(local_dtau=False),
+    dict(realtime=False),
+    dict(alpha_pi_p_row=False),
+    dict(realtime=False, local_dtau=False, gradp="minmod", cfl_tau=0.9),
+]
+
+
+@pytest.mark.parametrize("opts", OPTION_SETS, ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+def test_option_matrix(opts):
+    case = W.random_two_fluid(45, 21, ratio=200.0, c0=6.0, bc=("slip", "transmissive", "noslip", "slip"))
+    for k, v in opts.items():
+        setattr(case.options, k, v)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=5))
+
+
+def test_convergence_terminated_dam_break():
+    """Sec. 3.3.1 set-up (20x20, until the rho u and rho v residuals < 1e-3):
+    same iteration count, same state."""
+    case = W.dam_break_small()
+    case.max_iters = 3000
+    assert_parity(run_both(case, steps=1))
+
+
+def test_hydrostatic_column_paper_setup():
+    """Sec. 3.2 set-up (20x1, g along x, p = 0 at start, until rho u residual < 1e-5)."""
+    case = W.hydrostatic_column_1d()
+    case.max_iters = 5000
+    assert_parity(run_both(case, steps=1))
+
+
+@pytest.mark.parametrize("k", [1, 5])
+@pytest.mark.parametrize("along", ["x", "y"])
+def test_riemann_problem_pure_pseudo_time(k, along):
+    """Sec. 3.1 set-up (real-time term off, global pseudo-time step, minmod on p)."""
+    case = W.riemann_problem(k, 100, along=along)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=10))
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 17), (33, 1), (2, 2)])
+def test_degenerate_grids(nx, ny):
+    case = W.random_two_fluid(nx, ny, ratio=10.0, c0=3.0, velocity=0.01)
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3))
+
+
+def test_not_converged_status():
+    case = W.riemann_tank()
+    res = run_both(case, steps=1, tol=1e-14, max_iters=3)
+    got, ref, rc, its, st, oits, R, oR = res[0]
+    assert rc == ac.AC_NOT_CONVERGED and its == 3 and st == oracle.NOT_CONVERGED
+    assert_parity(res)
+
+
+def test_nonfinite_restores_state():
+    """A pseudo-CFL far beyond the stability limit makes the iteration blow
+    up: the call reports AC_ERR_NONFINITE and leaves the state as it was."""
+    case = W.random_two_fluid(32, 16, ratio=1000.0, c0=20.0)
+    case.options.cfl_tau = 40.0
+    t = ac.Tank.from_case(case)
+    before = t.get_state()
+    with pytest.raises(ac.ACError) as e:
+        t.physical_step(case.dt, -1.0, 400)
+    assert e.value.code == ac.AC_ERR_NONFINITE
+    after = t.get_state()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    t.close()
+
+
+def test_state_roundtrip_and_resume_bitwise():
+    """Checkpoint/resume: 3 steps == 1 step + get/set state + 2 steps, bitwise."""
+    case = W.random_two_fluid(40, 24, ratio=100.0, c0=5.0)
+    a = ac.Tank.from_case(case)
+    for _ in range(3):
+        a.physical_step(case.dt, -1.0, 4)
+    full = a.get_state()
+    b = ac.Tank.from_case(case)
+    b.physical_step(case.dt, -1.0, 4)
+    snap = b.get_state()
+    b.close()
+    c = ac.Tank.from_case(case)
+    c.set_state(*snap)
+    for _ in range(2):
+        c.physical_step(case.dt, -1.0, 4)
+    resumed = c.get_state()
+    for x, y in zip(full, resumed):
+        assert np.array_equal(x, y)
+    s0 = case.state()
+    d = ac.Tank.from_case(case)
+    for x, y in zip(s0, d.get_state()):
+        assert np.array_equal(x, y)
+    for t in (a, c, d):
+        t.close()
+
+
+def test_runs_on_a_torch_stream():
+    import torch
+    case = W.random_two_fluid(40, 24, ratio=100.0, c0=5.0)
+    s = torch.cuda.Stream()
+    t = ac.Tank.from_case(case)
+    t.set_stream(s.cuda_stream)
+    rc, its = t.physical_step(case.dt, -1.0, 4)
+    got = t.get_state()
+    ref, *_ = oracle.physical_step(case, case.state(), tol=-1.0, max_iters=4)
+    assert max(rel_errors(got, ref)) <= TOL
+    assert t.kernel_launches() == 1 + 4 * 4
+    t.close()
+
+
+def test_step_before_state_is_an_error():
+    t = ac.Tank(8, 8, 1.0, 1.0, 0.0, -9.81, 1e3, ("slip",) * 4)
+    with pytest.raises(ac.ACError) as e:
+        t.physical_step(1e-3, 1e-8, 10)
+    assert e.value.code == ac.AC_ERR_STATE
+    with pytest.raises(ac.ACError) as e:
+        t.set_state(np.zeros(64), np.zeros(64), np.zeros(64), np.zeros(64))
+    assert e.value.code == ac.AC_ERR_ARG
+    bad = np.ones(64)
+    bad[3] = math.nan
+    with pytest.raises(ac.ACError) as e:
+        t.set_state(np.ones(64), bad, np.zeros(64), np.zeros(64))
+    assert e.value.code == ac.AC_ERR_NONFINITE
+    t.close()
