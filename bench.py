@@ -252,7 +252,8 @@ def run_ours(args, ws, rank, local):
     flops = FP64_FLOPS_PER_CELL_STAGE * case.cells
     achieved = flops / per_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": FP64_TRAFFIC_PER_CELL_STAGE * case.cells,
                 "kernel": "stage_kernel<double,32,8>", "launch_ms": per_launch_s * 1e3,
                 "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
                 "hbm_frac_of_measured": (BYTES_PER_CELL_ITER_F64 / 3.0) * case.cells / per_launch_s / 1e9
@@ -276,8 +277,11 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-# FP64 operations of one stage sweep per cell ("roofline")
-FP64_FLOPS_PER_CELL_STAGE = 1500.0
+# FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
+# counted by ncu on stage_kernel<double,32,8> (profiles/stage_kernel_f64_*)
+FP64_FLOPS_PER_CELL_STAGE = 927.0
+# DRAM bytes per cell of one FP64 stage launch (ncu, 2048x2048 case, larger than L2)
+FP64_TRAFFIC_PER_CELL_STAGE = 115.3
 # algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3)
 BYTES_PER_CELL_ITER_F64 = 328.0
 

@@ -41,27 +41,40 @@ def run_both(case, steps=1, tol=None, max_iters=None):
     return out
 
 
-def assert_parity(res, tol=TOL, check_iters=True):
+def norm_atol(ref, case):
+    """Absolute floor for comparing residual norms: 1e-12 of the size of the
+    individual terms that cancel in the bracket (flux differences over a
+    cell), so norms at round-off level are compared against that level."""
+    rho, p = ref[0], ref[3]
+    h = min(case.dx, case.dy)
+    b = case.beta
+    mom = (np.abs(p).max() + 4.0 * b) / h
+    return 1e-12 * np.array([math.sqrt(4.0 * b * rho.max()) / h, mom, mom,
+                             b * math.sqrt(4.0 * b / rho.min()) / h])
+
+
+def assert_parity(res, tol=TOL, check_iters=True, case=None):
     for got, ref, rc, its, st, oits, R, oR in res:
         errs = rel_errors(got, ref)
         assert max(errs) <= tol, errs
         if check_iters:
             assert its == oits, (its, oits)
             assert rc == st, (rc, st)
-        assert np.allclose(R, oR, rtol=1e-9, atol=1e-300), (R, oR)
+        atol = norm_atol(ref, case) if case is not None else 0.0
+        assert np.all(np.abs(R - oR) <= 1e-9 * np.abs(oR) + atol), (R, oR, atol)
 
 
 def test_riemann_200x4_converged_steps():
     """1D density-discontinuity Riemann problem (200x4, periodic in y,
     transmissive in x): two physical steps ending on the 1e-8 residual drop."""
     case = W.riemann_tank()
-    assert_parity(run_both(case, steps=2))
+    assert_parity(run_both(case, steps=2), case=case)
 
 
 def test_hydrostatic_tank_64_fixed_iterations():
     case = W.hydrostatic_tank(64)
     res = run_both(case, steps=1, tol=-1.0, max_iters=12)
-    assert_parity(res)
+    assert_parity(res, case=case)
     got = res[0][0]
     assert np.abs(got[2]).max() < 1e-10
 
@@ -70,12 +83,12 @@ def test_hydrostatic_tank_256_full_size():
     """The benchmarked 256x256 workload in the benchmark's launch
     configuration, a few pseudo-iterations, against the oracle on every cell."""
     case = W.hydrostatic_tank(256)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3), case=case)
 
 
 def test_water_column_1024x512_full_size_one_iteration():
     case = W.water_column(1024, 512)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=1))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=1), case=case)
 
 
 BCS = [("slip",) * 4,
@@ -91,7 +104,7 @@ BCS = [("slip",) * 4,
 def test_boundary_kinds_ragged_grids(bc, nx, ny):
     case = W.random_two_fluid(nx, ny, ratio=500.0, c0=8.0, bc=bc, gx=1.5,
                               gy=0.0 if bc[2] == "periodic" else -9.81)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=4))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=4), case=case)
 
 
 OPTION_SETS = [
@@ -113,7 +126,7 @@ def test_option_matrix(opts):
     case = W.random_two_fluid(45, 21, ratio=200.0, c0=6.0, bc=("slip", "transmissive", "noslip", "slip"))
     for k, v in opts.items():
         setattr(case.options, k, v)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=5))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=5), case=case)
 
 
 def test_convergence_terminated_dam_break():
@@ -121,14 +134,14 @@ def test_convergence_terminated_dam_break():
     same iteration count, same state."""
     case = W.dam_break_small()
     case.max_iters = 3000
-    assert_parity(run_both(case, steps=1))
+    assert_parity(run_both(case, steps=1), case=case)
 
 
 def test_hydrostatic_column_paper_setup():
     """Sec. 3.2 set-up (20x1, g along x, p = 0 at start, until rho u residual < 1e-5)."""
     case = W.hydrostatic_column_1d()
     case.max_iters = 5000
-    assert_parity(run_both(case, steps=1))
+    assert_parity(run_both(case, steps=1), case=case)
 
 
 @pytest.mark.parametrize("k", [1, 5])
@@ -136,13 +149,13 @@ def test_hydrostatic_column_paper_setup():
 def test_riemann_problem_pure_pseudo_time(k, along):
     """Sec. 3.1 set-up (real-time term off, global pseudo-time step, minmod on p)."""
     case = W.riemann_problem(k, 100, along=along)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=10))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=10), case=case)
 
 
 @pytest.mark.parametrize("nx,ny", [(1, 1), (1, 17), (33, 1), (2, 2)])
 def test_degenerate_grids(nx, ny):
     case = W.random_two_fluid(nx, ny, ratio=10.0, c0=3.0, velocity=0.01)
-    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3))
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=3), case=case)
 
 
 def test_not_converged_status():
@@ -150,7 +163,7 @@ def test_not_converged_status():
     res = run_both(case, steps=1, tol=1e-14, max_iters=3)
     got, ref, rc, its, st, oits, R, oR = res[0]
     assert rc == ac.AC_NOT_CONVERGED and its == 3 and st == oracle.NOT_CONVERGED
-    assert_parity(res)
+    assert_parity(res, case=case)
 
 
 def test_nonfinite_restores_state():
