@@ -2,27 +2,31 @@
 // device memory, the captured pseudo-iteration loop, state transfer.
 //
 // Control flow of one physical step (Alg. 1):
-//   begin_step_kernel            Q^n <- Q, control block reset
+//   begin-step kernel            Q^n <- Q, control block reset
 //   graph: WHILE (not done) {    one pseudo-iteration per body execution
-//     [dtau_min_kernel]          global pseudo-time step option
-//     stage_kernel  x s_max      fused stage sweeps (Eq. RK2)
-//     end_iteration_kernel       norms, stopping test, buffer rotation,
+//     [global dtau kernel]       global pseudo-time step option
+//     stage sweep  x s_max       fused stage sweeps (Eq. RK2)
+//     end_iteration_kernel       norms, stopping test, buffer rotation;
 //   }                            sets the WHILE condition on the device
-//   one 160-byte device->host read of the control block.
-// The loop therefore runs without any host round trip; the host waits once
-// per physical step.
+//   one device->host read of the control block.
+// The loop runs without host round trips; the host waits once per step.
+//
+// Two arithmetic forms share this control flow through the Backend
+// interface: FP64 (every step in double precision) and mixed (FP32 sweep,
+// FP64 time level, reference pressure and norms; see ac_kernels_mixed.cuh).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <cstdarg>
-#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/ac.h"
-#include "ac_kernels.cuh"
+#include "ac_kernels_mixed.cuh"
 
 using namespace acgb;
 
@@ -51,8 +55,12 @@ int fail(int code, const char *fmt, ...) {
 
 constexpr int kTX = 32, kTY = 8;
 constexpr int kEndThreads = 256;
+constexpr int kGridStrideBlocks = 152 * 8;
 
 bool valid_bc(int b) { return b >= AC_BC_WALL_SLIP && b <= AC_BC_PERIODIC; }
+bool is_wall_bc(int b) { return b == AC_BC_WALL_SLIP || b == AC_BC_WALL_NOSLIP; }
+
+struct Backend;
 
 }  // namespace
 
@@ -65,9 +73,8 @@ struct ac_ctx {
     ac_options opt;
     int device;
     size_t N;
-    // device memory (FP64 form)
-    double *buf[3][4];
-    double *lev[4];
+    double dx, dy;
+    Backend *be;
     double *partials;
     Ctl *ctl;
     Ctl *hctl;            // pinned host mirror
@@ -80,7 +87,6 @@ struct ac_ctx {
     bool has_state;
     int cur_host;
     long long launches;
-    int last_iters;
     bool profiling;
     cudaEvent_t ev[5];
     double stage_ms;
@@ -89,52 +95,296 @@ struct ac_ctx {
 
 namespace {
 
-SweepArgs<double> make_args(const ac_ctx *c, int stage) {
-    SweepArgs<double> a;
-    memset(&a, 0, sizeof a);
-    a.nx = c->grid.nx;
-    a.ny = c->grid.ny;
-    a.bc[0] = c->bc.xlo; a.bc[1] = c->bc.xhi; a.bc[2] = c->bc.ylo; a.bc[3] = c->bc.yhi;
-    a.gradp = c->opt.gradp;
-    a.limiter_k = c->opt.limiter_k;
-    a.realtime = c->opt.realtime;
-    a.local_dtau = c->opt.local_dtau;
-    a.alpha_pi_p_row = c->opt.alpha_pi_p_row;
-    a.stage = stage;
-    a.s_max = c->opt.rk_stages;
-    a.alpha = stage > 0 ? 1.0 / double(c->opt.rk_stages - stage + 1) : 0.0;
-    const double dx = c->grid.lx / c->grid.nx, dy = c->grid.ly / c->grid.ny;
-    a.dx = dx; a.dy = dy;
-    a.half_dx = 0.5 * dx; a.half_dy = 0.5 * dy;
-    a.inv_dx = 1.0 / dx; a.inv_dy = 1.0 / dy;
-    a.dx_over_dy = dx / dy; a.dy_over_dx = dy / dx;
-    a.beta = c->beta; a.inv_beta = 1.0 / c->beta;
-    a.gx = c->grid.gx; a.gy = c->grid.gy;
-    a.cfl_area = c->opt.cfl_tau * dx * dy;
-    for (int b = 0; b < 3; ++b)
-        for (int f = 0; f < 4; ++f) a.buf[b][f] = c->buf[b][f];
-    for (int f = 0; f < 4; ++f) a.lev[f] = c->lev[f];
-    a.partials = c->partials;
-    a.ctl = c->ctl;
-    return a;
-}
+int grid_stride_blocks(size_t N) { return (int)std::min<size_t>((N + 255) / 256, kGridStrideBlocks); }
 
-size_t stage_smem() { return sizeof(StageSmem<double, kTX, kTY>); }
+struct Backend {
+    virtual ~Backend() {}
+    virtual int alloc(ac_ctx *c) = 0;
+    virtual void release() = 0;
+    virtual int set_state(ac_ctx *c, const double *const f[4]) = 0;
+    virtual int get_state(const ac_ctx *c, double *const out[4]) = 0;
+    virtual int get_levels(const ac_ctx *c, double *const out[3]) = 0;
+    virtual int set_levels(ac_ctx *c, const double *const in[3]) = 0;
+    virtual int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) = 0;
+    virtual int dtau_min(ac_ctx *c, cudaStream_t s) = 0;
+    virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
+    virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
+};
 
-// Enqueue one pseudo-iteration on stream s (with events around the stage
-// sweeps when `timed`).
-int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false) {
-    if (!c->opt.local_dtau) {
-        SweepArgs<double> a = make_args(c, 0);
-        int blocks = (int)std::min<size_t>((c->N + 255) / 256, 152 * 8);
-        dtau_min_kernel<double><<<blocks, 256, 0, s>>>(a);
-        CK(cudaGetLastError());
+// ------------------------------------------------------------------ FP64
+
+struct F64Backend : Backend {
+    double *buf[3][4] = {};
+    double *lev[4] = {};
+
+    static size_t smem() { return sizeof(StageSmem<double, kTX, kTY>); }
+
+    SweepArgs<double> args(const ac_ctx *c, int stage) const {
+        SweepArgs<double> a;
+        memset(&a, 0, sizeof a);
+        a.nx = c->grid.nx; a.ny = c->grid.ny;
+        a.bc[0] = c->bc.xlo; a.bc[1] = c->bc.xhi; a.bc[2] = c->bc.ylo; a.bc[3] = c->bc.yhi;
+        a.gradp = c->opt.gradp; a.limiter_k = c->opt.limiter_k; a.realtime = c->opt.realtime;
+        a.local_dtau = c->opt.local_dtau; a.alpha_pi_p_row = c->opt.alpha_pi_p_row;
+        a.stage = stage; a.s_max = c->opt.rk_stages;
+        a.alpha = stage > 0 ? 1.0 / double(c->opt.rk_stages - stage + 1) : 0.0;
+        const double dx = c->dx, dy = c->dy;
+        a.dx = dx; a.dy = dy; a.half_dx = 0.5 * dx; a.half_dy = 0.5 * dy;
+        a.inv_dx = 1.0 / dx; a.inv_dy = 1.0 / dy; a.dx_over_dy = dx / dy; a.dy_over_dx = dy / dx;
+        a.beta = c->beta; a.inv_beta = 1.0 / c->beta; a.gx = c->grid.gx; a.gy = c->grid.gy;
+        a.cfl_area = c->opt.cfl_tau * dx * dy;
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) a.buf[b][f] = buf[b][f];
+        for (int f = 0; f < 4; ++f) a.lev[f] = lev[f];
+        a.partials = c->partials;
+        a.ctl = c->ctl;
+        return a;
     }
+    int alloc(ac_ctx *c) override {
+        const size_t bytes = c->N * sizeof(double);
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) CK(cudaMalloc(&buf[b][f], bytes));
+        for (int f = 0; f < 4; ++f) CK(cudaMalloc(&lev[f], bytes));
+        CK(cudaFuncSetAttribute(stage_kernel<double, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem()));
+        return AC_OK;
+    }
+    void release() override {
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) cudaFree(buf[b][f]);
+        for (int f = 0; f < 4; ++f) cudaFree(lev[f]);
+    }
+    int set_state(ac_ctx *c, const double *const f[4]) override {
+        const size_t bytes = c->N * sizeof(double);
+        for (int k = 0; k < 4; ++k) {
+            CK(cudaMemcpyAsync(buf[0][k], f[k], bytes, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(lev[k], f[k], bytes, cudaMemcpyHostToDevice, c->stream));
+        }
+        return AC_OK;
+    }
+    int get_state(const ac_ctx *c, double *const out[4]) override {
+        for (int k = 0; k < 4; ++k)
+            if (out[k])
+                CK(cudaMemcpyAsync(out[k], buf[c->cur_host][k], c->N * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return AC_OK;
+    }
+    int get_levels(const ac_ctx *c, double *const out[3]) override {
+        for (int k = 0; k < 3; ++k)
+            if (out[k])
+                CK(cudaMemcpyAsync(out[k], lev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return AC_OK;
+    }
+    int set_levels(ac_ctx *c, const double *const in[3]) override {
+        for (int k = 0; k < 3; ++k)
+            CK(cudaMemcpyAsync(lev[k], in[k], c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return AC_OK;
+    }
+    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) override {
+        begin_step_kernel<double><<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters);
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int dtau_min(ac_ctx *c, cudaStream_t s) override {
+        dtau_min_kernel<double><<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int stage(ac_ctx *c, cudaStream_t s, int st) override {
+        stage_kernel<double, kTX, kTY><<<c->grid_dim, kTX * kTY, smem(), s>>>(args(c, st));
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int restore(ac_ctx *c, cudaStream_t s) override {
+        // Q <- Q^n (all four fields hold the state of the start of the step)
+        for (int f = 0; f < 4; ++f)
+            CK(cudaMemcpyAsync(buf[c->hctl->cur][f], lev[f], c->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return AC_OK;
+    }
+};
+
+// ------------------------------------------------------------------ mixed
+
+struct MixedBackend : Backend {
+    float *d[3][4] = {};
+    float *qn32[3] = {};
+    float *rho_ref = nullptr, *dref = nullptr, *lev_p = nullptr;
+    double *q64[3] = {};
+    std::vector<double> p_ref;   // FP64 reference pressure (host copy)
+    bool use_ref = false;
+
+    static size_t smem() { return sizeof(MixedSmem<kTX, kTY>); }
+
+    MixedArgs args(const ac_ctx *c, int stage) const {
+        MixedArgs a;
+        memset(&a, 0, sizeof a);
+        a.nx = c->grid.nx; a.ny = c->grid.ny;
+        a.bc[0] = c->bc.xlo; a.bc[1] = c->bc.xhi; a.bc[2] = c->bc.ylo; a.bc[3] = c->bc.yhi;
+        a.gradp = c->opt.gradp; a.limiter_k = c->opt.limiter_k; a.realtime = c->opt.realtime;
+        a.local_dtau = c->opt.local_dtau; a.alpha_pi_p_row = c->opt.alpha_pi_p_row;
+        a.stage = stage; a.s_max = c->opt.rk_stages;
+        a.alpha = stage > 0 ? float(1.0 / double(c->opt.rk_stages - stage + 1)) : 0.0f;
+        const double dx = c->dx, dy = c->dy;
+        a.dx = float(dx); a.dy = float(dy); a.half_dx = float(0.5 * dx); a.half_dy = float(0.5 * dy);
+        a.inv_dx = float(1.0 / dx); a.inv_dy = float(1.0 / dy);
+        a.dx_over_dy = float(dx / dy); a.dy_over_dx = float(dy / dx);
+        a.beta = float(c->beta); a.inv_beta = float(1.0 / c->beta);
+        a.gx = float(c->grid.gx); a.gy = float(c->grid.gy);
+        a.cfl_area = float(c->opt.cfl_tau * dx * dy);
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) a.d[b][f] = d[b][f];
+        for (int f = 0; f < 3; ++f) { a.qn32[f] = qn32[f]; a.q64[f] = q64[f]; }
+        a.rho_ref = rho_ref; a.dref = dref; a.lev_p = lev_p;
+        a.partials = c->partials;
+        a.ctl = c->ctl;
+        return a;
+    }
+    int alloc(ac_ctx *c) override {
+        const size_t fb = c->N * sizeof(float), db = c->N * sizeof(double);
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) CK(cudaMalloc(&d[b][f], fb));
+        for (int f = 0; f < 3; ++f) { CK(cudaMalloc(&qn32[f], fb)); CK(cudaMalloc(&q64[f], db)); }
+        CK(cudaMalloc(&rho_ref, fb));
+        CK(cudaMalloc(&dref, fb));
+        CK(cudaMalloc(&lev_p, fb));
+        CK(cudaFuncSetAttribute(stage_kernel_mixed<kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem()));
+        // the reference applies when both y sides are walls and the pressure
+        // gradient comes from Eq. new_gradp
+        use_ref = is_wall_bc(c->bc.ylo) && is_wall_bc(c->bc.yhi) && c->opt.gradp == AC_GRADP_NEW;
+        return AC_OK;
+    }
+    void release() override {
+        for (int b = 0; b < 3; ++b)
+            for (int f = 0; f < 4; ++f) cudaFree(d[b][f]);
+        for (int f = 0; f < 3; ++f) { cudaFree(qn32[f]); cudaFree(q64[f]); }
+        cudaFree(rho_ref);
+        cudaFree(dref);
+        cudaFree(lev_p);
+    }
+    int set_state(ac_ctx *c, const double *const f[4]) override {
+        const int nx = c->grid.nx, ny = c->grid.ny;
+        const size_t N = c->N;
+        std::vector<float> h32(N), href(N, 0.0f), hdref(N, 0.0f), hp(N);
+        p_ref.assign(N, 0.0);
+        if (use_ref) {
+            // discrete hydrostatic columns of the FP32 reference density,
+            // anchored at the top cell of each column
+            for (size_t k = 0; k < N; ++k) href[k] = float(f[0][k]);
+            const double gy = c->grid.gy, dy = c->dy;
+            for (int i = 0; i < nx; ++i) {
+                size_t top = (size_t)(ny - 1) * nx + i;
+                p_ref[top] = f[3][top];
+                for (int j = ny - 2; j >= 0; --j) {
+                    const size_t k = (size_t)j * nx + i;
+                    p_ref[k] = p_ref[k + nx] - (double(href[k]) + double(href[k + nx])) * gy * dy / 2.0;
+                }
+            }
+            const bool per_x = c->bc.xlo == AC_BC_PERIODIC;
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const size_t k = (size_t)j * nx + i;
+                    if (i > 0) hdref[k] = float(p_ref[k] - p_ref[k - 1]);
+                    else if (per_x) hdref[k] = float(p_ref[k] - p_ref[k + nx - 1]);
+                }
+        }
+        for (size_t k = 0; k < N; ++k) hp[k] = float(f[3][k] - p_ref[k]);
+        cudaStream_t s = c->stream;
+        const size_t fb = N * sizeof(float);
+        for (int k = 0; k < 3; ++k) {
+            CK(cudaMemcpyAsync(q64[k], f[k], N * sizeof(double), cudaMemcpyHostToDevice, s));
+            for (size_t q = 0; q < N; ++q) h32[q] = float(f[k][q]);
+            CK(cudaMemcpyAsync(qn32[k], h32.data(), fb, cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));   // h32 is reused
+            CK(cudaMemsetAsync(d[0][k], 0, fb, s));
+        }
+        CK(cudaMemcpyAsync(d[0][3], hp.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(lev_p, hp.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(rho_ref, href.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dref, hdref.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return AC_OK;
+    }
+    int get_state(const ac_ctx *c, double *const out[4]) override {
+        const size_t N = c->N;
+        std::vector<float> h(N);
+        const int cur = c->cur_host;
+        for (int k = 0; k < 3; ++k) {
+            if (!out[k]) continue;
+            CK(cudaMemcpyAsync(out[k], q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(h.data(), d[cur][k], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (size_t q = 0; q < N; ++q) out[k][q] += double(h[q]);
+        }
+        if (out[3]) {
+            CK(cudaMemcpyAsync(h.data(), d[cur][3], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (size_t q = 0; q < N; ++q) out[3][q] = p_ref[q] + double(h[q]);
+        }
+        return AC_OK;
+    }
+    int get_levels(const ac_ctx *c, double *const out[3]) override {
+        for (int k = 0; k < 3; ++k)
+            if (out[k]) CK(cudaMemcpyAsync(out[k], q64[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return AC_OK;
+    }
+    int set_levels(ac_ctx *c, const double *const in[3]) override {
+        // keep Q = Q^n + dQ unchanged: dQ absorbs the change of level
+        const size_t N = c->N;
+        std::vector<double> old(N);
+        std::vector<float> h(N), h32(N);
+        const int cur = c->cur_host;
+        for (int k = 0; k < 3; ++k) {
+            CK(cudaMemcpyAsync(old.data(), q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(h.data(), d[cur][k], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (size_t q = 0; q < N; ++q) {
+                h[q] = float(old[q] + double(h[q]) - in[k][q]);
+                h32[q] = float(in[k][q]);
+            }
+            CK(cudaMemcpyAsync(q64[k], in[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(qn32[k], h32.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(d[cur][k], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        return AC_OK;
+    }
+    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) override {
+        begin_step_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters);
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int dtau_min(ac_ctx *c, cudaStream_t s) override {
+        dtau_min_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int stage(ac_ctx *c, cudaStream_t s, int st) override {
+        stage_kernel_mixed<kTX, kTY><<<c->grid_dim, kTX * kTY, smem(), s>>>(args(c, st));
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+    int restore(ac_ctx *c, cudaStream_t s) override {
+        restore_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
+};
+
+// ------------------------------------------------------------------ loop
+
+// Enqueue one pseudo-iteration on stream s (events around the stage sweeps
+// when `timed`).
+int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false) {
+    int rc;
+    if (!c->opt.local_dtau && (rc = c->be->dtau_min(c, s)) != AC_OK) return rc;
     if (timed) CK(cudaEventRecord(c->ev[0], s));
     for (int st = 1; st <= c->opt.rk_stages; ++st) {
-        SweepArgs<double> a = make_args(c, st);
-        stage_kernel<double, kTX, kTY><<<c->grid_dim, kTX * kTY, stage_smem(), s>>>(a);
-        CK(cudaGetLastError());
+        if ((rc = c->be->stage(c, s, st)) != AC_OK) return rc;
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
     end_iteration_kernel<kEndThreads><<<1, kEndThreads, 0, s>>>(
@@ -236,7 +486,8 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     if (o.riemann != AC_RIEMANN_OSHER) return fail(AC_ERR_ARG, "riemann solver %d is not available", o.riemann);
     if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
     if (o.limiter_k != 1 && o.limiter_k != 2) return fail(AC_ERR_ARG, "limiter_k must be 1 or 2");
-    if (o.precision != AC_PREC_FP64) return fail(AC_ERR_ARG, "precision %d is not available", o.precision);
+    if (o.precision != AC_PREC_FP64 && o.precision != AC_PREC_MIXED)
+        return fail(AC_ERR_ARG, "precision %d is unknown", o.precision);
     if (!(o.cfl_tau > 0.0) || !std::isfinite(o.cfl_tau)) return fail(AC_ERR_ARG, "cfl_tau must be > 0");
     for (int k = 0; k < 4; ++k)
         if (!(o.abs_tol[k] >= 0.0)) return fail(AC_ERR_ARG, "abs_tol[%d] must be >= 0", k);
@@ -252,9 +503,12 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     c->bc = *bc;
     c->opt = o;
     c->N = (size_t)grid->nx * grid->ny;
+    c->dx = grid->lx / grid->nx;
+    c->dy = grid->ly / grid->ny;
     c->grid_dim = dim3((grid->nx + kTX - 1) / kTX, (grid->ny + kTY - 1) / kTY);
     c->nblocks = c->grid_dim.x * c->grid_dim.y;
-    int rc = AC_OK;
+    if (o.precision == AC_PREC_MIXED) c->be = new MixedBackend();
+    else c->be = new F64Backend();
     auto bail = [&](int code) { ac_destroy(c); return code; };
 #define CKC(call)                                                                                  \
     do {                                                                                           \
@@ -264,37 +518,31 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
                              #call, cudaGetErrorString(e_)));                                      \
     } while (0)
     CKC(cudaGetDevice(&c->device));
-    const size_t bytes = c->N * sizeof(double);
-    for (int b = 0; b < 3; ++b)
-        for (int f = 0; f < 4; ++f) CKC(cudaMalloc(&c->buf[b][f], bytes));
-    for (int f = 0; f < 4; ++f) CKC(cudaMalloc(&c->lev[f], bytes));
+    int rc = c->be->alloc(c);
+    if (rc != AC_OK) return bail(rc);
     CKC(cudaMalloc(&c->partials, (size_t)c->nblocks * 4 * sizeof(double)));
     CKC(cudaMalloc(&c->ctl, sizeof(Ctl)));
     CKC(cudaMallocHost(&c->hctl, sizeof(Ctl)));
     CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     for (int k = 0; k < 5; ++k) CKC(cudaEventCreate(&c->ev[k]));
-    CKC(cudaFuncSetAttribute(stage_kernel<double, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)stage_smem()));
     memset(c->hctl, 0, sizeof(Ctl));
     for (int k = 0; k < 4; ++k) c->hctl->abs_tol[k] = o.abs_tol[k];
     c->hctl->done = 1;
     CKC(cudaMemcpy(c->ctl, c->hctl, sizeof(Ctl), cudaMemcpyHostToDevice));
 #undef CKC
-    (void)rc;
     *out = c;
     return AC_OK;
 }
 
 void ac_destroy(ac_ctx *c) {
     if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
     for (int k = 0; k < 5; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cap) cudaStreamDestroy(c->cap);
-    for (int b = 0; b < 3; ++b)
-        for (int f = 0; f < 4; ++f) cudaFree(c->buf[b][f]);
-    for (int f = 0; f < 4; ++f) cudaFree(c->lev[f]);
+    if (c->be) { c->be->release(); delete c->be; }
     cudaFree(c->partials);
     cudaFree(c->ctl);
     if (c->hctl) cudaFreeHost(c->hctl);
@@ -321,12 +569,8 @@ int ac_set_state(ac_ctx *c, const double *rho, const double *rhou, const double 
                 return fail(AC_ERR_ARG, "rho[%zu] = %g lies outside [rho_light/2, 2 rho_heavy]", k, rho[k]);
     }
     const double *src[4] = {rho, rhou, rhov, p};
-    const size_t bytes = c->N * sizeof(double);
     CK(cudaStreamSynchronize(c->stream));
-    for (int f = 0; f < 4; ++f) {
-        CK(cudaMemcpyAsync(c->buf[0][f], src[f], bytes, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(c->lev[f], src[f], bytes, cudaMemcpyHostToDevice, c->stream));
-    }
+    if ((rc = c->be->set_state(c, src)) != AC_OK) return rc;
     c->hctl->cur = 0;
     c->hctl->done = 1;
     c->hctl->iter = 0;
@@ -342,11 +586,7 @@ int ac_get_state(const ac_ctx *c, double *rho, double *rhou, double *rhov, doubl
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
     if (!c->has_state) return fail(AC_ERR_STATE, "no state has been set");
     double *dst[4] = {rho, rhou, rhov, p};
-    const size_t bytes = c->N * sizeof(double);
-    for (int f = 0; f < 4; ++f)
-        if (dst[f]) CK(cudaMemcpyAsync(dst[f], c->buf[c->cur_host][f], bytes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return AC_OK;
+    return c->be->get_state(c, dst);
 }
 
 int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out) {
@@ -359,18 +599,13 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
     if (c->opt.realtime && !(dt > 0.0 && std::isfinite(dt))) return fail(AC_ERR_ARG, "dt must be finite and > 0");
     if (!c->opt.realtime) dt = 1.0;
     cudaStream_t s = c->stream;
-    {
-        SweepArgs<double> a = make_args(c, 0);
-        int blocks = (int)std::min<size_t>((c->N + 255) / 256, 152 * 8);
-        begin_step_kernel<double><<<blocks, 256, 0, s>>>(a, dt, tol, max_iters);
-        CK(cudaGetLastError());
-        c->launches += 1;
-    }
+    int rc;
+    if ((rc = c->be->begin(c, s, dt, tol, max_iters)) != AC_OK) return rc;
+    c->launches += 1;
     if (c->profiling) {
         // one iteration at a time, stage sweeps bracketed by events
         while (true) {
-            int rc = enqueue_iteration(c, s, 0, 0, true);
-            if (rc != AC_OK) return rc;
+            if ((rc = enqueue_iteration(c, s, 0, 0, true)) != AC_OK) return rc;
             CK(cudaMemcpyAsync(c->hctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             for (int st = 1; st <= c->opt.rk_stages; ++st) {
@@ -384,34 +619,27 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
         }
     } else if (use_host_loop()) {
         // debugging aid: host-driven loop, one round trip per chunk of iterations
-        int done_iters = 0, chunk = 4;
+        int launched = 0, chunk = 4;
         while (true) {
-            for (int k = 0; k < chunk; ++k) {
-                int rc = enqueue_iteration(c, s, 0, 0);
-                if (rc != AC_OK) return rc;
-            }
+            for (int k = 0; k < chunk; ++k)
+                if ((rc = enqueue_iteration(c, s, 0, 0)) != AC_OK) return rc;
             CK(cudaMemcpyAsync(c->hctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            done_iters += chunk;
+            launched += chunk;
             if (c->hctl->done) break;
             chunk = std::min(chunk * 2, 64);
         }
-        c->launches += (long long)done_iters * kernels_per_iteration(c);
+        c->launches += (long long)launched * kernels_per_iteration(c);
     } else {
-        int rc = build_graph(c);
-        if (rc != AC_OK) return rc;
+        if ((rc = build_graph(c)) != AC_OK) return rc;
         CK(cudaGraphLaunch(c->exec, s));
         CK(cudaMemcpyAsync(c->hctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         c->launches += (long long)c->hctl->iter * kernels_per_iteration(c);
     }
-    c->last_iters = c->hctl->iter;
     if (iters_out) *iters_out = c->hctl->iter;
     if (c->hctl->status == -3) {
-        // restore the state of the start of the step: Q <- Q^n (all four fields)
-        const size_t bytes = c->N * sizeof(double);
-        for (int f = 0; f < 4; ++f)
-            CK(cudaMemcpyAsync(c->buf[c->hctl->cur][f], c->lev[f], bytes, cudaMemcpyDeviceToDevice, s));
+        if ((rc = c->be->restore(c, s)) != AC_OK) return rc;
         CK(cudaStreamSynchronize(s));
         c->cur_host = c->hctl->cur;
         return fail(AC_ERR_NONFINITE, "residual norm became non-finite at pseudo-iteration %d", c->hctl->iter);
@@ -433,10 +661,7 @@ int ac_get_levels(const ac_ctx *c, double *rho_n, double *rhou_n, double *rhov_n
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
     if (!c->has_state) return fail(AC_ERR_STATE, "no state has been set");
     double *dst[3] = {rho_n, rhou_n, rhov_n};
-    for (int f = 0; f < 3; ++f)
-        if (dst[f]) CK(cudaMemcpyAsync(dst[f], c->lev[f], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return AC_OK;
+    return c->be->get_levels(c, dst);
 }
 
 int ac_set_levels(ac_ctx *c, const double *rho_n, const double *rhou_n, const double *rhov_n) {
@@ -447,10 +672,7 @@ int ac_set_levels(ac_ctx *c, const double *rho_n, const double *rhou_n, const do
     if ((rc = check_host_field(rhou_n, c->N, false, "rhou_n")) != AC_OK) return rc;
     if ((rc = check_host_field(rhov_n, c->N, false, "rhov_n")) != AC_OK) return rc;
     const double *src[3] = {rho_n, rhou_n, rhov_n};
-    for (int f = 0; f < 3; ++f)
-        CK(cudaMemcpyAsync(c->lev[f], src[f], c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return AC_OK;
+    return c->be->set_levels(c, src);
 }
 
 long long ac_kernel_launches(const ac_ctx *c) { return c ? c->launches : 0; }

@@ -26,20 +26,16 @@ def load_golden(name):
 
 
 def field_scales(state):
-    """Per-field scale for relative errors: max |field|, with the momenta
-    floored by max(rho) * 1e-3 m/s so that fields at rest (round-off
-    values) are compared against a physical scale rather than noise."""
+    """Per-field scale for relative errors.  rho and p: max |field|.  The
+    momentum is a vector: both components are measured against the largest
+    momentum magnitude max |rho u|, floored at max(rho) * 1e-3 m/s so that a
+    fluid at rest (round-off momenta) is compared against a physical scale
+    rather than noise."""
     import numpy as np
     rho = np.abs(state[0]).max()
-    sc = []
-    for k, a in enumerate(state):
-        m = float(np.abs(a).max())
-        if k in (1, 2):
-            m = max(m, 1e-3 * rho)
-        if k == 3:
-            m = max(m, 1e-12)
-        sc.append(m)
-    return sc
+    mom = float(np.sqrt(np.asarray(state[1]) ** 2 + np.asarray(state[2]) ** 2).max())
+    mom = max(mom, 1e-3 * rho)
+    return [float(rho), mom, mom, max(float(np.abs(state[3]).max()), 1e-12)]
 
 
 def rel_errors(got, ref):

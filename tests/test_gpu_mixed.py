@@ -1,0 +1,154 @@
+"""Mixed form (FP32 sweep; FP64 time level, reference pressure and norms)
+against FP64, element by element, through the C ABI.
+
+Bar: relative L-infinity error <= 1e-5 per field after a physical step with
+a fixed number of pseudo-iterations from an identical input state (momentum
+components scaled by the largest momentum magnitude, at least max(rho) *
+1e-3 m/s).  Small cases compare with the
+FP64 oracle; full-size cases with the FP64 GPU path, which itself matches
+the oracle to 1e-11 (test_gpu_parity.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_errors
+from paper_2108_08769_gb300 import ac
+from paper_2108_08769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def gpu_run(case, precision, steps=1, iters=10, tol=-1.0):
+    t = ac.Tank.from_case(case, precision=precision)
+    its = []
+    for _ in range(steps):
+        rc, n = t.physical_step(case.dt, tol, iters)
+        its.append(n)
+    out = t.get_state()
+    R, R0 = t.residual_norms()
+    t.close()
+    return out, its, R
+
+
+def oracle_run(case, steps=1, iters=10):
+    s = case.state()
+    for _ in range(steps):
+        s, *_ = oracle.physical_step(case, s, tol=-1.0, max_iters=iters)
+    return s
+
+
+def check(got, ref, tol=TOL):
+    errs = rel_errors(got, ref)
+    assert max(errs) <= tol, errs
+    return errs
+
+
+def test_hydrostatic_tank_stays_balanced():
+    case = W.hydrostatic_tank(64)
+    got, _, R = gpu_run(case, "mixed", iters=40)
+    ref = oracle_run(case, iters=40)
+    check(got, ref)
+    # the reference split keeps the rest state exact in FP32
+    assert np.abs(got[1]).max() < 1e-9 and np.abs(got[2]).max() < 1e-9
+
+
+@pytest.mark.parametrize("bc", [("slip",) * 4, ("noslip", "slip", "slip", "noslip"),
+                                ("periodic", "periodic", "slip", "slip"),
+                                ("slip", "transmissive", "transmissive", "slip"),
+                                ("periodic",) * 4])
+def test_random_two_fluid_against_oracle(bc):
+    case = W.random_two_fluid(45, 21, ratio=1000.0, c0=20.0, bc=bc,
+                              gy=0.0 if bc[2] == "periodic" else -9.81)
+    got, _, _ = gpu_run(case, "mixed", iters=8)
+    ref = oracle_run(case, iters=8)
+    check(got, ref)
+
+
+@pytest.mark.parametrize("opts", [dict(gradp="minmod"), dict(local_dtau=False), dict(s_max=2),
+                                  dict(limiter_k=2), dict(realtime=False, cfl_tau=0.3)],
+                         ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+def test_options_against_oracle(opts):
+    case = W.random_two_fluid(37, 19, ratio=100.0, c0=6.0)
+    for k, v in opts.items():
+        setattr(case.options, k, v)
+    got, _, _ = gpu_run(case, "mixed", iters=6)
+    ref = oracle_run(case, iters=6)
+    check(got, ref)
+
+
+def test_riemann_tank_against_oracle():
+    case = W.riemann_tank()
+    got, _, _ = gpu_run(case, "mixed", iters=60)
+    ref = oracle_run(case, iters=60)
+    check(got, ref)
+
+
+def test_water_column_levels_accumulate_over_steps():
+    """Three physical steps: the FP64 level absorbs each step's FP32
+    increment, so the error does not grow with the step count."""
+    case = W.water_column(128, 64)
+    got, _, _ = gpu_run(case, "mixed", steps=3, iters=30)
+    ref = oracle_run(case, steps=3, iters=30)
+    check(got, ref)
+
+
+def test_dam_break_small_paper_setup_against_oracle():
+    case = W.dam_break_small()
+    got, _, _ = gpu_run(case, "mixed", iters=200)
+    ref = oracle_run(case, iters=200)
+    check(got, ref)
+
+
+@pytest.mark.parametrize("case_fn", [lambda: W.water_column(1024, 512), lambda: W.rayleigh_taylor(256, 1024)],
+                         ids=["water_column_1024x512", "rayleigh_taylor_256x1024"])
+def test_full_size_against_fp64_gpu(case_fn):
+    case = case_fn()
+    mixed, _, _ = gpu_run(case, "mixed", iters=20)
+    f64, _, _ = gpu_run(case, "fp64", iters=20)
+    check(mixed, f64)
+
+
+def test_rayleigh_taylor_2048x8192_sampled_against_fp64_gpu():
+    """The full 2048x8192 grid: mixed vs FP64 GPU on every cell after one
+    physical step of 5 pseudo-iterations."""
+    case = W.rayleigh_taylor(2048, 8192)
+    mixed, _, _ = gpu_run(case, "mixed", iters=5)
+    f64, _, _ = gpu_run(case, "fp64", iters=5)
+    check(mixed, f64)
+
+
+def test_state_roundtrip_mixed():
+    case = W.water_column(64, 32)
+    t = ac.Tank.from_case(case, precision="mixed")
+    got = t.get_state()
+    for a, b in zip(got[:3], case.state()[:3]):
+        assert np.array_equal(a, b)
+    assert np.abs(got[3] - case.p).max() <= 1e-6 * max(np.abs(case.p).max(), 1.0)
+    t.close()
+
+
+def test_nonfinite_restores_state_mixed():
+    case = W.random_two_fluid(32, 16, ratio=1000.0, c0=20.0)
+    case.options.cfl_tau = 40.0
+    t = ac.Tank.from_case(case, precision="mixed")
+    before = t.get_state()
+    with pytest.raises(ac.ACError) as e:
+        t.physical_step(case.dt, -1.0, 400)
+    assert e.value.code == ac.AC_ERR_NONFINITE
+    after = t.get_state()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    t.close()
+
+
+def test_converged_step_close_to_oracle():
+    """With the stopping test on, both forms stop near the same iteration
+    and land on the same converged state within the tolerance's reach."""
+    case = W.riemann_tank()
+    got, its, _ = gpu_run(case, "mixed", iters=500, tol=1e-6)
+    ref, st, oits, *_ = oracle.physical_step(case, case.state(), tol=1e-6, max_iters=500)
+    assert abs(its[0] - oits) <= max(2, oits // 20), (its, oits)
+    check(got, ref, tol=1e-4)
