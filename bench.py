@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="hydrostatic_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048x8192 mixed-form leg")
     return ap.parse_args()
 
 
@@ -171,19 +172,59 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(tank, case, steps, stream, flush, barrier, tol=None, max_iters=None):
+    """K physical steps, each bracketed by CUDA events on the library's
+    stream, L2 flushed before each (outside the events)."""
+    import torch
+    tol = case.tol if tol is None else tol
+    max_iters = case.max_iters if max_iters is None else max_iters
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters = []
+    launches0 = tank.kernel_launches()
+    barrier()
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        rc, its = tank.physical_step(case.dt, tol, max_iters)
+        evs[k][1].record(stream)
+        iters.append(its)
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    return ms, iters, tank.kernel_launches() - launches0
+
+
+def stage_launch_ms(tank, case, steps, tol=None, max_iters=None):
+    """Average event-timed duration of one stage-sweep launch, measured on
+    the same physical steps (profiling mode brackets every launch)."""
+    tank.set_profiling(True)
+    for _ in range(steps):
+        tank.physical_step(case.dt, case.tol if tol is None else tol,
+                           case.max_iters if max_iters is None else max_iters)
+    ms, n = tank.stage_kernel_time()
+    tank.set_profiling(False)
+    return ms / max(n, 1)
+
+
+def field_errors(a, b):
+    """Relative L-inf error per field; both momentum components against the
+    largest momentum magnitude (floored at max(rho) * 1e-3 m/s)."""
+    import numpy as np
+    rho = float(np.abs(b[0]).max())
+    mom = max(float(np.sqrt(b[1] ** 2 + b[2] ** 2).max()), 1e-3 * rho)
+    sc = [rho, mom, mom, max(float(np.abs(b[3]).max()), 1e-12)]
+    return {k: float(np.abs(x - y).max() / s) for k, x, y, s in zip(("rho", "rhou", "rhov", "p"), a, b, sc)}
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
-    from paper_2108_08769_gb300 import ac
+    from paper_2108_08769_gb300 import ac, workloads as W
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case, desc = make_case(args.workload)
     stream = torch.cuda.current_stream(dev)
-    tank = ac.Tank.from_case(case)
-    tank.set_stream(stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    dt, tol, max_iters = case.dt, case.tol, case.max_iters
 
     def barrier():
         if ws > 1:
@@ -191,37 +232,24 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # ---- primary: the FP64 tank, state resident in HBM ----
+    tank = ac.Tank.from_case(case)
+    tank.set_stream(stream.cuda_stream)
     for _ in range(args.warmup):
-        tank.physical_step(dt, tol, max_iters)
-
-    # ---- timed region: state resident in HBM ----
+        tank.physical_step(case.dt, case.tol, case.max_iters)
     tank.set_state(*case.state())
-    launches0 = tank.kernel_launches()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    iters = []
-    barrier()
     with Clocks(local) as clk:
         wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            rc, its = tank.physical_step(dt, tol, max_iters)
-            evs[k][1].record(stream)
-            iters.append(its)
-        barrier()
+        dev_ms, iters, launches = timed_steps(tank, case, args.steps, stream, flush, barrier)
         wall = time.perf_counter() - wall0
-    torch.cuda.synchronize(dev)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    launches = tank.kernel_launches() - launches0
+    f64_state = tank.get_state()
     t_max = dev_ms
     if ws > 1:
         import torch.distributed as dist
         tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    cell_iters = case.cells * sum(iters)
-    value = ws * cell_iters / (t_max * 1e-3)
+    value = ws * case.cells * sum(iters) / (t_max * 1e-3)
 
     # ---- e2e: host buffers through the public API ----
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.state()]
@@ -233,7 +261,7 @@ def run_ours(args, ws, rank, local):
     e0 = time.perf_counter()
     for k in range(args.steps):
         tank.set_state(*host_in)
-        rc, its = tank.physical_step(dt, tol, max_iters)
+        rc, its = tank.physical_step(case.dt, case.tol, case.max_iters)
         tank.get_state_into(*host_out)
         e_iters.append(its)
     barrier()
@@ -241,25 +269,84 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": ws * case.cells * sum(e_iters) / e_wall, "unit": UNIT,
            "h2d_bytes_per_step": 4 * case.cells * 8, "d2h_bytes_per_step": 4 * case.cells * 8}
 
-    # ---- roofline: event-timed stage sweeps of the same steps ----
+    # ---- roofline of the FP64 stage sweep ----
     tank.set_state(*case.state())
-    tank.set_profiling(True)
-    for k in range(min(args.steps, 3)):
-        tank.physical_step(dt, tol, max_iters)
-    stage_ms, stage_n = tank.stage_kernel_time()
-    tank.set_profiling(False)
-    per_launch_s = stage_ms * 1e-3 / max(stage_n, 1)
-    flops = FP64_FLOPS_PER_CELL_STAGE * case.cells
-    achieved = flops / per_launch_s / 1e12
+    per_launch_s = stage_launch_ms(tank, case, min(args.steps, 3)) * 1e-3
+    achieved = FP64_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FP64_TRAFFIC_PER_CELL_STAGE * case.cells,
                 "kernel": "stage_kernel<double,32,8>", "launch_ms": per_launch_s * 1e3,
                 "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
-                "hbm_frac_of_measured": (BYTES_PER_CELL_ITER_F64 / 3.0) * case.cells / per_launch_s / 1e9
-                / measured_hbm_gbs(),
-                "peak_source": "nominal FP64 rate of the part (profiling recipe), not measured"}
+                "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM), not measured",
+                "hbm_frac_of_measured": BYTES_PER_CELL_ITER_F64 / 3.0 * case.cells / per_launch_s / 1e9
+                / measured_hbm_gbs()}
     tank.close()
+
+    # ---- the same tank in the mixed form ----
+    # Same work as the FP64 leg: the pseudo-iteration count is fixed at the
+    # FP64 leg's (with the stopping test on, the mixed form stops after one
+    # iteration here: the reference split makes the rest state exact, R = 0).
+    n_fixed = int(round(statistics.mean(iters)))
+    mt = ac.Tank.from_case(case, precision="mixed")
+    mt.set_stream(stream.cuda_stream)
+    for _ in range(args.warmup):
+        mt.physical_step(case.dt, -1.0, n_fixed)
+    mt.set_state(*case.state())
+    m_ms, m_iters, m_launches = timed_steps(mt, case, args.steps, stream, flush, barrier, tol=-1.0,
+                                            max_iters=n_fixed)
+    m_state = mt.get_state()
+    mt.set_state(*case.state())
+    m_launch_ms = stage_launch_ms(mt, case, min(args.steps, 3), tol=-1.0, max_iters=n_fixed)
+    mt.set_state(*case.state())
+    rc, conv_iters = mt.physical_step(case.dt, case.tol, case.max_iters)
+    mt.close()
+    m_value = ws * case.cells * sum(m_iters) / (m_ms * 1e-3)
+    mixed = {"value": m_value, "unit": UNIT, "speedup_vs_fp64": m_value / value,
+             "ms_per_step": m_ms / args.steps, "pseudo_iters_per_step": n_fixed, "launch_ms": m_launch_ms,
+             "gpu_launches": m_launches, "error_vs_fp64": field_errors(m_state, f64_state),
+             "error_note": f"after {args.steps} physical steps of {n_fixed} pseudo-iterations from the same state, "
+                           "relative L-inf per field (momentum against the momentum magnitude)",
+             "iters_with_stopping_test": conv_iters}
+
+    # ---- large grid in the mixed form: HBM-sized workload ----
+    large = None
+    if not args.no_large:
+        lc = W.rayleigh_taylor(2048, 8192)
+        lt = ac.Tank.from_case(lc, precision="mixed")
+        lt.set_stream(stream.cuda_stream)
+        lt.physical_step(lc.dt, lc.tol, lc.max_iters)
+        lt.set_state(*lc.state())
+        lk = min(args.steps, 3)
+        l_ms, l_iters, l_launches = timed_steps(lt, lc, lk, stream, flush, barrier)
+        lt.set_state(*lc.state())
+        l_launch_s = stage_launch_ms(lt, lc, 1, tol=-1.0, max_iters=30) * 1e-3
+        # error against the FP64 GPU path after one step of 20 iterations
+        lt.set_state(*lc.state())
+        lt.physical_step(lc.dt, -1.0, 20)
+        lm_state = lt.get_state()
+        lt.close()
+        ft = ac.Tank.from_case(lc)
+        ft.physical_step(lc.dt, -1.0, 20)
+        lf_state = ft.get_state()
+        ft.close()
+        l_value = ws * lc.cells * sum(l_iters) / (l_ms * 1e-3)
+        gbs = MIXED_BYTES_PER_CELL_ITER / 3.0 * lc.cells / l_launch_s / 1e9
+        ops = MIXED_FP32_OPS_PER_CELL_STAGE * lc.cells / l_launch_s / 1e12
+        large = {"workload": "Rayleigh-Taylor tank 2048x8192 (1x4 m, rho 3 over 1, cosine interface, slip walls, "
+                             "c0=10 m/s, dt=5e-4 s, 1e-8 drop or 500 pseudo-iterations), mixed form",
+                 "value": l_value, "unit": UNIT, "steps": lk, "ms_per_step": l_ms / lk,
+                 "pseudo_iters_per_step": statistics.mean(l_iters), "gpu_launches": l_launches,
+                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": measured_hbm_gbs(), "unit": "GB/s",
+                              "frac": gbs / measured_hbm_gbs(), "kernel": "stage_kernel_mixed",
+                              "launch_ms": l_launch_s * 1e3,
+                              "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
+                              "traffic": MIXED_TRAFFIC_PER_CELL_STAGE * lc.cells,
+                              "alu_frac": ops / FP32_PEAK_TOPS,
+                              "alu_note": f"{MIXED_FP32_OPS_PER_CELL_STAGE:.0f} FP32 arithmetic instructions per "
+                                          f"cell-stage (ncu) against {FP32_PEAK_TOPS:.1f} T/s (128 lanes/SM x 152 SMs "
+                                          "x 2.07 GHz)"},
+                 "error_vs_fp64_gpu": field_errors(lm_state, lf_state)}
 
     if rank != 0:
         return
@@ -267,11 +354,14 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "cells": case.cells, "rk_stages": case.options.s_max,
-                       "pseudo_iters_per_step": statistics.mean(iters), "tol": tol, "max_iters": max_iters,
+                       "pseudo_iters_per_step": statistics.mean(iters), "tol": case.tol,
+                       "max_iters": case.max_iters,
                        "l2": "flushed between timed steps (256 MiB write outside the event pairs)",
                        "parallelism": f"replicas x{ws}"},
             "wall_s": wall, "gpu_launches": launches, "roofline": roofline, "e2e": e2e,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "mixed": mixed}
+    if large is not None:
+        line["mixed_large"] = large
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline_sample(case)
     print(json.dumps(line), flush=True)
@@ -284,6 +374,14 @@ FP64_FLOPS_PER_CELL_STAGE = 927.0
 FP64_TRAFFIC_PER_CELL_STAGE = 115.3
 # algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3)
 BYTES_PER_CELL_ITER_F64 = 328.0
+# mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
+# (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
+MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
+# measured (ncu, stage_kernel_mixed, 2048x2048): DRAM bytes and FP32
+# arithmetic thread-instructions per cell of one stage launch
+MIXED_TRAFFIC_PER_CELL_STAGE = 64.1
+MIXED_FP32_OPS_PER_CELL_STAGE = 506.0
+FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
 def measured_hbm_gbs():

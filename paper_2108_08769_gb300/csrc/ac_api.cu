@@ -78,8 +78,6 @@ struct ac_ctx {
     double *partials;
     Ctl *ctl;
     Ctl *hctl;            // pinned host mirror
-    dim3 grid_dim;
-    int nblocks;
     cudaStream_t stream;  // user stream (0 = default)
     cudaStream_t cap;     // private stream used for capture
     cudaGraph_t graph;
@@ -98,7 +96,10 @@ namespace {
 int grid_stride_blocks(size_t N) { return (int)std::min<size_t>((N + 255) / 256, kGridStrideBlocks); }
 
 struct Backend {
+    dim3 grid;        // stage-sweep grid of the chosen tile shape
+    int nblocks = 0;  // its CTA count (residual partial sums)
     virtual ~Backend() {}
+    virtual int tune(ac_ctx *c, cudaStream_t s) { (void)c; (void)s; return AC_OK; }
     virtual int alloc(ac_ctx *c) = 0;
     virtual void release() = 0;
     virtual int set_state(ac_ctx *c, const double *const f[4]) = 0;
@@ -141,6 +142,8 @@ struct F64Backend : Backend {
         return a;
     }
     int alloc(ac_ctx *c) override {
+        grid = dim3((c->grid.nx + kTX - 1) / kTX, (c->grid.ny + kTY - 1) / kTY);
+        nblocks = grid.x * grid.y;
         const size_t bytes = c->N * sizeof(double);
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) CK(cudaMalloc(&buf[b][f], bytes));
@@ -194,7 +197,7 @@ struct F64Backend : Backend {
         return AC_OK;
     }
     int stage(ac_ctx *c, cudaStream_t s, int st) override {
-        stage_kernel<double, kTX, kTY><<<c->grid_dim, kTX * kTY, smem(), s>>>(args(c, st));
+        stage_kernel<double, kTX, kTY><<<grid, kTX * kTY, smem(), s>>>(args(c, st));
         CK(cudaGetLastError());
         return AC_OK;
     }
@@ -208,7 +211,35 @@ struct F64Backend : Backend {
 
 // ------------------------------------------------------------------ mixed
 
+// Tile shapes of the mixed sweep: TX x TY cells per CTA of NT threads.
+struct MixedVariant {
+    int tx, ty, nt;
+};
+constexpr MixedVariant kMixedVariants[] = {
+    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256}, {64, 8, 512}, {64, 16, 512}, {16, 16, 256},
+};
+constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
+
+template <int TX, int TY, int NT>
+int launch_mixed(const MixedArgs &a, dim3 g, cudaStream_t s) {
+    stage_kernel_mixed<TX, TY, NT><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? AC_OK : AC_ERR_CUDA;
+}
+
+template <int TX, int TY, int NT>
+cudaError_t allow_mixed_smem() {
+    return cudaFuncSetAttribute(stage_kernel_mixed<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(MixedSmem<TX, TY>));
+}
+
+// chosen tile shape per grid size, shared by the contexts of this process
+struct TuneKey {
+    int nx, ny;
+};
+std::vector<std::pair<TuneKey, int>> g_tuned;
+
 struct MixedBackend : Backend {
+    int variant = -1;
     float *d[3][4] = {};
     float *qn32[3] = {};
     float *rho_ref = nullptr, *dref = nullptr, *lev_p = nullptr;
@@ -216,7 +247,61 @@ struct MixedBackend : Backend {
     std::vector<double> p_ref;   // FP64 reference pressure (host copy)
     bool use_ref = false;
 
-    static size_t smem() { return sizeof(MixedSmem<kTX, kTY>); }
+    void set_variant(const ac_ctx *c, int v) {
+        variant = v;
+        const MixedVariant &m = kMixedVariants[v];
+        grid = dim3((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
+        nblocks = grid.x * grid.y;
+    }
+
+    int launch(const ac_ctx *c, cudaStream_t s, int st, int v) const {
+        const MixedArgs a = args(c, st);
+        const MixedVariant &m = kMixedVariants[v];
+        const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
+        switch (v) {
+            case 0: return launch_mixed<32, 8, 256>(a, g, s);
+            case 1: return launch_mixed<32, 16, 256>(a, g, s);
+            case 2: return launch_mixed<32, 16, 512>(a, g, s);
+            case 3: return launch_mixed<64, 8, 256>(a, g, s);
+            case 4: return launch_mixed<64, 8, 512>(a, g, s);
+            case 5: return launch_mixed<64, 16, 512>(a, g, s);
+            default: return launch_mixed<16, 16, 256>(a, g, s);
+        }
+    }
+
+    // Autotuner: time stage 1 of every tile shape on this grid (it writes
+    // only scratch: a stage-1 output buffer and the residual partials, both
+    // rewritten by the real stage 1) and keep the fastest.
+    int tune(ac_ctx *c, cudaStream_t s) override {
+        if (variant >= 0) return AC_OK;
+        const char *env = getenv("AC_TILE");
+        if (env) {
+            int v = atoi(env);
+            if (v >= 0 && v < kNumMixedVariants) { set_variant(c, v); return AC_OK; }
+        }
+        for (auto &kv : g_tuned)
+            if (kv.first.nx == c->grid.nx && kv.first.ny == c->grid.ny) { set_variant(c, kv.second); return AC_OK; }
+        int best = 0;
+        float best_ms = 1e30f;
+        const int reps = c->N > (1u << 22) ? 3 : 8;
+        for (int v = 0; v < kNumMixedVariants; ++v) {
+            int rc;
+            for (int w = 0; w < 2; ++w)
+                if ((rc = launch(c, s, 1, v)) != AC_OK) return fail(rc, "tile variant %d failed to launch", v);
+            CK(cudaEventRecord(c->ev[0], s));
+            for (int r = 0; r < reps; ++r)
+                if ((rc = launch(c, s, 1, v)) != AC_OK) return fail(rc, "tile variant %d failed to launch", v);
+            CK(cudaEventRecord(c->ev[1], s));
+            CK(cudaEventSynchronize(c->ev[1]));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            c->launches += 2 + reps;
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        set_variant(c, best);
+        g_tuned.push_back({TuneKey{c->grid.nx, c->grid.ny}, best});
+        return AC_OK;
+    }
 
     MixedArgs args(const ac_ctx *c, int stage) const {
         MixedArgs a;
@@ -250,8 +335,15 @@ struct MixedBackend : Backend {
         CK(cudaMalloc(&rho_ref, fb));
         CK(cudaMalloc(&dref, fb));
         CK(cudaMalloc(&lev_p, fb));
-        CK(cudaFuncSetAttribute(stage_kernel_mixed<kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem()));
+        CK((allow_mixed_smem<32, 8, 256>()));
+        CK((allow_mixed_smem<32, 16, 256>()));
+        CK((allow_mixed_smem<32, 16, 512>()));
+        CK((allow_mixed_smem<64, 8, 256>()));
+        CK((allow_mixed_smem<64, 8, 512>()));
+        CK((allow_mixed_smem<64, 16, 512>()));
+        CK((allow_mixed_smem<16, 16, 256>()));
+        set_variant(c, 0);
+        variant = -1;   // tuned at the first physical step
         // the reference applies when both y sides are walls and the pressure
         // gradient comes from Eq. new_gradp
         use_ref = is_wall_bc(c->bc.ylo) && is_wall_bc(c->bc.yhi) && c->opt.gradp == AC_GRADP_NEW;
@@ -364,8 +456,8 @@ struct MixedBackend : Backend {
         return AC_OK;
     }
     int stage(ac_ctx *c, cudaStream_t s, int st) override {
-        stage_kernel_mixed<kTX, kTY><<<c->grid_dim, kTX * kTY, smem(), s>>>(args(c, st));
-        CK(cudaGetLastError());
+        const int rc = launch(c, s, st, variant < 0 ? 0 : variant);
+        if (rc != AC_OK) return fail(rc, "stage sweep launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return AC_OK;
     }
     int restore(ac_ctx *c, cudaStream_t s) override {
@@ -388,7 +480,7 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
     end_iteration_kernel<kEndThreads><<<1, kEndThreads, 0, s>>>(
-        c->ctl, c->partials, c->nblocks, 1.0 / double(c->N), c->opt.rk_stages, cond, use_cond);
+        c->ctl, c->partials, c->be->nblocks, 1.0 / double(c->N), c->opt.rk_stages, cond, use_cond);
     CK(cudaGetLastError());
     return AC_OK;
 }
@@ -505,8 +597,6 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     c->N = (size_t)grid->nx * grid->ny;
     c->dx = grid->lx / grid->nx;
     c->dy = grid->ly / grid->ny;
-    c->grid_dim = dim3((grid->nx + kTX - 1) / kTX, (grid->ny + kTY - 1) / kTY);
-    c->nblocks = c->grid_dim.x * c->grid_dim.y;
     if (o.precision == AC_PREC_MIXED) c->be = new MixedBackend();
     else c->be = new F64Backend();
     auto bail = [&](int code) { ac_destroy(c); return code; };
@@ -520,7 +610,9 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     CKC(cudaGetDevice(&c->device));
     int rc = c->be->alloc(c);
     if (rc != AC_OK) return bail(rc);
-    CKC(cudaMalloc(&c->partials, (size_t)c->nblocks * 4 * sizeof(double)));
+    // partial sums for the smallest tile (16 x 8 cells) any backend uses
+    const size_t max_blocks = (size_t)((grid->nx + 15) / 16) * ((grid->ny + 7) / 8);
+    CKC(cudaMalloc(&c->partials, max_blocks * 4 * sizeof(double)));
     CKC(cudaMalloc(&c->ctl, sizeof(Ctl)));
     CKC(cudaMallocHost(&c->hctl, sizeof(Ctl)));
     CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
@@ -602,6 +694,7 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
     int rc;
     if ((rc = c->be->begin(c, s, dt, tol, max_iters)) != AC_OK) return rc;
     c->launches += 1;
+    if ((rc = c->be->tune(c, s)) != AC_OK) return rc;
     if (c->profiling) {
         // one iteration at a time, stage sweeps bracketed by events
         while (true) {

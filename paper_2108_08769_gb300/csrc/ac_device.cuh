@@ -78,11 +78,13 @@ __device__ __forceinline__ T limiter(T a, T b, T k) {
     return s * fmax(T(0), m);
 }
 
-// minmod fast form (k = 1): the k-limiter reduces to s * max(0, min(|b|, s a)).
+// Half of the k = 1 limiter (minmod), branch-free:
+//   G(a, b)/2 = (sgn a + sgn b)/4 * min(|a|, |b|),
+// which is 0 for opposite signs or a zero argument and +-min(|a|,|b|)/2
+// otherwise -- the same value, bit for bit (the factors are powers of two).
 template <typename T>
-__device__ __forceinline__ T minmod(T a, T b) {
-    T s = (b > T(0)) ? T(1) : ((b < T(0)) ? T(-1) : T(0));
-    return s * fmax(T(0), fmin(fabs(b), s * a));
+__device__ __forceinline__ T half_minmod(T a, T b) {
+    return (copysign(T(0.25), a) + copysign(T(0.25), b)) * fmin(fabs(a), fabs(b));
 }
 
 // ---------------------------------------------------------------------------
@@ -109,7 +111,10 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     // Gauss-Legendre points mapped to [0,1]: (xi + 1)/2, weights w/2
     const T tq[3] = {T(0.11270166537925831148), T(0.5), T(0.88729833462074168852)};
     const T wq[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
-    T D0 = T(0), D1 = T(0), D2 = T(0), D3 = T(0);
+    // D = sum_j w_j |A_j| dQ, accumulated as
+    //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
+    //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
+    T Sau = T(0), Se = T(0), Sue = T(0), Sve = T(0), Sg = T(0), Sh = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const T r = rL + tq[j] * dr;
@@ -120,25 +125,29 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T c2 = u * u + four_beta * ir;
         T c, ic;
         Ar<T>::sqrt_rsqrt(c2, c, ic);
-        const T l4 = T(0.5) * (u + c), l5 = T(0.5) * (u - c);
+        const T hu = T(0.5) * u, hc = T(0.5) * c;
+        const T l4 = hu + hc, l5 = hu - hc;
         const T au = fabs(u);
         const T a = (dm - u * dr) * inv_beta;
         const T k = r * ic;
         const T g4 = (l4 - au) * k * (l4 * a + dq);
         const T g5 = (l5 + au) * k * (l5 * a + dq);
-        const T e = g4 * l4 + g5 * l5;
         const T w = wq[j];
-        D0 += w * (au * dr + e);
-        D1 += w * (au * dm + u * e + beta * ir * (g4 + g5));
-        D2 += w * (au * dn + v * e);
-        D3 += w * (au * dq - (g4 * l5 + g5 * l4) * ir);
+        const T we = w * (g4 * l4 + g5 * l5);
+        const T wir = w * ir;
+        Sau += w * au;
+        Se += we;
+        Sue += u * we;
+        Sve += v * we;
+        Sg += wir * (g4 + g5);
+        Sh += wir * (g4 * l5 + g5 * l4);
     }
     // central part 1/2 (F(Q_L) + F(Q_R)); dissipation 1/2 * D (D already
     // carries the 1/2 of the [0,1] quadrature)
-    F[0] = T(0.5) * (mL + mR) - T(0.5) * D0;
-    F[1] = T(0.5) * (mL * uL + pL + mR * uR + pR) - T(0.5) * D1;
-    F[2] = T(0.5) * (mL * vL + mR * vR) - T(0.5) * D2;
-    F[3] = T(0.5) * (uL + uR) - T(0.5) * D3;
+    F[0] = T(0.5) * ((mL + mR) - (dr * Sau + Se));
+    F[1] = T(0.5) * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
+    F[2] = T(0.5) * ((mL * vL + mR * vR) - (dn * Sau + Sve));
+    F[3] = T(0.5) * ((uL + uR) - (dq * Sau - Sh));
 }
 
 }  // namespace acgb

@@ -154,12 +154,12 @@ stage_kernel(const SweepArgs<T> a) {
         const T *R = sm.w[0], *U = sm.w[1], *V = sm.w[2], *P = sm.w[3];
         T hrx, hry, hux, huy, hvx, hvy;
         if (a.limiter_k == 1) {
-            hrx = T(0.5) * minmod(R[e] - R[c], R[c] - R[wv]);
-            hry = T(0.5) * minmod(R[nn] - R[c], R[c] - R[ss]);
-            hux = T(0.5) * minmod(U[e] - U[c], U[c] - U[wv]);
-            huy = T(0.5) * minmod(U[nn] - U[c], U[c] - U[ss]);
-            hvx = T(0.5) * minmod(V[e] - V[c], V[c] - V[wv]);
-            hvy = T(0.5) * minmod(V[nn] - V[c], V[c] - V[ss]);
+            hrx = half_minmod(R[e] - R[c], R[c] - R[wv]);
+            hry = half_minmod(R[nn] - R[c], R[c] - R[ss]);
+            hux = half_minmod(U[e] - U[c], U[c] - U[wv]);
+            huy = half_minmod(U[nn] - U[c], U[c] - U[ss]);
+            hvx = half_minmod(V[e] - V[c], V[c] - V[wv]);
+            hvy = half_minmod(V[nn] - V[c], V[c] - V[ss]);
         } else {
             hrx = T(0.5) * limiter(R[e] - R[c], R[c] - R[wv], klim);
             hry = T(0.5) * limiter(R[nn] - R[c], R[c] - R[ss], klim);

@@ -69,16 +69,36 @@ struct MixedSmem {
     float fx[4][NXF];
     float fy[4][NYF];
     float dxf[NXF];            // reference jump on each x-face
-    double red[4][TX * TY / 32];
+    double red[4][32];
 };
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+// Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell into W (interior or folded).
+struct CellLoad {
+    const float *__restrict__ qn0, *__restrict__ qn1, *__restrict__ qn2;
+    const float *__restrict__ d0, *__restrict__ d1, *__restrict__ d2, *__restrict__ d3;
+    __device__ __forceinline__ void operator()(int s, bool fx, bool fy, float &r, float &u, float &v,
+                                               float &p) const {
+        r = __ldg(qn0 + s) + d0[s];
+        float m = __ldg(qn1 + s) + d1[s];
+        float n = __ldg(qn2 + s) + d2[s];
+        m = fx ? -m : m;
+        n = fy ? -n : n;
+        const float ir = Ar<float>::rcp(r);
+        u = m * ir;
+        v = n * ir;
+        p = d3[s];
+    }
+};
+
+// TX x TY cells per CTA of NT threads (NT divides TX*TY; several cells per
+// thread in the update when NT < TX*TY).
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
 stage_kernel_mixed(const MixedArgs a) {
     using S = MixedSmem<TX, TY>;
+    static_assert((TX * TY) % NT == 0 && NT % 32 == 0, "tile/thread shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
-    constexpr int NT = TX * TY;
     constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
 
     const Ctl *ctl = a.ctl;
@@ -94,43 +114,56 @@ stage_kernel_mixed(const MixedArgs a) {
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    // halo entirely inside the domain: no ghost folding for this tile
+    const bool interior = (x0 >= 2) && (x0 + TX + 2 <= nx) && (y0 >= 2) && (y0 + TY + 2 <= ny);
+    const CellLoad ld{a.qn32[0], a.qn32[1], a.qn32[2], din[0], din[1], din[2], din[3]};
 
     // ---- 1. stage Q^{s-1} = Q^n + dQ^{s-1} (+ halo) as W = (rho, u, v, p') ----
-    for (int k = tid; k < RW * RH; k += NT) {
-        const int gi = x0 + (k % RW) - 2, gj = y0 + (k / RW) - 2;
-        int nfx, tfx, nfy, tfy;
-        const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
-        const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
-        const size_t s = (size_t)sj * nx + si;
-        const float r = a.qn32[0][s] + din[0][s];
-        float m = a.qn32[1][s] + din[1][s];
-        float n = a.qn32[2][s] + din[2][s];
-        if ((nfx + tfy) & 1) m = -m;
-        if ((nfy + tfx) & 1) n = -n;
-        const float ir = Ar<float>::rcp(r);
-        sm.w[0][k] = r;
-        sm.w[1][k] = m * ir;
-        sm.w[2][k] = n * ir;
-        sm.w[3][k] = din[3][s];
+    if (interior) {
+        const int base = (y0 - 2) * nx + (x0 - 2);
+        for (int k = tid; k < RW * RH; k += NT) {
+            const int rr = k / RW, cc = k - rr * RW;
+            float r, u, v, p;
+            ld(base + rr * nx + cc, false, false, r, u, v, p);
+            sm.w[0][k] = r; sm.w[1][k] = u; sm.w[2][k] = v; sm.w[3][k] = p;
+        }
+    } else {
+        for (int k = tid; k < RW * RH; k += NT) {
+            const int rr = k / RW, cc = k - rr * RW;
+            int nfx, tfx, nfy, tfy;
+            const int si = fold_axis(x0 + cc - 2, nx, a.bc[0], a.bc[1], nfx, tfx);
+            const int sj = fold_axis(y0 + rr - 2, ny, a.bc[2], a.bc[3], nfy, tfy);
+            float r, u, v, p;
+            ld(sj * nx + si, (nfx + tfy) & 1, (nfy + tfx) & 1, r, u, v, p);
+            sm.w[0][k] = r; sm.w[1][k] = u; sm.w[2][k] = v; sm.w[3][k] = p;
+        }
     }
     const bool new_gradp = (a.gradp == kGradNew);
     const bool need_rt = new_gradp && a.realtime;
     if (new_gradp) {
+        const float *__restrict__ e1 = d0[1];
+        const float *__restrict__ e2 = d0[2];
+        const float *__restrict__ rref = a.rho_ref;
         for (int k = tid; k < GW * GH; k += NT) {
-            const int gi = x0 + (k % GW) - 1, gj = y0 + (k / GW) - 1;
-            int nfx, tfx, nfy, tfy;
-            const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
-            const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
-            const size_t s = (size_t)sj * nx + si;
-            if (need_rt) {
-                float rx = d0[1][s] * inv_dt;   // (Q^{m} - Q^n)/dt of rho u
-                float ry = d0[2][s] * inv_dt;
-                if ((nfx + tfy) & 1) rx = -rx;
-                if ((nfy + tfx) & 1) ry = -ry;
-                sm.rt[0][k] = rx;
-                sm.rt[1][k] = ry;
+            const int rr = k / GW, cc = k - rr * GW;
+            int s, fx = 0, fy = 0;
+            if (interior) {
+                s = (y0 + rr - 1) * nx + (x0 + cc - 1);
+            } else {
+                int nfx, tfx, nfy, tfy;
+                const int si = fold_axis(x0 + cc - 1, nx, a.bc[0], a.bc[1], nfx, tfx);
+                const int sj = fold_axis(y0 + rr - 1, ny, a.bc[2], a.bc[3], nfy, tfy);
+                s = sj * nx + si;
+                fx = (nfx + tfy) & 1;
+                fy = (nfy + tfx) & 1;
             }
-            sm.rr[k] = a.rho_ref[s];
+            if (need_rt) {
+                const float rx = e1[s] * inv_dt;   // (Q^{m} - Q^n)/dt of rho u
+                const float ry = e2[s] * inv_dt;
+                sm.rt[0][k] = fx ? -rx : rx;
+                sm.rt[1][k] = fy ? -ry : ry;
+            }
+            sm.rr[k] = __ldg(rref + s);
         }
     }
     __syncthreads();
@@ -139,18 +172,18 @@ stage_kernel_mixed(const MixedArgs a) {
     const float klim = float(a.limiter_k);
     const float kp = (a.gradp == kGradSuperbee) ? 2.0f : 1.0f;
     for (int k = tid; k < GW * GH; k += NT) {
-        const int li = k % GW, lj = k / GW;
+        const int lj = k / GW, li = k - lj * GW;
         const int c = (lj + 1) * RW + (li + 1);
         const int e = c + 1, wv = c - 1, nn = c + RW, ss = c - RW;
         const float *R = sm.w[0], *U = sm.w[1], *V = sm.w[2], *P = sm.w[3];
         float hrx, hry, hux, huy, hvx, hvy;
         if (a.limiter_k == 1) {
-            hrx = 0.5f * minmod(R[e] - R[c], R[c] - R[wv]);
-            hry = 0.5f * minmod(R[nn] - R[c], R[c] - R[ss]);
-            hux = 0.5f * minmod(U[e] - U[c], U[c] - U[wv]);
-            huy = 0.5f * minmod(U[nn] - U[c], U[c] - U[ss]);
-            hvx = 0.5f * minmod(V[e] - V[c], V[c] - V[wv]);
-            hvy = 0.5f * minmod(V[nn] - V[c], V[c] - V[ss]);
+            hrx = half_minmod(R[e] - R[c], R[c] - R[wv]);
+            hry = half_minmod(R[nn] - R[c], R[c] - R[ss]);
+            hux = half_minmod(U[e] - U[c], U[c] - U[wv]);
+            huy = half_minmod(U[nn] - U[c], U[c] - U[ss]);
+            hvx = half_minmod(V[e] - V[c], V[c] - V[wv]);
+            hvy = half_minmod(V[nn] - V[c], V[c] - V[ss]);
         } else {
             hrx = 0.5f * limiter(R[e] - R[c], R[c] - R[wv], klim);
             hry = 0.5f * limiter(R[nn] - R[c], R[c] - R[ss], klim);
@@ -161,8 +194,8 @@ stage_kernel_mixed(const MixedArgs a) {
         }
         float hpx, hpy;
         if (new_gradp) {
-            const int gi = x0 + li - 1, gj = y0 + lj - 1;
-            const float sg = wall_ghost_sign<float>(gi, gj, nx, ny, a.bc);
+            float sg = 1.0f;
+            if (!interior) sg = wall_ghost_sign<float>(x0 + li - 1, y0 + lj - 1, nx, ny, a.bc);
             const float rho = R[c], u = U[c], v = V[c];
             const float rtx = need_rt ? sm.rt[0][k] : 0.0f;
             const float rty = need_rt ? sm.rt[1][k] : 0.0f;
@@ -186,12 +219,12 @@ stage_kernel_mixed(const MixedArgs a) {
     for (int k = tid; k < S::NXF + S::NYF; k += NT) {
         float F[4];
         if (k < S::NXF) {
-            const int fi = k % (TX + 1), fj = k / (TX + 1);
+            const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
             const int gi = x0 + fi, gj = y0 + fj;
             float jump = 0.0f;
             if (gj < ny) {
-                if (gi >= 0 && gi < nx) jump = a.dref[(size_t)gj * nx + gi];
-                else if (gi == nx && per_x) jump = a.dref[(size_t)gj * nx];
+                if (gi < nx) jump = __ldg(a.dref + gj * nx + gi);
+                else if (gi == nx && per_x) jump = __ldg(a.dref + gj * nx);
             }
             sm.dxf[k] = jump;
             const int ga = (fj + 1) * GW + fi, gb = ga + 1;
@@ -205,7 +238,7 @@ stage_kernel_mixed(const MixedArgs a) {
             sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
         } else {
             const int kk = k - S::NXF;
-            const int fi = kk % TX, fj = kk / TX;
+            const int fj = kk / TX, fi = kk - fj * TX;
             const int ga = fj * GW + fi + 1, gb = ga + GW;
             const int ca = (fj + 1) * RW + fi + 2, cb = ca + RW;
             const float rL = sm.w[0][ca] + sm.gy[0][ga], rR = sm.w[0][cb] - sm.gy[0][gb];
@@ -219,47 +252,51 @@ stage_kernel_mixed(const MixedArgs a) {
     __syncthreads();
 
     // ---- 4. divergence + sources + point-implicit update of dQ and p' ----
-    const int li = tid % TX, lj = tid / TX;
-    const int gi = x0 + li, gj = y0 + lj;
-    const bool inside = (gi < nx) && (gj < ny);
     float sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (inside) {
-        const size_t g = (size_t)gj * nx + gi;
+#pragma unroll
+    for (int cell = tid; cell < TX * TY; cell += NT) {
+        const int lj = cell / TX, li = cell - lj * TX;
+        const int gi = x0 + li, gj = y0 + lj;
+        if (gi >= nx || gj >= ny) continue;
+        const int g = gj * nx + gi;
         const int fw = lj * (TX + 1) + li, fe = fw + 1;
-        const int fs = lj * TX + li, fn = fs + TX;
+        const int fs = cell, fn = fs + TX;
         float div[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f)
             div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * a.inv_dx + (sm.fy[f][fn] - sm.fy[f][fs]) * a.inv_dy;
         const float e0 = d0[0][g], e1 = d0[1][g], e2 = d0[2][g], p0 = d0[3][g];
-        const float r0 = a.qn32[0][g] + e0, m0 = a.qn32[1][g] + e1, n0 = a.qn32[2][g] + e2;
+        const float r0 = __ldg(a.qn32[0] + g) + e0;
+        const float m0 = __ldg(a.qn32[1] + g) + e1;
+        const float n0 = __ldg(a.qn32[2] + g) + e2;
         const float rt0 = e0 * inv_dt, rt1 = e1 * inv_dt, rt2 = e2 * inv_dt;
         // reference force: -(divergence of the x-face reference means)
         const float sref = -0.5f * (sm.dxf[fe] + sm.dxf[fw]) * a.inv_dx;
         const float b0 = -div[0] - rt0;
         const float b1 = -div[1] - rt1 + r0 * a.gx + sref;
-        const float b2 = -div[2] - rt2 + (r0 - a.rho_ref[g]) * a.gy;
+        const float b2 = -div[2] - rt2 + (r0 - __ldg(a.rho_ref + g)) * a.gy;
         const float b3 = -div[3];
         float dtau;
         if (a.local_dtau) {
             const float ir = Ar<float>::rcp(r0);
             const float u = m0 * ir, v = n0 * ir, fb = 4.0f * a.beta * ir;
-            const float cx = sqrtf(u * u + fb), cy = sqrtf(v * v + fb);
+            const float u2 = u * u + fb, v2 = v * v + fb;
+            const float cx = u2 * rsqrtf(u2), cy = v2 * rsqrtf(v2);
             const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
-            dtau = a.cfl_area / den;
+            dtau = __fdividef(a.cfl_area, den);
         } else {
             dtau = float(__longlong_as_double((long long)ctl->dtau_bits));
         }
-        const float api = 1.0f + a.alpha * dtau * inv_dt;
-        const float coef = a.alpha * dtau / api;
-        const float coef_p = a.alpha_pi_p_row ? coef : a.alpha * dtau;
+        const float adt = a.alpha * dtau;
+        const float coef = __fdividef(adt, 1.0f + adt * inv_dt);   // Eq. point_implicit, B0 = 1
+        const float coef_p = a.alpha_pi_p_row ? coef : adt;
         dout[0][g] = e0 + coef * b0;
         dout[1][g] = e1 + coef * b1;
         dout[2][g] = e2 + coef * b2;
         dout[3][g] = p0 + a.beta * coef_p * b3;
         if (a.stage == 1) {
             const float pb = a.beta * b3;
-            sq[0] = b0 * b0; sq[1] = b1 * b1; sq[2] = b2 * b2; sq[3] = pb * pb;
+            sq[0] += b0 * b0; sq[1] += b1 * b1; sq[2] += b2 * b2; sq[3] += pb * pb;
         }
     }
     if (a.stage == 1) {
