@@ -164,6 +164,40 @@ long long ac_kernel_launches(const ac_ctx *ctx);
 int ac_set_profiling(ac_ctx *ctx, int on);
 int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launches);
 
+/* ---- stage sweep without device allocation ------------------------------
+ * This entry point has no counterpart in the paper: it exists for callers
+ * that cannot allocate device memory -- code running inside a memory pool
+ * it does not own, a sandbox or plug-in host that forbids allocation after
+ * start-up, or a real-time loop where an allocation could stall or fail.
+ *
+ * One FP64 Runge-Kutta stage sweep (the same kernel ac_physical_step runs)
+ * on caller-owned DEVICE arrays of nx*ny doubles (row-major, x fastest):
+ *   q_prev  Q^{s-1} = (rho, rho u, rho v, p)   (ignored for stage 1)
+ *   q0      Q^{m}, the state at the start of the pseudo-iteration
+ *   qn      Q^n = (rho, rho u, rho v), the real-time level (may be NULL
+ *           when opt->realtime is 0)
+ *   q_out   receives Q^s (must not alias any input)
+ *   norms   device array of 4 doubles receiving the residual norms R of
+ *           the stage-1 bracket (stage 1 only; may be NULL)
+ * grid, beta, bc and opt mean what they mean for ac_create; opt->precision
+ * must be AC_PREC_FP64; stage is 1..opt->rk_stages; dt as in
+ * ac_physical_step.  Work is enqueued on `stream` (a cudaStream_t; NULL =
+ * default stream) and the call returns without waiting.
+ *
+ * No cudaMalloc, cudaFree or allocating library call is made.  The sweep's
+ * scratch (control block and per-tile partial sums) is a fixed 1 MiB array
+ * inside the library, so grids are limited to 32760 tiles of 32x8 cells
+ * (about 8.39 million cells); larger grids are rejected with AC_ERR_ARG.
+ * Every GPU that loads the library holds that 1 MiB until the process
+ * exits.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device
+ * address and sets the kernel's shared-memory limit; make that first call
+ * before any stream capture. */
+int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac_bc *bc, const ac_options *opt,
+                           int stage, double dt, const double *const q_prev[4], const double *const q0[4],
+                           const double *const qn[3], double *const q_out[4], double *norms, void *stream);
+
 /* Message describing the last error on this thread ("" if none). */
 const char *ac_last_error(void);
 

@@ -36,6 +36,7 @@ EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_levels",
     "ac_set_levels", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
+    "ac_stage_sweep_noalloc",
 )
 
 
@@ -99,6 +100,10 @@ def load(build: bool = True):
     L.ac_kernel_launches.restype = C.c_longlong
     L.ac_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.ac_stage_kernel_time.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
+    _PA4 = C.c_void_p * 4
+    _PA3 = C.c_void_p * 3
+    L.ac_stage_sweep_noalloc.argtypes = [C.POINTER(ac_grid), C.c_double, C.POINTER(ac_bc), C.POINTER(ac_options),
+                                         C.c_int, C.c_double, _PA4, _PA4, _PA3, _PA4, C.c_void_p, C.c_void_p]
     L.ac_last_error.argtypes = []
     L.ac_last_error.restype = C.c_char_p
     _lib = L
@@ -153,6 +158,23 @@ def options_from(case_options, precision: str = "fp64") -> ac_options:
     for k in range(4):
         o.abs_tol[k] = case_options.abs_tol[k]
     return o
+
+
+def ac_stage_sweep_noalloc(nx, ny, lx, ly, gx, gy, beta, bc, options, stage, dt, q_prev, q0, qn, q_out,
+                           norms=0, stream=0):
+    """One FP64 stage sweep on caller-owned device arrays, allocating
+    nothing (see include/ac.h).  Field arguments are sequences of device
+    addresses (ints); norms is a device address of 4 doubles or 0."""
+    L = load()
+    g = ac_grid(nx, ny, lx, ly, gx, gy)
+    b = ac_bc(*[BC[s] for s in bc])
+    A4 = C.c_void_p * 4
+    A3 = C.c_void_p * 3
+    qp = A4(*(q_prev if q_prev is not None else [0, 0, 0, 0]))
+    rc = L.ac_stage_sweep_noalloc(C.byref(g), beta, C.byref(b), C.byref(options), stage, dt, qp, A4(*q0),
+                                  A3(*qn) if qn is not None else None, A4(*q_out), C.c_void_p(norms or 0),
+                                  C.c_void_p(stream or 0))
+    _check(rc)
 
 
 class Tank:

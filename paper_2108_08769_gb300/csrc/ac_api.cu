@@ -26,13 +26,26 @@
 #include <vector>
 
 #include "../../include/ac.h"
+#include "ac_internal.h"
 #include "ac_kernels_mixed.cuh"
 
 using namespace acgb;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+int acgb::set_last_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+namespace {
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
