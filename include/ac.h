@@ -164,6 +164,47 @@ long long ac_kernel_launches(const ac_ctx *ctx);
 int ac_set_profiling(ac_ctx *ctx, int on);
 int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launches);
 
+/* ---- many tanks at once (mixed form) -------------------------------------
+ * A batch advances n independent tanks of any sizes, densities and beta in
+ * the mixed form (FP32 sweep; FP64 time levels, reference pressure and
+ * norms).  Every Runge-Kutta stage of every tank is one kernel launch over
+ * the flattened tiles of all tanks; each tank keeps its own pseudo-iteration
+ * count, residual norms and convergence flag (Alg. 1 per tank), and a tank
+ * that has converged stops consuming work while the others iterate.  One
+ * physical step is one graph launch whose WHILE loop runs until every tank
+ * has stopped.  The tile shape (cells per CTA, threads per CTA) is chosen by
+ * timing every compiled shape on the batch at its first step.
+ * The tanks' own numbers do not depend on the rest of the batch: with the
+ * same tile shape they equal a single-tank context's bit for bit. */
+typedef struct ac_batch ac_batch;
+
+/* grids[n], beta[n] (Pa) and bcs[n] describe the tanks; opt (may be NULL)
+ * applies to all of them and must select AC_PREC_MIXED and the local
+ * pseudo-time step.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA. */
+int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc *bcs, const ac_options *opt,
+                    ac_batch **out);
+void ac_batch_destroy(ac_batch *b);
+int ac_batch_set_stream(ac_batch *b, void *stream);
+/* State of tank k (0 <= k < n) from host arrays, as ac_set_state. */
+int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou, const double *rhov,
+                       const double *p);
+int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, double *rhov, double *p);
+/* One physical step of every tank with its own dt[k]; tol and max_iters as
+ * in ac_physical_step.  iters_out[n] and status_out[n] (may be NULL)
+ * receive each tank's iterations and status (AC_OK, AC_NOT_CONVERGED,
+ * AC_ERR_NONFINITE).  Returns AC_OK when every tank converged (or tol < 0),
+ * AC_NOT_CONVERGED when some tank hit max_iters, AC_ERR_NONFINITE when some
+ * tank's norm became non-finite (those tanks are restored to the start of
+ * the step, the others advanced). */
+int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
+                           int *status_out);
+int ac_batch_residual_norms(const ac_batch *b, int k, double out[4], double out0[4]);
+/* The tile shape the autotuner chose (AC_ERR_STATE before the first step). */
+int ac_batch_tile_shape(const ac_batch *b, int *tx, int *ty, int *threads);
+int ac_batch_set_profiling(ac_batch *b, int on);
+int ac_batch_stage_kernel_time(const ac_batch *b, double *total_ms, long long *launches);
+long long ac_batch_kernel_launches(const ac_batch *b);
+
 /* ---- stage sweep without device allocation ------------------------------
  * This entry point has no counterpart in the paper: it exists for callers
  * that cannot allocate device memory -- code running inside a memory pool

@@ -36,7 +36,9 @@ EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_levels",
     "ac_set_levels", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
-    "ac_stage_sweep_noalloc",
+    "ac_stage_sweep_noalloc", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
+    "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
+    "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
 )
 
 
@@ -104,6 +106,21 @@ def load(build: bool = True):
     _PA3 = C.c_void_p * 3
     L.ac_stage_sweep_noalloc.argtypes = [C.POINTER(ac_grid), C.c_double, C.POINTER(ac_bc), C.POINTER(ac_options),
                                          C.c_int, C.c_double, _PA4, _PA4, _PA3, _PA4, C.c_void_p, C.c_void_p]
+    _I = C.POINTER(C.c_int)
+    L.ac_batch_create.argtypes = [C.c_int, C.POINTER(ac_grid), _D, C.POINTER(ac_bc), C.POINTER(ac_options),
+                                  C.POINTER(C.c_void_p)]
+    L.ac_batch_destroy.argtypes = [C.c_void_p]
+    L.ac_batch_destroy.restype = None
+    L.ac_batch_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.ac_batch_set_state.argtypes = [C.c_void_p, C.c_int, _D, _D, _D, _D]
+    L.ac_batch_get_state.argtypes = [C.c_void_p, C.c_int, _D, _D, _D, _D]
+    L.ac_batch_physical_step.argtypes = [C.c_void_p, _D, C.c_double, C.c_int, _I, _I]
+    L.ac_batch_residual_norms.argtypes = [C.c_void_p, C.c_int, _D, _D]
+    L.ac_batch_tile_shape.argtypes = [C.c_void_p, _I, _I, _I]
+    L.ac_batch_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    L.ac_batch_stage_kernel_time.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
+    L.ac_batch_kernel_launches.argtypes = [C.c_void_p]
+    L.ac_batch_kernel_launches.restype = C.c_longlong
     L.ac_last_error.argtypes = []
     L.ac_last_error.restype = C.c_char_p
     _lib = L
@@ -255,3 +272,85 @@ class Tank:
         n = C.c_longlong(0)
         _check(load().ac_stage_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+
+class Batch:
+    """Many tanks advanced together in the mixed form (an ``ac_batch``)."""
+
+    def __init__(self, cases, options: Optional[ac_options] = None):
+        L = load()
+        n = len(cases)
+        self.cases = list(cases)
+        grids = (ac_grid * n)(*[ac_grid(c.nx, c.ny, c.lx, c.ly, c.gx, c.gy) for c in cases])
+        bcs = (ac_bc * n)(*[ac_bc(*[BC[s] for s in c.bc]) for c in cases])
+        betas = (C.c_double * n)(*[c.beta for c in cases])
+        if options is None:
+            options = options_from(cases[0].options, "mixed")
+        h = C.c_void_p()
+        _check(L.ac_batch_create(n, grids, betas, bcs, C.byref(options), C.byref(h)))
+        self._h = h
+        self.n = n
+
+    @classmethod
+    def from_cases(cls, cases, options: Optional[ac_options] = None) -> "Batch":
+        b = cls(cases, options)
+        for k, c in enumerate(cases):
+            b.set_state(k, *c.state())
+        return b
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ac_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr: int):
+        _check(load().ac_batch_set_stream(self._h, C.c_void_p(stream_ptr)))
+
+    def set_state(self, k, rho, rhou, rhov, p):
+        c = self.cases[k]
+        n = c.nx * c.ny
+        arrs = [_host(a, n) for a in (rho, rhou, rhov, p)]
+        _check(load().ac_batch_set_state(self._h, k, *[_ptr(a) for a in arrs]))
+
+    def get_state(self, k):
+        c = self.cases[k]
+        out = [np.empty((c.ny, c.nx)) for _ in range(4)]
+        _check(load().ac_batch_get_state(self._h, k, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def physical_step(self, dt, tol: float, max_iters: int):
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n,)))
+        its = (C.c_int * self.n)()
+        st = (C.c_int * self.n)()
+        rc = load().ac_batch_physical_step(self._h, _ptr(dts), tol, max_iters, its, st)
+        _check(rc, (AC_OK, AC_NOT_CONVERGED))
+        return rc, list(its), list(st)
+
+    def residual_norms(self, k):
+        R = np.zeros(4)
+        R0 = np.zeros(4)
+        _check(load().ac_batch_residual_norms(self._h, k, _ptr(R), _ptr(R0)))
+        return R, R0
+
+    def tile_shape(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        load().ac_batch_tile_shape(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    def set_profiling(self, on: bool):
+        _check(load().ac_batch_set_profiling(self._h, int(on)))
+
+    def stage_kernel_time(self):
+        ms = C.c_double(0.0)
+        n = C.c_longlong(0)
+        _check(load().ac_batch_stage_kernel_time(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def kernel_launches(self) -> int:
+        return load().ac_batch_kernel_launches(self._h)

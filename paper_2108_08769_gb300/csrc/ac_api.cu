@@ -28,6 +28,7 @@
 #include "../../include/ac.h"
 #include "ac_internal.h"
 #include "ac_kernels_mixed.cuh"
+#include "ac_mixed_host.h"
 
 using namespace acgb;
 
@@ -71,7 +72,6 @@ constexpr int kEndThreads = 256;
 constexpr int kGridStrideBlocks = 152 * 8;
 
 bool valid_bc(int b) { return b >= AC_BC_WALL_SLIP && b <= AC_BC_PERIODIC; }
-bool is_wall_bc(int b) { return b == AC_BC_WALL_SLIP || b == AC_BC_WALL_NOSLIP; }
 
 struct Backend;
 
@@ -359,7 +359,7 @@ struct MixedBackend : Backend {
         variant = -1;   // tuned at the first physical step
         // the reference applies when both y sides are walls and the pressure
         // gradient comes from Eq. new_gradp
-        use_ref = is_wall_bc(c->bc.ylo) && is_wall_bc(c->bc.yhi) && c->opt.gradp == AC_GRADP_NEW;
+        use_ref = mixed_uses_reference(c->bc, c->opt.gradp);
         return AC_OK;
     }
     void release() override {
@@ -371,32 +371,11 @@ struct MixedBackend : Backend {
         cudaFree(lev_p);
     }
     int set_state(ac_ctx *c, const double *const f[4]) override {
-        const int nx = c->grid.nx, ny = c->grid.ny;
         const size_t N = c->N;
-        std::vector<float> h32(N), href(N, 0.0f), hdref(N, 0.0f), hp(N);
-        p_ref.assign(N, 0.0);
-        if (use_ref) {
-            // discrete hydrostatic columns of the FP32 reference density,
-            // anchored at the top cell of each column
-            for (size_t k = 0; k < N; ++k) href[k] = float(f[0][k]);
-            const double gy = c->grid.gy, dy = c->dy;
-            for (int i = 0; i < nx; ++i) {
-                size_t top = (size_t)(ny - 1) * nx + i;
-                p_ref[top] = f[3][top];
-                for (int j = ny - 2; j >= 0; --j) {
-                    const size_t k = (size_t)j * nx + i;
-                    p_ref[k] = p_ref[k + nx] - (double(href[k]) + double(href[k + nx])) * gy * dy / 2.0;
-                }
-            }
-            const bool per_x = c->bc.xlo == AC_BC_PERIODIC;
-            for (int j = 0; j < ny; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    const size_t k = (size_t)j * nx + i;
-                    if (i > 0) hdref[k] = float(p_ref[k] - p_ref[k - 1]);
-                    else if (per_x) hdref[k] = float(p_ref[k] - p_ref[k + nx - 1]);
-                }
-        }
-        for (size_t k = 0; k < N; ++k) hp[k] = float(f[3][k] - p_ref[k]);
+        MixedReference ref;
+        build_mixed_reference(c->grid.nx, c->grid.ny, c->dy, c->grid.gy, c->bc, use_ref, f, ref);
+        p_ref = ref.p_ref;
+        std::vector<float> h32(N);
         cudaStream_t s = c->stream;
         const size_t fb = N * sizeof(float);
         for (int k = 0; k < 3; ++k) {
@@ -406,10 +385,10 @@ struct MixedBackend : Backend {
             CK(cudaStreamSynchronize(s));   // h32 is reused
             CK(cudaMemsetAsync(d[0][k], 0, fb, s));
         }
-        CK(cudaMemcpyAsync(d[0][3], hp.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(lev_p, hp.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(rho_ref, href.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(dref, hdref.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d[0][3], ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(lev_p, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(rho_ref, ref.rho_ref.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dref, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         return AC_OK;
     }

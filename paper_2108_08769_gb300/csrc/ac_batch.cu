@@ -1,0 +1,696 @@
+// ac_batch.cu -- many independent tanks of uneven size advanced together in
+// the mixed form (declared in include/ac.h, ac_batch_*).
+//
+// Every stage of every tank is one launch over the flattened list of all
+// tanks' tiles: CTA b looks up its tank in a tile -> tank map, copies the
+// tank's descriptor into shared memory and runs the same tile sweep as the
+// single-tank kernel (mixed_tile), so a tank's numbers do not depend on
+// what else is in the batch.  Each tank has its own control block: its own
+// pseudo-iteration count, residual norms, stopping test, convergence flag
+// and buffer rotation; the tiles of a tank that has converged return at
+// once.  The end-of-iteration kernel runs one CTA per tank; the last CTA to
+// arrive (an atomic counter, no waiting) sets the graph's WHILE condition
+// to "some tank still iterating".  The whole pseudo-iteration loop of one
+// physical step is one graph launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ac.h"
+#include "ac_internal.h"
+#include "ac_kernels_mixed.cuh"
+#include "ac_mixed_host.h"
+
+using namespace acgb;
+
+#define fail acgb::set_last_error
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA, "%s failed: %s", #call, \
+                        cudaGetErrorString(e_));                                                        \
+    } while (0)
+
+namespace {
+
+struct BatchTank {
+    MixedArgs a;   // the tank's arrays, scalars and control block (stage fields unset)
+    int tile0;     // its first tile in the flattened list
+    int tiles_x;   // tiles along x
+    int ntiles;
+    int pad;
+};
+
+struct BatchSync {
+    unsigned int arrive;       // end-of-iteration CTAs arrived
+    unsigned int still_active; // tanks still iterating after this iteration
+};
+
+// Stage s of every active tank; blockIdx.x runs over the flattened tiles.
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ MixedArgs sa;
+    __shared__ int s_local, s_tiles_x;
+    const int k = tile_tank[blockIdx.x];
+    const BatchTank &t = tanks[k];
+    if (t.a.ctl->done) return;
+    // descriptor -> shared memory (word by word), then the stage fields
+    const unsigned int *src = reinterpret_cast<const unsigned int *>(&t.a);
+    unsigned int *dst = reinterpret_cast<unsigned int *>(&sa);
+    for (int w = threadIdx.x; w < (int)(sizeof(MixedArgs) / 4); w += NT) dst[w] = src[w];
+    if (threadIdx.x == 0) {
+        s_local = blockIdx.x - t.tile0;
+        s_tiles_x = t.tiles_x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sa.stage = stage;
+        sa.alpha = 1.0f / float(sa.s_max - stage + 1);
+    }
+    __syncthreads();
+    const int local = s_local;
+    const int by = local / s_tiles_x, bx = local - by * s_tiles_x;
+    mixed_tile<TX, TY, NT>(sa, bx, by, sa.partials + (size_t)local * 4, smem_raw);
+}
+
+// Start of a physical step for every tank (blockIdx.y = tank): level shift
+// in FP64 and control-block reset (Alg. 1).
+__global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const double *dt, double tol,
+                                   int max_iters) {
+    const MixedArgs &a = tanks[blockIdx.y].a;
+    Ctl *ctl = a.ctl;
+    const int cur = ctl->cur;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const double q = a.q64[f][g] + double(a.d[cur][f][g]);
+            a.q64[f][g] = q;
+            a.qn32[f][g] = float(q);
+            a.d[cur][f][g] = 0.0f;
+        }
+        a.lev_p[g] = a.d[cur][3][g];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double h = dt[blockIdx.y];
+        ctl->iter = 0;
+        ctl->done = 0;
+        ctl->status = 1;
+        ctl->max_iters = max_iters;
+        ctl->fixed = tol < 0.0;
+        ctl->tol = tol;
+        ctl->dt = h;
+        ctl->inv_dt = 1.0 / h;
+        ctl->dtau_bits = 0x7ff0000000000000ull;
+        if (blockIdx.y == 0) {
+            sync->arrive = 0;
+            sync->still_active = 0;
+        }
+    }
+}
+
+// End of a pseudo-iteration for every tank (blockIdx.x = tank): its norms
+// from its own tiles' partial sums (fixed order), its stopping test and
+// buffer rotation; the last CTA sets the WHILE condition.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long long cond, int use_cond) {
+    __shared__ double red[4][NT];
+    const int tid = threadIdx.x;
+    const BatchTank &t = tanks[blockIdx.x];
+    Ctl *ctl = t.a.ctl;
+    const bool was_done = ctl->done != 0;
+    if (!was_done) {
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = tid; b < t.ntiles; b += NT)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s[f] += t.a.partials[(size_t)b * 4 + f];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) red[f][tid] = s[f];
+        __syncthreads();
+        for (int w = NT / 2; w > 0; w >>= 1) {
+            if (tid < w)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) red[f][tid] += red[f][tid + w];
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        int active = 0;
+        if (!was_done) {
+            const double inv_cells = 1.0 / ((double)t.a.nx * t.a.ny);
+            const int it = ctl->iter + 1;
+            ctl->iter = it;
+            bool finite = true, conv = true;
+            for (int f = 0; f < 4; ++f) {
+                const double R = sqrt(red[f][0] * inv_cells);
+                ctl->R[f] = R;
+                if (it == 1) ctl->R0[f] = R;
+                if (!isfinite(R)) finite = false;
+                if (!(R <= fmax(ctl->tol * ctl->R0[f], ctl->abs_tol[f]))) conv = false;
+            }
+            ctl->cur = final_buffer(ctl->cur, t.a.s_max);
+            int done = 0;
+            if (!finite) { ctl->status = -3; done = 1; }
+            else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
+            else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
+            ctl->done = done;
+            active = !done;
+        }
+        if (active) atomicAdd(&sync->still_active, 1u);
+        __threadfence();
+        const unsigned int prev = atomicAdd(&sync->arrive, 1u);
+        if (prev == (unsigned int)ntanks - 1) {
+            __threadfence();
+            const unsigned int left = atomicExch(&sync->still_active, 0u);
+            sync->arrive = 0;
+            if (use_cond) cudaGraphSetConditional(cond, left ? 1u : 0u);
+        }
+    }
+}
+
+// After a non-finite residual in some tanks: those tanks back to the start
+// of the step.
+__global__ void batch_restore_kernel(BatchTank *tanks) {
+    const MixedArgs &a = tanks[blockIdx.y].a;
+    if (a.ctl->status != -3) return;
+    const int cur = a.ctl->cur;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        a.d[cur][0][g] = 0.0f;
+        a.d[cur][1][g] = 0.0f;
+        a.d[cur][2][g] = 0.0f;
+        a.d[cur][3][g] = a.lev_p[g];
+    }
+}
+
+struct Variant {
+    int tx, ty, nt;
+};
+constexpr Variant kVariants[] = {
+    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256}, {64, 8, 512}, {64, 16, 512}, {16, 16, 256},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <int TX, int TY, int NT>
+cudaError_t allow_smem() {
+    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(MixedSmem<TX, TY>));
+}
+
+template <int TX, int TY, int NT>
+cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, cudaStream_t s) {
+    batch_stage_kernel<TX, TY, NT><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage);
+    return cudaGetLastError();
+}
+
+constexpr size_t kAlign = 64;   // cells: each tank's arrays start on a 256-byte boundary
+
+}  // namespace
+
+struct ac_batch {
+    int n;
+    std::vector<ac_grid> grids;
+    std::vector<ac_bc> bcs;
+    std::vector<double> betas;
+    ac_options opt;
+    std::vector<size_t> off;            // first cell of each tank in the pooled arrays
+    size_t total;                       // pooled cells (with alignment padding)
+    // pooled device arrays
+    float *d[3][4];
+    float *qn32[3];
+    float *rho_ref, *dref, *lev_p;
+    double *q64[3];
+    double *partials;
+    Ctl *ctl;
+    BatchSync *sync;
+    BatchTank *tanks_dev;
+    int *tile_map;                      // per variant: flattened tile -> tank
+    double *dt_dev;
+    std::vector<BatchTank> tanks_host;
+    std::vector<std::vector<double>> p_ref;
+    std::vector<char> use_ref;
+    Ctl *hctl;                          // pinned mirror of all control blocks
+    int variant;
+    int ntiles;
+    std::vector<int> map_host;
+    cudaStream_t stream, cap;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool has_state;
+    long long launches;
+    bool profiling;
+    cudaEvent_t ev[5];
+    double stage_ms;
+    long long stage_launches;
+};
+
+namespace {
+
+int build_tiles(ac_batch *b, int v) {
+    const Variant &m = kVariants[v];
+    b->map_host.clear();
+    for (int k = 0; k < b->n; ++k) {
+        const int tx = (b->grids[k].nx + m.tx - 1) / m.tx, ty = (b->grids[k].ny + m.ty - 1) / m.ty;
+        BatchTank &t = b->tanks_host[k];
+        t.tile0 = (int)b->map_host.size();
+        t.tiles_x = tx;
+        t.ntiles = tx * ty;
+        for (int q = 0; q < tx * ty; ++q) b->map_host.push_back(k);
+    }
+    b->ntiles = (int)b->map_host.size();
+    b->variant = v;
+    CK(cudaMemcpyAsync(b->tile_map, b->map_host.data(), b->map_host.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_host.data(), b->n * sizeof(BatchTank), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return AC_OK;
+}
+
+int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
+    cudaError_t e;
+    switch (v) {
+        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        default: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+    }
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
+// Autotuner for the batch: stage 1 of every tile shape over all tanks (it
+// writes only scratch), fastest kept.
+int tune(ac_batch *b, cudaStream_t s) {
+    if (b->variant >= 0) return AC_OK;
+    const char *env = getenv("AC_TILE");
+    if (env) {
+        const int v = atoi(env);
+        if (v >= 0 && v < kNumVariants) return build_tiles(b, v);
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumVariants; ++v) {
+        int rc = build_tiles(b, v);
+        if (rc != AC_OK) return rc;
+        for (int w = 0; w < 2; ++w)
+            if ((rc = stage_launch(b, s, 1, v)) != AC_OK) return rc;
+        CK(cudaEventRecord(b->ev[0], s));
+        for (int r = 0; r < 3; ++r)
+            if ((rc = stage_launch(b, s, 1, v)) != AC_OK) return rc;
+        CK(cudaEventRecord(b->ev[1], s));
+        CK(cudaEventSynchronize(b->ev[1]));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+        b->launches += 5;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    return build_tiles(b, best);
+}
+
+int enqueue_iteration(ac_batch *b, cudaStream_t s, unsigned long long cond, int use_cond, bool timed) {
+    int rc;
+    if (timed) CK(cudaEventRecord(b->ev[0], s));
+    for (int st = 1; st <= b->opt.rk_stages; ++st) {
+        if ((rc = stage_launch(b, s, st, b->variant)) != AC_OK) return rc;
+        if (timed) CK(cudaEventRecord(b->ev[st], s));
+    }
+    batch_end_kernel<256><<<b->n, 256, 0, s>>>(b->tanks_dev, b->sync, b->n, cond, use_cond);
+    CK(cudaGetLastError());
+    return AC_OK;
+}
+
+int build_graph(ac_batch *b) {
+    if (b->exec) return AC_OK;
+    CK(cudaGraphCreate(&b->graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_iteration(b, b->cap, (unsigned long long)h, 1, false);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &captured);
+    if (rc != AC_OK) return rc;
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return AC_OK;
+}
+
+int check_field(const double *a, size_t n, bool positive, const char *name) {
+    if (!a) return fail(AC_ERR_ARG, "%s is NULL", name);
+    for (size_t k = 0; k < n; ++k) {
+        if (!std::isfinite(a[k])) return fail(AC_ERR_NONFINITE, "%s[%zu] is not finite", name, k);
+        if (positive && !(a[k] > 0.0)) return fail(AC_ERR_ARG, "%s[%zu] = %g is not > 0", name, k, a[k]);
+    }
+    return AC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ac_batch_destroy(ac_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < 5; ++k)
+        if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (int x = 0; x < 3; ++x)
+        for (int f = 0; f < 4; ++f) cudaFree(b->d[x][f]);
+    for (int f = 0; f < 3; ++f) { cudaFree(b->qn32[f]); cudaFree(b->q64[f]); }
+    cudaFree(b->rho_ref);
+    cudaFree(b->dref);
+    cudaFree(b->lev_p);
+    cudaFree(b->partials);
+    cudaFree(b->ctl);
+    cudaFree(b->sync);
+    cudaFree(b->tanks_dev);
+    cudaFree(b->tile_map);
+    cudaFree(b->dt_dev);
+    if (b->hctl) cudaFreeHost(b->hctl);
+    delete b;
+}
+
+int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc *bcs, const ac_options *opt,
+                    ac_batch **out) {
+    set_last_error(AC_OK, "%s", "");
+    if (!out) return fail(AC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 65535) return fail(AC_ERR_ARG, "the batch needs 1..65535 tanks (got %d)", n);
+    if (!grids || !beta || !bcs) return fail(AC_ERR_ARG, "grids, beta and bcs must not be NULL");
+    ac_options o;
+    ac_default_options(&o);
+    o.precision = AC_PREC_MIXED;
+    if (opt) o = *opt;
+    if (o.precision != AC_PREC_MIXED) return fail(AC_ERR_ARG, "batched tanks run in the mixed form (AC_PREC_MIXED)");
+    if (o.rk_stages < 1 || o.rk_stages > 4) return fail(AC_ERR_ARG, "rk_stages must be 1..4");
+    if (o.riemann != AC_RIEMANN_OSHER) return fail(AC_ERR_ARG, "riemann solver %d is not available", o.riemann);
+    if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
+    if (o.limiter_k != 1 && o.limiter_k != 2) return fail(AC_ERR_ARG, "limiter_k must be 1 or 2");
+    if (!o.local_dtau) return fail(AC_ERR_ARG, "batched tanks use the local pseudo-time step");
+    if (!(o.cfl_tau > 0.0)) return fail(AC_ERR_ARG, "cfl_tau must be > 0");
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        const ac_grid &g = grids[k];
+        if (g.nx < 1 || g.ny < 1 || !(g.lx > 0.0) || !(g.ly > 0.0))
+            return fail(AC_ERR_ARG, "tank %d: invalid grid", k);
+        if (!(beta[k] > 0.0) || !std::isfinite(beta[k])) return fail(AC_ERR_ARG, "tank %d: beta must be > 0", k);
+        const ac_bc &c = bcs[k];
+        const int sides[4] = {c.xlo, c.xhi, c.ylo, c.yhi};
+        for (int q = 0; q < 4; ++q)
+            if (sides[q] < AC_BC_WALL_SLIP || sides[q] > AC_BC_PERIODIC)
+                return fail(AC_ERR_ARG, "tank %d: boundary kind %d is unknown", k, sides[q]);
+        if ((c.xlo == AC_BC_PERIODIC) != (c.xhi == AC_BC_PERIODIC) ||
+            (c.ylo == AC_BC_PERIODIC) != (c.yhi == AC_BC_PERIODIC))
+            return fail(AC_ERR_ARG, "tank %d: periodic boundaries must be set on both sides", k);
+        total += ((size_t)g.nx * g.ny + kAlign - 1) / kAlign * kAlign;
+    }
+    if (total > (size_t)1 << 31) return fail(AC_ERR_ARG, "the batch holds more than 2^31 cells");
+    ac_batch *b = new ac_batch();
+    b->n = n;
+    b->grids.assign(grids, grids + n);
+    b->bcs.assign(bcs, bcs + n);
+    b->betas.assign(beta, beta + n);
+    b->opt = o;
+    b->total = total;
+    b->variant = -1;
+    b->off.resize(n);
+    b->p_ref.resize(n);
+    b->use_ref.resize(n);
+    b->tanks_host.resize(n);
+#define CKB(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            int c_ = fail(e_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA, "%s: %s", #call,   \
+                          cudaGetErrorString(e_));                                                       \
+            ac_batch_destroy(b);                                                                         \
+            return c_;                                                                                   \
+        }                                                                                                \
+    } while (0)
+    const size_t fb = total * sizeof(float), db = total * sizeof(double);
+    for (int x = 0; x < 3; ++x)
+        for (int f = 0; f < 4; ++f) CKB(cudaMalloc(&b->d[x][f], fb));
+    for (int f = 0; f < 3; ++f) { CKB(cudaMalloc(&b->qn32[f], fb)); CKB(cudaMalloc(&b->q64[f], db)); }
+    CKB(cudaMalloc(&b->rho_ref, fb));
+    CKB(cudaMalloc(&b->dref, fb));
+    CKB(cudaMalloc(&b->lev_p, fb));
+    // tiles of the smallest shape (16 x 8 cells) bound every variant's tile count
+    size_t max_tiles = 0;
+    for (int k = 0; k < n; ++k) max_tiles += (size_t)((grids[k].nx + 15) / 16) * ((grids[k].ny + 7) / 8);
+    CKB(cudaMalloc(&b->partials, max_tiles * 4 * sizeof(double)));
+    CKB(cudaMalloc(&b->tile_map, max_tiles * sizeof(int)));
+    CKB(cudaMalloc(&b->ctl, n * sizeof(Ctl)));
+    CKB(cudaMalloc(&b->sync, sizeof(BatchSync)));
+    CKB(cudaMalloc(&b->tanks_dev, n * sizeof(BatchTank)));
+    CKB(cudaMalloc(&b->dt_dev, n * sizeof(double)));
+    CKB(cudaMallocHost(&b->hctl, n * sizeof(Ctl)));
+    CKB(cudaMemset(b->sync, 0, sizeof(BatchSync)));
+    CKB(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    for (int k = 0; k < 5; ++k) CKB(cudaEventCreate(&b->ev[k]));
+    CKB((allow_smem<32, 8, 256>()));
+    CKB((allow_smem<32, 16, 256>()));
+    CKB((allow_smem<32, 16, 512>()));
+    CKB((allow_smem<64, 8, 256>()));
+    CKB((allow_smem<64, 8, 512>()));
+    CKB((allow_smem<64, 16, 512>()));
+    CKB((allow_smem<16, 16, 256>()));
+    // per-tank descriptors: arrays offset into the pools, scalars, control block
+    size_t pos = 0, tpos = 0;
+    memset(b->hctl, 0, n * sizeof(Ctl));
+    for (int k = 0; k < n; ++k) {
+        const ac_grid &g = grids[k];
+        b->off[k] = pos;
+        MixedArgs &a = b->tanks_host[k].a;
+        memset(&a, 0, sizeof a);
+        a.nx = g.nx; a.ny = g.ny;
+        a.bc[0] = bcs[k].xlo; a.bc[1] = bcs[k].xhi; a.bc[2] = bcs[k].ylo; a.bc[3] = bcs[k].yhi;
+        a.gradp = o.gradp; a.limiter_k = o.limiter_k; a.realtime = o.realtime ? 1 : 0;
+        a.local_dtau = 1; a.alpha_pi_p_row = o.alpha_pi_p_row ? 1 : 0;
+        a.s_max = o.rk_stages;
+        const double dx = g.lx / g.nx, dy = g.ly / g.ny;
+        a.dx = float(dx); a.dy = float(dy); a.half_dx = float(0.5 * dx); a.half_dy = float(0.5 * dy);
+        a.inv_dx = float(1.0 / dx); a.inv_dy = float(1.0 / dy);
+        a.dx_over_dy = float(dx / dy); a.dy_over_dx = float(dy / dx);
+        a.beta = float(beta[k]); a.inv_beta = float(1.0 / beta[k]);
+        a.gx = float(g.gx); a.gy = float(g.gy);
+        a.cfl_area = float(o.cfl_tau * dx * dy);
+        for (int x = 0; x < 3; ++x)
+            for (int f = 0; f < 4; ++f) a.d[x][f] = b->d[x][f] + pos;
+        for (int f = 0; f < 3; ++f) { a.qn32[f] = b->qn32[f] + pos; a.q64[f] = b->q64[f] + pos; }
+        a.rho_ref = b->rho_ref + pos;
+        a.dref = b->dref + pos;
+        a.lev_p = b->lev_p + pos;
+        a.partials = b->partials + tpos * 4;
+        a.ctl = b->ctl + k;
+        b->use_ref[k] = mixed_uses_reference(bcs[k], o.gradp);
+        for (int q = 0; q < 4; ++q) b->hctl[k].abs_tol[q] = o.abs_tol[q];
+        b->hctl[k].done = 1;
+        pos += ((size_t)g.nx * g.ny + kAlign - 1) / kAlign * kAlign;
+        tpos += (size_t)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
+    }
+    CKB(cudaMemcpy(b->ctl, b->hctl, n * sizeof(Ctl), cudaMemcpyHostToDevice));
+    if (int rc = build_tiles(b, 0)) { ac_batch_destroy(b); return rc; }
+    b->variant = -1;
+#undef CKB
+    *out = b;
+    return AC_OK;
+}
+
+int ac_batch_set_stream(ac_batch *b, void *stream) {
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    b->stream = (cudaStream_t)stream;
+    return AC_OK;
+}
+
+int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou, const double *rhov,
+                       const double *p) {
+    set_last_error(AC_OK, "%s", "");
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    if (k < 0 || k >= b->n) return fail(AC_ERR_ARG, "tank index %d out of range", k);
+    const size_t N = (size_t)b->grids[k].nx * b->grids[k].ny;
+    int rc;
+    if ((rc = check_field(rho, N, true, "rho")) != AC_OK) return rc;
+    if ((rc = check_field(rhou, N, false, "rhou")) != AC_OK) return rc;
+    if ((rc = check_field(rhov, N, false, "rhov")) != AC_OK) return rc;
+    if ((rc = check_field(p, N, false, "p")) != AC_OK) return rc;
+    const double *f[4] = {rho, rhou, rhov, p};
+    const ac_grid &g = b->grids[k];
+    MixedReference ref;
+    build_mixed_reference(g.nx, g.ny, g.ly / g.ny, g.gy, b->bcs[k], b->use_ref[k] != 0, f, ref);
+    b->p_ref[k] = ref.p_ref;
+    cudaStream_t s = b->stream;
+    CK(cudaStreamSynchronize(s));
+    // the tank's control block: buffer 0 holds its state from now on
+    Ctl hc;
+    CK(cudaMemcpy(&hc, b->ctl + k, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    hc.cur = 0;
+    hc.done = 1;
+    hc.iter = 0;
+    const size_t o = b->off[k], fb = N * sizeof(float);
+    std::vector<float> h32(N);
+    for (int q = 0; q < 3; ++q) {
+        CK(cudaMemcpyAsync(b->q64[q] + o, f[q], N * sizeof(double), cudaMemcpyHostToDevice, s));
+        for (size_t i = 0; i < N; ++i) h32[i] = float(f[q][i]);
+        CK(cudaMemcpyAsync(b->qn32[q] + o, h32.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMemsetAsync(b->d[0][q] + o, 0, fb, s));
+    }
+    CK(cudaMemcpyAsync(b->d[0][3] + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->lev_p + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->rho_ref + o, ref.rho_ref.data(), fb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->dref + o, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->ctl + k, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    b->hctl[k] = hc;
+    b->has_state = true;
+    return AC_OK;
+}
+
+int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, double *rhov, double *p) {
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    if (k < 0 || k >= b->n) return fail(AC_ERR_ARG, "tank index %d out of range", k);
+    const size_t N = (size_t)b->grids[k].nx * b->grids[k].ny, o = b->off[k];
+    const int cur = b->hctl[k].cur;
+    double *out[4] = {rho, rhou, rhov, p};
+    std::vector<float> h(N);
+    for (int q = 0; q < 3; ++q) {
+        if (!out[q]) continue;
+        CK(cudaMemcpyAsync(out[q], b->q64[q] + o, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaMemcpyAsync(h.data(), b->d[cur][q] + o, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (size_t i = 0; i < N; ++i) out[q][i] += double(h[i]);
+    }
+    if (p) {
+        CK(cudaMemcpyAsync(h.data(), b->d[cur][3] + o, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (size_t i = 0; i < N; ++i) p[i] = b->p_ref[k][i] + double(h[i]);
+    }
+    return AC_OK;
+}
+
+int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
+                           int *status_out) {
+    set_last_error(AC_OK, "%s", "");
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    if (!b->has_state) return fail(AC_ERR_STATE, "ac_batch_set_state must be called before a step");
+    if (!dt) return fail(AC_ERR_ARG, "dt is NULL");
+    if (max_iters < 1) return fail(AC_ERR_ARG, "max_iters must be >= 1");
+    if (!std::isfinite(tol)) return fail(AC_ERR_ARG, "tol must be finite");
+    std::vector<double> h(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        h[k] = b->opt.realtime ? dt[k] : 1.0;
+        if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(AC_ERR_ARG, "dt[%d] must be finite and > 0", k);
+    }
+    cudaStream_t s = b->stream;
+    CK(cudaMemcpyAsync(b->dt_dev, h.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, s));
+    size_t maxN = 0;
+    for (int k = 0; k < b->n; ++k) maxN = std::max(maxN, (size_t)b->grids[k].nx * b->grids[k].ny);
+    const dim3 bg((unsigned)std::min<size_t>((maxN + 255) / 256, 64), b->n);
+    batch_begin_kernel<<<bg, 256, 0, s>>>(b->tanks_dev, b->sync, b->dt_dev, tol, max_iters);
+    CK(cudaGetLastError());
+    b->launches += 1;
+    int rc = tune(b, s);
+    if (rc != AC_OK) return rc;
+    long long iters_run = 0;
+    if (b->profiling) {
+        while (true) {
+            if ((rc = enqueue_iteration(b, s, 0, 0, true)) != AC_OK) return rc;
+            CK(cudaMemcpyAsync(b->hctl, b->ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int st = 1; st <= b->opt.rk_stages; ++st) {
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, b->ev[st - 1], b->ev[st]));
+                b->stage_ms += ms;
+            }
+            b->stage_launches += b->opt.rk_stages;
+            ++iters_run;
+            bool all = true;
+            for (int k = 0; k < b->n; ++k) all = all && b->hctl[k].done;
+            if (all) break;
+        }
+    } else {
+        if ((rc = build_graph(b)) != AC_OK) return rc;
+        CK(cudaGraphLaunch(b->exec, s));
+        CK(cudaMemcpyAsync(b->hctl, b->ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < b->n; ++k) iters_run = std::max<long long>(iters_run, b->hctl[k].iter);
+    }
+    b->launches += iters_run * (b->opt.rk_stages + 1);
+    int ret = AC_OK;
+    bool any_nonfinite = false;
+    for (int k = 0; k < b->n; ++k) {
+        if (iters_out) iters_out[k] = b->hctl[k].iter;
+        const int st = b->hctl[k].status;
+        if (status_out) status_out[k] = st == -3 ? AC_ERR_NONFINITE : (st == 0 ? AC_OK : AC_NOT_CONVERGED);
+        if (st == -3) any_nonfinite = true;
+        else if (st == 1 && ret == AC_OK) ret = AC_NOT_CONVERGED;
+    }
+    if (any_nonfinite) {
+        batch_restore_kernel<<<dim3(bg.x, b->n), 256, 0, s>>>(b->tanks_dev);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+        return fail(AC_ERR_NONFINITE, "a residual norm became non-finite; those tanks are back at the step's start");
+    }
+    return ret;
+}
+
+int ac_batch_residual_norms(const ac_batch *b, int k, double out[4], double out0[4]) {
+    if (!b || !out) return fail(AC_ERR_ARG, "NULL argument");
+    if (k < 0 || k >= b->n) return fail(AC_ERR_ARG, "tank index %d out of range", k);
+    for (int q = 0; q < 4; ++q) {
+        out[q] = b->hctl[k].R[q];
+        if (out0) out0[q] = b->hctl[k].R0[q];
+    }
+    return AC_OK;
+}
+
+int ac_batch_tile_shape(const ac_batch *b, int *tx, int *ty, int *threads) {
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    const Variant &m = kVariants[b->variant < 0 ? 0 : b->variant];
+    if (tx) *tx = m.tx;
+    if (ty) *ty = m.ty;
+    if (threads) *threads = m.nt;
+    return b->variant < 0 ? AC_ERR_STATE : AC_OK;
+}
+
+int ac_batch_set_profiling(ac_batch *b, int on) {
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    b->profiling = on != 0;
+    b->stage_ms = 0.0;
+    b->stage_launches = 0;
+    return AC_OK;
+}
+
+int ac_batch_stage_kernel_time(const ac_batch *b, double *total_ms, long long *launches) {
+    if (!b) return fail(AC_ERR_ARG, "batch is NULL");
+    if (total_ms) *total_ms = b->stage_ms;
+    if (launches) *launches = b->stage_launches;
+    return AC_OK;
+}
+
+long long ac_batch_kernel_launches(const ac_batch *b) { return b ? b->launches : 0; }
+
+}  // extern "C"

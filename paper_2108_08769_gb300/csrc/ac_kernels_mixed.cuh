@@ -90,19 +90,19 @@ struct CellLoad {
     }
 };
 
-// TX x TY cells per CTA of NT threads (NT divides TX*TY; several cells per
-// thread in the update when NT < TX*TY).
+// One TX x TY tile (tile coordinates bx, by) of one stage of one tank, by
+// a CTA of NT threads (NT divides TX*TY; several cells per thread in the
+// update when NT < TX*TY).  `partial` receives the tile's four residual
+// partial sums at stage 1.  Shared by the single-tank and batched kernels.
 template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
-stage_kernel_mixed(const MixedArgs a) {
+__device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, double *partial,
+                                           unsigned char *smem_raw) {
     using S = MixedSmem<TX, TY>;
     static_assert((TX * TY) % NT == 0 && NT % 32 == 0, "tile/thread shape");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
     constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
 
     const Ctl *ctl = a.ctl;
-    if (ctl->done) return;
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, a.stage, in, out);
@@ -113,7 +113,7 @@ stage_kernel_mixed(const MixedArgs a) {
 
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     // halo entirely inside the domain: no ghost folding for this tile
     const bool interior = (x0 >= 2) && (x0 + TX + 2 <= nx) && (y0 >= 2) && (y0 + TY + 2 <= ny);
     const CellLoad ld{a.qn32[0], a.qn32[1], a.qn32[2], din[0], din[1], din[2], din[3]};
@@ -312,13 +312,22 @@ stage_kernel_mixed(const MixedArgs a) {
         if (tid < 4) {
             double s = 0.0;
             for (int w = 0; w < NT / 32; ++w) s += sm.red[tid][w];
-            a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = s;
+            partial[tid] = s;
         }
     }
 }
 
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+stage_kernel_mixed(const MixedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.ctl->done) return;
+    mixed_tile<TX, TY, NT>(a, blockIdx.x, blockIdx.y,
+                           a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
+}
+
 // Global pseudo-time step option for the mixed form.
-__global__ void dtau_min_kernel_mixed(const MixedArgs a) {
+static __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
     const Ctl *ctl = a.ctl;
     if (ctl->done) return;
     const float *const *d = a.d[ctl->cur];
@@ -342,7 +351,7 @@ __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
 // Start of a physical step in the mixed form: the FP64 level absorbs the
 // increments (Q^n <- Q^n + dQ, Alg. 1), its FP32 copy is refreshed, the
 // increments restart from zero, and p' is kept for a restore.
-__global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters) {
+static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters) {
     Ctl *ctl = a.ctl;
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
@@ -370,7 +379,7 @@ __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol
 }
 
 // After a non-finite residual: back to the state at the start of the step.
-__global__ void restore_kernel_mixed(const MixedArgs a) {
+static __global__ void restore_kernel_mixed(const MixedArgs a) {
     const int cur = a.ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {

@@ -1,0 +1,122 @@
+"""Batched tanks (ac_batch_*) through the C ABI.
+
+A tank's numbers must not depend on the rest of the batch: with a fixed
+number of pseudo-iterations every tank equals a single-tank context in the
+mixed form bit for bit (whatever tile shapes the two autotuners pick), and
+with the stopping test on every tank stops at its own iteration count, the
+same as alone when both use one tile shape.  Against the FP64 oracle each
+tank stays within the mixed form's 1e-5 relative field error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_errors
+from paper_2108_08769_gb300 import ac
+from paper_2108_08769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def uneven_cases():
+    cases = W.batched_tanks(count=6, nmin=20, nmax=90, seed=11)
+    # add tanks of other kinds: ragged rectangle, open sides, periodic x
+    cases.append(W.random_two_fluid(37, 19, ratio=300.0, c0=8.0, seed=3))
+    cases.append(W.random_two_fluid(45, 21, ratio=50.0, c0=5.0, seed=4,
+                                    bc=("transmissive", "slip", "noslip", "slip")))
+    cases.append(W.random_two_fluid(33, 17, ratio=20.0, c0=4.0, seed=5,
+                                    bc=("periodic", "periodic", "slip", "slip")))
+    return cases
+
+
+def single_mixed(case, dt, tol, iters):
+    t = ac.Tank.from_case(case, precision="mixed")
+    rc, n = t.physical_step(dt, tol, iters)
+    s = t.get_state()
+    R, _ = t.residual_norms()
+    t.close()
+    return s, n, R
+
+
+def test_batch_equals_single_tanks_bitwise_fixed_iterations():
+    cases = uneven_cases()
+    b = ac.Batch.from_cases(cases)
+    rc, its, st = b.physical_step(1e-3, -1.0, 7)
+    assert its == [7] * len(cases) and st == [ac.AC_OK] * len(cases)
+    for k, c in enumerate(cases):
+        got = b.get_state(k)
+        ref, _, _ = single_mixed(c, 1e-3, -1.0, 7)
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y), k
+    assert b.tile_shape()[0] > 0
+    b.close()
+
+
+def test_batch_against_oracle():
+    cases = uneven_cases()[:4] + uneven_cases()[6:]
+    b = ac.Batch.from_cases(cases)
+    b.physical_step(1e-3, -1.0, 8)
+    for k, c in enumerate(cases):
+        ref, *_ = oracle.physical_step(c, c.state(), dt=1e-3, tol=-1.0, max_iters=8)
+        errs = rel_errors(b.get_state(k), ref)
+        assert max(errs) <= 1e-5, (k, errs)
+    b.close()
+
+
+def test_per_tank_convergence_flags_and_counts(monkeypatch):
+    """Each tank stops on its own test; counts and states equal the tank
+    run alone (one tile shape for both, so the norms are summed alike).
+    Absolute residual floors, as the paper's own stopping rules are (the
+    relative drop cannot pass here: the first iteration's rho v residual is
+    round-off in columns that start in vertical balance)."""
+    monkeypatch.setenv("AC_TILE", "0")
+    cases = W.batched_tanks(count=5, nmin=16, nmax=48, seed=21)
+    for c in cases:
+        c.options.abs_tol = (0.03, 0.3, 0.3, 100.0)
+    b = ac.Batch.from_cases(cases)
+    rc, its, st = b.physical_step(1e-3, 0.0, 2500)
+    assert rc == ac.AC_OK and st == [ac.AC_OK] * len(cases), (rc, st)
+    assert len(set(its)) == len(cases), its    # each tank stops at its own count
+    for k, c in enumerate(cases):
+        ref, n, R = single_mixed(c, 1e-3, 0.0, 2500)
+        assert its[k] == n, (k, its[k], n)
+        for x, y in zip(b.get_state(k), ref):
+            assert np.array_equal(x, y)
+        bR, _ = b.residual_norms(k)
+        assert np.array_equal(bR, R)
+    b.close()
+
+
+def test_two_physical_steps_and_levels():
+    cases = W.batched_tanks(count=3, nmin=30, nmax=60, seed=5)
+    b = ac.Batch.from_cases(cases)
+    singles = [ac.Tank.from_case(c, precision="mixed") for c in cases]
+    for step in range(2):
+        b.physical_step([1e-3, 2e-3, 5e-4], -1.0, 5)
+        for t, dt in zip(singles, [1e-3, 2e-3, 5e-4]):
+            t.physical_step(dt, -1.0, 5)
+    for k, t in enumerate(singles):
+        for x, y in zip(b.get_state(k), t.get_state()):
+            assert np.array_equal(x, y)
+        t.close()
+    b.close()
+
+
+def test_nonfinite_tank_is_restored_alone():
+    """A pseudo-CFL far beyond stability blows up the dynamic tank; the
+    hydrostatic tank beside it is an exact steady state in the mixed form
+    (zero residual, so any CFL leaves it put) and runs all its iterations."""
+    rest = W.hydrostatic_tank(32)
+    bad = W.random_two_fluid(32, 16, ratio=1000.0, c0=20.0, seed=2)
+    o = ac.options_from(bad.options, "mixed")
+    o.cfl_tau = 40.0
+    b = ac.Batch.from_cases([rest, bad], options=o)
+    before = b.get_state(1)
+    with pytest.raises(ac.ACError) as e:
+        b.physical_step(1e-3, -1.0, 300)
+    assert e.value.code == ac.AC_ERR_NONFINITE
+    for x, y in zip(before, b.get_state(1)):
+        assert np.array_equal(x, y)
+    got = b.get_state(0)
+    assert np.abs(got[2]).max() == 0.0 and np.array_equal(got[0], rest.rho)
+    b.close()
