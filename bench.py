@@ -243,13 +243,8 @@ def run_ours(args, ws, rank, local):
         dev_ms, iters, launches = timed_steps(tank, case, args.steps, stream, flush, barrier)
         wall = time.perf_counter() - wall0
     f64_state = tank.get_state()
-    t_max = dev_ms
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * case.cells * sum(iters) / (t_max * 1e-3)
+    from paper_2108_08769_gb300.replicas import aggregate
+    _, t_max, value = aggregate(case.cells * sum(iters), dev_ms, device=dev)
 
     # ---- e2e: host buffers through the public API ----
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.state()]

@@ -67,7 +67,16 @@ int fail(int code, const char *fmt, ...) {
                         __LINE__);                                                          \
     } while (0)
 
-constexpr int kTX = 32, kTY = 8;
+// Largest tile count any tile shape of either form produces on an nx x ny
+// grid (sizes the residual partial sums).
+size_t max_tiles(int nx, int ny) {
+    static const int shapes[][2] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16},
+                                    {32, 16}, {64, 8}, {64, 16}};
+    size_t m = 0;
+    for (const auto &sh : shapes)
+        m = std::max(m, (size_t)((nx + sh[0] - 1) / sh[0]) * ((ny + sh[1] - 1) / sh[1]));
+    return m;
+}
 constexpr int kEndThreads = 256;
 constexpr int kGridStrideBlocks = 152 * 8;
 
@@ -127,11 +136,93 @@ struct Backend {
 
 // ------------------------------------------------------------------ FP64
 
+// Tile shapes of the FP64 sweep (one thread per cell).  The FP64 pipe bounds
+// this sweep, so the shapes differ mainly in how evenly the CTAs fill the
+// SMs: small grids favour shapes whose CTA count is near a multiple of the
+// SM count.
+struct F64Variant {
+    int tx, ty;
+};
+constexpr F64Variant kF64Variants[] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16}};
+constexpr int kNumF64Variants = sizeof(kF64Variants) / sizeof(kF64Variants[0]);
+
+template <int TX, int TY>
+cudaError_t allow_f64_smem() {
+    return cudaFuncSetAttribute(stage_kernel<double, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(StageSmem<double, TX, TY>));
+}
+
+template <int TX, int TY>
+cudaError_t launch_f64(const SweepArgs<double> &a, dim3 g, cudaStream_t s) {
+    stage_kernel<double, TX, TY><<<g, TX * TY, sizeof(StageSmem<double, TX, TY>), s>>>(a);
+    return cudaGetLastError();
+}
+
+std::vector<std::pair<std::pair<int, int>, int>> g_tuned_f64;
+
 struct F64Backend : Backend {
+    int variant = -1;
     double *buf[3][4] = {};
     double *lev[4] = {};
 
-    static size_t smem() { return sizeof(StageSmem<double, kTX, kTY>); }
+    void set_variant(const ac_ctx *c, int v) {
+        variant = v;
+        const F64Variant &m = kF64Variants[v];
+        grid = dim3((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
+        nblocks = grid.x * grid.y;
+    }
+
+    int launch(const ac_ctx *c, cudaStream_t s, int st, int v) const {
+        const SweepArgs<double> a = args(c, st);
+        const F64Variant &m = kF64Variants[v];
+        const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
+        cudaError_t e;
+        switch (v) {
+            case 0: e = launch_f64<32, 8>(a, g, s); break;
+            case 1: e = launch_f64<32, 7>(a, g, s); break;
+            case 2: e = launch_f64<32, 6>(a, g, s); break;
+            case 3: e = launch_f64<32, 4>(a, g, s); break;
+            case 4: e = launch_f64<16, 8>(a, g, s); break;
+            default: e = launch_f64<16, 16>(a, g, s); break;
+        }
+        if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stage sweep launch failed: %s", cudaGetErrorString(e));
+        return AC_OK;
+    }
+
+    // Autotuner: stage 1 of every shape on this grid (writes only scratch),
+    // fastest kept per grid size.
+    int tune(ac_ctx *c, cudaStream_t s) override {
+        if (variant >= 0) return AC_OK;
+        const char *env = getenv("AC_TILE_F64");
+        if (env) {
+            const int v = atoi(env);
+            if (v >= 0 && v < kNumF64Variants) { set_variant(c, v); return AC_OK; }
+        }
+        for (auto &kv : g_tuned_f64)
+            if (kv.first.first == c->grid.nx && kv.first.second == c->grid.ny) {
+                set_variant(c, kv.second);
+                return AC_OK;
+            }
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int v = 0; v < kNumF64Variants; ++v) {
+            int rc;
+            for (int w = 0; w < 1; ++w)
+                if ((rc = launch(c, s, 1, v)) != AC_OK) return rc;
+            CK(cudaEventRecord(c->ev[0], s));
+            for (int r = 0; r < 3; ++r)
+                if ((rc = launch(c, s, 1, v)) != AC_OK) return rc;
+            CK(cudaEventRecord(c->ev[1], s));
+            CK(cudaEventSynchronize(c->ev[1]));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            c->launches += 4;
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        set_variant(c, best);
+        g_tuned_f64.push_back({{c->grid.nx, c->grid.ny}, best});
+        return AC_OK;
+    }
 
     SweepArgs<double> args(const ac_ctx *c, int stage) const {
         SweepArgs<double> a;
@@ -155,14 +246,18 @@ struct F64Backend : Backend {
         return a;
     }
     int alloc(ac_ctx *c) override {
-        grid = dim3((c->grid.nx + kTX - 1) / kTX, (c->grid.ny + kTY - 1) / kTY);
-        nblocks = grid.x * grid.y;
+        set_variant(c, 0);
+        variant = -1;   // tuned at the first physical step
         const size_t bytes = c->N * sizeof(double);
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) CK(cudaMalloc(&buf[b][f], bytes));
         for (int f = 0; f < 4; ++f) CK(cudaMalloc(&lev[f], bytes));
-        CK(cudaFuncSetAttribute(stage_kernel<double, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem()));
+        CK((allow_f64_smem<32, 8>()));
+        CK((allow_f64_smem<32, 7>()));
+        CK((allow_f64_smem<32, 6>()));
+        CK((allow_f64_smem<32, 4>()));
+        CK((allow_f64_smem<16, 8>()));
+        CK((allow_f64_smem<16, 16>()));
         return AC_OK;
     }
     void release() override {
@@ -209,11 +304,7 @@ struct F64Backend : Backend {
         CK(cudaGetLastError());
         return AC_OK;
     }
-    int stage(ac_ctx *c, cudaStream_t s, int st) override {
-        stage_kernel<double, kTX, kTY><<<grid, kTX * kTY, smem(), s>>>(args(c, st));
-        CK(cudaGetLastError());
-        return AC_OK;
-    }
+    int stage(ac_ctx *c, cudaStream_t s, int st) override { return launch(c, s, st, variant < 0 ? 0 : variant); }
     int restore(ac_ctx *c, cudaStream_t s) override {
         // Q <- Q^n (all four fields hold the state of the start of the step)
         for (int f = 0; f < 4; ++f)
@@ -602,9 +693,7 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     CKC(cudaGetDevice(&c->device));
     int rc = c->be->alloc(c);
     if (rc != AC_OK) return bail(rc);
-    // partial sums for the smallest tile (16 x 8 cells) any backend uses
-    const size_t max_blocks = (size_t)((grid->nx + 15) / 16) * ((grid->ny + 7) / 8);
-    CKC(cudaMalloc(&c->partials, max_blocks * 4 * sizeof(double)));
+    CKC(cudaMalloc(&c->partials, max_tiles(grid->nx, grid->ny) * 4 * sizeof(double)));
     CKC(cudaMalloc(&c->ctl, sizeof(Ctl)));
     CKC(cudaMallocHost(&c->hctl, sizeof(Ctl)));
     CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));

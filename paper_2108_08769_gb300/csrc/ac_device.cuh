@@ -28,6 +28,7 @@ template <> struct Ar<double> {
         rs = 1.0 / s;
     }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
 };
 template <> struct Ar<float> {
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
@@ -36,6 +37,7 @@ template <> struct Ar<float> {
         s = x * rs;
     }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
 };
 
 // ---------------------------------------------------------------------------

@@ -250,12 +250,12 @@ stage_kernel(const SweepArgs<T> a) {
             const T u = m0 * ir, v = n0 * ir, fb = T(4) * a.beta * ir;
             const T cx = Ar<T>::sqrt_(u * u + fb), cy = Ar<T>::sqrt_(v * v + fb);
             const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
-            dtau = a.cfl_area / den;
+            dtau = Ar<T>::div(a.cfl_area, den);
         } else {
             dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
         }
         const T api = T(1) + a.alpha * dtau * inv_dt;      // Eq. point_implicit, B0 = 1
-        const T coef = a.alpha * dtau / api;
+        const T coef = Ar<T>::div(a.alpha * dtau, api);
         const T coef_p = a.alpha_pi_p_row ? coef : a.alpha * dtau;
         qout[0][g] = r0 + coef * b0;
         qout[1][g] = m0 + coef * b1;
@@ -302,7 +302,7 @@ __global__ void dtau_min_kernel(const SweepArgs<T> a) {
         const T u = q[1][g] * ir, v = q[2][g] * ir, fb = T(4) * a.beta * ir;
         const T cx = Ar<T>::sqrt_(u * u + fb), cy = Ar<T>::sqrt_(v * v + fb);
         const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
-        mn = fmin(mn, double(a.cfl_area / den));
+        mn = fmin(mn, double(Ar<T>::div(a.cfl_area, den)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));

@@ -61,34 +61,52 @@ struct MixedSmem {
     static constexpr int GW = TX + 2, GH = TY + 2;
     static constexpr int NXF = (TX + 1) * TY;
     static constexpr int NYF = TX * (TY + 1);
-    float w[4][RW * RH];       // rho, u, v, p'
-    float rt[2][GW * GH];      // frozen real-time term of rho u, rho v
-    float rr[GW * GH];         // reference density on the ring
-    float gx[4][GW * GH];      // half slopes along x
-    float gy[4][GW * GH];      // half slopes along y (p: of p - p_ref)
-    float fx[4][NXF];
-    float fy[4][NYF];
-    float dxf[NXF];            // reference jump on each x-face
+    // one 16-byte vector per cell or face: a face or a cell reads all four
+    // components with one shared-memory instruction
+    float4 w[RW * RH];       // (rho, u, v, p') of the tile + two-cell halo
+    float4 aux[GW * GH];     // (RT of rho u, RT of rho v, rho_ref, -) on the ring
+    float4 gx[GW * GH];      // half slopes along x: (rho, u, v, p)
+    float4 gy[GW * GH];      // half slopes along y: (rho, u, v, p - p_ref)
+    float4 fx[NXF];          // x-face fluxes: (mass, x-mom, y-mom, p/beta)
+    float4 fy[NYF];          // y-face fluxes
+    float dxf[NXF];          // reference jump on each x-face
     double red[4][32];
 };
 
-// Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell into W (interior or folded).
+// Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell as W = (rho, u, v, p').
 struct CellLoad {
     const float *__restrict__ qn0, *__restrict__ qn1, *__restrict__ qn2;
     const float *__restrict__ d0, *__restrict__ d1, *__restrict__ d2, *__restrict__ d3;
-    __device__ __forceinline__ void operator()(int s, bool fx, bool fy, float &r, float &u, float &v,
-                                               float &p) const {
-        r = __ldg(qn0 + s) + d0[s];
+    __device__ __forceinline__ float4 operator()(int s, bool fx, bool fy) const {
+        const float r = __ldg(qn0 + s) + d0[s];
         float m = __ldg(qn1 + s) + d1[s];
         float n = __ldg(qn2 + s) + d2[s];
         m = fx ? -m : m;
         n = fy ? -n : n;
         const float ir = Ar<float>::rcp(r);
-        u = m * ir;
-        v = n * ir;
-        p = d3[s];
+        return make_float4(r, m * ir, n * ir, d3[s]);
     }
 };
+
+__device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, const float4 &w, const float4 &n,
+                                             const float4 &s, int k, float klim, float &hrx, float &hry,
+                                             float &hux, float &huy, float &hvx, float &hvy) {
+    if (k == 1) {
+        hrx = half_minmod(e.x - c.x, c.x - w.x);
+        hry = half_minmod(n.x - c.x, c.x - s.x);
+        hux = half_minmod(e.y - c.y, c.y - w.y);
+        huy = half_minmod(n.y - c.y, c.y - s.y);
+        hvx = half_minmod(e.z - c.z, c.z - w.z);
+        hvy = half_minmod(n.z - c.z, c.z - s.z);
+    } else {
+        hrx = 0.5f * limiter(e.x - c.x, c.x - w.x, klim);
+        hry = 0.5f * limiter(n.x - c.x, c.x - s.x, klim);
+        hux = 0.5f * limiter(e.y - c.y, c.y - w.y, klim);
+        huy = 0.5f * limiter(n.y - c.y, c.y - s.y, klim);
+        hvx = 0.5f * limiter(e.z - c.z, c.z - w.z, klim);
+        hvy = 0.5f * limiter(n.z - c.z, c.z - s.z, klim);
+    }
+}
 
 // One TX x TY tile (tile coordinates bx, by) of one stage of one tank, by
 // a CTA of NT threads (NT divides TX*TY; several cells per thread in the
@@ -123,9 +141,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const int base = (y0 - 2) * nx + (x0 - 2);
         for (int k = tid; k < RW * RH; k += NT) {
             const int rr = k / RW, cc = k - rr * RW;
-            float r, u, v, p;
-            ld(base + rr * nx + cc, false, false, r, u, v, p);
-            sm.w[0][k] = r; sm.w[1][k] = u; sm.w[2][k] = v; sm.w[3][k] = p;
+            sm.w[k] = ld(base + rr * nx + cc, false, false);
         }
     } else {
         for (int k = tid; k < RW * RH; k += NT) {
@@ -133,9 +149,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             int nfx, tfx, nfy, tfy;
             const int si = fold_axis(x0 + cc - 2, nx, a.bc[0], a.bc[1], nfx, tfx);
             const int sj = fold_axis(y0 + rr - 2, ny, a.bc[2], a.bc[3], nfy, tfy);
-            float r, u, v, p;
-            ld(sj * nx + si, (nfx + tfy) & 1, (nfy + tfx) & 1, r, u, v, p);
-            sm.w[0][k] = r; sm.w[1][k] = u; sm.w[2][k] = v; sm.w[3][k] = p;
+            sm.w[k] = ld(sj * nx + si, (nfx + tfy) & 1, (nfy + tfx) & 1);
         }
     }
     const bool new_gradp = (a.gradp == kGradNew);
@@ -157,13 +171,14 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
                 fx = (nfx + tfy) & 1;
                 fy = (nfy + tfx) & 1;
             }
+            float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                const float rx = e1[s] * inv_dt;   // (Q^{m} - Q^n)/dt of rho u
-                const float ry = e2[s] * inv_dt;
-                sm.rt[0][k] = fx ? -rx : rx;
-                sm.rt[1][k] = fy ? -ry : ry;
+                rx = e1[s] * inv_dt;   // (Q^{m} - Q^n)/dt of rho u
+                ry = e2[s] * inv_dt;
+                rx = fx ? -rx : rx;
+                ry = fy ? -ry : ry;
             }
-            sm.rr[k] = __ldg(rref + s);
+            sm.aux[k] = make_float4(rx, ry, __ldg(rref + s), 0.0f);
         }
     }
     __syncthreads();
@@ -174,43 +189,27 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
     for (int k = tid; k < GW * GH; k += NT) {
         const int lj = k / GW, li = k - lj * GW;
         const int c = (lj + 1) * RW + (li + 1);
-        const int e = c + 1, wv = c - 1, nn = c + RW, ss = c - RW;
-        const float *R = sm.w[0], *U = sm.w[1], *V = sm.w[2], *P = sm.w[3];
+        const float4 Wc = sm.w[c], We = sm.w[c + 1], Ww = sm.w[c - 1], Wn = sm.w[c + RW], Ws = sm.w[c - RW];
         float hrx, hry, hux, huy, hvx, hvy;
-        if (a.limiter_k == 1) {
-            hrx = half_minmod(R[e] - R[c], R[c] - R[wv]);
-            hry = half_minmod(R[nn] - R[c], R[c] - R[ss]);
-            hux = half_minmod(U[e] - U[c], U[c] - U[wv]);
-            huy = half_minmod(U[nn] - U[c], U[c] - U[ss]);
-            hvx = half_minmod(V[e] - V[c], V[c] - V[wv]);
-            hvy = half_minmod(V[nn] - V[c], V[c] - V[ss]);
-        } else {
-            hrx = 0.5f * limiter(R[e] - R[c], R[c] - R[wv], klim);
-            hry = 0.5f * limiter(R[nn] - R[c], R[c] - R[ss], klim);
-            hux = 0.5f * limiter(U[e] - U[c], U[c] - U[wv], klim);
-            huy = 0.5f * limiter(U[nn] - U[c], U[c] - U[ss], klim);
-            hvx = 0.5f * limiter(V[e] - V[c], V[c] - V[wv], klim);
-            hvy = 0.5f * limiter(V[nn] - V[c], V[c] - V[ss], klim);
-        }
+        limit_slopes(Wc, We, Ww, Wn, Ws, a.limiter_k, klim, hrx, hry, hux, huy, hvx, hvy);
         float hpx, hpy;
         if (new_gradp) {
             float sg = 1.0f;
             if (!interior) sg = wall_ghost_sign<float>(x0 + li - 1, y0 + lj - 1, nx, ny, a.bc);
-            const float rho = R[c], u = U[c], v = V[c];
-            const float rtx = need_rt ? sm.rt[0][k] : 0.0f;
-            const float rty = need_rt ? sm.rt[1][k] : 0.0f;
+            const float4 ax = sm.aux[k];
+            const float rho = Wc.x, u = Wc.y, v = Wc.z;
             const float ru = rho * u, rv = rho * v, uv = u * v;
-            hpx = -a.half_dx * rtx - (u * u * hrx + 2.0f * ru * hux) -
+            hpx = -a.half_dx * ax.x - (u * u * hrx + 2.0f * ru * hux) -
                   a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
             // slope of p - p_ref: the reference slope rho_ref g_y is removed
-            hpy = -a.half_dy * rty - (v * v * hry + 2.0f * rv * hvy) -
-                  a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - sm.rr[k]) * a.gy * sg;
+            hpy = -a.half_dy * ax.y - (v * v * hry + 2.0f * rv * hvy) -
+                  a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - ax.z) * a.gy * sg;
         } else {
-            hpx = 0.5f * limiter(P[e] - P[c], P[c] - P[wv], kp);
-            hpy = 0.5f * limiter(P[nn] - P[c], P[c] - P[ss], kp);
+            hpx = 0.5f * limiter(We.w - Wc.w, Wc.w - Ww.w, kp);
+            hpy = 0.5f * limiter(Wn.w - Wc.w, Wc.w - Ws.w, kp);
         }
-        sm.gx[0][k] = hrx; sm.gx[1][k] = hux; sm.gx[2][k] = hvx; sm.gx[3][k] = hpx;
-        sm.gy[0][k] = hry; sm.gy[1][k] = huy; sm.gy[2][k] = hvy; sm.gy[3][k] = hpy;
+        sm.gx[k] = make_float4(hrx, hux, hvx, hpx);
+        sm.gy[k] = make_float4(hry, huy, hvy, hpy);
     }
     __syncthreads();
 
@@ -227,26 +226,24 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
                 else if (gi == nx && per_x) jump = __ldg(a.dref + gj * nx);
             }
             sm.dxf[k] = jump;
-            const int ga = (fj + 1) * GW + fi, gb = ga + 1;
-            const int ca = (fj + 2) * RW + fi + 1, cb = ca + 1;
-            const float rL = sm.w[0][ca] + sm.gx[0][ga], rR = sm.w[0][cb] - sm.gx[0][gb];
-            const float uL = sm.w[1][ca] + sm.gx[1][ga], uR = sm.w[1][cb] - sm.gx[1][gb];
-            const float vL = sm.w[2][ca] + sm.gx[2][ga], vR = sm.w[2][cb] - sm.gx[2][gb];
-            const float pL = sm.w[3][ca] + sm.gx[3][ga] - 0.5f * jump;
-            const float pR = sm.w[3][cb] - sm.gx[3][gb] + 0.5f * jump;
-            osher_flux<float>(rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
-            sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
+            const int ga = (fj + 1) * GW + fi;
+            const int ca = (fj + 2) * RW + fi + 1;
+            const float4 A = sm.w[ca], B = sm.w[ca + 1], SA = sm.gx[ga], SB = sm.gx[ga + 1];
+            osher_flux<float>(A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
+                              B.x - SB.x, B.y - SB.y, B.z - SB.z, B.w - SB.w + 0.5f * jump,
+                              a.beta, a.inv_beta, F);
+            sm.fx[k] = make_float4(F[0], F[1], F[2], F[3]);
         } else {
             const int kk = k - S::NXF;
             const int fj = kk / TX, fi = kk - fj * TX;
-            const int ga = fj * GW + fi + 1, gb = ga + GW;
-            const int ca = (fj + 1) * RW + fi + 2, cb = ca + RW;
-            const float rL = sm.w[0][ca] + sm.gy[0][ga], rR = sm.w[0][cb] - sm.gy[0][gb];
-            const float uL = sm.w[1][ca] + sm.gy[1][ga], uR = sm.w[1][cb] - sm.gy[1][gb];
-            const float vL = sm.w[2][ca] + sm.gy[2][ga], vR = sm.w[2][cb] - sm.gy[2][gb];
-            const float pL = sm.w[3][ca] + sm.gy[3][ga], pR = sm.w[3][cb] - sm.gy[3][gb];
-            osher_flux<float>(rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
-            sm.fy[0][kk] = F[0]; sm.fy[1][kk] = F[2]; sm.fy[2][kk] = F[1]; sm.fy[3][kk] = F[3];
+            const int ga = fj * GW + fi + 1;
+            const int ca = (fj + 1) * RW + fi + 2;
+            const float4 A = sm.w[ca], B = sm.w[ca + RW], SA = sm.gy[ga], SB = sm.gy[ga + GW];
+            // rotation (Alg. 2, n = y): normal velocity v, tangential u
+            osher_flux<float>(A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
+                              B.x - SB.x, B.z - SB.z, B.y - SB.y, B.w - SB.w,
+                              a.beta, a.inv_beta, F);
+            sm.fy[kk] = make_float4(F[0], F[2], F[1], F[3]);
         }
     }
     __syncthreads();
@@ -259,23 +256,23 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const int gi = x0 + li, gj = y0 + lj;
         if (gi >= nx || gj >= ny) continue;
         const int g = gj * nx + gi;
-        const int fw = lj * (TX + 1) + li, fe = fw + 1;
-        const int fs = cell, fn = fs + TX;
-        float div[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-            div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * a.inv_dx + (sm.fy[f][fn] - sm.fy[f][fs]) * a.inv_dy;
+        const int fw = lj * (TX + 1) + li;
+        const float4 Fw = sm.fx[fw], Fe = sm.fx[fw + 1], Fs = sm.fy[cell], Fn = sm.fy[cell + TX];
+        const float div0 = (Fe.x - Fw.x) * a.inv_dx + (Fn.x - Fs.x) * a.inv_dy;
+        const float div1 = (Fe.y - Fw.y) * a.inv_dx + (Fn.y - Fs.y) * a.inv_dy;
+        const float div2 = (Fe.z - Fw.z) * a.inv_dx + (Fn.z - Fs.z) * a.inv_dy;
+        const float div3 = (Fe.w - Fw.w) * a.inv_dx + (Fn.w - Fs.w) * a.inv_dy;
         const float e0 = d0[0][g], e1 = d0[1][g], e2 = d0[2][g], p0 = d0[3][g];
         const float r0 = __ldg(a.qn32[0] + g) + e0;
         const float m0 = __ldg(a.qn32[1] + g) + e1;
         const float n0 = __ldg(a.qn32[2] + g) + e2;
         const float rt0 = e0 * inv_dt, rt1 = e1 * inv_dt, rt2 = e2 * inv_dt;
         // reference force: -(divergence of the x-face reference means)
-        const float sref = -0.5f * (sm.dxf[fe] + sm.dxf[fw]) * a.inv_dx;
-        const float b0 = -div[0] - rt0;
-        const float b1 = -div[1] - rt1 + r0 * a.gx + sref;
-        const float b2 = -div[2] - rt2 + (r0 - __ldg(a.rho_ref + g)) * a.gy;
-        const float b3 = -div[3];
+        const float sref = -0.5f * (sm.dxf[fw + 1] + sm.dxf[fw]) * a.inv_dx;
+        const float b0 = -div0 - rt0;
+        const float b1 = -div1 - rt1 + r0 * a.gx + sref;
+        const float b2 = -div2 - rt2 + (r0 - __ldg(a.rho_ref + g)) * a.gy;
+        const float b3 = -div3;
         float dtau;
         if (a.local_dtau) {
             const float ir = Ar<float>::rcp(r0);
