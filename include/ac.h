@@ -57,9 +57,13 @@ extern "C" {
 #define AC_GRADP_NEW 0         /* rearranged momentum equation (Eq. new_gradp), default */
 #define AC_GRADP_MINMOD 1      /* standard k-limiter on p, k = 1 */
 #define AC_GRADP_SUPERBEE 2    /* standard k-limiter on p, k = 2 */
+#define AC_GRADP_SPLIT_MINMOD 3   /* Qian et al. hydrostatic/kinematic split, k = 1 */
+#define AC_GRADP_SPLIT_SUPERBEE 4 /* Qian et al. hydrostatic/kinematic split, k = 2 */
 
 /* ---- Riemann solvers (Sec. 2.4) ---------------------------------------- */
 #define AC_RIEMANN_OSHER 0     /* Dumbser-Toro Osher flux, 3-point Gauss path (default) */
+#define AC_RIEMANN_BASSI 1     /* flux of the exact solution of Bassi et al. (Sec. 2.4.1) */
+#define AC_RIEMANN_ROE 2       /* Roe flux with the Roe averages of Sec. 2.4.2 */
 
 /* ---- arithmetic -------------------------------------------------------- */
 #define AC_PREC_FP64 0         /* every step in FP64 */
@@ -91,6 +95,9 @@ typedef struct {
     int precision;       /* AC_PREC_* (default AC_PREC_FP64) */
     double cfl_tau;      /* pseudo-time Courant number (default 0.45) */
     double abs_tol[4];   /* absolute residual floors for rho, rho u, rho v, p (default 0) */
+    int bdf_order;       /* real-time derivative (Eq. bdf, Table BDF): 1 Backward-Euler (default),
+                            2 BDF2, 3 BDF3; a context's first step after ac_set_state is always
+                            Backward-Euler, its second at most BDF2 (Sec. 2.2.2) */
 } ac_options;
 
 typedef struct ac_ctx ac_ctx;
@@ -146,10 +153,17 @@ int ac_physical_step(ac_ctx *ctx, double dt, double tol, int max_iters, int *ite
  * rho v, p), out0[4] (may be NULL) = first-iteration R0. */
 int ac_residual_norms(const ac_ctx *ctx, double out[4], double out0[4]);
 
-/* Real-time level Q^n (rho, rho u, rho v) of the last physical step, for
- * checkpointing; ac_set_levels restores it (same layout as ac_set_state). */
-int ac_get_levels(const ac_ctx *ctx, double *rho_n, double *rhou_n, double *rhov_n);
-int ac_set_levels(ac_ctx *ctx, const double *rho_n, const double *rhou_n, const double *rhov_n);
+/* Real-time history, for checkpointing and for BDF2/BDF3: level k (1 or 2)
+ * is (rho, rho u, rho v) of the state k physical steps before the current
+ * one.  Level 1 exists after one step (or ac_set_history(ctx, 1, ...)),
+ * level 2 after two steps and only when bdf_order >= 2.  Restoring a
+ * checkpoint: ac_set_state, then ac_set_history for level 1, then level 2.
+ * ac_set_state forgets the history; so does a step that fails with
+ * AC_ERR_NONFINITE (the next step is Backward-Euler).
+ * Errors: AC_ERR_ARG (k out of range, level 2 without bdf_order >= 2),
+ * AC_ERR_STATE (level not available yet, or level 2 set before level 1). */
+int ac_get_history(const ac_ctx *ctx, int k, double *rho, double *rhou, double *rhov);
+int ac_set_history(ac_ctx *ctx, int k, const double *rho, const double *rhou, const double *rhov);
 
 /* Number of kernels this context has launched since creation (device work
  * inside captured graphs is counted per replay). */
@@ -221,7 +235,8 @@ long long ac_batch_kernel_launches(const ac_batch *b);
  *   norms   device array of 4 doubles receiving the residual norms R of
  *           the stage-1 bracket (stage 1 only; may be NULL)
  * grid, beta, bc and opt mean what they mean for ac_create; opt->precision
- * must be AC_PREC_FP64; stage is 1..opt->rk_stages; dt as in
+ * must be AC_PREC_FP64 and opt->bdf_order 1 (Backward-Euler real-time
+ * term); stage is 1..opt->rk_stages; dt as in
  * ac_physical_step.  Work is enqueued on `stream` (a cudaStream_t; NULL =
  * default stream) and the call returns without waiting.
  *

@@ -27,15 +27,15 @@ AC_ERR_OOM = -5
 AC_ERR_STATE = -6
 
 BC = {"slip": 0, "noslip": 1, "transmissive": 2, "periodic": 3}
-GRADP = {"new": 0, "minmod": 1, "superbee": 2}
-RIEMANN = {"osher": 0}
+GRADP = {"new": 0, "minmod": 1, "superbee": 2, "split_minmod": 3, "split_superbee": 4}
+RIEMANN = {"osher": 0, "bassi": 1, "roe": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 
 # every entry point include/ac.h declares
 EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
-    "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_levels",
-    "ac_set_levels", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
+    "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_history",
+    "ac_set_history", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
     "ac_stage_sweep_noalloc", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
     "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
     "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
@@ -58,7 +58,8 @@ class ac_bc(C.Structure):
 class ac_options(C.Structure):
     _fields_ = [("rk_stages", C.c_int), ("riemann", C.c_int), ("gradp", C.c_int), ("limiter_k", C.c_int),
                 ("local_dtau", C.c_int), ("realtime", C.c_int), ("alpha_pi_p_row", C.c_int),
-                ("precision", C.c_int), ("cfl_tau", C.c_double), ("abs_tol", C.c_double * 4)]
+                ("precision", C.c_int), ("cfl_tau", C.c_double), ("abs_tol", C.c_double * 4),
+                ("bdf_order", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -96,8 +97,8 @@ def load(build: bool = True):
     L.ac_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
     L.ac_physical_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.ac_residual_norms.argtypes = [C.c_void_p, _D, _D]
-    L.ac_get_levels.argtypes = [C.c_void_p, _D, _D, _D]
-    L.ac_set_levels.argtypes = [C.c_void_p, _D, _D, _D]
+    L.ac_get_history.argtypes = [C.c_void_p, C.c_int, _D, _D, _D]
+    L.ac_set_history.argtypes = [C.c_void_p, C.c_int, _D, _D, _D]
     L.ac_kernel_launches.argtypes = [C.c_void_p]
     L.ac_kernel_launches.restype = C.c_longlong
     L.ac_set_profiling.argtypes = [C.c_void_p, C.c_int]
@@ -174,6 +175,7 @@ def options_from(case_options, precision: str = "fp64") -> ac_options:
     o.cfl_tau = case_options.cfl_tau
     for k in range(4):
         o.abs_tol[k] = case_options.abs_tol[k]
+    o.bdf_order = case_options.bdf_order
     return o
 
 
@@ -260,6 +262,16 @@ class Tank:
         R0 = np.zeros(4)
         _check(load().ac_residual_norms(self._h, _ptr(R), _ptr(R0)))
         return R, R0
+
+    def get_history(self, k: int) -> Tuple[np.ndarray, ...]:
+        out = [np.empty((self.ny, self.nx)) for _ in range(3)]
+        _check(load().ac_get_history(self._h, k, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def set_history(self, k: int, rho, rhou, rhov):
+        n = self.nx * self.ny
+        arrs = [_host(a, n) for a in (rho, rhou, rhov)]
+        _check(load().ac_set_history(self._h, k, *[_ptr(a) for a in arrs]))
 
     def kernel_launches(self) -> int:
         return load().ac_kernel_launches(self._h)

@@ -111,6 +111,9 @@ struct ac_ctx {
     cudaEvent_t ev[5];
     double stage_ms;
     long long stage_launches;
+    int nhist;            // older real-time levels held (0..2) before the next step
+    int order_now;        // backward-difference order of the current step
+    int graph_order;      // order the captured graph was built for
 };
 
 namespace {
@@ -126,12 +129,20 @@ struct Backend {
     virtual void release() = 0;
     virtual int set_state(ac_ctx *c, const double *const f[4]) = 0;
     virtual int get_state(const ac_ctx *c, double *const out[4]) = 0;
-    virtual int get_levels(const ac_ctx *c, double *const out[3]) = 0;
-    virtual int set_levels(ac_ctx *c, const double *const in[3]) = 0;
+    virtual int get_history(const ac_ctx *c, int k, double *const out[3]) = 0;
+    virtual int set_history(ac_ctx *c, int k, const double *const in[3]) = 0;
     virtual int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) = 0;
     virtual int dtau_min(ac_ctx *c, cudaStream_t s) = 0;
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
+};
+
+// Backward-difference coefficients B0..B3 (Table BDF).
+const double kBDF[4][4] = {
+    {0.0, 0.0, 0.0, 0.0},
+    {1.0, -1.0, 0.0, 0.0},
+    {1.5, -2.0, 0.5, 0.0},
+    {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0},
 };
 
 // ------------------------------------------------------------------ FP64
@@ -164,6 +175,7 @@ struct F64Backend : Backend {
     int variant = -1;
     double *buf[3][4] = {};
     double *lev[4] = {};
+    double *lev1[3] = {}, *lev2[3] = {};   // Q^{n-1}, Q^{n-2} (BDF2, BDF3)
 
     void set_variant(const ac_ctx *c, int v) {
         variant = v;
@@ -230,6 +242,7 @@ struct F64Backend : Backend {
         a.nx = c->grid.nx; a.ny = c->grid.ny;
         a.bc[0] = c->bc.xlo; a.bc[1] = c->bc.xhi; a.bc[2] = c->bc.ylo; a.bc[3] = c->bc.yhi;
         a.gradp = c->opt.gradp; a.limiter_k = c->opt.limiter_k; a.realtime = c->opt.realtime;
+        a.riemann = c->opt.riemann;
         a.local_dtau = c->opt.local_dtau; a.alpha_pi_p_row = c->opt.alpha_pi_p_row;
         a.stage = stage; a.s_max = c->opt.rk_stages;
         a.alpha = stage > 0 ? 1.0 / double(c->opt.rk_stages - stage + 1) : 0.0;
@@ -241,6 +254,9 @@ struct F64Backend : Backend {
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) a.buf[b][f] = buf[b][f];
         for (int f = 0; f < 4; ++f) a.lev[f] = lev[f];
+        for (int f = 0; f < 3; ++f) { a.lev1[f] = lev1[f]; a.lev2[f] = lev2[f]; }
+        a.order = c->order_now;
+        for (int q = 0; q < 4; ++q) a.B[q] = kBDF[c->order_now][q];
         a.partials = c->partials;
         a.ctl = c->ctl;
         return a;
@@ -252,6 +268,10 @@ struct F64Backend : Backend {
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) CK(cudaMalloc(&buf[b][f], bytes));
         for (int f = 0; f < 4; ++f) CK(cudaMalloc(&lev[f], bytes));
+        for (int f = 0; f < 3; ++f) {
+            if (c->opt.bdf_order >= 2) CK(cudaMalloc(&lev1[f], bytes));
+            if (c->opt.bdf_order >= 3) CK(cudaMalloc(&lev2[f], bytes));
+        }
         CK((allow_f64_smem<32, 8>()));
         CK((allow_f64_smem<32, 7>()));
         CK((allow_f64_smem<32, 6>()));
@@ -264,6 +284,7 @@ struct F64Backend : Backend {
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) cudaFree(buf[b][f]);
         for (int f = 0; f < 4; ++f) cudaFree(lev[f]);
+        for (int f = 0; f < 3; ++f) { cudaFree(lev1[f]); cudaFree(lev2[f]); }
     }
     int set_state(ac_ctx *c, const double *const f[4]) override {
         const size_t bytes = c->N * sizeof(double);
@@ -281,16 +302,20 @@ struct F64Backend : Backend {
         CK(cudaStreamSynchronize(c->stream));
         return AC_OK;
     }
-    int get_levels(const ac_ctx *c, double *const out[3]) override {
-        for (int k = 0; k < 3; ++k)
-            if (out[k])
-                CK(cudaMemcpyAsync(out[k], lev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    // Between steps, history k (the state k physical steps back) is in
+    // lev (k = 1) and lev1 (k = 2); the step's begin shifts them to lev1, lev2.
+    int get_history(const ac_ctx *c, int k, double *const out[3]) override {
+        double *const *src = (k == 1) ? lev : lev1;
+        for (int f = 0; f < 3; ++f)
+            if (out[f])
+                CK(cudaMemcpyAsync(out[f], src[f], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         return AC_OK;
     }
-    int set_levels(ac_ctx *c, const double *const in[3]) override {
-        for (int k = 0; k < 3; ++k)
-            CK(cudaMemcpyAsync(lev[k], in[k], c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int set_history(ac_ctx *c, int k, const double *const in[3]) override {
+        double *const *dst = (k == 1) ? lev : lev1;
+        for (int f = 0; f < 3; ++f)
+            CK(cudaMemcpyAsync(dst[f], in[f], c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         return AC_OK;
     }
@@ -347,6 +372,7 @@ struct MixedBackend : Backend {
     float *d[3][4] = {};
     float *qn32[3] = {};
     float *rho_ref = nullptr, *dref = nullptr, *lev_p = nullptr;
+    float *D1[3] = {}, *D2[3] = {};   // Q^n - Q^{n-1}, Q^n - Q^{n-2} (BDF2, BDF3)
     double *q64[3] = {};
     std::vector<double> p_ref;   // FP64 reference pressure (host copy)
     bool use_ref = false;
@@ -413,6 +439,7 @@ struct MixedBackend : Backend {
         a.nx = c->grid.nx; a.ny = c->grid.ny;
         a.bc[0] = c->bc.xlo; a.bc[1] = c->bc.xhi; a.bc[2] = c->bc.ylo; a.bc[3] = c->bc.yhi;
         a.gradp = c->opt.gradp; a.limiter_k = c->opt.limiter_k; a.realtime = c->opt.realtime;
+        a.riemann = c->opt.riemann;
         a.local_dtau = c->opt.local_dtau; a.alpha_pi_p_row = c->opt.alpha_pi_p_row;
         a.stage = stage; a.s_max = c->opt.rk_stages;
         a.alpha = stage > 0 ? float(1.0 / double(c->opt.rk_stages - stage + 1)) : 0.0f;
@@ -427,6 +454,11 @@ struct MixedBackend : Backend {
             for (int f = 0; f < 4; ++f) a.d[b][f] = d[b][f];
         for (int f = 0; f < 3; ++f) { a.qn32[f] = qn32[f]; a.q64[f] = q64[f]; }
         a.rho_ref = rho_ref; a.dref = dref; a.lev_p = lev_p;
+        for (int f = 0; f < 3; ++f) { a.D1[f] = D1[f]; a.D2[f] = D2[f]; }
+        a.order = c->order_now;
+        a.B0 = float(kBDF[c->order_now][0]);
+        a.B2 = float(kBDF[c->order_now][2]);
+        a.B3 = float(kBDF[c->order_now][3]);
         a.partials = c->partials;
         a.ctl = c->ctl;
         return a;
@@ -439,6 +471,10 @@ struct MixedBackend : Backend {
         CK(cudaMalloc(&rho_ref, fb));
         CK(cudaMalloc(&dref, fb));
         CK(cudaMalloc(&lev_p, fb));
+        for (int f = 0; f < 3; ++f) {
+            if (c->opt.bdf_order >= 2) CK(cudaMalloc(&D1[f], fb));
+            if (c->opt.bdf_order >= 3) CK(cudaMalloc(&D2[f], fb));
+        }
         CK((allow_mixed_smem<32, 8, 256>()));
         CK((allow_mixed_smem<32, 16, 256>()));
         CK((allow_mixed_smem<32, 16, 512>()));
@@ -460,9 +496,14 @@ struct MixedBackend : Backend {
         cudaFree(rho_ref);
         cudaFree(dref);
         cudaFree(lev_p);
+        for (int f = 0; f < 3; ++f) { cudaFree(D1[f]); cudaFree(D2[f]); }
     }
     int set_state(ac_ctx *c, const double *const f[4]) override {
         const size_t N = c->N;
+        for (int q = 0; q < 3; ++q) {
+            if (D1[q]) CK(cudaMemsetAsync(D1[q], 0, N * sizeof(float), c->stream));
+            if (D2[q]) CK(cudaMemsetAsync(D2[q], 0, N * sizeof(float), c->stream));
+        }
         MixedReference ref;
         build_mixed_reference(c->grid.nx, c->grid.ny, c->dy, c->grid.gy, c->bc, use_ref, f, ref);
         p_ref = ref.p_ref;
@@ -501,29 +542,43 @@ struct MixedBackend : Backend {
         }
         return AC_OK;
     }
-    int get_levels(const ac_ctx *c, double *const out[3]) override {
-        for (int k = 0; k < 3; ++k)
-            if (out[k]) CK(cudaMemcpyAsync(out[k], q64[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+    // Between steps, history 1 is the FP64 level q64 and history 2 is
+    // q64 - D1 (D1 = difference of the last two levels).
+    int get_history(const ac_ctx *c, int k, double *const out[3]) override {
+        const size_t N = c->N;
+        std::vector<float> h(N);
+        for (int f = 0; f < 3; ++f) {
+            if (!out[f]) continue;
+            CK(cudaMemcpyAsync(out[f], q64[f], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            if (k == 2) CK(cudaMemcpyAsync(h.data(), D1[f], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (k == 2)
+                for (size_t q = 0; q < N; ++q) out[f][q] -= double(h[q]);
+        }
         return AC_OK;
     }
-    int set_levels(ac_ctx *c, const double *const in[3]) override {
-        // keep Q = Q^n + dQ unchanged: dQ absorbs the change of level
+    int set_history(ac_ctx *c, int k, const double *const in[3]) override {
         const size_t N = c->N;
         std::vector<double> old(N);
         std::vector<float> h(N), h32(N);
         const int cur = c->cur_host;
-        for (int k = 0; k < 3; ++k) {
-            CK(cudaMemcpyAsync(old.data(), q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaMemcpyAsync(h.data(), d[cur][k], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        for (int f = 0; f < 3; ++f) {
+            CK(cudaMemcpyAsync(old.data(), q64[f], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            if (k == 1) CK(cudaMemcpyAsync(h.data(), d[cur][f], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
-            for (size_t q = 0; q < N; ++q) {
-                h[q] = float(old[q] + double(h[q]) - in[k][q]);
-                h32[q] = float(in[k][q]);
+            if (k == 1) {
+                // the state Q = q64 + dQ stays; the level and dQ change
+                for (size_t q = 0; q < N; ++q) {
+                    h[q] = float((old[q] - in[f][q]) + double(h[q]));
+                    h32[q] = float(in[f][q]);
+                }
+                CK(cudaMemcpyAsync(q64[f], in[f], N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+                CK(cudaMemcpyAsync(qn32[f], h32.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+                CK(cudaMemcpyAsync(d[cur][f], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            } else {
+                for (size_t q = 0; q < N; ++q) h[q] = float(old[q] - in[f][q]);
+                CK(cudaMemcpyAsync(D1[f], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             }
-            CK(cudaMemcpyAsync(q64[k], in[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-            CK(cudaMemcpyAsync(qn32[k], h32.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-            CK(cudaMemcpyAsync(d[cur][k], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             CK(cudaStreamSynchronize(c->stream));
         }
         return AC_OK;
@@ -571,7 +626,14 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
 int kernels_per_iteration(const ac_ctx *c) { return c->opt.rk_stages + 1 + (c->opt.local_dtau ? 0 : 1); }
 
 int build_graph(ac_ctx *c) {
-    if (c->exec) return AC_OK;
+    if (c->exec && c->graph_order == c->order_now) return AC_OK;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        cudaGraphDestroy(c->graph);
+        c->exec = nullptr;
+        c->graph = nullptr;
+    }
+    c->graph_order = c->order_now;
     CK(cudaGraphCreate(&c->graph, 0));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
@@ -626,6 +688,7 @@ int ac_default_options(ac_options *o) {
     o->alpha_pi_p_row = 1;
     o->precision = AC_PREC_FP64;
     o->cfl_tau = 0.45;
+    o->bdf_order = 1;
     return AC_OK;
 }
 
@@ -658,12 +721,14 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     ac_default_options(&o);
     if (opt) o = *opt;
     if (o.rk_stages < 1 || o.rk_stages > 4) return fail(AC_ERR_ARG, "rk_stages must be 1..4");
-    if (o.riemann != AC_RIEMANN_OSHER) return fail(AC_ERR_ARG, "riemann solver %d is not available", o.riemann);
-    if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
+    if (o.riemann < AC_RIEMANN_OSHER || o.riemann > AC_RIEMANN_ROE)
+        return fail(AC_ERR_ARG, "riemann solver %d is unknown", o.riemann);
+    if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SPLIT_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
     if (o.limiter_k != 1 && o.limiter_k != 2) return fail(AC_ERR_ARG, "limiter_k must be 1 or 2");
     if (o.precision != AC_PREC_FP64 && o.precision != AC_PREC_MIXED)
         return fail(AC_ERR_ARG, "precision %d is unknown", o.precision);
     if (!(o.cfl_tau > 0.0) || !std::isfinite(o.cfl_tau)) return fail(AC_ERR_ARG, "cfl_tau must be > 0");
+    if (o.bdf_order < 1 || o.bdf_order > 3) return fail(AC_ERR_ARG, "bdf_order must be 1, 2 or 3");
     for (int k = 0; k < 4; ++k)
         if (!(o.abs_tol[k] >= 0.0)) return fail(AC_ERR_ARG, "abs_tol[%d] must be >= 0", k);
     o.local_dtau = o.local_dtau ? 1 : 0;
@@ -678,6 +743,7 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     c->bc = *bc;
     c->opt = o;
     c->N = (size_t)grid->nx * grid->ny;
+    c->order_now = 1;
     c->dx = grid->lx / grid->nx;
     c->dy = grid->ly / grid->ny;
     if (o.precision == AC_PREC_MIXED) c->be = new MixedBackend();
@@ -750,6 +816,7 @@ int ac_set_state(ac_ctx *c, const double *rho, const double *rhou, const double 
     CK(cudaMemcpyAsync(c->ctl, c->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->cur_host = 0;
+    c->nhist = 0;
     c->has_state = true;
     return AC_OK;
 }
@@ -773,6 +840,9 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
     if (!c->opt.realtime) dt = 1.0;
     cudaStream_t s = c->stream;
     int rc;
+    // the first real-time step can only be Backward-Euler, the second at
+    // most BDF2, and so on (Sec. 2.2.2)
+    c->order_now = c->opt.realtime ? std::min(c->opt.bdf_order, c->nhist + 1) : 1;
     if ((rc = c->be->begin(c, s, dt, tol, max_iters)) != AC_OK) return rc;
     c->launches += 1;
     if ((rc = c->be->tune(c, s)) != AC_OK) return rc;
@@ -816,9 +886,11 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
         if ((rc = c->be->restore(c, s)) != AC_OK) return rc;
         CK(cudaStreamSynchronize(s));
         c->cur_host = c->hctl->cur;
+        c->nhist = 0;   // the levels were shifted: restart from Backward-Euler
         return fail(AC_ERR_NONFINITE, "residual norm became non-finite at pseudo-iteration %d", c->hctl->iter);
     }
     c->cur_host = c->hctl->cur;
+    c->nhist = std::min(c->nhist + 1, 2);
     return c->hctl->status == 0 ? AC_OK : AC_NOT_CONVERGED;
 }
 
@@ -831,22 +903,31 @@ int ac_residual_norms(const ac_ctx *c, double out[4], double out0[4]) {
     return AC_OK;
 }
 
-int ac_get_levels(const ac_ctx *c, double *rho_n, double *rhou_n, double *rhov_n) {
+int ac_get_history(const ac_ctx *c, int k, double *rho, double *rhou, double *rhov) {
+    g_err.clear();
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
-    if (!c->has_state) return fail(AC_ERR_STATE, "no state has been set");
-    double *dst[3] = {rho_n, rhou_n, rhov_n};
-    return c->be->get_levels(c, dst);
+    if (k < 1 || k > 2) return fail(AC_ERR_ARG, "history level must be 1 or 2 (got %d)", k);
+    if (!c->has_state || c->nhist < k) return fail(AC_ERR_STATE, "history level %d is not available", k);
+    if (k == 2 && c->opt.bdf_order < 2) return fail(AC_ERR_STATE, "history level 2 is kept only for bdf_order >= 2");
+    double *dst[3] = {rho, rhou, rhov};
+    return c->be->get_history(c, k, dst);
 }
 
-int ac_set_levels(ac_ctx *c, const double *rho_n, const double *rhou_n, const double *rhov_n) {
+int ac_set_history(ac_ctx *c, int k, const double *rho, const double *rhou, const double *rhov) {
+    g_err.clear();
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
     if (!c->has_state) return fail(AC_ERR_STATE, "no state has been set");
+    if (k < 1 || k > 2) return fail(AC_ERR_ARG, "history level must be 1 or 2 (got %d)", k);
+    if (k == 2 && c->opt.bdf_order < 2) return fail(AC_ERR_ARG, "history level 2 is kept only for bdf_order >= 2");
+    if (k == 2 && c->nhist < 1) return fail(AC_ERR_STATE, "set history level 1 before level 2");
     int rc;
-    if ((rc = check_host_field(rho_n, c->N, true, "rho_n")) != AC_OK) return rc;
-    if ((rc = check_host_field(rhou_n, c->N, false, "rhou_n")) != AC_OK) return rc;
-    if ((rc = check_host_field(rhov_n, c->N, false, "rhov_n")) != AC_OK) return rc;
-    const double *src[3] = {rho_n, rhou_n, rhov_n};
-    return c->be->set_levels(c, src);
+    if ((rc = check_host_field(rho, c->N, true, "rho")) != AC_OK) return rc;
+    if ((rc = check_host_field(rhou, c->N, false, "rhou")) != AC_OK) return rc;
+    if ((rc = check_host_field(rhov, c->N, false, "rhov")) != AC_OK) return rc;
+    const double *src[3] = {rho, rhou, rhov};
+    if ((rc = c->be->set_history(c, k, src)) != AC_OK) return rc;
+    c->nhist = k;
+    return AC_OK;
 }
 
 long long ac_kernel_launches(const ac_ctx *c) { return c ? c->launches : 0; }

@@ -91,7 +91,10 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const double q = a.q64[f][g] + double(a.d[cur][f][g]);
+            const float dq = a.d[cur][f][g];
+            const double q = a.q64[f][g] + double(dq);
+            if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
+            if (a.D1[0]) a.D1[f][g] = dq;
             a.q64[f][g] = q;
             a.qn32[f][g] = float(q);
             a.d[cur][f][g] = 0.0f;
@@ -227,6 +230,7 @@ struct ac_batch {
     float *d[3][4];
     float *qn32[3];
     float *rho_ref, *dref, *lev_p;
+    float *D1[3], *D2[3];               // BDF2/BDF3 level differences (pools)
     double *q64[3];
     double *partials;
     Ctl *ctl;
@@ -245,6 +249,8 @@ struct ac_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool has_state;
+    int nhist;                          // older real-time levels held before the next step
+    int order_now;                      // backward-difference order in the descriptors
     long long launches;
     bool profiling;
     cudaEvent_t ev[5];
@@ -379,7 +385,7 @@ void ac_batch_destroy(ac_batch *b) {
     if (b->cap) cudaStreamDestroy(b->cap);
     for (int x = 0; x < 3; ++x)
         for (int f = 0; f < 4; ++f) cudaFree(b->d[x][f]);
-    for (int f = 0; f < 3; ++f) { cudaFree(b->qn32[f]); cudaFree(b->q64[f]); }
+    for (int f = 0; f < 3; ++f) { cudaFree(b->qn32[f]); cudaFree(b->q64[f]); cudaFree(b->D1[f]); cudaFree(b->D2[f]); }
     cudaFree(b->rho_ref);
     cudaFree(b->dref);
     cudaFree(b->lev_p);
@@ -406,11 +412,13 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     if (opt) o = *opt;
     if (o.precision != AC_PREC_MIXED) return fail(AC_ERR_ARG, "batched tanks run in the mixed form (AC_PREC_MIXED)");
     if (o.rk_stages < 1 || o.rk_stages > 4) return fail(AC_ERR_ARG, "rk_stages must be 1..4");
-    if (o.riemann != AC_RIEMANN_OSHER) return fail(AC_ERR_ARG, "riemann solver %d is not available", o.riemann);
-    if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
+    if (o.riemann < AC_RIEMANN_OSHER || o.riemann > AC_RIEMANN_ROE)
+        return fail(AC_ERR_ARG, "riemann solver %d is unknown", o.riemann);
+    if (o.gradp < AC_GRADP_NEW || o.gradp > AC_GRADP_SPLIT_SUPERBEE) return fail(AC_ERR_ARG, "gradp %d is unknown", o.gradp);
     if (o.limiter_k != 1 && o.limiter_k != 2) return fail(AC_ERR_ARG, "limiter_k must be 1 or 2");
     if (!o.local_dtau) return fail(AC_ERR_ARG, "batched tanks use the local pseudo-time step");
     if (!(o.cfl_tau > 0.0)) return fail(AC_ERR_ARG, "cfl_tau must be > 0");
+    if (o.bdf_order < 1 || o.bdf_order > 3) return fail(AC_ERR_ARG, "bdf_order must be 1, 2 or 3");
     size_t total = 0;
     for (int k = 0; k < n; ++k) {
         const ac_grid &g = grids[k];
@@ -436,6 +444,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     b->opt = o;
     b->total = total;
     b->variant = -1;
+    b->order_now = 1;
     b->off.resize(n);
     b->p_ref.resize(n);
     b->use_ref.resize(n);
@@ -457,6 +466,10 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     CKB(cudaMalloc(&b->rho_ref, fb));
     CKB(cudaMalloc(&b->dref, fb));
     CKB(cudaMalloc(&b->lev_p, fb));
+    for (int f = 0; f < 3; ++f) {
+        if (o.bdf_order >= 2) CKB(cudaMalloc(&b->D1[f], fb));
+        if (o.bdf_order >= 3) CKB(cudaMalloc(&b->D2[f], fb));
+    }
     // tiles of the smallest shape (16 x 8 cells) bound every variant's tile count
     size_t max_tiles = 0;
     for (int k = 0; k < n; ++k) max_tiles += (size_t)((grids[k].nx + 15) / 16) * ((grids[k].ny + 7) / 8);
@@ -488,6 +501,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.nx = g.nx; a.ny = g.ny;
         a.bc[0] = bcs[k].xlo; a.bc[1] = bcs[k].xhi; a.bc[2] = bcs[k].ylo; a.bc[3] = bcs[k].yhi;
         a.gradp = o.gradp; a.limiter_k = o.limiter_k; a.realtime = o.realtime ? 1 : 0;
+        a.riemann = o.riemann;
         a.local_dtau = 1; a.alpha_pi_p_row = o.alpha_pi_p_row ? 1 : 0;
         a.s_max = o.rk_stages;
         const double dx = g.lx / g.nx, dy = g.ly / g.ny;
@@ -503,6 +517,12 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.rho_ref = b->rho_ref + pos;
         a.dref = b->dref + pos;
         a.lev_p = b->lev_p + pos;
+        for (int f = 0; f < 3; ++f) {
+            a.D1[f] = b->D1[f] ? b->D1[f] + pos : nullptr;
+            a.D2[f] = b->D2[f] ? b->D2[f] + pos : nullptr;
+        }
+        a.order = 1;
+        a.B0 = 1.0f;
         a.partials = b->partials + tpos * 4;
         a.ctl = b->ctl + k;
         b->use_ref[k] = mixed_uses_reference(bcs[k], o.gradp);
@@ -558,6 +578,10 @@ int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou
         CK(cudaStreamSynchronize(s));
         CK(cudaMemsetAsync(b->d[0][q] + o, 0, fb, s));
     }
+    for (int q = 0; q < 3; ++q) {
+        if (b->D1[q]) CK(cudaMemsetAsync(b->D1[q] + o, 0, fb, s));
+        if (b->D2[q]) CK(cudaMemsetAsync(b->D2[q] + o, 0, fb, s));
+    }
     CK(cudaMemcpyAsync(b->d[0][3] + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->lev_p + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->rho_ref + o, ref.rho_ref.data(), fb, cudaMemcpyHostToDevice, s));
@@ -566,6 +590,7 @@ int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou
     CK(cudaStreamSynchronize(s));
     b->hctl[k] = hc;
     b->has_state = true;
+    b->nhist = 0;   // the batch's levels restart with any tank's new state
     return AC_OK;
 }
 
@@ -605,6 +630,22 @@ int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_it
         if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(AC_ERR_ARG, "dt[%d] must be finite and > 0", k);
     }
     cudaStream_t s = b->stream;
+    // backward-difference order of this step (the first step can only be
+    // Backward-Euler, Sec. 2.2.2); the kernels read it from the descriptors
+    static const double bdf[4][4] = {{0, 0, 0, 0}, {1.0, -1.0, 0, 0}, {1.5, -2.0, 0.5, 0},
+                                     {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0}};
+    const int order = b->opt.realtime ? std::min(b->opt.bdf_order, b->nhist + 1) : 1;
+    if (order != b->order_now) {
+        for (int k = 0; k < b->n; ++k) {
+            MixedArgs &a = b->tanks_host[k].a;
+            a.order = order;
+            a.B0 = float(bdf[order][0]);
+            a.B2 = float(bdf[order][2]);
+            a.B3 = float(bdf[order][3]);
+        }
+        CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_host.data(), b->n * sizeof(BatchTank), cudaMemcpyHostToDevice, s));
+        b->order_now = order;
+    }
     CK(cudaMemcpyAsync(b->dt_dev, h.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, s));
     size_t maxN = 0;
     for (int k = 0; k < b->n; ++k) maxN = std::max(maxN, (size_t)b->grids[k].nx * b->grids[k].ny);
@@ -652,8 +693,10 @@ int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_it
         batch_restore_kernel<<<dim3(bg.x, b->n), 256, 0, s>>>(b->tanks_dev);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
+        b->nhist = 0;
         return fail(AC_ERR_NONFINITE, "a residual norm became non-finite; those tanks are back at the step's start");
     }
+    b->nhist = std::min(b->nhist + 1, 2);
     return ret;
 }
 

@@ -12,7 +12,8 @@
 namespace acgb {
 
 enum BcKind { kSlip = 0, kNoSlip = 1, kTransmissive = 2, kPeriodic = 3 };
-enum GradP { kGradNew = 0, kGradMinmod = 1, kGradSuperbee = 2 };
+enum GradP { kGradNew = 0, kGradMinmod = 1, kGradSuperbee = 2, kGradSplitMinmod = 3, kGradSplitSuperbee = 4 };
+enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2 };
 
 // ---------------------------------------------------------------------------
 // Arithmetic traits.  FP64 uses IEEE division and square root; FP32 uses
@@ -150,6 +151,82 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     F[1] = T(0.5) * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
     F[2] = T(0.5) * ((mL * vL + mR * vR) - (dn * Sau + Sve));
     F[3] = T(0.5) * ((uL + uR) - (dq * Sau - Sh));
+}
+
+// ---------------------------------------------------------------------------
+// Roe flux with the Roe averages of Sec. 2.4.2 (no entropy fix, none being
+// needed here): F = 1/2 (F(Q_L) + F(Q_R) - |A(Q~)| dQ), |A| dQ in the same
+// rank-2 form as one Osher quadrature point with weight 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void roe_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta, T inv_beta,
+                                         T F[4]) {
+    const T mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
+    const T mR = rR * uR, nR = rR * vR, qR = pR * inv_beta;
+    const T dr = rR - rL, dm = mR - mL, dn = nR - nL, dq = qR - qL;
+    const T sL = Ar<T>::sqrt_(rL), sR = Ar<T>::sqrt_(rR);
+    const T isum = Ar<T>::rcp(sL + sR);
+    const T r = sL * sR;
+    const T u = (sL * uL + sR * uR) * isum, v = (sL * vL + sR * vR) * isum;
+    const T ir = Ar<T>::rcp(r);
+    const T c2 = u * u + T(4) * beta * ir;
+    T c, ic;
+    Ar<T>::sqrt_rsqrt(c2, c, ic);
+    const T hu = T(0.5) * u, hc = T(0.5) * c;
+    const T l4 = hu + hc, l5 = hu - hc;
+    const T au = fabs(u);
+    const T a = (dm - u * dr) * inv_beta;
+    const T k = r * ic;
+    const T g4 = (l4 - au) * k * (l4 * a + dq);
+    const T g5 = (l5 + au) * k * (l5 * a + dq);
+    const T e = g4 * l4 + g5 * l5;
+    F[0] = T(0.5) * ((mL + mR) - (au * dr + e));
+    F[1] = T(0.5) * ((mL * uL + pL + mR * uR + pR) - (au * dm + u * e + beta * ir * (g4 + g5)));
+    F[2] = T(0.5) * ((mL * vL + mR * vR) - (au * dn + v * e));
+    F[3] = T(0.5) * ((uL + uR) - (au * dq - (g4 * l5 + g5 * l4) * ir));
+}
+
+// ---------------------------------------------------------------------------
+// Flux of the exact (non-iterative) Riemann solution of Bassi et al.
+// (Sec. 2.4.1): acoustic speeds S_L = (u_L - c_L)/2, S_R = (u_R + c_R)/2, the
+// star values u*, p*, rho*_L, rho*_R, and the state at x/tau = 0 sampled as
+// left (0 <= S_L), left star (0 <= u*), right star (0 <= S_R) or right.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta, T inv_beta,
+                                           T F[4]) {
+    const T cL = Ar<T>::sqrt_(uL * uL + T(4) * beta * Ar<T>::rcp(rL));
+    const T cR = Ar<T>::sqrt_(uR * uR + T(4) * beta * Ar<T>::rcp(rR));
+    const T l4L = T(0.5) * (uL + cL), l5L = T(0.5) * (uL - cL);
+    const T l4R = T(0.5) * (uR + cR), l5R = T(0.5) * (uR - cR);
+    const T SL = l5L, SR = l4R;
+    T r, u, v, p;
+    if (T(0) <= SL) {
+        r = rL; u = uL; v = vL; p = pL;
+    } else {
+        const T us = Ar<T>::div(pR - pL + rR * uR * l5R - rL * uL * l4L, rR * l5R - rL * l4L);
+        const T ps = pR + rR * l5R * (uR - us);
+        if (T(0) <= us) {
+            r = Ar<T>::div(rL * l4L, us - l5L); u = us; v = vL; p = ps;
+        } else if (T(0) <= SR) {
+            r = Ar<T>::div(rR * l5R, us - l4R); u = us; v = vR; p = ps;
+        } else {
+            r = rR; u = uR; v = vR; p = pR;
+        }
+    }
+    const T m = r * u;
+    F[0] = m;
+    F[1] = m * u + p;
+    F[2] = m * v;
+    F[3] = u;
+}
+
+template <typename T>
+__device__ __forceinline__ void riemann_flux(int kind, T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
+                                             T inv_beta, T F[4]) {
+    if (kind == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else if (kind == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
 }
 
 }  // namespace acgb

@@ -41,6 +41,7 @@ struct SweepArgs {
     int nx, ny;
     int bc[4];
     int gradp, limiter_k, realtime, local_dtau, alpha_pi_p_row;
+    int riemann;                   // kOsher / kBassi / kRoe
     int stage, s_max;
     T alpha;                       // alpha_s of this stage
     T dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
@@ -48,6 +49,9 @@ struct SweepArgs {
     T cfl_area;                    // CFL_tau * |Omega|
     T *buf[3][4];                  // three state buffers: rho, rho u, rho v, p
     T *lev[4];                     // real-time level Q^n (rho, rho u, rho v, p)
+    T *lev1[3], *lev2[3];          // Q^{n-1}, Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
+    int order;                     // backward-difference order used in this step (1..3)
+    T B[4];                        // its coefficients B0..B3 (Table BDF)
     double *partials;              // per-CTA residual partial sums [nblocks][4]
     Ctl *ctl;
 };
@@ -134,8 +138,18 @@ stage_kernel(const SweepArgs<T> a) {
             const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
             const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
             const size_t s = (size_t)sj * nx + si;
-            T rx = (q0[1][s] - a.lev[1][s]) * inv_dt;
-            T ry = (q0[2][s] - a.lev[2][s]) * inv_dt;
+            T rx = a.B[0] * q0[1][s] + a.B[1] * a.lev[1][s];
+            T ry = a.B[0] * q0[2][s] + a.B[1] * a.lev[2][s];
+            if (a.order >= 2) {
+                rx += a.B[2] * a.lev1[1][s];
+                ry += a.B[2] * a.lev1[2][s];
+            }
+            if (a.order >= 3) {
+                rx += a.B[3] * a.lev2[1][s];
+                ry += a.B[3] * a.lev2[2][s];
+            }
+            rx *= inv_dt;
+            ry *= inv_dt;
             if ((nfx + tfy) & 1) rx = -rx;
             if ((nfy + tfx) & 1) ry = -ry;
             sm.rt[0][k] = rx;
@@ -146,7 +160,7 @@ stage_kernel(const SweepArgs<T> a) {
 
     // ---- 2. limited half slopes and pressure gradient on the ring ----
     const T klim = T(a.limiter_k);
-    const T kp = (a.gradp == kGradSuperbee) ? T(2) : T(1);
+    const T kp = (a.gradp == kGradSuperbee || a.gradp == kGradSplitSuperbee) ? T(2) : T(1);
     for (int k = tid; k < GW * GH; k += NT) {
         const int li = k % GW, lj = k / GW;            // ring coords (cell li-1, lj-1)
         const int c = (lj + 1) * RW + (li + 1);
@@ -181,6 +195,17 @@ stage_kernel(const SweepArgs<T> a) {
                   a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
             hpy = -a.half_dy * rty - (v * v * hry + T(2) * rv * hvy) -
                   a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * rho * a.gy * sg;
+        } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
+            // Qian et al. split (Sec. 2.3.2): limit the kinematic part of the
+            // one-sided pressure differences, add the cell's hydrostatic
+            // slope back; gravity reversed in wall ghosts as for Eq. new_gradp
+            const int gi = x0 + li - 1, gj = y0 + lj - 1;
+            const T sg = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc);
+            const T gxs = a.gx * sg, gys = a.gy * sg;
+            hpx = T(0.5) * limiter(P[e] - P[c] - a.half_dx * (R[c] + R[e]) * gxs,
+                                   P[c] - P[wv] - a.half_dx * (R[wv] + R[c]) * gxs, kp) + a.half_dx * R[c] * gxs;
+            hpy = T(0.5) * limiter(P[nn] - P[c] - a.half_dy * (R[c] + R[nn]) * gys,
+                                   P[c] - P[ss] - a.half_dy * (R[ss] + R[c]) * gys, kp) + a.half_dy * R[c] * gys;
         } else {
             hpx = T(0.5) * limiter(P[e] - P[c], P[c] - P[wv], kp);
             hpy = T(0.5) * limiter(P[nn] - P[c], P[c] - P[ss], kp);
@@ -201,7 +226,7 @@ stage_kernel(const SweepArgs<T> a) {
             const T uL = sm.w[1][ca] + sm.gx[1][ga], uR = sm.w[1][cb] - sm.gx[1][gb];
             const T vL = sm.w[2][ca] + sm.gx[2][ga], vR = sm.w[2][cb] - sm.gx[2][gb];
             const T pL = sm.w[3][ca] + sm.gx[3][ga], pR = sm.w[3][cb] - sm.gx[3][gb];
-            osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
+            riemann_flux<T>(a.riemann, rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
             sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
         } else {
             const int kk = k - S::NXF;
@@ -213,7 +238,7 @@ stage_kernel(const SweepArgs<T> a) {
             const T vL = sm.w[2][ca] + sm.gy[2][ga], vR = sm.w[2][cb] - sm.gy[2][gb];
             const T pL = sm.w[3][ca] + sm.gy[3][ga], pR = sm.w[3][cb] - sm.gy[3][gb];
             // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            osher_flux<T>(rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
+            riemann_flux<T>(a.riemann, rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
             sm.fy[0][kk] = F[0]; sm.fy[1][kk] = F[2]; sm.fy[2][kk] = F[1]; sm.fy[3][kk] = F[3];
         }
     }
@@ -235,9 +260,23 @@ stage_kernel(const SweepArgs<T> a) {
         const T r0 = q0[0][g], m0 = q0[1][g], n0 = q0[2][g], p0 = q0[3][g];
         T rt0 = T(0), rt1 = T(0), rt2 = T(0);
         if (a.realtime) {
-            rt0 = (r0 - a.lev[0][g]) * inv_dt;
-            rt1 = (m0 - a.lev[1][g]) * inv_dt;
-            rt2 = (n0 - a.lev[2][g]) * inv_dt;
+            // Eq. bdf: (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} + B3 Q^{n-2}) / dt
+            rt0 = a.B[0] * r0 + a.B[1] * a.lev[0][g];
+            rt1 = a.B[0] * m0 + a.B[1] * a.lev[1][g];
+            rt2 = a.B[0] * n0 + a.B[1] * a.lev[2][g];
+            if (a.order >= 2) {
+                rt0 += a.B[2] * a.lev1[0][g];
+                rt1 += a.B[2] * a.lev1[1][g];
+                rt2 += a.B[2] * a.lev1[2][g];
+            }
+            if (a.order >= 3) {
+                rt0 += a.B[3] * a.lev2[0][g];
+                rt1 += a.B[3] * a.lev2[1][g];
+                rt2 += a.B[3] * a.lev2[2][g];
+            }
+            rt0 *= inv_dt;
+            rt1 *= inv_dt;
+            rt2 *= inv_dt;
         }
         const T b0 = -div[0] - rt0;
         const T b1 = -div[1] - rt1 + r0 * a.gx;
@@ -254,7 +293,7 @@ stage_kernel(const SweepArgs<T> a) {
         } else {
             dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
         }
-        const T api = T(1) + a.alpha * dtau * inv_dt;      // Eq. point_implicit, B0 = 1
+        const T api = T(1) + a.B[0] * a.alpha * dtau * inv_dt;   // Eq. point_implicit
         const T coef = Ar<T>::div(a.alpha * dtau, api);
         const T coef_p = a.alpha_pi_p_row ? coef : a.alpha * dtau;
         qout[0][g] = r0 + coef * b0;
@@ -317,6 +356,13 @@ __global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, i
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        // older levels move back one step: Q^{n-2} <- Q^{n-1} <- Q^n
+        if (a.lev2[0])
+#pragma unroll
+            for (int f = 0; f < 3; ++f) a.lev2[f][g] = a.lev1[f][g];
+        if (a.lev1[0])
+#pragma unroll
+            for (int f = 0; f < 3; ++f) a.lev1[f][g] = a.lev[f][g];
 #pragma unroll
         for (int f = 0; f < 4; ++f) a.lev[f][g] = a.buf[cur][f][g];
     }

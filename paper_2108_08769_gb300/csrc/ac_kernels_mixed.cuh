@@ -13,8 +13,11 @@
 //             (Q^{n+1} = Q^n + dQ in FP64: the level accumulation)
 //
 // Why this is exact algebra and not an approximation of the scheme:
-//   * The real-time term of Eq. bdf (Backward-Euler) is (Q^{m} - Q^n)/dt =
-//     dQ^{m}/dt: no cancellation between two large FP32 numbers.
+//   * The real-time term of Eq. bdf is (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} +
+//     B3 Q^{n-2})/dt; the coefficients sum to zero, so it equals
+//     (B0 dQ^{m} - B2 D1 - B3 D2)/dt with D1 = Q^n - Q^{n-1}, D2 = Q^n -
+//     Q^{n-2}: small FP32 differences, no cancellation between large FP32
+//     numbers (Backward-Euler: dQ^{m}/dt).
 //   * Every Riemann flux here is affine in a pressure offset common to the
 //     two face states (|A| does not depend on p), so each face may be solved
 //     with p'' = p - P_f for any face constant P_f, adding P_f back to the
@@ -40,6 +43,7 @@ struct MixedArgs {
     int nx, ny;
     int bc[4];
     int gradp, limiter_k, realtime, local_dtau, alpha_pi_p_row;
+    int riemann;           // kOsher / kBassi / kRoe
     int stage, s_max;
     float alpha;
     float dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
@@ -50,6 +54,9 @@ struct MixedArgs {
     const float *rho_ref;  // reference density
     const float *dref;     // reference jump across the west x-face
     float *lev_p;          // p' at the start of the physical step
+    float *D1[3], *D2[3];  // Q^n - Q^{n-1}, Q^n - Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
+    int order;             // backward-difference order used in this step (1..3)
+    float B0, B2, B3;      // its coefficients (Table BDF); B1 = -(B0 + B2 + B3)
     double *q64[3];        // FP64 real-time level
     double *partials;
     Ctl *ctl;
@@ -173,8 +180,18 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             }
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                rx = e1[s] * inv_dt;   // (Q^{m} - Q^n)/dt of rho u
-                ry = e2[s] * inv_dt;
+                rx = a.B0 * e1[s];     // B0 (Q^{m} - Q^n) of rho u, ...
+                ry = a.B0 * e2[s];
+                if (a.order >= 2) {
+                    rx -= a.B2 * a.D1[1][s];
+                    ry -= a.B2 * a.D1[2][s];
+                }
+                if (a.order >= 3) {
+                    rx -= a.B3 * a.D2[1][s];
+                    ry -= a.B3 * a.D2[2][s];
+                }
+                rx *= inv_dt;
+                ry *= inv_dt;
                 rx = fx ? -rx : rx;
                 ry = fy ? -ry : ry;
             }
@@ -185,7 +202,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
 
     // ---- 2. limited half slopes and pressure gradient on the ring ----
     const float klim = float(a.limiter_k);
-    const float kp = (a.gradp == kGradSuperbee) ? 2.0f : 1.0f;
+    const float kp = (a.gradp == kGradSuperbee || a.gradp == kGradSplitSuperbee) ? 2.0f : 1.0f;
     for (int k = tid; k < GW * GH; k += NT) {
         const int lj = k / GW, li = k - lj * GW;
         const int c = (lj + 1) * RW + (li + 1);
@@ -204,6 +221,15 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             // slope of p - p_ref: the reference slope rho_ref g_y is removed
             hpy = -a.half_dy * ax.y - (v * v * hry + 2.0f * rv * hvy) -
                   a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - ax.z) * a.gy * sg;
+        } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
+            // Qian et al. split (Sec. 2.3.2); p' = p here (no reference)
+            float sg = 1.0f;
+            if (!interior) sg = wall_ghost_sign<float>(x0 + li - 1, y0 + lj - 1, nx, ny, a.bc);
+            const float gxs = a.gx * sg, gys = a.gy * sg;
+            hpx = 0.5f * limiter(We.w - Wc.w - a.half_dx * (Wc.x + We.x) * gxs,
+                                 Wc.w - Ww.w - a.half_dx * (Ww.x + Wc.x) * gxs, kp) + a.half_dx * Wc.x * gxs;
+            hpy = 0.5f * limiter(Wn.w - Wc.w - a.half_dy * (Wc.x + Wn.x) * gys,
+                                 Wc.w - Ws.w - a.half_dy * (Ws.x + Wc.x) * gys, kp) + a.half_dy * Wc.x * gys;
         } else {
             hpx = 0.5f * limiter(We.w - Wc.w, Wc.w - Ww.w, kp);
             hpy = 0.5f * limiter(Wn.w - Wc.w, Wc.w - Ws.w, kp);
@@ -229,7 +255,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             const int ga = (fj + 1) * GW + fi;
             const int ca = (fj + 2) * RW + fi + 1;
             const float4 A = sm.w[ca], B = sm.w[ca + 1], SA = sm.gx[ga], SB = sm.gx[ga + 1];
-            osher_flux<float>(A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
+            riemann_flux<float>(a.riemann, A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
                               B.x - SB.x, B.y - SB.y, B.z - SB.z, B.w - SB.w + 0.5f * jump,
                               a.beta, a.inv_beta, F);
             sm.fx[k] = make_float4(F[0], F[1], F[2], F[3]);
@@ -240,7 +266,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             const int ca = (fj + 1) * RW + fi + 2;
             const float4 A = sm.w[ca], B = sm.w[ca + RW], SA = sm.gy[ga], SB = sm.gy[ga + GW];
             // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            osher_flux<float>(A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
+            riemann_flux<float>(a.riemann, A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
                               B.x - SB.x, B.z - SB.z, B.y - SB.y, B.w - SB.w,
                               a.beta, a.inv_beta, F);
             sm.fy[kk] = make_float4(F[0], F[2], F[1], F[3]);
@@ -266,7 +292,20 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const float r0 = __ldg(a.qn32[0] + g) + e0;
         const float m0 = __ldg(a.qn32[1] + g) + e1;
         const float n0 = __ldg(a.qn32[2] + g) + e2;
-        const float rt0 = e0 * inv_dt, rt1 = e1 * inv_dt, rt2 = e2 * inv_dt;
+        float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
+        if (a.order >= 2) {
+            rt0 -= a.B2 * a.D1[0][g];
+            rt1 -= a.B2 * a.D1[1][g];
+            rt2 -= a.B2 * a.D1[2][g];
+        }
+        if (a.order >= 3) {
+            rt0 -= a.B3 * a.D2[0][g];
+            rt1 -= a.B3 * a.D2[1][g];
+            rt2 -= a.B3 * a.D2[2][g];
+        }
+        rt0 *= inv_dt;
+        rt1 *= inv_dt;
+        rt2 *= inv_dt;
         // reference force: -(divergence of the x-face reference means)
         const float sref = -0.5f * (sm.dxf[fw + 1] + sm.dxf[fw]) * a.inv_dx;
         const float b0 = -div0 - rt0;
@@ -285,7 +324,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             dtau = float(__longlong_as_double((long long)ctl->dtau_bits));
         }
         const float adt = a.alpha * dtau;
-        const float coef = __fdividef(adt, 1.0f + adt * inv_dt);   // Eq. point_implicit, B0 = 1
+        const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
         const float coef_p = a.alpha_pi_p_row ? coef : adt;
         dout[0][g] = e0 + coef * b0;
         dout[1][g] = e1 + coef * b1;
@@ -355,7 +394,11 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const double q = a.q64[f][g] + double(a.d[cur][f][g]);
+            const float dq = a.d[cur][f][g];
+            const double q = a.q64[f][g] + double(dq);
+            // differences to the older levels, relative to the new Q^n
+            if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
+            if (a.D1[0]) a.D1[f][g] = dq;
             a.q64[f][g] = q;
             a.qn32[f][g] = float(q);
             a.d[cur][f][g] = 0.0f;

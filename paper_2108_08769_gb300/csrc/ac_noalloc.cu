@@ -109,9 +109,11 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
     if (opt->precision != AC_PREC_FP64) return fail(AC_ERR_ARG, "only the FP64 sweep has a no-allocation variant");
     if (opt->rk_stages < 1 || opt->rk_stages > 4) return fail(AC_ERR_ARG, "rk_stages must be 1..4");
     if (stage < 1 || stage > opt->rk_stages) return fail(AC_ERR_ARG, "stage must be 1..rk_stages (got %d)", stage);
-    if (opt->gradp < AC_GRADP_NEW || opt->gradp > AC_GRADP_SUPERBEE) return fail(AC_ERR_ARG, "gradp is unknown");
+    if (opt->gradp < AC_GRADP_NEW || opt->gradp > AC_GRADP_SPLIT_SUPERBEE) return fail(AC_ERR_ARG, "gradp is unknown");
+    if (opt->riemann < AC_RIEMANN_OSHER || opt->riemann > AC_RIEMANN_ROE) return fail(AC_ERR_ARG, "riemann is unknown");
     if (opt->limiter_k != 1 && opt->limiter_k != 2) return fail(AC_ERR_ARG, "limiter_k must be 1 or 2");
     if (!(opt->cfl_tau > 0.0)) return fail(AC_ERR_ARG, "cfl_tau must be > 0");
+    if (opt->bdf_order > 1) return fail(AC_ERR_ARG, "the no-allocation sweep uses the Backward-Euler real-time term");
     if (opt->realtime && !(dt > 0.0 && std::isfinite(dt))) return fail(AC_ERR_ARG, "dt must be finite and > 0");
     if (stage > 1 && !q_prev) return fail(AC_ERR_ARG, "q_prev is required for stage > 1");
     if (opt->realtime && !qn) return fail(AC_ERR_ARG, "qn is required when the real-time term is on");
@@ -151,9 +153,13 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
         if (stage > 1) a.buf[in][f] = const_cast<double *>(q_prev[f]);
     }
     for (int f = 0; f < 3; ++f) a.lev[f] = qn ? const_cast<double *>(qn[f]) : nullptr;
+    a.order = 1;                     // Backward-Euler real-time term
+    a.B[0] = 1.0;
+    a.B[1] = -1.0;
     a.nx = grid->nx; a.ny = grid->ny;
     for (int k = 0; k < 4; ++k) a.bc[k] = sides[k];
     a.gradp = opt->gradp; a.limiter_k = opt->limiter_k; a.realtime = opt->realtime ? 1 : 0;
+    a.riemann = opt->riemann;
     a.local_dtau = opt->local_dtau ? 1 : 0; a.alpha_pi_p_row = opt->alpha_pi_p_row ? 1 : 0;
     a.stage = stage; a.s_max = opt->rk_stages;
     a.alpha = 1.0 / double(opt->rk_stages - stage + 1);

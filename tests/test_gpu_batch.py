@@ -120,3 +120,20 @@ def test_nonfinite_tank_is_restored_alone():
     got = b.get_state(0)
     assert np.abs(got[2]).max() == 0.0 and np.array_equal(got[0], rest.rho)
     b.close()
+
+
+def test_bdf2_batch_equals_single_tanks():
+    cases = W.batched_tanks(count=3, nmin=24, nmax=56, seed=8)
+    for c in cases:
+        c.options.bdf_order = 2
+    b = ac.Batch.from_cases(cases)
+    singles = [ac.Tank.from_case(c, precision="mixed") for c in cases]
+    for step in range(3):
+        b.physical_step(1e-3, -1.0, 6)
+        for t in singles:
+            t.physical_step(1e-3, -1.0, 6)
+    for k, t in enumerate(singles):
+        for x, y in zip(b.get_state(k), t.get_state()):
+            assert np.array_equal(x, y)
+        t.close()
+    b.close()

@@ -68,7 +68,8 @@ def test_random_two_fluid_against_oracle(bc):
 
 
 @pytest.mark.parametrize("opts", [dict(gradp="minmod"), dict(local_dtau=False), dict(s_max=2),
-                                  dict(limiter_k=2), dict(realtime=False, cfl_tau=0.3)],
+                                  dict(limiter_k=2), dict(realtime=False, cfl_tau=0.3),
+                                  dict(riemann="bassi"), dict(riemann="roe"), dict(gradp="split_minmod")],
                          ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
 def test_options_against_oracle(opts):
     case = W.random_two_fluid(37, 19, ratio=100.0, c0=6.0)
@@ -152,3 +153,21 @@ def test_converged_step_close_to_oracle():
     ref, st, oits, *_ = oracle.physical_step(case, case.state(), tol=1e-6, max_iters=500)
     assert abs(its[0] - oits) <= max(2, oits // 20), (its, oits)
     check(got, ref, tol=1e-4)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_bdf_levels_against_oracle(order):
+    """Four physical steps with BDF2/BDF3: the mixed form carries the older
+    levels as FP32 differences to the FP64 level; against the oracle run
+    with its explicit history."""
+    case = W.water_column(96, 48)
+    case.options.bdf_order = order
+    t = ac.Tank.from_case(case, precision="mixed")
+    states = [case.state()]
+    for step in range(4):
+        t.physical_step(case.dt, -1.0, 12)
+        older = [(s[0], s[1], s[2]) for s in states[::-1][1:3]]   # Q^{n-1}, Q^{n-2}
+        ref, *_ = oracle.physical_step(case, states[-1], tol=-1.0, max_iters=12, history=older)
+        states.append(ref)
+    check(t.get_state(), states[-1])
+    t.close()

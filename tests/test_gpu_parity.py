@@ -118,6 +118,10 @@ OPTION_SETS = [
     dict(realtime=False),
     dict(alpha_pi_p_row=False),
     dict(realtime=False, local_dtau=False, gradp="minmod", cfl_tau=0.9),
+    dict(riemann="bassi"),
+    dict(riemann="roe"),
+    dict(gradp="split_minmod"),
+    dict(gradp="split_superbee"),
 ]
 
 
@@ -239,3 +243,62 @@ def test_step_before_state_is_an_error():
         t.set_state(np.ones(64), bad, np.zeros(64), np.zeros(64))
     assert e.value.code == ac.AC_ERR_NONFINITE
     t.close()
+
+
+@pytest.mark.parametrize("riemann", ["bassi", "roe"])
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_riemann_problems_other_fluxes(riemann, k):
+    """Sec. 3.1 set-up with the exact (Bassi) and Roe fluxes."""
+    case = W.riemann_problem(k, 100)
+    case.options.riemann = riemann
+    assert_parity(run_both(case, steps=1, tol=-1.0, max_iters=10), case=case)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_bdf_steps_from_identical_history(order):
+    """BDF2/BDF3 (Table BDF): each step starts GPU and oracle from the same
+    state and the same older levels (ac_set_history / the oracle's history)."""
+    case = W.random_two_fluid(37, 19, ratio=300.0, c0=8.0)
+    case.options.bdf_order = order
+    states = [case.state()]
+    for step in range(4):
+        older = [(s[0], s[1], s[2]) for s in states[::-1][1:3]]   # Q^{n-1}, Q^{n-2}
+        ref, st, oits, oR, _ = oracle.physical_step(case, states[-1], tol=-1.0, max_iters=5, history=older)
+        t = ac.Tank.from_case(case)
+        t.set_state(*states[-1])
+        for lvl, s_ in enumerate(states[::-1][1:3], start=1):
+            if lvl == 2 and order < 2:
+                break
+            t.set_history(lvl, s_[0], s_[1], s_[2])
+        t.physical_step(case.dt, -1.0, 5)
+        got = t.get_state()
+        t.close()
+        errs = rel_errors(got, ref)
+        assert max(errs) <= TOL, (step, errs)
+        states.append(ref)
+
+
+def test_bdf2_checkpoint_resume_bitwise():
+    case = W.random_two_fluid(40, 24, ratio=100.0, c0=5.0)
+    case.options.bdf_order = 2
+    a = ac.Tank.from_case(case)
+    for _ in range(4):
+        a.physical_step(case.dt, -1.0, 4)
+    full = a.get_state()
+    b = ac.Tank.from_case(case)
+    for _ in range(2):
+        b.physical_step(case.dt, -1.0, 4)
+    snap, h1, h2 = b.get_state(), b.get_history(1), b.get_history(2)
+    b.close()
+    c = ac.Tank.from_case(case)
+    c.set_state(*snap)
+    c.set_history(1, *h1)
+    c.set_history(2, *h2)
+    for _ in range(2):
+        c.physical_step(case.dt, -1.0, 4)
+    for x, y in zip(full, c.get_state()):
+        assert np.array_equal(x, y)
+    with pytest.raises(ac.ACError):
+        a.get_history(3)
+    a.close()
+    c.close()
