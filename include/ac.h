@@ -153,6 +153,13 @@ int ac_physical_step(ac_ctx *ctx, double dt, double tol, int max_iters, int *ite
  * rho v, p), out0[4] (may be NULL) = first-iteration R0. */
 int ac_residual_norms(const ac_ctx *ctx, double out[4], double out0[4]);
 
+/* Global real-time step from a real-time Courant number (Sec. 2.2.4):
+ * dt = min over cells of CFL_t |Omega| / (|u| dy + |v| dx), from the current
+ * state; +inf when the fluid is at rest everywhere.  cfl_t > 0.  The
+ * real-time term is point-implicit, so this sets resolution, not
+ * stability.  Synchronises the context's stream. */
+int ac_realtime_dt(ac_ctx *ctx, double cfl_t, double *dt_out);
+
 /* Real-time history, for checkpointing and for BDF2/BDF3: level k (1 or 2)
  * is (rho, rho u, rho v) of the state k physical steps before the current
  * one.  Level 1 exists after one step (or ac_set_history(ctx, 1, ...)),

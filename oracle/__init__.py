@@ -77,6 +77,8 @@ def lib():
         L.orc_limiter.restype = C.c_double
         L.orc_bracket.argtypes = [C.POINTER(Problem), C.POINTER(_D), C.POINTER(_D), _D, C.POINTER(_D)]
         L.orc_dtau.argtypes = [C.POINTER(Problem), C.POINTER(_D), _D]
+        L.orc_realtime_dt.argtypes = [C.POINTER(Problem), C.POINTER(_D), C.c_double]
+        L.orc_realtime_dt.restype = C.c_double
         L.orc_physical_step.argtypes = [C.POINTER(Problem), C.POINTER(_D), C.c_void_p, C.c_double,
                                         C.c_double, C.c_int, C.POINTER(C.c_int), _D, _D]
         L.orc_physical_step.restype = C.c_int
@@ -226,6 +228,12 @@ def dtau(case, state, **override):
     out = np.zeros_like(q[0])
     lib().orc_dtau(C.byref(pb), _ptrs(q), _p(out))
     return out
+
+
+def realtime_dt(case, state, cfl_t: float, **override) -> float:
+    pb = problem(case, **override)
+    q = [np.ascontiguousarray(np.array(a, dtype=np.float64)) for a in state]
+    return lib().orc_realtime_dt(C.byref(pb), _ptrs(q), float(cfl_t))
 
 
 def pseudo_time_run(case, state, tau_end: float, max_iters: int = 1000000, **override):

@@ -547,6 +547,25 @@ void orc_dtau(const orc_problem *pb, const double *const q[4], double *dtau)
         for (int k = 0; k < N; ++k) dtau[k] = mn;
 }
 
+/* Global real-time step (Sec. 2.2.4): dt = min_i CFL_t |Omega| / (Lx + Ly),
+ * Lx = |u| dS_x, Ly = |v| dS_y with the projected areas of Sec. 2.2.3.
+ * +inf when the fluid is at rest everywhere. */
+double orc_realtime_dt(const orc_problem *pb, const double *const q[4], double cfl_t)
+{
+    int N = pb->nx * pb->ny;
+    double dSx = 0.5 * (pb->dy + pb->dy);
+    double dSy = 0.5 * (pb->dx + pb->dx);
+    double area = pb->dx * pb->dy;
+    double mn = INFINITY;
+    for (int k = 0; k < N; ++k) {
+        double u = q[1][k] / q[0][k], v = q[2][k] / q[0][k];
+        double den = fabs(u) * dSx + fabs(v) * dSy;
+        double dt = cfl_t * area / den;   /* +inf for a cell at rest */
+        if (dt < mn) mn = dt;
+    }
+    return mn;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dual time stepping (Alg. 1, Eqs. RK1-RK2, bdf, point_implicit)             */
 /* ------------------------------------------------------------------------ */

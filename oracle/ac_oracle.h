@@ -54,6 +54,7 @@ double orc_limiter(double a, double b, double k);
 void orc_bracket(const orc_problem *pb, const double *const q[4], const double *const rt[3],
                  const double *rho0, double *br[4]);
 void orc_dtau(const orc_problem *pb, const double *const q[4], double *dtau);
+double orc_realtime_dt(const orc_problem *pb, const double *const q[4], double cfl_t);
 int orc_physical_step(const orc_problem *pb, double *q[4], const double *const hist[2][3],
                       double dt, double tol, int max_iters, int *iters, double R[4], double R0[4]);
 int orc_pseudo_time_run(const orc_problem *pb, double *q[4], double tau_end, int max_iters, int *iters);

@@ -36,7 +36,7 @@ EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_history",
     "ac_set_history", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
-    "ac_stage_sweep_noalloc", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
+    "ac_stage_sweep_noalloc", "ac_realtime_dt", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
     "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
     "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
 )
@@ -97,6 +97,7 @@ def load(build: bool = True):
     L.ac_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
     L.ac_physical_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.ac_residual_norms.argtypes = [C.c_void_p, _D, _D]
+    L.ac_realtime_dt.argtypes = [C.c_void_p, C.c_double, _D]
     L.ac_get_history.argtypes = [C.c_void_p, C.c_int, _D, _D, _D]
     L.ac_set_history.argtypes = [C.c_void_p, C.c_int, _D, _D, _D]
     L.ac_kernel_launches.argtypes = [C.c_void_p]
@@ -262,6 +263,11 @@ class Tank:
         R0 = np.zeros(4)
         _check(load().ac_residual_norms(self._h, _ptr(R), _ptr(R0)))
         return R, R0
+
+    def realtime_dt(self, cfl_t: float) -> float:
+        out = C.c_double(0.0)
+        _check(load().ac_realtime_dt(self._h, cfl_t, C.byref(out)))
+        return out.value
 
     def get_history(self, k: int) -> Tuple[np.ndarray, ...]:
         out = [np.empty((self.ny, self.nx)) for _ in range(3)]

@@ -111,6 +111,7 @@ struct ac_ctx {
     cudaEvent_t ev[5];
     double stage_ms;
     long long stage_launches;
+    unsigned long long *dt_word;   // device result of ac_realtime_dt
     int nhist;            // older real-time levels held (0..2) before the next step
     int order_now;        // backward-difference order of the current step
     int graph_order;      // order the captured graph was built for
@@ -135,6 +136,7 @@ struct Backend {
     virtual int dtau_min(ac_ctx *c, cudaStream_t s) = 0;
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
+    virtual int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) = 0;
 };
 
 // Backward-difference coefficients B0..B3 (Table BDF).
@@ -330,6 +332,12 @@ struct F64Backend : Backend {
         return AC_OK;
     }
     int stage(ac_ctx *c, cudaStream_t s, int st) override { return launch(c, s, st, variant < 0 ? 0 : variant); }
+    int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) override {
+        realtime_dt_kernel<double><<<grid_stride_blocks(c->N), 256, 0, c->stream>>>(args(c, 0), c->cur_host,
+                                                                                     cfl_area, out);
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
     int restore(ac_ctx *c, cudaStream_t s) override {
         // Q <- Q^n (all four fields hold the state of the start of the step)
         for (int f = 0; f < 4; ++f)
@@ -598,6 +606,12 @@ struct MixedBackend : Backend {
         if (rc != AC_OK) return fail(rc, "stage sweep launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return AC_OK;
     }
+    int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) override {
+        realtime_dt_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, c->stream>>>(args(c, 0), c->cur_host,
+                                                                                   cfl_area, out);
+        CK(cudaGetLastError());
+        return AC_OK;
+    }
     int restore(ac_ctx *c, cudaStream_t s) override {
         restore_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
         CK(cudaGetLastError());
@@ -761,6 +775,7 @@ int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const a
     if (rc != AC_OK) return bail(rc);
     CKC(cudaMalloc(&c->partials, max_tiles(grid->nx, grid->ny) * 4 * sizeof(double)));
     CKC(cudaMalloc(&c->ctl, sizeof(Ctl)));
+    CKC(cudaMalloc(&c->dt_word, sizeof(unsigned long long)));
     CKC(cudaMallocHost(&c->hctl, sizeof(Ctl)));
     CKC(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     for (int k = 0; k < 5; ++k) CKC(cudaEventCreate(&c->ev[k]));
@@ -784,6 +799,7 @@ void ac_destroy(ac_ctx *c) {
     if (c->be) { c->be->release(); delete c->be; }
     cudaFree(c->partials);
     cudaFree(c->ctl);
+    cudaFree(c->dt_word);
     if (c->hctl) cudaFreeHost(c->hctl);
     delete c;
 }
@@ -927,6 +943,23 @@ int ac_set_history(ac_ctx *c, int k, const double *rho, const double *rhou, cons
     const double *src[3] = {rho, rhou, rhov};
     if ((rc = c->be->set_history(c, k, src)) != AC_OK) return rc;
     c->nhist = k;
+    return AC_OK;
+}
+
+int ac_realtime_dt(ac_ctx *c, double cfl_t, double *dt_out) {
+    g_err.clear();
+    if (!c || !dt_out) return fail(AC_ERR_ARG, "ctx and dt_out must not be NULL");
+    if (!c->has_state) return fail(AC_ERR_STATE, "no state has been set");
+    if (!(cfl_t > 0.0) || !std::isfinite(cfl_t)) return fail(AC_ERR_ARG, "cfl_t must be finite and > 0");
+    const unsigned long long inf_bits = 0x7ff0000000000000ull;
+    CK(cudaMemcpyAsync(c->dt_word, &inf_bits, sizeof inf_bits, cudaMemcpyHostToDevice, c->stream));
+    int rc = c->be->realtime_dt(c, cfl_t * c->dx * c->dy, c->dt_word);
+    if (rc != AC_OK) return rc;
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->dt_word, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->launches += 1;
+    memcpy(dt_out, &bits, sizeof bits);
     return AC_OK;
 }
 

@@ -349,6 +349,24 @@ __global__ void dtau_min_kernel(const SweepArgs<T> a) {
         atomicMin(&a.ctl->dtau_bits, (unsigned long long)__double_as_longlong(mn));
 }
 
+// Global real-time step (Sec. 2.2.4): min over cells of
+// CFL_t |Omega| / (|u| dS_x + |v| dS_y), from buffer `cur`; +inf at rest.
+template <typename T>
+__global__ void realtime_dt_kernel(const SweepArgs<T> a, int cur, double cfl_area, unsigned long long *out) {
+    const T *const *q = a.buf[cur];
+    const size_t N = (size_t)a.nx * a.ny;
+    double mn = INFINITY;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        const double ir = 1.0 / double(q[0][g]);
+        const double u = double(q[1][g]) * ir, v = double(q[2][g]) * ir;
+        const double den = fabs(u) * double(a.dy) + fabs(v) * double(a.dx);
+        mn = fmin(mn, cfl_area / den);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, (unsigned long long)__double_as_longlong(mn));
+}
+
 // Start of a physical step: Q^n <- Q (Alg. 1) and reset of the control block.
 template <typename T>
 __global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, int max_iters) {

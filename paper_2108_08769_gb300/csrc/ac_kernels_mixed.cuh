@@ -384,6 +384,23 @@ static __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
         atomicMin(&a.ctl->dtau_bits, (unsigned long long)__double_as_longlong(mn));
 }
 
+// Global real-time step (Sec. 2.2.4) in the mixed form, Q = Q^n + dQ.
+static __global__ void realtime_dt_kernel_mixed(const MixedArgs a, int cur, double cfl_area,
+                                                unsigned long long *out) {
+    const float *const *d = a.d[cur];
+    const size_t N = (size_t)a.nx * a.ny;
+    double mn = INFINITY;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        const double r = double(a.qn32[0][g]) + double(d[0][g]);
+        const double u = (double(a.qn32[1][g]) + double(d[1][g])) / r;
+        const double v = (double(a.qn32[2][g]) + double(d[2][g])) / r;
+        mn = fmin(mn, cfl_area / (fabs(u) * double(a.dy) + fabs(v) * double(a.dx)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, (unsigned long long)__double_as_longlong(mn));
+}
+
 // Start of a physical step in the mixed form: the FP64 level absorbs the
 // increments (Q^n <- Q^n + dQ, Alg. 1), its FP32 copy is refreshed, the
 // increments restart from zero, and p' is kept for a restore.

@@ -302,3 +302,16 @@ def test_bdf2_checkpoint_resume_bitwise():
         a.get_history(3)
     a.close()
     c.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("mixed", 1e-6)])
+def test_realtime_dt_from_cfl(precision, tol):
+    """Sec. 2.2.4 global real-time step against the oracle, and +inf at rest."""
+    case = W.random_two_fluid(45, 21, ratio=300.0, c0=8.0, velocity=0.3)
+    t = ac.Tank.from_case(case, precision=precision)
+    assert t.realtime_dt(0.45) == pytest.approx(oracle.realtime_dt(case, case.state(), 0.45), rel=tol)
+    t.close()
+    rest = W.hydrostatic_tank(32)
+    t = ac.Tank.from_case(rest, precision=precision)
+    assert t.realtime_dt(0.45) == math.inf
+    t.close()

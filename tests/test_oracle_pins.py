@@ -368,6 +368,20 @@ def test_dtau_is_the_acoustic_cfl_limit():
     assert np.allclose(oracle.dtau(c, s), d.min(), rtol=0)
 
 
+def test_realtime_dt_is_the_convective_cfl_limit():
+    """Sec. 2.2.4: the global real-time step lets the fastest fluid move
+    CFL_t cells (|u| dt/dx + |v| dt/dy = CFL_t at the worst cell), and a fluid
+    at rest has no limit."""
+    c = W.random_two_fluid(9, 7, ratio=10.0, c0=2.0, velocity=0.5)
+    s = c.state()
+    dt = oracle.realtime_dt(c, s, 0.45)
+    u, v = s[1] / s[0], s[2] / s[0]
+    courant = np.abs(u) * dt / c.dx + np.abs(v) * dt / c.dy
+    assert courant.max() == pytest.approx(0.45, rel=1e-13)
+    rest = W.hydrostatic_tank(8)
+    assert oracle.realtime_dt(rest, rest.state(), 0.45) == math.inf
+
+
 def test_bdf_fixed_point_matches_paper_table():
     """A uniform box at rest with no gravity has zero flux, so the converged
     pseudo-iteration solves sum_s B_s Q^{n+1-s} = 0 with the paper's BDF
