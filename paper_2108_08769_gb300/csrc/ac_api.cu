@@ -159,15 +159,15 @@ struct F64Variant {
 constexpr F64Variant kF64Variants[] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16}};
 constexpr int kNumF64Variants = sizeof(kF64Variants) / sizeof(kF64Variants[0]);
 
-template <int TX, int TY>
+template <int TX, int TY, int RS = kOsher>
 cudaError_t allow_f64_smem() {
-    return cudaFuncSetAttribute(stage_kernel<double, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(stage_kernel<double, TX, TY, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(StageSmem<double, TX, TY>));
 }
 
-template <int TX, int TY>
+template <int TX, int TY, int RS = kOsher>
 cudaError_t launch_f64(const SweepArgs<double> &a, dim3 g, cudaStream_t s) {
-    stage_kernel<double, TX, TY><<<g, TX * TY, sizeof(StageSmem<double, TX, TY>), s>>>(a);
+    stage_kernel<double, TX, TY, RS><<<g, TX * TY, sizeof(StageSmem<double, TX, TY>), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -191,7 +191,10 @@ struct F64Backend : Backend {
         const F64Variant &m = kF64Variants[v];
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
         cudaError_t e;
-        switch (v) {
+        // the Bassi and Roe fluxes are compiled for the first tile shape only
+        if (c->opt.riemann == AC_RIEMANN_BASSI) e = launch_f64<32, 8, kBassi>(a, g, s);
+        else if (c->opt.riemann == AC_RIEMANN_ROE) e = launch_f64<32, 8, kRoe>(a, g, s);
+        else switch (v) {
             case 0: e = launch_f64<32, 8>(a, g, s); break;
             case 1: e = launch_f64<32, 7>(a, g, s); break;
             case 2: e = launch_f64<32, 6>(a, g, s); break;
@@ -207,6 +210,7 @@ struct F64Backend : Backend {
     // fastest kept per grid size.
     int tune(ac_ctx *c, cudaStream_t s) override {
         if (variant >= 0) return AC_OK;
+        if (c->opt.riemann != AC_RIEMANN_OSHER) { set_variant(c, 0); return AC_OK; }
         const char *env = getenv("AC_TILE_F64");
         if (env) {
             const int v = atoi(env);
@@ -280,6 +284,8 @@ struct F64Backend : Backend {
         CK((allow_f64_smem<32, 4>()));
         CK((allow_f64_smem<16, 8>()));
         CK((allow_f64_smem<16, 16>()));
+        CK((allow_f64_smem<32, 8, kBassi>()));
+        CK((allow_f64_smem<32, 8, kRoe>()));
         return AC_OK;
     }
     void release() override {
@@ -348,25 +354,29 @@ struct F64Backend : Backend {
 
 // ------------------------------------------------------------------ mixed
 
-// Tile shapes of the mixed sweep: TX x TY cells per CTA of NT threads.
+// Tile shapes of the mixed sweep: TX x TY cells per CTA of NT threads, and
+// the CTAs per SM the register allocation is asked to allow (1 = no limit).
 struct MixedVariant {
-    int tx, ty, nt;
+    int tx, ty, nt, minb;
 };
+// (Without a CTAs-per-SM hint the compiler spends ~63 registers on this
+// sweep; 6 x 256 or 3 x 512 threads per SM hold it at 40 without spills.)
 constexpr MixedVariant kMixedVariants[] = {
-    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256}, {64, 8, 512}, {64, 16, 512}, {16, 16, 256},
+    {32, 8, 256, 6}, {32, 16, 256, 6}, {32, 16, 512, 3}, {64, 8, 256, 6}, {64, 8, 512, 3}, {64, 16, 512, 3},
+    {16, 16, 256, 6}, {16, 16, 256, 7}, {32, 8, 256, 7}, {32, 16, 512, 1},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false>
 int launch_mixed(const MixedArgs &a, dim3 g, cudaStream_t s) {
-    stage_kernel_mixed<TX, TY, NT><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
+    stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
     return cudaGetLastError() == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false>
 cudaError_t allow_mixed_smem() {
-    return cudaFuncSetAttribute(stage_kernel_mixed<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(MixedSmem<TX, TY>));
+    return cudaFuncSetAttribute(stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedSmem<TX, TY>));
 }
 
 // chosen tile shape per grid size, shared by the contexts of this process
@@ -396,14 +406,22 @@ struct MixedBackend : Backend {
         const MixedArgs a = args(c, st);
         const MixedVariant &m = kMixedVariants[v];
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
+        // the Bassi and Roe fluxes are compiled for the first tile shape only
+        const bool bdf = c->opt.bdf_order > 1;
+        if (c->opt.riemann == AC_RIEMANN_BASSI) return launch_mixed<32, 8, 256, 6, kBassi, true>(a, g, s);
+        if (c->opt.riemann == AC_RIEMANN_ROE) return launch_mixed<32, 8, 256, 6, kRoe, true>(a, g, s);
+        if (bdf) return launch_mixed<32, 8, 256, 6, kOsher, true>(a, g, s);
         switch (v) {
-            case 0: return launch_mixed<32, 8, 256>(a, g, s);
-            case 1: return launch_mixed<32, 16, 256>(a, g, s);
-            case 2: return launch_mixed<32, 16, 512>(a, g, s);
-            case 3: return launch_mixed<64, 8, 256>(a, g, s);
-            case 4: return launch_mixed<64, 8, 512>(a, g, s);
-            case 5: return launch_mixed<64, 16, 512>(a, g, s);
-            default: return launch_mixed<16, 16, 256>(a, g, s);
+            case 0: return launch_mixed<32, 8, 256, 6>(a, g, s);
+            case 1: return launch_mixed<32, 16, 256, 6>(a, g, s);
+            case 2: return launch_mixed<32, 16, 512, 3>(a, g, s);
+            case 3: return launch_mixed<64, 8, 256, 6>(a, g, s);
+            case 4: return launch_mixed<64, 8, 512, 3>(a, g, s);
+            case 5: return launch_mixed<64, 16, 512, 3>(a, g, s);
+            case 6: return launch_mixed<16, 16, 256, 6>(a, g, s);
+            case 7: return launch_mixed<16, 16, 256, 7>(a, g, s);
+            case 8: return launch_mixed<32, 8, 256, 7>(a, g, s);
+            default: return launch_mixed<32, 16, 512, 1>(a, g, s);
         }
     }
 
@@ -412,6 +430,8 @@ struct MixedBackend : Backend {
     // rewritten by the real stage 1) and keep the fastest.
     int tune(ac_ctx *c, cudaStream_t s) override {
         if (variant >= 0) return AC_OK;
+        // other solvers and BDF2/BDF3 run one compiled shape (32 x 8)
+        if (c->opt.riemann != AC_RIEMANN_OSHER || c->opt.bdf_order > 1) { set_variant(c, 0); return AC_OK; }
         const char *env = getenv("AC_TILE");
         if (env) {
             int v = atoi(env);
@@ -483,13 +503,19 @@ struct MixedBackend : Backend {
             if (c->opt.bdf_order >= 2) CK(cudaMalloc(&D1[f], fb));
             if (c->opt.bdf_order >= 3) CK(cudaMalloc(&D2[f], fb));
         }
-        CK((allow_mixed_smem<32, 8, 256>()));
-        CK((allow_mixed_smem<32, 16, 256>()));
-        CK((allow_mixed_smem<32, 16, 512>()));
-        CK((allow_mixed_smem<64, 8, 256>()));
-        CK((allow_mixed_smem<64, 8, 512>()));
-        CK((allow_mixed_smem<64, 16, 512>()));
-        CK((allow_mixed_smem<16, 16, 256>()));
+        CK((allow_mixed_smem<32, 8, 256, 6>()));
+        CK((allow_mixed_smem<32, 16, 256, 6>()));
+        CK((allow_mixed_smem<32, 16, 512, 3>()));
+        CK((allow_mixed_smem<64, 8, 256, 6>()));
+        CK((allow_mixed_smem<64, 8, 512, 3>()));
+        CK((allow_mixed_smem<64, 16, 512, 3>()));
+        CK((allow_mixed_smem<16, 16, 256, 6>()));
+        CK((allow_mixed_smem<16, 16, 256, 7>()));
+        CK((allow_mixed_smem<32, 8, 256, 7>()));
+        CK((allow_mixed_smem<32, 16, 512, 1>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));
         set_variant(c, 0);
         variant = -1;   // tuned at the first physical step
         // the reference applies when both y sides are walls and the pressure

@@ -52,8 +52,9 @@ struct BatchSync {
 };
 
 // Stage s of every active tank; blockIdx.x runs over the flattened tiles.
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+// (the CTAs-per-SM hint keeps the sweep at 40 registers, see ac_api.cu)
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
+__global__ void __launch_bounds__(NT, NT == 512 ? 3 : 6)
 batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ MixedArgs sa;
@@ -77,7 +78,7 @@ batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
     __syncthreads();
     const int local = s_local;
     const int by = local / s_tiles_x, bx = local - by * s_tiles_x;
-    mixed_tile<TX, TY, NT>(sa, bx, by, sa.partials + (size_t)local * 4, smem_raw);
+    mixed_tile<TX, TY, NT, RS, BDF>(sa, bx, by, sa.partials + (size_t)local * 4, smem_raw);
 }
 
 // Start of a physical step for every tank (blockIdx.y = tank): level shift
@@ -202,15 +203,15 @@ constexpr Variant kVariants[] = {
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
 cudaError_t allow_smem() {
-    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(MixedSmem<TX, TY>));
 }
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
 cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, cudaStream_t s) {
-    batch_stage_kernel<TX, TY, NT><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage);
+    batch_stage_kernel<TX, TY, NT, RS, BDF><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage);
     return cudaGetLastError();
 }
 
@@ -283,7 +284,14 @@ int build_tiles(ac_batch *b, int v) {
 
 int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     cudaError_t e;
-    switch (v) {
+    // the Bassi and Roe fluxes are compiled for the first tile shape only
+    if (b->opt.riemann == AC_RIEMANN_BASSI)
+        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+    else if (b->opt.riemann == AC_RIEMANN_ROE)
+        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+    else if (b->opt.bdf_order > 1)
+        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+    else switch (v) {
         case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
         case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
         case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
@@ -300,6 +308,7 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
 // writes only scratch), fastest kept.
 int tune(ac_batch *b, cudaStream_t s) {
     if (b->variant >= 0) return AC_OK;
+    if (b->opt.riemann != AC_RIEMANN_OSHER || b->opt.bdf_order > 1) return build_tiles(b, 0);
     const char *env = getenv("AC_TILE");
     if (env) {
         const int v = atoi(env);
@@ -490,6 +499,9 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     CKB((allow_smem<64, 8, 512>()));
     CKB((allow_smem<64, 16, 512>()));
     CKB((allow_smem<16, 16, 256>()));
+    CKB((allow_smem<32, 8, 256, kBassi, true>()));
+    CKB((allow_smem<32, 8, 256, kRoe, true>()));
+    CKB((allow_smem<32, 8, 256, kOsher, true>()));
     // per-tank descriptors: arrays offset into the pools, scalars, control block
     size_t pos = 0, tpos = 0;
     memset(b->hctl, 0, n * sizeof(Ctl));

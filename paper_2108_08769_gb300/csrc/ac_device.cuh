@@ -221,11 +221,13 @@ __device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     F[3] = u;
 }
 
-template <typename T>
-__device__ __forceinline__ void riemann_flux(int kind, T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
+// Face flux of the solver RS, chosen at compile time so that a kernel built
+// for one solver carries none of the others' registers.
+template <int RS, typename T>
+__device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
                                              T inv_beta, T F[4]) {
-    if (kind == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
-    else if (kind == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    if constexpr (RS == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else if constexpr (RS == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
 }
 

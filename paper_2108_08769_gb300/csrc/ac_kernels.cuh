@@ -89,7 +89,7 @@ struct StageSmem {
     double red[4][TX * TY / 32];
 };
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int RS = kOsher>
 __global__ void __launch_bounds__(TX * TY)
 stage_kernel(const SweepArgs<T> a) {
     using S = StageSmem<T, TX, TY>;
@@ -226,7 +226,7 @@ stage_kernel(const SweepArgs<T> a) {
             const T uL = sm.w[1][ca] + sm.gx[1][ga], uR = sm.w[1][cb] - sm.gx[1][gb];
             const T vL = sm.w[2][ca] + sm.gx[2][ga], vR = sm.w[2][cb] - sm.gx[2][gb];
             const T pL = sm.w[3][ca] + sm.gx[3][ga], pR = sm.w[3][cb] - sm.gx[3][gb];
-            riemann_flux<T>(a.riemann, rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
+            riemann_flux<RS, T>(rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
             sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
         } else {
             const int kk = k - S::NXF;
@@ -238,7 +238,7 @@ stage_kernel(const SweepArgs<T> a) {
             const T vL = sm.w[2][ca] + sm.gy[2][ga], vR = sm.w[2][cb] - sm.gy[2][gb];
             const T pL = sm.w[3][ca] + sm.gy[3][ga], pR = sm.w[3][cb] - sm.gy[3][gb];
             // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            riemann_flux<T>(a.riemann, rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
+            riemann_flux<RS, T>(rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
             sm.fy[0][kk] = F[0]; sm.fy[1][kk] = F[2]; sm.fy[2][kk] = F[1]; sm.fy[3][kk] = F[3];
         }
     }

@@ -71,10 +71,12 @@ struct MixedSmem {
     // one 16-byte vector per cell or face: a face or a cell reads all four
     // components with one shared-memory instruction
     float4 w[RW * RH];       // (rho, u, v, p') of the tile + two-cell halo
-    float4 aux[GW * GH];     // (RT of rho u, RT of rho v, rho_ref, -) on the ring
+    union {                  // aux is dead once the slopes exist; fx reuses it
+        float4 aux[GW * GH]; // (RT of rho u, RT of rho v, rho_ref, -) on the ring
+        float4 fx[NXF];      // x-face fluxes: (mass, x-mom, y-mom, p/beta)
+    };
     float4 gx[GW * GH];      // half slopes along x: (rho, u, v, p)
     float4 gy[GW * GH];      // half slopes along y: (rho, u, v, p - p_ref)
-    float4 fx[NXF];          // x-face fluxes: (mass, x-mom, y-mom, p/beta)
     float4 fy[NYF];          // y-face fluxes
     float dxf[NXF];          // reference jump on each x-face
     double red[4][32];
@@ -119,7 +121,7 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
 // a CTA of NT threads (NT divides TX*TY; several cells per thread in the
 // update when NT < TX*TY).  `partial` receives the tile's four residual
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, int RS, bool BDF>
 __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, double *partial,
                                            unsigned char *smem_raw) {
     using S = MixedSmem<TX, TY>;
@@ -182,13 +184,15 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             if (need_rt) {
                 rx = a.B0 * e1[s];     // B0 (Q^{m} - Q^n) of rho u, ...
                 ry = a.B0 * e2[s];
-                if (a.order >= 2) {
-                    rx -= a.B2 * a.D1[1][s];
-                    ry -= a.B2 * a.D1[2][s];
-                }
-                if (a.order >= 3) {
-                    rx -= a.B3 * a.D2[1][s];
-                    ry -= a.B3 * a.D2[2][s];
+                if constexpr (BDF) {
+                    if (a.order >= 2) {
+                        rx -= a.B2 * a.D1[1][s];
+                        ry -= a.B2 * a.D1[2][s];
+                    }
+                    if (a.order >= 3) {
+                        rx -= a.B3 * a.D2[1][s];
+                        ry -= a.B3 * a.D2[2][s];
+                    }
                 }
                 rx *= inv_dt;
                 ry *= inv_dt;
@@ -255,7 +259,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             const int ga = (fj + 1) * GW + fi;
             const int ca = (fj + 2) * RW + fi + 1;
             const float4 A = sm.w[ca], B = sm.w[ca + 1], SA = sm.gx[ga], SB = sm.gx[ga + 1];
-            riemann_flux<float>(a.riemann, A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
+            riemann_flux<RS, float>(A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
                               B.x - SB.x, B.y - SB.y, B.z - SB.z, B.w - SB.w + 0.5f * jump,
                               a.beta, a.inv_beta, F);
             sm.fx[k] = make_float4(F[0], F[1], F[2], F[3]);
@@ -266,7 +270,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
             const int ca = (fj + 1) * RW + fi + 2;
             const float4 A = sm.w[ca], B = sm.w[ca + RW], SA = sm.gy[ga], SB = sm.gy[ga + GW];
             // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            riemann_flux<float>(a.riemann, A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
+            riemann_flux<RS, float>(A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
                               B.x - SB.x, B.z - SB.z, B.y - SB.y, B.w - SB.w,
                               a.beta, a.inv_beta, F);
             sm.fy[kk] = make_float4(F[0], F[2], F[1], F[3]);
@@ -293,15 +297,17 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const float m0 = __ldg(a.qn32[1] + g) + e1;
         const float n0 = __ldg(a.qn32[2] + g) + e2;
         float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
-        if (a.order >= 2) {
-            rt0 -= a.B2 * a.D1[0][g];
-            rt1 -= a.B2 * a.D1[1][g];
-            rt2 -= a.B2 * a.D1[2][g];
-        }
-        if (a.order >= 3) {
-            rt0 -= a.B3 * a.D2[0][g];
-            rt1 -= a.B3 * a.D2[1][g];
-            rt2 -= a.B3 * a.D2[2][g];
+        if constexpr (BDF) {
+            if (a.order >= 2) {
+                rt0 -= a.B2 * a.D1[0][g];
+                rt1 -= a.B2 * a.D1[1][g];
+                rt2 -= a.B2 * a.D1[2][g];
+            }
+            if (a.order >= 3) {
+                rt0 -= a.B3 * a.D2[0][g];
+                rt1 -= a.B3 * a.D2[1][g];
+                rt2 -= a.B3 * a.D2[2][g];
+            }
         }
         rt0 *= inv_dt;
         rt1 *= inv_dt;
@@ -353,12 +359,12 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
     }
 }
 
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+template <int TX, int TY, int NT, int MINB = 1, int RS = kOsher, bool BDF = false>
+__global__ void __launch_bounds__(NT, MINB)
 stage_kernel_mixed(const MixedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.ctl->done) return;
-    mixed_tile<TX, TY, NT>(a, blockIdx.x, blockIdx.y,
+    mixed_tile<TX, TY, NT, RS, BDF>(a, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
 }
 

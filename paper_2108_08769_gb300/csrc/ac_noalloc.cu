@@ -50,8 +50,12 @@ int setup_device(int dev, unsigned char **scratch) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(StageSmem<double, kTX, kTY>));
+        const int smem = (int)sizeof(StageSmem<double, kTX, kTY>);
+        e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kOsher>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kBassi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kRoe>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         g_scratch_ptr[dev] = p;
     }
@@ -179,7 +183,10 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
         dtau_min_kernel<double><<<blocks, 256, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(AC_ERR_CUDA, "dtau launch: %s", cudaGetErrorString(e));
     }
-    stage_kernel<double, kTX, kTY><<<g, kTX * kTY, sizeof(StageSmem<double, kTX, kTY>), s>>>(a);
+    const size_t smem = sizeof(StageSmem<double, kTX, kTY>);
+    if (opt->riemann == AC_RIEMANN_BASSI) stage_kernel<double, kTX, kTY, kBassi><<<g, kTX * kTY, smem, s>>>(a);
+    else if (opt->riemann == AC_RIEMANN_ROE) stage_kernel<double, kTX, kTY, kRoe><<<g, kTX * kTY, smem, s>>>(a);
+    else stage_kernel<double, kTX, kTY, kOsher><<<g, kTX * kTY, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(AC_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(e));
     if (stage == 1 && norms) {
         noalloc_norms_kernel<<<1, 256, 0, s>>>(partials, (int)tiles, 1.0 / ((double)grid->nx * grid->ny), norms);
