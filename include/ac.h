@@ -185,6 +185,14 @@ long long ac_kernel_launches(const ac_ctx *ctx);
 int ac_set_profiling(ac_ctx *ctx, int on);
 int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launches);
 
+/* The stage-sweep variant the autotuner chose at the first physical step
+ * (AC_ERR_STATE before it): tile width tx, height ty, threads per CTA and
+ * the variant's index in the library's table.  Setting the environment
+ * variable AC_TILE (mixed form) or AC_TILE_F64 (FP64) to an index before the
+ * first step forces that variant; other solvers than Osher and BDF2/BDF3
+ * always run variant 0. */
+int ac_tile_shape(const ac_ctx *ctx, int *tx, int *ty, int *threads, int *variant);
+
 /* ---- many tanks at once (mixed form) -------------------------------------
  * A batch advances n independent tanks of any sizes, densities and beta in
  * the mixed form (FP32 sweep; FP64 time levels, reference pressure and

@@ -36,6 +36,7 @@ EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_history",
     "ac_set_history", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
+    "ac_tile_shape",
     "ac_stage_sweep_noalloc", "ac_realtime_dt", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
     "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
     "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
@@ -104,6 +105,8 @@ def load(build: bool = True):
     L.ac_kernel_launches.restype = C.c_longlong
     L.ac_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.ac_stage_kernel_time.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
+    _IP = C.POINTER(C.c_int)
+    L.ac_tile_shape.argtypes = [C.c_void_p, _IP, _IP, _IP, _IP]
     _PA4 = C.c_void_p * 4
     _PA3 = C.c_void_p * 3
     L.ac_stage_sweep_noalloc.argtypes = [C.POINTER(ac_grid), C.c_double, C.POINTER(ac_bc), C.POINTER(ac_options),
@@ -290,6 +293,12 @@ class Tank:
         n = C.c_longlong(0)
         _check(load().ac_stage_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def tile_shape(self):
+        """(tx, ty, threads, variant) of the tuned stage sweep (variant -1 before the first step)."""
+        a, b, c, v = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        load().ac_tile_shape(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(v))
+        return a.value, b.value, c.value, v.value
 
 
 class Batch:

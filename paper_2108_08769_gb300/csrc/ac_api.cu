@@ -71,7 +71,7 @@ int fail(int code, const char *fmt, ...) {
 // grid (sizes the residual partial sums).
 size_t max_tiles(int nx, int ny) {
     static const int shapes[][2] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16},
-                                    {32, 16}, {64, 8}, {64, 16}};
+                                    {32, 14}, {64, 7}, {32, 16}, {64, 8}, {64, 16}};
     size_t m = 0;
     for (const auto &sh : shapes)
         m = std::max(m, (size_t)((nx + sh[0] - 1) / sh[0]) * ((ny + sh[1] - 1) / sh[1]));
@@ -137,6 +137,8 @@ struct Backend {
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
     virtual int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) = 0;
+    // chosen variant (-1 before tuning) and its tile shape
+    virtual int shape(int &tx, int &ty, int &nt) const = 0;
 };
 
 // Backward-difference coefficients B0..B3 (Table BDF).
@@ -156,7 +158,8 @@ const double kBDF[4][4] = {
 struct F64Variant {
     int tx, ty;
 };
-constexpr F64Variant kF64Variants[] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16}};
+// 32x14 and 64x7 make one 448-cell tile per SM on a 256^2 grid (152 SMs)
+constexpr F64Variant kF64Variants[] = {{32, 8}, {32, 7}, {32, 6}, {32, 4}, {16, 8}, {16, 16}, {32, 14}, {64, 7}};
 constexpr int kNumF64Variants = sizeof(kF64Variants) / sizeof(kF64Variants[0]);
 
 template <int TX, int TY, int RS = kOsher>
@@ -179,6 +182,14 @@ struct F64Backend : Backend {
     double *lev[4] = {};
     double *lev1[3] = {}, *lev2[3] = {};   // Q^{n-1}, Q^{n-2} (BDF2, BDF3)
 
+    int shape(int &tx, int &ty, int &nt) const override {
+        const F64Variant &m = kF64Variants[variant < 0 ? 0 : variant];
+        tx = m.tx;
+        ty = m.ty;
+        nt = m.tx * m.ty;
+        return variant;
+    }
+
     void set_variant(const ac_ctx *c, int v) {
         variant = v;
         const F64Variant &m = kF64Variants[v];
@@ -200,7 +211,9 @@ struct F64Backend : Backend {
             case 2: e = launch_f64<32, 6>(a, g, s); break;
             case 3: e = launch_f64<32, 4>(a, g, s); break;
             case 4: e = launch_f64<16, 8>(a, g, s); break;
-            default: e = launch_f64<16, 16>(a, g, s); break;
+            case 5: e = launch_f64<16, 16>(a, g, s); break;
+            case 6: e = launch_f64<32, 14>(a, g, s); break;
+            default: e = launch_f64<64, 7>(a, g, s); break;
         }
         if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stage sweep launch failed: %s", cudaGetErrorString(e));
         return AC_OK;
@@ -284,6 +297,8 @@ struct F64Backend : Backend {
         CK((allow_f64_smem<32, 4>()));
         CK((allow_f64_smem<16, 8>()));
         CK((allow_f64_smem<16, 16>()));
+        CK((allow_f64_smem<32, 14>()));
+        CK((allow_f64_smem<64, 7>()));
         CK((allow_f64_smem<32, 8, kBassi>()));
         CK((allow_f64_smem<32, 8, kRoe>()));
         return AC_OK;
@@ -358,24 +373,27 @@ struct F64Backend : Backend {
 // the CTAs per SM the register allocation is asked to allow (1 = no limit).
 struct MixedVariant {
     int tx, ty, nt, minb;
+    bool pf;   // ring terms and update inputs prefetched (cp.async / early loads)
 };
 // (Without a CTAs-per-SM hint the compiler spends ~63 registers on this
 // sweep; 6 x 256 or 3 x 512 threads per SM hold it at 40 without spills.)
 constexpr MixedVariant kMixedVariants[] = {
     {32, 8, 256, 6}, {32, 16, 256, 6}, {32, 16, 512, 3}, {64, 8, 256, 6}, {64, 8, 512, 3}, {64, 16, 512, 3},
     {16, 16, 256, 6}, {16, 16, 256, 7}, {32, 8, 256, 7}, {32, 16, 512, 1},
+    {32, 8, 256, 6, true}, {16, 16, 256, 6, true}, {32, 16, 512, 3, true}, {32, 8, 256, 5, true},
+    {16, 16, 256, 5, true},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
-template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false>
+template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, bool PF = false>
 int launch_mixed(const MixedArgs &a, dim3 g, cudaStream_t s) {
-    stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
+    stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
     return cudaGetLastError() == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
-template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false>
+template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, bool PF = false>
 cudaError_t allow_mixed_smem() {
-    return cudaFuncSetAttribute(stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF>,
+    return cudaFuncSetAttribute(stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedSmem<TX, TY>));
 }
 
@@ -394,6 +412,14 @@ struct MixedBackend : Backend {
     double *q64[3] = {};
     std::vector<double> p_ref;   // FP64 reference pressure (host copy)
     bool use_ref = false;
+
+    int shape(int &tx, int &ty, int &nt) const override {
+        const MixedVariant &m = kMixedVariants[variant < 0 ? 0 : variant];
+        tx = m.tx;
+        ty = m.ty;
+        nt = m.nt;
+        return variant;
+    }
 
     void set_variant(const ac_ctx *c, int v) {
         variant = v;
@@ -421,7 +447,12 @@ struct MixedBackend : Backend {
             case 6: return launch_mixed<16, 16, 256, 6>(a, g, s);
             case 7: return launch_mixed<16, 16, 256, 7>(a, g, s);
             case 8: return launch_mixed<32, 8, 256, 7>(a, g, s);
-            default: return launch_mixed<32, 16, 512, 1>(a, g, s);
+            case 9: return launch_mixed<32, 16, 512, 1>(a, g, s);
+            case 10: return launch_mixed<32, 8, 256, 6, kOsher, false, true>(a, g, s);
+            case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, s);
+            case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, s);
+            case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, s);
+            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
         }
     }
 
@@ -513,6 +544,11 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<16, 16, 256, 7>()));
         CK((allow_mixed_smem<32, 8, 256, 7>()));
         CK((allow_mixed_smem<32, 16, 512, 1>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kOsher, false, true>()));
+        CK((allow_mixed_smem<16, 16, 256, 6, kOsher, false, true>()));
+        CK((allow_mixed_smem<32, 16, 512, 3, kOsher, false, true>()));
+        CK((allow_mixed_smem<32, 8, 256, 5, kOsher, false, true>()));
+        CK((allow_mixed_smem<16, 16, 256, 5, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));
@@ -997,6 +1033,17 @@ int ac_set_profiling(ac_ctx *c, int on) {
     c->stage_ms = 0.0;
     c->stage_launches = 0;
     return AC_OK;
+}
+
+int ac_tile_shape(const ac_ctx *c, int *tx, int *ty, int *threads, int *variant) {
+    if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
+    int x, y, n;
+    const int v = c->be->shape(x, y, n);
+    if (tx) *tx = x;
+    if (ty) *ty = y;
+    if (threads) *threads = n;
+    if (variant) *variant = v;
+    return v < 0 ? AC_ERR_STATE : AC_OK;
 }
 
 int ac_stage_kernel_time(const ac_ctx *c, double *total_ms, long long *launches) {

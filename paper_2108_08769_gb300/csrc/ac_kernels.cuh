@@ -217,30 +217,40 @@ stage_kernel(const SweepArgs<T> a) {
 
     // ---- 3. face states and Osher fluxes ----
     for (int k = tid; k < S::NXF + S::NYF; k += NT) {
-        T F[4];
-        if (k < S::NXF) {
+        const bool isx = k < S::NXF;
+        // face states: density, normal and tangential velocity (rotation,
+        // Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure
+        T rL, nL, tL, pL, rR, nR, tR, pR;
+        int fo;   // face index within its kind
+        if (isx) {
             const int fi = k % (TX + 1), fj = k / (TX + 1);  // face between cells fi-1 and fi
             const int ga = (fj + 1) * GW + fi, gb = ga + 1;
             const int ca = (fj + 2) * RW + fi + 1, cb = ca + 1;
-            const T rL = sm.w[0][ca] + sm.gx[0][ga], rR = sm.w[0][cb] - sm.gx[0][gb];
-            const T uL = sm.w[1][ca] + sm.gx[1][ga], uR = sm.w[1][cb] - sm.gx[1][gb];
-            const T vL = sm.w[2][ca] + sm.gx[2][ga], vR = sm.w[2][cb] - sm.gx[2][gb];
-            const T pL = sm.w[3][ca] + sm.gx[3][ga], pR = sm.w[3][cb] - sm.gx[3][gb];
-            riemann_flux<RS, T>(rL, uL, vL, pL, rR, uR, vR, pR, a.beta, a.inv_beta, F);
-            sm.fx[0][k] = F[0]; sm.fx[1][k] = F[1]; sm.fx[2][k] = F[2]; sm.fx[3][k] = F[3];
+            rL = sm.w[0][ca] + sm.gx[0][ga]; rR = sm.w[0][cb] - sm.gx[0][gb];
+            nL = sm.w[1][ca] + sm.gx[1][ga]; nR = sm.w[1][cb] - sm.gx[1][gb];
+            tL = sm.w[2][ca] + sm.gx[2][ga]; tR = sm.w[2][cb] - sm.gx[2][gb];
+            pL = sm.w[3][ca] + sm.gx[3][ga]; pR = sm.w[3][cb] - sm.gx[3][gb];
+            fo = k;
         } else {
             const int kk = k - S::NXF;
             const int fi = kk % TX, fj = kk / TX;            // face between cells fj-1 and fj
             const int ga = fj * GW + fi + 1, gb = ga + GW;
             const int ca = (fj + 1) * RW + fi + 2, cb = ca + RW;
-            const T rL = sm.w[0][ca] + sm.gy[0][ga], rR = sm.w[0][cb] - sm.gy[0][gb];
-            const T uL = sm.w[1][ca] + sm.gy[1][ga], uR = sm.w[1][cb] - sm.gy[1][gb];
-            const T vL = sm.w[2][ca] + sm.gy[2][ga], vR = sm.w[2][cb] - sm.gy[2][gb];
-            const T pL = sm.w[3][ca] + sm.gy[3][ga], pR = sm.w[3][cb] - sm.gy[3][gb];
-            // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            riemann_flux<RS, T>(rL, vL, uL, pL, rR, vR, uR, pR, a.beta, a.inv_beta, F);
-            sm.fy[0][kk] = F[0]; sm.fy[1][kk] = F[2]; sm.fy[2][kk] = F[1]; sm.fy[3][kk] = F[3];
+            rL = sm.w[0][ca] + sm.gy[0][ga]; rR = sm.w[0][cb] - sm.gy[0][gb];
+            tL = sm.w[1][ca] + sm.gy[1][ga]; tR = sm.w[1][cb] - sm.gy[1][gb];
+            nL = sm.w[2][ca] + sm.gy[2][ga]; nR = sm.w[2][cb] - sm.gy[2][gb];
+            pL = sm.w[3][ca] + sm.gy[3][ga]; pR = sm.w[3][cb] - sm.gy[3][gb];
+            fo = kk;
         }
+        // one flux call for both kinds: no divergence where a warp holds both
+        T F[4];
+        riemann_flux<RS, T>(rL, nL, tL, pL, rR, nR, tR, pR, a.beta, a.inv_beta, F);
+        T *fd = isx ? &sm.fx[0][fo] : &sm.fy[0][fo];
+        const int fs = isx ? S::NXF : S::NYF;
+        fd[0] = F[0];
+        fd[fs] = isx ? F[1] : F[2];
+        fd[2 * fs] = isx ? F[2] : F[1];
+        fd[3 * fs] = F[3];
     }
     __syncthreads();
 

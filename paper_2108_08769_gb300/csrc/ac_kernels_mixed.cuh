@@ -117,94 +117,82 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
     }
 }
 
-// One TX x TY tile (tile coordinates bx, by) of one stage of one tank, by
-// a CTA of NT threads (NT divides TX*TY; several cells per thread in the
-// update when NT < TX*TY).  `partial` receives the tile's four residual
-// partial sums at stage 1.  Shared by the single-tank and batched kernels.
-template <int TX, int TY, int NT, int RS, bool BDF>
-__device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, double *partial,
-                                           unsigned char *smem_raw) {
-    using S = MixedSmem<TX, TY>;
-    static_assert((TX * TY) % NT == 0 && NT % 32 == 0, "tile/thread shape");
-    S &sm = *reinterpret_cast<S *>(smem_raw);
-    constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
+// 4-byte global -> shared copy that completes asynchronously (cp.async);
+// cp_async_wait_all() makes this thread's copies visible to itself, a
+// barrier after it to the block.
+__device__ __forceinline__ void cp_async4(void *smem, const float *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Inputs of phases 3-4 read straight from global memory when used.
+struct DirectSrc {
+    static constexpr bool kDxfStaged = false;
+    const MixedArgs &a;
+    const float *const *d0;
+    __device__ __forceinline__ void prefetch(int, int) {}
+    __device__ __forceinline__ float jump(int k, int gi, int gj, bool per_x) const {
+        float j = 0.0f;
+        if (gj < a.ny) {
+            if (gi < a.nx) j = __ldg(a.dref + gj * a.nx + gi);
+            else if (gi == a.nx && per_x) j = __ldg(a.dref + gj * a.nx);
+        }
+        return j;
+    }
+    // (dQ^{m} of rho, rho u, rho v, p'^{m}; Q^n of rho, rho u, rho v; rho_ref) of cell g
+    __device__ __forceinline__ void cell(int cell, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
+                                         float &q1, float &q2, float &rr) const {
+        (void)cell;
+        e0 = d0[0][g]; e1 = d0[1][g]; e2 = d0[2][g]; p0 = d0[3][g];
+        q0 = __ldg(a.qn32[0] + g); q1 = __ldg(a.qn32[1] + g); q2 = __ldg(a.qn32[2] + g);
+        rr = __ldg(a.rho_ref + g);
+    }
+};
+
+// Inputs of phase 4 loaded into registers at the start of phase 3, so that
+// their latency overlaps the face fluxes (one cell per thread); the x-face
+// reference jumps are already in shared memory (staged with cp.async).
+struct PrefetchSrc {
+    static constexpr bool kDxfStaged = true;
+    const MixedArgs &a;
+    const float *const *d0;
+    float v[8];
+    __device__ __forceinline__ void prefetch(int gi, int gj) {
+        if (gi < a.nx && gj < a.ny) {
+            const int g = gj * a.nx + gi;
+            v[0] = d0[0][g]; v[1] = d0[1][g]; v[2] = d0[2][g]; v[3] = d0[3][g];
+            v[4] = __ldg(a.qn32[0] + g); v[5] = __ldg(a.qn32[1] + g); v[6] = __ldg(a.qn32[2] + g);
+            v[7] = __ldg(a.rho_ref + g);
+        }
+    }
+    __device__ __forceinline__ float jump(int, int, int, bool) const { return 0.0f; }
+    __device__ __forceinline__ void cell(int, int, float &e0, float &e1, float &e2, float &p0, float &q0,
+                                         float &q1, float &q2, float &rr) const {
+        e0 = v[0]; e1 = v[1]; e2 = v[2]; p0 = v[3]; q0 = v[4]; q1 = v[5]; q2 = v[6]; rr = v[7];
+    }
+};
+
+// Phases 2-4 of one tile, on W and the ring terms already in shared memory.
+// RAW_AUX: the ring holds (dQ of rho u, dQ of rho v, rho_ref, fold bits) as
+// copied, and the real-time terms are formed here (Backward-Euler only).
+template <int TX, int TY, int NT, int RS, bool BDF, bool RAW_AUX, typename Src>
+__device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int x0, int y0, bool interior,
+                                                   double *partial, MixedSmem<TX, TY> &sm, Src &src) {
+    static_assert(!(RAW_AUX && BDF), "raw ring terms are Backward-Euler only");
+    using S = MixedSmem<TX, TY>;
+    constexpr int RW = S::RW, GW = S::GW, GH = S::GH;
     const Ctl *ctl = a.ctl;
     int in, out;
-    const int cur = ctl->cur;
-    stage_buffers(cur, a.stage, in, out);
-    const float *const *din = a.d[in];
-    const float *const *d0 = a.d[cur];
+    stage_buffers(ctl->cur, a.stage, in, out);
     float *const *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
-
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
-    const int x0 = bx * TX, y0 = by * TY;
-    // halo entirely inside the domain: no ghost folding for this tile
-    const bool interior = (x0 >= 2) && (x0 + TX + 2 <= nx) && (y0 >= 2) && (y0 + TY + 2 <= ny);
-    const CellLoad ld{a.qn32[0], a.qn32[1], a.qn32[2], din[0], din[1], din[2], din[3]};
-
-    // ---- 1. stage Q^{s-1} = Q^n + dQ^{s-1} (+ halo) as W = (rho, u, v, p') ----
-    if (interior) {
-        const int base = (y0 - 2) * nx + (x0 - 2);
-        for (int k = tid; k < RW * RH; k += NT) {
-            const int rr = k / RW, cc = k - rr * RW;
-            sm.w[k] = ld(base + rr * nx + cc, false, false);
-        }
-    } else {
-        for (int k = tid; k < RW * RH; k += NT) {
-            const int rr = k / RW, cc = k - rr * RW;
-            int nfx, tfx, nfy, tfy;
-            const int si = fold_axis(x0 + cc - 2, nx, a.bc[0], a.bc[1], nfx, tfx);
-            const int sj = fold_axis(y0 + rr - 2, ny, a.bc[2], a.bc[3], nfy, tfy);
-            sm.w[k] = ld(sj * nx + si, (nfx + tfy) & 1, (nfy + tfx) & 1);
-        }
-    }
     const bool new_gradp = (a.gradp == kGradNew);
-    const bool need_rt = new_gradp && a.realtime;
-    if (new_gradp) {
-        const float *__restrict__ e1 = d0[1];
-        const float *__restrict__ e2 = d0[2];
-        const float *__restrict__ rref = a.rho_ref;
-        for (int k = tid; k < GW * GH; k += NT) {
-            const int rr = k / GW, cc = k - rr * GW;
-            int s, fx = 0, fy = 0;
-            if (interior) {
-                s = (y0 + rr - 1) * nx + (x0 + cc - 1);
-            } else {
-                int nfx, tfx, nfy, tfy;
-                const int si = fold_axis(x0 + cc - 1, nx, a.bc[0], a.bc[1], nfx, tfx);
-                const int sj = fold_axis(y0 + rr - 1, ny, a.bc[2], a.bc[3], nfy, tfy);
-                s = sj * nx + si;
-                fx = (nfx + tfy) & 1;
-                fy = (nfy + tfx) & 1;
-            }
-            float rx = 0.0f, ry = 0.0f;
-            if (need_rt) {
-                rx = a.B0 * e1[s];     // B0 (Q^{m} - Q^n) of rho u, ...
-                ry = a.B0 * e2[s];
-                if constexpr (BDF) {
-                    if (a.order >= 2) {
-                        rx -= a.B2 * a.D1[1][s];
-                        ry -= a.B2 * a.D1[2][s];
-                    }
-                    if (a.order >= 3) {
-                        rx -= a.B3 * a.D2[1][s];
-                        ry -= a.B3 * a.D2[2][s];
-                    }
-                }
-                rx *= inv_dt;
-                ry *= inv_dt;
-                rx = fx ? -rx : rx;
-                ry = fy ? -ry : ry;
-            }
-            sm.aux[k] = make_float4(rx, ry, __ldg(rref + s), 0.0f);
-        }
-    }
-    __syncthreads();
 
     // ---- 2. limited half slopes and pressure gradient on the ring ----
+    const bool need_rt = new_gradp && a.realtime;
     const float klim = float(a.limiter_k);
     const float kp = (a.gradp == kGradSuperbee || a.gradp == kGradSplitSuperbee) ? 2.0f : 1.0f;
     for (int k = tid; k < GW * GH; k += NT) {
@@ -217,7 +205,21 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         if (new_gradp) {
             float sg = 1.0f;
             if (!interior) sg = wall_ghost_sign<float>(x0 + li - 1, y0 + lj - 1, nx, ny, a.bc);
-            const float4 ax = sm.aux[k];
+            float4 ax = sm.aux[k];
+            if constexpr (RAW_AUX) {
+                float rx = 0.0f, ry = 0.0f;
+                if (need_rt) {
+                    rx = (a.B0 * ax.x) * inv_dt;
+                    ry = (a.B0 * ax.y) * inv_dt;
+                    if (!interior) {
+                        const int f = __float_as_int(ax.w);
+                        rx = (f & 1) ? -rx : rx;
+                        ry = (f & 2) ? -ry : ry;
+                    }
+                }
+                ax.x = rx;
+                ax.y = ry;
+            }
             const float rho = Wc.x, u = Wc.y, v = Wc.z;
             const float ru = rho * u, rv = rho * v, uv = u * v;
             hpx = -a.half_dx * ax.x - (u * u * hrx + 2.0f * ru * hux) -
@@ -245,36 +247,42 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
 
     // ---- 3. face states and Osher fluxes (pressures relative to P_f) ----
     const bool per_x = (a.bc[0] == kPeriodic);
+    src.prefetch(x0 + tid % TX, y0 + tid / TX);
     for (int k = tid; k < S::NXF + S::NYF; k += NT) {
-        float F[4];
-        if (k < S::NXF) {
+        const bool isx = k < S::NXF;
+        // face states: density, normal and tangential velocity (rotation,
+        // Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure
+        float rL, nL, tL, pL, rR, nR, tR, pR;
+        float4 *dst;
+        if (isx) {
             const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
-            const int gi = x0 + fi, gj = y0 + fj;
-            float jump = 0.0f;
-            if (gj < ny) {
-                if (gi < nx) jump = __ldg(a.dref + gj * nx + gi);
-                else if (gi == nx && per_x) jump = __ldg(a.dref + gj * nx);
+            float jump;
+            if constexpr (Src::kDxfStaged) {
+                jump = sm.dxf[k];
+            } else {
+                jump = src.jump(k, x0 + fi, y0 + fj, per_x);
+                sm.dxf[k] = jump;
             }
-            sm.dxf[k] = jump;
             const int ga = (fj + 1) * GW + fi;
             const int ca = (fj + 2) * RW + fi + 1;
             const float4 A = sm.w[ca], B = sm.w[ca + 1], SA = sm.gx[ga], SB = sm.gx[ga + 1];
-            riemann_flux<RS, float>(A.x + SA.x, A.y + SA.y, A.z + SA.z, A.w + SA.w - 0.5f * jump,
-                              B.x - SB.x, B.y - SB.y, B.z - SB.z, B.w - SB.w + 0.5f * jump,
-                              a.beta, a.inv_beta, F);
-            sm.fx[k] = make_float4(F[0], F[1], F[2], F[3]);
+            rL = A.x + SA.x; nL = A.y + SA.y; tL = A.z + SA.z; pL = A.w + SA.w - 0.5f * jump;
+            rR = B.x - SB.x; nR = B.y - SB.y; tR = B.z - SB.z; pR = B.w - SB.w + 0.5f * jump;
+            dst = &sm.fx[k];
         } else {
             const int kk = k - S::NXF;
             const int fj = kk / TX, fi = kk - fj * TX;
             const int ga = fj * GW + fi + 1;
             const int ca = (fj + 1) * RW + fi + 2;
             const float4 A = sm.w[ca], B = sm.w[ca + RW], SA = sm.gy[ga], SB = sm.gy[ga + GW];
-            // rotation (Alg. 2, n = y): normal velocity v, tangential u
-            riemann_flux<RS, float>(A.x + SA.x, A.z + SA.z, A.y + SA.y, A.w + SA.w,
-                              B.x - SB.x, B.z - SB.z, B.y - SB.y, B.w - SB.w,
-                              a.beta, a.inv_beta, F);
-            sm.fy[kk] = make_float4(F[0], F[2], F[1], F[3]);
+            rL = A.x + SA.x; nL = A.z + SA.z; tL = A.y + SA.y; pL = A.w + SA.w;
+            rR = B.x - SB.x; nR = B.z - SB.z; tR = B.y - SB.y; pR = B.w - SB.w;
+            dst = &sm.fy[kk];
         }
+        // one flux call for both kinds: no divergence where a warp holds both
+        float F[4];
+        riemann_flux<RS, float>(rL, nL, tL, pL, rR, nR, tR, pR, a.beta, a.inv_beta, F);
+        *dst = make_float4(F[0], isx ? F[1] : F[2], isx ? F[2] : F[1], F[3]);
     }
     __syncthreads();
 
@@ -292,10 +300,11 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const float div1 = (Fe.y - Fw.y) * a.inv_dx + (Fn.y - Fs.y) * a.inv_dy;
         const float div2 = (Fe.z - Fw.z) * a.inv_dx + (Fn.z - Fs.z) * a.inv_dy;
         const float div3 = (Fe.w - Fw.w) * a.inv_dx + (Fn.w - Fs.w) * a.inv_dy;
-        const float e0 = d0[0][g], e1 = d0[1][g], e2 = d0[2][g], p0 = d0[3][g];
-        const float r0 = __ldg(a.qn32[0] + g) + e0;
-        const float m0 = __ldg(a.qn32[1] + g) + e1;
-        const float n0 = __ldg(a.qn32[2] + g) + e2;
+        float e0, e1, e2, p0, q0, q1, q2, rref;
+        src.cell(cell, g, e0, e1, e2, p0, q0, q1, q2, rref);
+        const float r0 = q0 + e0;
+        const float m0 = q1 + e1;
+        const float n0 = q2 + e2;
         float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
         if constexpr (BDF) {
             if (a.order >= 2) {
@@ -316,7 +325,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         const float sref = -0.5f * (sm.dxf[fw + 1] + sm.dxf[fw]) * a.inv_dx;
         const float b0 = -div0 - rt0;
         const float b1 = -div1 - rt1 + r0 * a.gx + sref;
-        const float b2 = -div2 - rt2 + (r0 - __ldg(a.rho_ref + g)) * a.gy;
+        const float b2 = -div2 - rt2 + (r0 - rref) * a.gy;
         const float b3 = -div3;
         float dtau;
         if (a.local_dtau) {
@@ -359,12 +368,149 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
     }
 }
 
-template <int TX, int TY, int NT, int MINB = 1, int RS = kOsher, bool BDF = false>
+
+// One TX x TY tile (tile coordinates bx, by) of one stage of one tank, by
+// a CTA of NT threads (NT divides TX*TY; several cells per thread in the
+// update when NT < TX*TY).  `partial` receives the tile's four residual
+// partial sums at stage 1.  Shared by the single-tank and batched kernels.
+// PF (one cell per thread, Backward-Euler): the ring terms and the x-face
+// reference jumps are copied with cp.async while the halo is being loaded,
+// and the update's own-cell inputs are prefetched at the start of phase 3.
+template <int TX, int TY, int NT, int RS, bool BDF, bool PF = false>
+__device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, double *partial,
+                                           unsigned char *smem_raw) {
+    using S = MixedSmem<TX, TY>;
+    static_assert((TX * TY) % NT == 0 && NT % 32 == 0, "tile/thread shape");
+    static_assert(!PF || (NT == TX * TY && !BDF), "prefetch: one cell per thread, Backward-Euler");
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
+
+    const Ctl *ctl = a.ctl;
+    int in, out;
+    const int cur = ctl->cur;
+    stage_buffers(cur, a.stage, in, out);
+    const float *const *din = a.d[in];
+    const float *const *d0 = a.d[cur];
+    float *const *dout = a.d[out];
+    const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
+
+    const int nx = a.nx, ny = a.ny;
+    const int tid = threadIdx.x;
+    const int x0 = bx * TX, y0 = by * TY;
+    // halo entirely inside the domain: no ghost folding for this tile
+    const bool interior = (x0 >= 2) && (x0 + TX + 2 <= nx) && (y0 >= 2) && (y0 + TY + 2 <= ny);
+    const CellLoad ld{a.qn32[0], a.qn32[1], a.qn32[2], din[0], din[1], din[2], din[3]};
+    const bool new_gradp = (a.gradp == kGradNew);
+    const bool need_rt = new_gradp && a.realtime;
+
+    if constexpr (PF) {
+        // x-face reference jumps (zero outside the domain)
+        const bool per_x = (a.bc[0] == kPeriodic);
+        for (int k = tid; k < S::NXF; k += NT) {
+            const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
+            const int gi = x0 + fi, gj = y0 + fj;
+            if (gj < ny && gi < nx) cp_async4(&sm.dxf[k], a.dref + gj * nx + gi);
+            else if (gj < ny && gi == nx && per_x) cp_async4(&sm.dxf[k], a.dref + gj * nx);
+            else sm.dxf[k] = 0.0f;
+        }
+        // ring: (dQ of rho u, dQ of rho v, rho_ref, fold bits)
+        if (new_gradp) {
+            for (int k = tid; k < GW * GH; k += NT) {
+                const int rr = k / GW, cc = k - rr * GW;
+                int s, fl = 0;
+                if (interior) {
+                    s = (y0 + rr - 1) * nx + (x0 + cc - 1);
+                } else {
+                    int nfx, tfx, nfy, tfy;
+                    const int si = fold_axis(x0 + cc - 1, nx, a.bc[0], a.bc[1], nfx, tfx);
+                    const int sj = fold_axis(y0 + rr - 1, ny, a.bc[2], a.bc[3], nfy, tfy);
+                    s = sj * nx + si;
+                    fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
+                }
+                float *dst = reinterpret_cast<float *>(&sm.aux[k]);
+                if (need_rt) {
+                    cp_async4(dst, d0[1] + s);
+                    cp_async4(dst + 1, d0[2] + s);
+                }
+                cp_async4(dst + 2, a.rho_ref + s);
+                dst[3] = __int_as_float(fl);
+            }
+        }
+    }
+
+    // ---- 1. stage Q^{s-1} = Q^n + dQ^{s-1} (+ halo) as W = (rho, u, v, p') ----
+    if (interior) {
+        const int base = (y0 - 2) * nx + (x0 - 2);
+        for (int k = tid; k < RW * RH; k += NT) {
+            const int rr = k / RW, cc = k - rr * RW;
+            sm.w[k] = ld(base + rr * nx + cc, false, false);
+        }
+    } else {
+        for (int k = tid; k < RW * RH; k += NT) {
+            const int rr = k / RW, cc = k - rr * RW;
+            int nfx, tfx, nfy, tfy;
+            const int si = fold_axis(x0 + cc - 2, nx, a.bc[0], a.bc[1], nfx, tfx);
+            const int sj = fold_axis(y0 + rr - 2, ny, a.bc[2], a.bc[3], nfy, tfy);
+            sm.w[k] = ld(sj * nx + si, (nfx + tfy) & 1, (nfy + tfx) & 1);
+        }
+    }
+    if (!PF && new_gradp) {
+        const float *__restrict__ e1 = d0[1];
+        const float *__restrict__ e2 = d0[2];
+        const float *__restrict__ rref = a.rho_ref;
+        for (int k = tid; k < GW * GH; k += NT) {
+            const int rr = k / GW, cc = k - rr * GW;
+            int s, fx = 0, fy = 0;
+            if (interior) {
+                s = (y0 + rr - 1) * nx + (x0 + cc - 1);
+            } else {
+                int nfx, tfx, nfy, tfy;
+                const int si = fold_axis(x0 + cc - 1, nx, a.bc[0], a.bc[1], nfx, tfx);
+                const int sj = fold_axis(y0 + rr - 1, ny, a.bc[2], a.bc[3], nfy, tfy);
+                s = sj * nx + si;
+                fx = (nfx + tfy) & 1;
+                fy = (nfy + tfx) & 1;
+            }
+            float rx = 0.0f, ry = 0.0f;
+            if (need_rt) {
+                rx = a.B0 * e1[s];     // B0 (Q^{m} - Q^n) of rho u, ...
+                ry = a.B0 * e2[s];
+                if constexpr (BDF) {
+                    if (a.order >= 2) {
+                        rx -= a.B2 * a.D1[1][s];
+                        ry -= a.B2 * a.D1[2][s];
+                    }
+                    if (a.order >= 3) {
+                        rx -= a.B3 * a.D2[1][s];
+                        ry -= a.B3 * a.D2[2][s];
+                    }
+                }
+                rx *= inv_dt;
+                ry *= inv_dt;
+                rx = fx ? -rx : rx;
+                ry = fy ? -ry : ry;
+            }
+            sm.aux[k] = make_float4(rx, ry, __ldg(rref + s), 0.0f);
+        }
+    }
+    if constexpr (PF) {
+        cp_async_wait_all();
+        __syncthreads();
+        PrefetchSrc src{a, d0, {}};
+        mixed_tile_compute<TX, TY, NT, RS, BDF, true>(a, x0, y0, interior, partial, sm, src);
+    } else {
+        __syncthreads();
+        DirectSrc src{a, d0};
+        mixed_tile_compute<TX, TY, NT, RS, BDF, false>(a, x0, y0, interior, partial, sm, src);
+    }
+}
+
+template <int TX, int TY, int NT, int MINB = 1, int RS = kOsher, bool BDF = false, bool PF = false>
 __global__ void __launch_bounds__(NT, MINB)
 stage_kernel_mixed(const MixedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.ctl->done) return;
-    mixed_tile<TX, TY, NT, RS, BDF>(a, blockIdx.x, blockIdx.y,
+    mixed_tile<TX, TY, NT, RS, BDF, PF>(a, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
 }
 

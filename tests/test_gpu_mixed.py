@@ -171,3 +171,25 @@ def test_bdf_levels_against_oracle(order):
         states.append(ref)
     check(t.get_state(), states[-1])
     t.close()
+
+
+N_MIXED_VARIANTS = 15
+
+
+@pytest.mark.parametrize("v", range(N_MIXED_VARIANTS))
+@pytest.mark.parametrize("bc", [("periodic", "periodic", "slip", "noslip"), ("slip", "transmissive", "slip", "slip"),
+                                ("slip", "slip", "transmissive", "slip")],
+                         ids=["periodic_x_walls_y", "walls_transmissive_x", "reference_off"])
+def test_every_tile_variant_against_oracle(monkeypatch, v, bc):
+    """Each compiled tile shape and load scheme (direct or prefetched),
+    forced in place of the autotuner's pick, on a grid with ragged tails in
+    both directions; the first two boundary sets use the hydrostatic
+    reference, the third runs without it."""
+    monkeypatch.setenv("AC_TILE", str(v))
+    case = W.random_two_fluid(70, 45, ratio=1000.0, c0=20.0, bc=bc)
+    t = ac.Tank.from_case(case, precision="mixed")
+    t.physical_step(case.dt, -1.0, 6)
+    assert t.tile_shape()[3] == v
+    got = t.get_state()
+    t.close()
+    check(got, oracle_run(case, iters=6))

@@ -315,3 +315,23 @@ def test_realtime_dt_from_cfl(precision, tol):
     t = ac.Tank.from_case(rest, precision=precision)
     assert t.realtime_dt(0.45) == math.inf
     t.close()
+
+
+N_F64_VARIANTS = 8
+
+
+@pytest.mark.parametrize("v", range(N_F64_VARIANTS))
+@pytest.mark.parametrize("bc", [("periodic", "periodic", "slip", "noslip"), ("slip", "transmissive", "slip", "slip")])
+def test_every_tile_variant(monkeypatch, v, bc):
+    """Each compiled tile shape, forced in place of the autotuner's pick, on
+    a grid with ragged tails in both directions for every shape."""
+    monkeypatch.setenv("AC_TILE_F64", str(v))
+    case = W.random_two_fluid(70, 45, ratio=1000.0, c0=20.0, bc=bc)
+    t = ac.Tank.from_case(case)
+    t.physical_step(case.dt, -1.0, 4)
+    assert t.tile_shape()[3] == v
+    got = t.get_state()
+    t.close()
+    ref, *_ = oracle.physical_step(case, case.state(), tol=-1.0, max_iters=4)
+    errs = rel_errors(got, ref)
+    assert max(errs) <= TOL, errs
