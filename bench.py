@@ -267,11 +267,12 @@ def run_ours(args, ws, rank, local):
     # ---- roofline of the FP64 stage sweep ----
     tank.set_state(*case.state())
     per_launch_s = stage_launch_ms(tank, case, min(args.steps, 3)) * 1e-3
+    ftx, fty, _, fv = tank.tile_shape()
     achieved = FP64_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FP64_TRAFFIC_PER_CELL_STAGE * case.cells,
-                "kernel": "stage_kernel<double,32,8>", "launch_ms": per_launch_s * 1e3,
+                "kernel": f"stage_kernel<double,{ftx},{fty}>", "tile_variant": fv, "launch_ms": per_launch_s * 1e3,
                 "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
                 "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM), not measured",
                 "hbm_frac_of_measured": BYTES_PER_CELL_ITER_F64 / 3.0 * case.cells / per_launch_s / 1e9
@@ -316,6 +317,7 @@ def run_ours(args, ws, rank, local):
         l_ms, l_iters, l_launches = timed_steps(lt, lc, lk, stream, flush, barrier)
         lt.set_state(*lc.state())
         l_launch_s = stage_launch_ms(lt, lc, 1, tol=-1.0, max_iters=30) * 1e-3
+        ltx, lty, lnt, lv = lt.tile_shape()
         # error against the FP64 GPU path after one step of 20 iterations
         lt.set_state(*lc.state())
         lt.physical_step(lc.dt, -1.0, 20)
@@ -333,7 +335,8 @@ def run_ours(args, ws, rank, local):
                  "value": l_value, "unit": UNIT, "steps": lk, "ms_per_step": l_ms / lk,
                  "pseudo_iters_per_step": statistics.mean(l_iters), "gpu_launches": l_launches,
                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": measured_hbm_gbs(), "unit": "GB/s",
-                              "frac": gbs / measured_hbm_gbs(), "kernel": "stage_kernel_mixed",
+                              "frac": gbs / measured_hbm_gbs(),
+                              "kernel": f"stage_kernel_mixed<{ltx},{lty},{lnt}>", "tile_variant": lv,
                               "launch_ms": l_launch_s * 1e3,
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
                               "traffic": MIXED_TRAFFIC_PER_CELL_STAGE * lc.cells,
@@ -448,10 +451,12 @@ def run_batched(args, stream, flush, barrier):
 
 
 # FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
-# counted by ncu on stage_kernel<double,32,8> (profiles/stage_kernel_f64_*)
-FP64_FLOPS_PER_CELL_STAGE = 927.0
-# DRAM bytes per cell of one FP64 stage launch (ncu, 2048x2048 case, larger than L2)
-FP64_TRAFFIC_PER_CELL_STAGE = 115.3
+# counted by ncu on stage_kernel<double,32,14> on this 256x256 tank
+# (profiles/stage_kernel_f64_hydrostatic_256.md)
+FP64_FLOPS_PER_CELL_STAGE = 851.1
+# DRAM bytes per cell of one FP64 stage launch, same capture (5.83 MB read,
+# the output stays in L2)
+FP64_TRAFFIC_PER_CELL_STAGE = 89.0
 # algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3)
 BYTES_PER_CELL_ITER_F64 = 328.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref

@@ -2,10 +2,10 @@
 // the mixed form (declared in include/ac.h, ac_batch_*).
 //
 // Every stage of every tank is one launch over the flattened list of all
-// tanks' tiles: CTA b looks up its tank in a tile -> tank map, copies the
-// tank's descriptor into shared memory and runs the same tile sweep as the
-// single-tank kernel (mixed_tile), so a tank's numbers do not depend on
-// what else is in the batch.  Each tank has its own control block: its own
+// tanks' tiles: CTA b looks up its tank in a tile -> tank map, reads the
+// tank's descriptor for this stage from global memory and runs the same
+// tile sweep as the single-tank kernel (mixed_tile), so a tank's numbers do
+// not depend on what else is in the batch.  Each tank has its own control block: its own
 // pseudo-iteration count, residual norms, stopping test, convergence flag
 // and buffer rotation; the tiles of a tank that has converged return at
 // once.  The end-of-iteration kernel runs one CTA per tank; the last CTA to
@@ -52,33 +52,19 @@ struct BatchSync {
 };
 
 // Stage s of every active tank; blockIdx.x runs over the flattened tiles.
-// (the CTAs-per-SM hint keeps the sweep at 40 registers, see ac_api.cu)
+// The tank's descriptor for this stage (stage and alpha_s set on the host)
+// is read from global memory, tanks[(stage - 1) * ntanks + k].  (The
+// CTAs-per-SM hint keeps the sweep at 40 registers, see ac_api.cu.)
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
 __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 6)
-batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage) {
+batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage, int ntanks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ MixedArgs sa;
-    __shared__ int s_local, s_tiles_x;
     const int k = tile_tank[blockIdx.x];
-    const BatchTank &t = tanks[k];
+    const BatchTank &t = tanks[(stage - 1) * ntanks + k];
     if (t.a.ctl->done) return;
-    // descriptor -> shared memory (word by word), then the stage fields
-    const unsigned int *src = reinterpret_cast<const unsigned int *>(&t.a);
-    unsigned int *dst = reinterpret_cast<unsigned int *>(&sa);
-    for (int w = threadIdx.x; w < (int)(sizeof(MixedArgs) / 4); w += NT) dst[w] = src[w];
-    if (threadIdx.x == 0) {
-        s_local = blockIdx.x - t.tile0;
-        s_tiles_x = t.tiles_x;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sa.stage = stage;
-        sa.alpha = 1.0f / float(sa.s_max - stage + 1);
-    }
-    __syncthreads();
-    const int local = s_local;
-    const int by = local / s_tiles_x, bx = local - by * s_tiles_x;
-    mixed_tile<TX, TY, NT, RS, BDF>(sa, bx, by, sa.partials + (size_t)local * 4, smem_raw);
+    const int local = blockIdx.x - t.tile0;
+    const int by = local / t.tiles_x, bx = local - by * t.tiles_x;
+    mixed_tile<TX, TY, NT, RS, BDF>(t.a, bx, by, t.a.partials + (size_t)local * 4, smem_raw);
 }
 
 // Start of a physical step for every tank (blockIdx.y = tank): level shift
@@ -195,6 +181,8 @@ __global__ void batch_restore_kernel(BatchTank *tanks) {
     }
 }
 
+// (The prefetching tile sweep of the single-tank kernel was measured here
+// too and is slower: the descriptor already costs registers.)
 struct Variant {
     int tx, ty, nt;
 };
@@ -205,13 +193,14 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
 cudaError_t allow_smem() {
-    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(MixedSmem<TX, TY>));
+    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedSmem<TX, TY>));
 }
 
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
-cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, cudaStream_t s) {
-    batch_stage_kernel<TX, TY, NT, RS, BDF><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage);
+cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, int ntanks, cudaStream_t s) {
+    batch_stage_kernel<TX, TY, NT, RS, BDF><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage,
+                                                                                              ntanks);
     return cudaGetLastError();
 }
 
@@ -240,6 +229,7 @@ struct ac_batch {
     int *tile_map;                      // per variant: flattened tile -> tank
     double *dt_dev;
     std::vector<BatchTank> tanks_host;
+    std::vector<BatchTank> tanks_stage;    // host image of tanks_dev (per stage)
     std::vector<std::vector<double>> p_ref;
     std::vector<char> use_ref;
     Ctl *hctl;                          // pinned mirror of all control blocks
@@ -261,6 +251,23 @@ struct ac_batch {
 
 namespace {
 
+// Device descriptors: one copy of every tank's per stage (stage and alpha_s
+// set), stage 1's first; the other batch kernels read the first n.
+int upload_tanks(ac_batch *b, cudaStream_t s) {
+    const int S = b->opt.rk_stages;
+    b->tanks_stage.resize((size_t)S * b->n);
+    for (int st = 1; st <= S; ++st)
+        for (int k = 0; k < b->n; ++k) {
+            BatchTank t = b->tanks_host[k];
+            t.a.stage = st;
+            t.a.alpha = float(1.0 / double(S - st + 1));
+            b->tanks_stage[(size_t)(st - 1) * b->n + k] = t;
+        }
+    CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_stage.data(), b->tanks_stage.size() * sizeof(BatchTank),
+                       cudaMemcpyHostToDevice, s));
+    return AC_OK;
+}
+
 int build_tiles(ac_batch *b, int v) {
     const Variant &m = kVariants[v];
     b->map_host.clear();
@@ -276,8 +283,8 @@ int build_tiles(ac_batch *b, int v) {
     b->variant = v;
     CK(cudaMemcpyAsync(b->tile_map, b->map_host.data(), b->map_host.size() * sizeof(int), cudaMemcpyHostToDevice,
                        b->stream));
-    CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_host.data(), b->n * sizeof(BatchTank), cudaMemcpyHostToDevice,
-                       b->stream));
+    int rc = upload_tanks(b, b->stream);
+    if (rc != AC_OK) return rc;
     CK(cudaStreamSynchronize(b->stream));
     return AC_OK;
 }
@@ -286,19 +293,19 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     cudaError_t e;
     // the Bassi and Roe fluxes are compiled for the first tile shape only
     if (b->opt.riemann == AC_RIEMANN_BASSI)
-        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
     else if (b->opt.riemann == AC_RIEMANN_ROE)
-        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
     else if (b->opt.bdf_order > 1)
-        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, s);
+        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
     else switch (v) {
-        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
-        default: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, s); break;
+        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        default: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
     return AC_OK;
@@ -309,7 +316,7 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
 int tune(ac_batch *b, cudaStream_t s) {
     if (b->variant >= 0) return AC_OK;
     if (b->opt.riemann != AC_RIEMANN_OSHER || b->opt.bdf_order > 1) return build_tiles(b, 0);
-    const char *env = getenv("AC_TILE");
+    const char *env = getenv("AC_BATCH_TILE");
     if (env) {
         const int v = atoi(env);
         if (v >= 0 && v < kNumVariants) return build_tiles(b, v);
@@ -486,7 +493,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     CKB(cudaMalloc(&b->tile_map, max_tiles * sizeof(int)));
     CKB(cudaMalloc(&b->ctl, n * sizeof(Ctl)));
     CKB(cudaMalloc(&b->sync, sizeof(BatchSync)));
-    CKB(cudaMalloc(&b->tanks_dev, n * sizeof(BatchTank)));
+    CKB(cudaMalloc(&b->tanks_dev, (size_t)n * o.rk_stages * sizeof(BatchTank)));
     CKB(cudaMalloc(&b->dt_dev, n * sizeof(double)));
     CKB(cudaMallocHost(&b->hctl, n * sizeof(Ctl)));
     CKB(cudaMemset(b->sync, 0, sizeof(BatchSync)));
@@ -655,7 +662,8 @@ int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_it
             a.B2 = float(bdf[order][2]);
             a.B3 = float(bdf[order][3]);
         }
-        CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_host.data(), b->n * sizeof(BatchTank), cudaMemcpyHostToDevice, s));
+        const int urc = upload_tanks(b, s);
+        if (urc != AC_OK) return urc;
         b->order_now = order;
     }
     CK(cudaMemcpyAsync(b->dt_dev, h.data(), b->n * sizeof(double), cudaMemcpyHostToDevice, s));

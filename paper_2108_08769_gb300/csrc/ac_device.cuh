@@ -22,11 +22,13 @@ enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2 };
 // ---------------------------------------------------------------------------
 template <typename T> struct Ar;
 template <> struct Ar<double> {
-    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    // returns sqrt(x) and 1/sqrt(x)
+    // correctly rounded reciprocal (the division routine's numerator handling is not needed)
+    static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+    // returns sqrt(x) and 1/sqrt(x): one reciprocal square root (<= 1 ulp) and
+    // a product, in place of a square root and a division
     static __device__ __forceinline__ void sqrt_rsqrt(double x, double &s, double &rs) {
-        s = sqrt(x);
-        rs = 1.0 / s;
+        rs = rsqrt(x);
+        s = x * rs;
     }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }

@@ -391,7 +391,6 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
     stage_buffers(cur, a.stage, in, out);
     const float *const *din = a.d[in];
     const float *const *d0 = a.d[cur];
-    float *const *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
 
     const int nx = a.nx, ny = a.ny;

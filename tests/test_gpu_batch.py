@@ -52,6 +52,24 @@ def test_batch_equals_single_tanks_bitwise_fixed_iterations():
     b.close()
 
 
+N_BATCH_VARIANTS = 7
+
+
+@pytest.mark.parametrize("v", range(N_BATCH_VARIANTS))
+def test_every_batch_variant_equals_single_tanks_bitwise(monkeypatch, v):
+    """Each compiled batch tile shape, forced in place of the autotuner's
+    pick."""
+    monkeypatch.setenv("AC_BATCH_TILE", str(v))
+    cases = uneven_cases()
+    b = ac.Batch.from_cases(cases)
+    b.physical_step(1e-3, -1.0, 5)
+    for k, c in enumerate(cases):
+        ref, _, _ = single_mixed(c, 1e-3, -1.0, 5)
+        for x, y in zip(b.get_state(k), ref):
+            assert np.array_equal(x, y), k
+    b.close()
+
+
 def test_batch_against_oracle():
     cases = uneven_cases()[:4] + uneven_cases()[6:]
     b = ac.Batch.from_cases(cases)
@@ -69,7 +87,8 @@ def test_per_tank_convergence_flags_and_counts(monkeypatch):
     Absolute residual floors, as the paper's own stopping rules are (the
     relative drop cannot pass here: the first iteration's rho v residual is
     round-off in columns that start in vertical balance)."""
-    monkeypatch.setenv("AC_TILE", "0")
+    monkeypatch.setenv("AC_TILE", "0")         # single tank: 32x8 tiles
+    monkeypatch.setenv("AC_BATCH_TILE", "0")   # batch: 32x8 tiles (same partial-sum order)
     cases = W.batched_tanks(count=5, nmin=16, nmax=48, seed=21)
     for c in cases:
         c.options.abs_tol = (0.03, 0.3, 0.3, 100.0)
