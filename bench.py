@@ -462,10 +462,11 @@ BYTES_PER_CELL_ITER_F64 = 328.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, stage_kernel_mixed, 2048x2048): DRAM bytes and FP32
-# arithmetic thread-instructions per cell of one stage launch
-MIXED_TRAFFIC_PER_CELL_STAGE = 64.1
-MIXED_FP32_OPS_PER_CELL_STAGE = 506.0
+# measured (ncu, stage_kernel_mixed<32,8,256> prefetching variant, 2048x2048,
+# profiles/stage_kernel_mixed_rayleigh_taylor_2048.md): DRAM bytes and FP32
+# arithmetic thread-instructions (FFMA + FADD + FMUL) per cell of one stage launch
+MIXED_TRAFFIC_PER_CELL_STAGE = 64.2
+MIXED_FP32_OPS_PER_CELL_STAGE = 463.2
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
