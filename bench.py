@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default="hydrostatic_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048x8192 mixed-form leg")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the benchmark line: one line per test configuration (FP64, mixed, oracle)")
     return ap.parse_args()
 
 
@@ -477,10 +479,64 @@ def measured_hbm_gbs():
         return 6800.0
 
 
+def run_configs(args, rank, local):
+    """Every single-tank configuration of the test set in both forms: a
+    fixed number of pseudo-iterations per physical step (the same work in
+    both forms), CUDA events around K steps, the mixed form's error against
+    the FP64 GPU run from the same state, the HBM fraction from the
+    algorithmic bytes, and the FP64 oracle's rate on 2 pseudo-iterations of
+    the same tank (of a 512x2048 tank for the 2048x8192 one)."""
+    import torch
+    import oracle
+    from paper_2108_08769_gb300 import ac, workloads as W
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    oracle.build()
+    configs = [("riemann_200x4", W.riemann_tank, 500, None),
+               ("hydrostatic_256", lambda: W.hydrostatic_tank(256), 500, None),
+               ("water_column_1024x512", lambda: W.water_column(1024, 512), 200, None),
+               ("rayleigh_taylor_2048x8192", lambda: W.rayleigh_taylor(2048, 8192), 50,
+                lambda: W.rayleigh_taylor(512, 2048))]
+    for name, fn, iters, sample_fn in configs:
+        case = fn()
+        line = {"config": name, "cells": case.cells, "pseudo_iters_per_step": iters, "steps": args.steps,
+                "unit": UNIT}
+        states = {}
+        for prec, bpc in (("fp64", BYTES_PER_CELL_ITER_F64), ("mixed", MIXED_BYTES_PER_CELL_ITER)):
+            t = ac.Tank.from_case(case, precision=prec)
+            t.set_stream(stream.cuda_stream)
+            t.physical_step(case.dt, -1.0, iters)          # warm-up (tuning)
+            t.set_state(*case.state())
+            ms, its, _ = timed_steps(t, case, args.steps, stream, flush, torch.cuda.synchronize, tol=-1.0,
+                                     max_iters=iters)
+            t.set_state(*case.state())
+            t.physical_step(case.dt, -1.0, iters)
+            states[prec] = t.get_state()
+            tx, ty, nt, v = t.tile_shape()
+            t.close()
+            val = case.cells * sum(its) / (ms * 1e-3)
+            line[prec] = {"value": val, "hbm_frac_of_measured": val * bpc / 1e9 / measured_hbm_gbs(),
+                          "tile": [tx, ty, nt], "tile_variant": v}
+        line["mixed"]["speedup_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
+        line["mixed"]["error_vs_fp64_gpu"] = field_errors(states["mixed"], states["fp64"])
+        oc = sample_fn() if sample_fn else case
+        t0 = time.perf_counter()
+        _, _, oits, _, _ = oracle.physical_step(oc, oc.state(), tol=-1.0, max_iters=2)
+        line["oracle_1_core"] = {"value": oc.cells * oits / (time.perf_counter() - t0),
+                                 "sample": f"2 pseudo-iterations of a {oc.nx}x{oc.ny} tank"}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init()
-    if args.impl == "reference":
+    if args.configs:
+        run_configs(args, rank, local)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_ours(args, ws, rank, local)

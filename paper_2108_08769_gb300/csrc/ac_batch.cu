@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ac.h"
@@ -51,20 +52,37 @@ struct BatchSync {
     unsigned int still_active; // tanks still iterating after this iteration
 };
 
-// Stage s of every active tank; blockIdx.x runs over the flattened tiles.
-// The tank's descriptor for this stage (stage and alpha_s set on the host)
-// is read from global memory, tanks[(stage - 1) * ntanks + k].  (The
-// CTAs-per-SM hint keeps the sweep at 40 registers, see ac_api.cu.)
-template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
+// Descriptors of batches that fit, in constant memory: a CTA's loads of its
+// tank's sizes, beta and pointers are then uniform constant-cache reads.  A
+// batch owns a contiguous range of slots (first fit); larger batches, or
+// batches created while the table is full, read their descriptors from
+// global memory.
+constexpr int kConstTanks = 160;
+__constant__ BatchTank c_tanks[kConstTanks];
+
+// Stage `stage` (coefficient alpha_s) of every active tank; blockIdx.x runs
+// over the flattened tiles.  CD: the tank's descriptor is c_tanks[slot0 + k],
+// else tanks[k].  PF: the prefetching tile sweep (see mixed_tile).  (The CTAs-per-SM hint keeps the sweep at 40 registers, see
+// ac_api.cu.)
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool CD = false, bool PF = false>
 __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 6)
-batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage, int ntanks) {
+batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage, float alpha,
+                   int slot0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = tile_tank[blockIdx.x];
-    const BatchTank &t = tanks[(stage - 1) * ntanks + k];
-    if (t.a.ctl->done) return;
-    const int local = blockIdx.x - t.tile0;
-    const int by = local / t.tiles_x, bx = local - by * t.tiles_x;
-    mixed_tile<TX, TY, NT, RS, BDF>(t.a, bx, by, t.a.partials + (size_t)local * 4, smem_raw);
+    if constexpr (CD) {
+        const BatchTank &t = c_tanks[slot0 + k];
+        if (t.a.ctl->done) return;
+        const int local = blockIdx.x - t.tile0;
+        const int by = local / t.tiles_x, bx = local - by * t.tiles_x;
+        mixed_tile<TX, TY, NT, RS, BDF, PF>(t.a, stage, alpha, bx, by, t.a.partials + (size_t)local * 4, smem_raw);
+    } else {
+        const BatchTank &t = tanks[k];
+        if (t.a.ctl->done) return;
+        const int local = blockIdx.x - t.tile0;
+        const int by = local / t.tiles_x, bx = local - by * t.tiles_x;
+        mixed_tile<TX, TY, NT, RS, BDF, PF>(t.a, stage, alpha, bx, by, t.a.partials + (size_t)local * 4, smem_raw);
+    }
 }
 
 // Start of a physical step for every tank (blockIdx.y = tank): level shift
@@ -181,27 +199,60 @@ __global__ void batch_restore_kernel(BatchTank *tanks) {
     }
 }
 
-// (The prefetching tile sweep of the single-tank kernel was measured here
-// too and is slower: the descriptor already costs registers.)
 struct Variant {
     int tx, ty, nt;
+    bool pf;   // prefetching tile sweep
 };
 constexpr Variant kVariants[] = {
-    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256}, {64, 8, 512}, {64, 16, 512}, {16, 16, 256},
+    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256},       {64, 8, 512},
+    {64, 16, 512}, {16, 16, 256}, {32, 8, 256, true}, {16, 16, 256, true},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
 cudaError_t allow_smem() {
-    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF>,
+    cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF, false, PF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedSmem<TX, TY>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batch_stage_kernel<TX, TY, NT, RS, BDF, true, PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedSmem<TX, TY>));
 }
 
-template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false>
-cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, int ntanks, cudaStream_t s) {
-    batch_stage_kernel<TX, TY, NT, RS, BDF><<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage,
-                                                                                              ntanks);
+// slot0 < 0: descriptors in global memory
+template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
+cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, float alpha, int slot0,
+                         cudaStream_t s) {
+    if (slot0 >= 0)
+        batch_stage_kernel<TX, TY, NT, RS, BDF, true, PF>
+            <<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage, alpha, slot0);
+    else
+        batch_stage_kernel<TX, TY, NT, RS, BDF, false, PF>
+            <<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage, alpha, 0);
     return cudaGetLastError();
+}
+
+// First-fit allocator over the constant descriptor table (process-wide).
+std::mutex g_slot_mu;
+std::vector<char> g_slot_used(kConstTanks, 0);
+
+int acquire_slots(int n) {
+    if (getenv("AC_BATCH_GLOBAL_DESC")) return -1;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int s = 0; s + n <= kConstTanks; ++s) {
+        bool free_run = true;
+        for (int q = s; q < s + n && free_run; ++q) free_run = !g_slot_used[q];
+        if (free_run) {
+            for (int q = s; q < s + n; ++q) g_slot_used[q] = 1;
+            return s;
+        }
+    }
+    return -1;
+}
+
+void release_slots(int s, int n) {
+    if (s < 0) return;
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int q = s; q < s + n; ++q) g_slot_used[q] = 0;
 }
 
 constexpr size_t kAlign = 64;   // cells: each tank's arrays start on a 256-byte boundary
@@ -229,7 +280,7 @@ struct ac_batch {
     int *tile_map;                      // per variant: flattened tile -> tank
     double *dt_dev;
     std::vector<BatchTank> tanks_host;
-    std::vector<BatchTank> tanks_stage;    // host image of tanks_dev (per stage)
+    int slot0;                          // first constant-table slot, -1: descriptors in global memory
     std::vector<std::vector<double>> p_ref;
     std::vector<char> use_ref;
     Ctl *hctl;                          // pinned mirror of all control blocks
@@ -251,20 +302,13 @@ struct ac_batch {
 
 namespace {
 
-// Device descriptors: one copy of every tank's per stage (stage and alpha_s
-// set), stage 1's first; the other batch kernels read the first n.
+// Device descriptors (global memory, and the constant table when the batch
+// holds slots there), stream-ordered before the next launch that reads them.
 int upload_tanks(ac_batch *b, cudaStream_t s) {
-    const int S = b->opt.rk_stages;
-    b->tanks_stage.resize((size_t)S * b->n);
-    for (int st = 1; st <= S; ++st)
-        for (int k = 0; k < b->n; ++k) {
-            BatchTank t = b->tanks_host[k];
-            t.a.stage = st;
-            t.a.alpha = float(1.0 / double(S - st + 1));
-            b->tanks_stage[(size_t)(st - 1) * b->n + k] = t;
-        }
-    CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_stage.data(), b->tanks_stage.size() * sizeof(BatchTank),
-                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->tanks_dev, b->tanks_host.data(), b->n * sizeof(BatchTank), cudaMemcpyHostToDevice, s));
+    if (b->slot0 >= 0)
+        CK(cudaMemcpyToSymbolAsync(c_tanks, b->tanks_host.data(), b->n * sizeof(BatchTank),
+                                   b->slot0 * sizeof(BatchTank), cudaMemcpyHostToDevice, s));
     return AC_OK;
 }
 
@@ -291,21 +335,30 @@ int build_tiles(ac_batch *b, int v) {
 
 int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     cudaError_t e;
+    const float alpha = float(1.0 / double(b->opt.rk_stages - stage + 1));   // alpha_s
     // the Bassi and Roe fluxes are compiled for the first tile shape only
     if (b->opt.riemann == AC_RIEMANN_BASSI)
-        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
+        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
     else if (b->opt.riemann == AC_RIEMANN_ROE)
-        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
+        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
     else if (b->opt.bdf_order > 1)
-        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s);
+        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
     else switch (v) {
-        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
-        default: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, b->n, s); break;
+        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 6: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
+        case 7:
+            e = launch_stage<32, 8, 256, kOsher, false, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha,
+                                                              b->slot0, s);
+            break;
+        default:
+            e = launch_stage<16, 16, 256, kOsher, false, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha,
+                                                               b->slot0, s);
+            break;
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
     return AC_OK;
@@ -393,7 +446,7 @@ extern "C" {
 
 void ac_batch_destroy(ac_batch *b) {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream);   // (0: the default stream) nothing of this batch still runs
     for (int k = 0; k < 5; ++k)
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -412,6 +465,7 @@ void ac_batch_destroy(ac_batch *b) {
     cudaFree(b->tile_map);
     cudaFree(b->dt_dev);
     if (b->hctl) cudaFreeHost(b->hctl);
+    release_slots(b->slot0, b->n);
     delete b;
 }
 
@@ -461,6 +515,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     b->total = total;
     b->variant = -1;
     b->order_now = 1;
+    b->slot0 = acquire_slots(n);
     b->off.resize(n);
     b->p_ref.resize(n);
     b->use_ref.resize(n);
@@ -493,7 +548,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     CKB(cudaMalloc(&b->tile_map, max_tiles * sizeof(int)));
     CKB(cudaMalloc(&b->ctl, n * sizeof(Ctl)));
     CKB(cudaMalloc(&b->sync, sizeof(BatchSync)));
-    CKB(cudaMalloc(&b->tanks_dev, (size_t)n * o.rk_stages * sizeof(BatchTank)));
+    CKB(cudaMalloc(&b->tanks_dev, n * sizeof(BatchTank)));
     CKB(cudaMalloc(&b->dt_dev, n * sizeof(double)));
     CKB(cudaMallocHost(&b->hctl, n * sizeof(Ctl)));
     CKB(cudaMemset(b->sync, 0, sizeof(BatchSync)));
@@ -506,6 +561,8 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     CKB((allow_smem<64, 8, 512>()));
     CKB((allow_smem<64, 16, 512>()));
     CKB((allow_smem<16, 16, 256>()));
+    CKB((allow_smem<32, 8, 256, kOsher, false, true>()));
+    CKB((allow_smem<16, 16, 256, kOsher, false, true>()));
     CKB((allow_smem<32, 8, 256, kBassi, true>()));
     CKB((allow_smem<32, 8, 256, kRoe, true>()));
     CKB((allow_smem<32, 8, 256, kOsher, true>()));

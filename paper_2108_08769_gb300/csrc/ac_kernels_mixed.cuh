@@ -177,14 +177,14 @@ struct PrefetchSrc {
 // RAW_AUX: the ring holds (dQ of rho u, dQ of rho v, rho_ref, fold bits) as
 // copied, and the real-time terms are formed here (Backward-Euler only).
 template <int TX, int TY, int NT, int RS, bool BDF, bool RAW_AUX, typename Src>
-__device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int x0, int y0, bool interior,
-                                                   double *partial, MixedSmem<TX, TY> &sm, Src &src) {
+__device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage, float alpha, int x0, int y0,
+                                                   bool interior, double *partial, MixedSmem<TX, TY> &sm, Src &src) {
     static_assert(!(RAW_AUX && BDF), "raw ring terms are Backward-Euler only");
     using S = MixedSmem<TX, TY>;
     constexpr int RW = S::RW, GW = S::GW, GH = S::GH;
     const Ctl *ctl = a.ctl;
     int in, out;
-    stage_buffers(ctl->cur, a.stage, in, out);
+    stage_buffers(ctl->cur, stage, in, out);
     float *const *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
     const int nx = a.nx, ny = a.ny;
@@ -338,19 +338,19 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int x0, i
         } else {
             dtau = float(__longlong_as_double((long long)ctl->dtau_bits));
         }
-        const float adt = a.alpha * dtau;
+        const float adt = alpha * dtau;
         const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
         const float coef_p = a.alpha_pi_p_row ? coef : adt;
         dout[0][g] = e0 + coef * b0;
         dout[1][g] = e1 + coef * b1;
         dout[2][g] = e2 + coef * b2;
         dout[3][g] = p0 + a.beta * coef_p * b3;
-        if (a.stage == 1) {
+        if (stage == 1) {
             const float pb = a.beta * b3;
             sq[0] += b0 * b0; sq[1] += b1 * b1; sq[2] += b2 * b2; sq[3] += pb * pb;
         }
     }
-    if (a.stage == 1) {
+    if (stage == 1) {
         // per-warp sums in FP32, block and grid sums in FP64
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
@@ -377,8 +377,8 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int x0, i
 // reference jumps are copied with cp.async while the halo is being loaded,
 // and the update's own-cell inputs are prefetched at the start of phase 3.
 template <int TX, int TY, int NT, int RS, bool BDF, bool PF = false>
-__device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, double *partial,
-                                           unsigned char *smem_raw) {
+__device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float alpha, int bx, int by,
+                                           double *partial, unsigned char *smem_raw) {
     using S = MixedSmem<TX, TY>;
     static_assert((TX * TY) % NT == 0 && NT % 32 == 0, "tile/thread shape");
     static_assert(!PF || (NT == TX * TY && !BDF), "prefetch: one cell per thread, Backward-Euler");
@@ -388,7 +388,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
     const Ctl *ctl = a.ctl;
     int in, out;
     const int cur = ctl->cur;
-    stage_buffers(cur, a.stage, in, out);
+    stage_buffers(cur, stage, in, out);
     const float *const *din = a.d[in];
     const float *const *d0 = a.d[cur];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
@@ -496,11 +496,11 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int bx, int by, d
         cp_async_wait_all();
         __syncthreads();
         PrefetchSrc src{a, d0, {}};
-        mixed_tile_compute<TX, TY, NT, RS, BDF, true>(a, x0, y0, interior, partial, sm, src);
+        mixed_tile_compute<TX, TY, NT, RS, BDF, true>(a, stage, alpha, x0, y0, interior, partial, sm, src);
     } else {
         __syncthreads();
         DirectSrc src{a, d0};
-        mixed_tile_compute<TX, TY, NT, RS, BDF, false>(a, x0, y0, interior, partial, sm, src);
+        mixed_tile_compute<TX, TY, NT, RS, BDF, false>(a, stage, alpha, x0, y0, interior, partial, sm, src);
     }
 }
 
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(NT, MINB)
 stage_kernel_mixed(const MixedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.ctl->done) return;
-    mixed_tile<TX, TY, NT, RS, BDF, PF>(a, blockIdx.x, blockIdx.y,
+    mixed_tile<TX, TY, NT, RS, BDF, PF>(a, a.stage, a.alpha, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
 }
 

@@ -52,13 +52,13 @@ def test_batch_equals_single_tanks_bitwise_fixed_iterations():
     b.close()
 
 
-N_BATCH_VARIANTS = 7
+N_BATCH_VARIANTS = 9
 
 
 @pytest.mark.parametrize("v", range(N_BATCH_VARIANTS))
 def test_every_batch_variant_equals_single_tanks_bitwise(monkeypatch, v):
-    """Each compiled batch tile shape, forced in place of the autotuner's
-    pick."""
+    """Each compiled batch variant (tile shape, direct or prefetching
+    loads), forced in place of the autotuner's pick."""
     monkeypatch.setenv("AC_BATCH_TILE", str(v))
     cases = uneven_cases()
     b = ac.Batch.from_cases(cases)
@@ -155,4 +155,40 @@ def test_bdf2_batch_equals_single_tanks():
         for x, y in zip(b.get_state(k), t.get_state()):
             assert np.array_equal(x, y)
         t.close()
+    b.close()
+
+
+def test_two_batches_alive_at_once():
+    """Two batches hold separate ranges of the constant descriptor table;
+    stepping them in turn leaves each equal to its tanks run alone."""
+    ca = uneven_cases()[:4]
+    cb = W.batched_tanks(count=5, nmin=24, nmax=70, seed=31)
+    a = ac.Batch.from_cases(ca)
+    b = ac.Batch.from_cases(cb)
+    for _ in range(2):
+        a.physical_step(1e-3, -1.0, 4)
+        b.physical_step(1e-3, -1.0, 4)
+    for batch, cases in ((a, ca), (b, cb)):
+        for k, c in enumerate(cases):
+            t = ac.Tank.from_case(c, precision="mixed")
+            t.physical_step(1e-3, -1.0, 4)
+            t.physical_step(1e-3, -1.0, 4)
+            ref = t.get_state()
+            t.close()
+            for x, y in zip(batch.get_state(k), ref):
+                assert np.array_equal(x, y), k
+    a.close()
+    b.close()
+
+
+def test_batch_larger_than_the_constant_table():
+    """170 small tanks do not fit the 160-slot constant table: the batch
+    reads its descriptors from global memory, with the same results."""
+    cases = W.batched_tanks(count=170, nmin=8, nmax=20, seed=41)
+    b = ac.Batch.from_cases(cases)
+    b.physical_step(1e-3, -1.0, 3)
+    for k in (0, 1, 97, 169):
+        ref, _, _ = single_mixed(cases[k], 1e-3, -1.0, 3)
+        for x, y in zip(b.get_state(k), ref):
+            assert np.array_equal(x, y), k
     b.close()
