@@ -374,6 +374,7 @@ struct F64Backend : Backend {
 struct MixedVariant {
     int tx, ty, nt, minb;
     bool pf;   // ring terms and update inputs prefetched (cp.async / early loads)
+    bool x2;   // Osher flux on packed FP32x2 instructions
 };
 // (Without a CTAs-per-SM hint the compiler spends ~63 registers on this
 // sweep; 6 x 256 or 3 x 512 threads per SM hold it at 40 without spills.)
@@ -382,6 +383,8 @@ constexpr MixedVariant kMixedVariants[] = {
     {16, 16, 256, 6}, {16, 16, 256, 7}, {32, 8, 256, 7}, {32, 16, 512, 1},
     {32, 8, 256, 6, true}, {16, 16, 256, 6, true}, {32, 16, 512, 3, true}, {32, 8, 256, 5, true},
     {16, 16, 256, 5, true},
+    {32, 8, 256, 6, true, true}, {16, 16, 256, 6, true, true}, {32, 8, 256, 6, false, true},
+    {32, 8, 256, 5, true, true},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
@@ -452,7 +455,11 @@ struct MixedBackend : Backend {
             case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, s);
             case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, s);
             case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, s);
-            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
+            case 14: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
+            case 15: return launch_mixed<32, 8, 256, 6, kOsherX2, false, true>(a, g, s);
+            case 16: return launch_mixed<16, 16, 256, 6, kOsherX2, false, true>(a, g, s);
+            case 17: return launch_mixed<32, 8, 256, 6, kOsherX2, false, false>(a, g, s);
+            default: return launch_mixed<32, 8, 256, 5, kOsherX2, false, true>(a, g, s);
         }
     }
 
@@ -549,6 +556,10 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<32, 16, 512, 3, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 5, kOsher, false, true>()));
         CK((allow_mixed_smem<16, 16, 256, 5, kOsher, false, true>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kOsherX2, false, true>()));
+        CK((allow_mixed_smem<16, 16, 256, 6, kOsherX2, false, true>()));
+        CK((allow_mixed_smem<32, 8, 256, 6, kOsherX2, false, false>()));
+        CK((allow_mixed_smem<32, 8, 256, 5, kOsherX2, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));

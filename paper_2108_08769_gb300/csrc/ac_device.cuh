@@ -13,7 +13,7 @@ namespace acgb {
 
 enum BcKind { kSlip = 0, kNoSlip = 1, kTransmissive = 2, kPeriodic = 3 };
 enum GradP { kGradNew = 0, kGradMinmod = 1, kGradSuperbee = 2, kGradSplitMinmod = 3, kGradSplitSuperbee = 4 };
-enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2 };
+enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2, kOsherX2 = 3 };   // kOsherX2: FP32 Osher on packed FP32x2 (compile-time only)
 
 // ---------------------------------------------------------------------------
 // Arithmetic traits.  FP64 uses IEEE division and square root; FP32 uses
@@ -223,6 +223,75 @@ __device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     F[3] = u;
 }
 
+// FP32 form of osher_flux for sm_100-class parts: the two outer Gauss points
+// (same weight 5/18, positions 1/2 -+ sqrt(15)/10) run as the two lanes of
+// packed FP32x2 instructions (__ffma2_rn, __fmul2_rn, __fadd2_rn: one issue
+// slot for two operations, per-lane rounding as the scalar forms), the
+// middle point in scalar code.  Same quadrature and the same terms as
+// osher_flux; only the order of the three point sums differs.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, float pL, float rR, float uR,
+                                              float vR, float pR, float beta, float inv_beta, float F[4]) {
+    const float mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
+    const float mR = rR * uR, nR = rR * vR, qR = pR * inv_beta;
+    const float dr = rR - rL, dm = mR - mL, dn = nR - nL, dq = qR - qL;
+    const float four_beta = 4.0f * beta;
+    const float w13 = 5.0f / 18.0f, w2 = 8.0f / 18.0f;
+    // ---- points 1 and 3 ----
+    const float2 t = make_float2(0.11270166537925831148f, 0.88729833462074168852f);
+    const float2 r = __ffma2_rn(t, dup2(dr), dup2(rL));
+    const float2 mm = __ffma2_rn(t, dup2(dm), dup2(mL));
+    const float2 nn = __ffma2_rn(t, dup2(dn), dup2(nL));
+    const float2 ir = make_float2(Ar<float>::rcp(r.x), Ar<float>::rcp(r.y));
+    const float2 u = __fmul2_rn(mm, ir), v = __fmul2_rn(nn, ir);
+    const float2 c2 = __ffma2_rn(u, u, __fmul2_rn(dup2(four_beta), ir));
+    const float2 ic = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
+    const float2 c = __fmul2_rn(c2, ic);
+    const float2 hu = __fmul2_rn(dup2(0.5f), u), hc = __fmul2_rn(dup2(0.5f), c);
+    const float2 l4 = __fadd2_rn(hu, hc), l5 = __fadd2_rn(hu, neg2(hc));
+    const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
+    const float2 a = __fmul2_rn(__ffma2_rn(neg2(u), dup2(dr), dup2(dm)), dup2(inv_beta));
+    const float2 k = __fmul2_rn(r, ic);
+    const float2 g4 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l4, neg2(au)), k), __ffma2_rn(l4, a, dup2(dq)));
+    const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dup2(dq)));
+    const float2 e = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
+    const float2 gs = __fadd2_rn(g4, g5);
+    const float2 h = __ffma2_rn(g5, l4, __fmul2_rn(g4, l5));
+    // lane sums of (|u|, e, u e, v e, ir (g4 + g5), ir (g4 l5 + g5 l4)), times w13
+    const float2 ue = __fmul2_rn(u, e), ve = __fmul2_rn(v, e);
+    const float2 ig = __fmul2_rn(ir, gs), ih = __fmul2_rn(ir, h);
+    float Sau = w13 * (au.x + au.y), Se = w13 * (e.x + e.y), Sue = w13 * (ue.x + ue.y);
+    float Sve = w13 * (ve.x + ve.y), Sg = w13 * (ig.x + ig.y), Sh = w13 * (ih.x + ih.y);
+    // ---- point 2 ----
+    {
+        const float r2 = rL + 0.5f * dr, m2 = mL + 0.5f * dm, n2 = nL + 0.5f * dn;
+        const float ir2 = Ar<float>::rcp(r2);
+        const float u2 = m2 * ir2, v2 = n2 * ir2;
+        const float c22 = u2 * u2 + four_beta * ir2;
+        const float ic2 = rsqrtf(c22), cc = c22 * ic2;
+        const float hu2 = 0.5f * u2, hc2 = 0.5f * cc;
+        const float l42 = hu2 + hc2, l52 = hu2 - hc2;
+        const float au2 = fabsf(u2);
+        const float a2 = (dm - u2 * dr) * inv_beta;
+        const float k2 = r2 * ic2;
+        const float g42 = (l42 - au2) * k2 * (l42 * a2 + dq);
+        const float g52 = (l52 + au2) * k2 * (l52 * a2 + dq);
+        const float e2 = g42 * l42 + g52 * l52;
+        Sau += w2 * au2;
+        Se += w2 * e2;
+        Sue += w2 * (u2 * e2);
+        Sve += w2 * (v2 * e2);
+        Sg += w2 * (ir2 * (g42 + g52));
+        Sh += w2 * (ir2 * (g42 * l52 + g52 * l42));
+    }
+    F[0] = 0.5f * ((mL + mR) - (dr * Sau + Se));
+    F[1] = 0.5f * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
+    F[2] = 0.5f * ((mL * vL + mR * vR) - (dn * Sau + Sve));
+    F[3] = 0.5f * ((uL + uR) - (dq * Sau - Sh));
+}
+
 // Face flux of the solver RS, chosen at compile time so that a kernel built
 // for one solver carries none of the others' registers.
 template <int RS, typename T>
@@ -230,6 +299,7 @@ __device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR,
                                              T inv_beta, T F[4]) {
     if constexpr (RS == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else if constexpr (RS == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else if constexpr (RS == kOsherX2) osher_flux_x2(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
 }
 
