@@ -337,7 +337,7 @@ def run_ours(args, ws, rank, local):
                  "value": l_value, "unit": UNIT, "steps": lk, "ms_per_step": l_ms / lk,
                  "pseudo_iters_per_step": statistics.mean(l_iters), "gpu_launches": l_launches,
                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": measured_hbm_gbs(), "unit": "GB/s",
-                              "frac": gbs / measured_hbm_gbs(),
+                              "frac": gbs / measured_hbm_gbs(), "frac_of_nominal_8tbs": gbs / 8000.0,
                               "kernel": f"stage_kernel_mixed<{ltx},{lty},{lnt}>", "tile_variant": lv,
                               "launch_ms": l_launch_s * 1e3,
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,

@@ -219,8 +219,9 @@ struct F64Backend : Backend {
         return AC_OK;
     }
 
-    // Autotuner: stage 1 of every shape on this grid (writes only scratch),
-    // fastest kept per grid size.
+    // Autotuner: one pseudo-iteration's stages of every shape on this grid
+    // (they write only the two scratch buffers and the residual partials,
+    // all rewritten by the real iteration), fastest kept per grid size.
     int tune(ac_ctx *c, cudaStream_t s) override {
         if (variant >= 0) return AC_OK;
         if (c->opt.riemann != AC_RIEMANN_OSHER) { set_variant(c, 0); return AC_OK; }
@@ -234,20 +235,31 @@ struct F64Backend : Backend {
                 set_variant(c, kv.second);
                 return AC_OK;
             }
+        // the scratch buffers start as copies of the state, so that every
+        // timed stage sees real data
+        for (int b = 0; b < 3; ++b)
+            if (b != c->cur_host)
+                for (int f = 0; f < 4; ++f)
+                    CK(cudaMemcpyAsync(buf[b][f], buf[c->cur_host][f], c->N * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
         int best = 0;
         float best_ms = 1e30f;
+        const int S = c->opt.rk_stages;
         for (int v = 0; v < kNumF64Variants; ++v) {
             int rc;
-            for (int w = 0; w < 1; ++w)
-                if ((rc = launch(c, s, 1, v)) != AC_OK) return rc;
+            // every stage of one pseudo-iteration (stages write only the two
+            // scratch buffers; the level Q^m is untouched)
+            for (int st = 1; st <= S; ++st)
+                if ((rc = launch(c, s, st, v)) != AC_OK) return rc;
             CK(cudaEventRecord(c->ev[0], s));
-            for (int r = 0; r < 3; ++r)
-                if ((rc = launch(c, s, 1, v)) != AC_OK) return rc;
+            for (int r = 0; r < 2; ++r)
+                for (int st = 1; st <= S; ++st)
+                    if ((rc = launch(c, s, st, v)) != AC_OK) return rc;
             CK(cudaEventRecord(c->ev[1], s));
             CK(cudaEventSynchronize(c->ev[1]));
             float ms = 0.0f;
             CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-            c->launches += 4;
+            c->launches += 3 * S;
             if (ms < best_ms) { best_ms = ms; best = v; }
         }
         set_variant(c, best);
@@ -374,7 +386,6 @@ struct F64Backend : Backend {
 struct MixedVariant {
     int tx, ty, nt, minb;
     bool pf;   // ring terms and update inputs prefetched (cp.async / early loads)
-    bool x2;   // Osher flux on packed FP32x2 instructions
 };
 // (Without a CTAs-per-SM hint the compiler spends ~63 registers on this
 // sweep; 6 x 256 or 3 x 512 threads per SM hold it at 40 without spills.)
@@ -383,8 +394,6 @@ constexpr MixedVariant kMixedVariants[] = {
     {16, 16, 256, 6}, {16, 16, 256, 7}, {32, 8, 256, 7}, {32, 16, 512, 1},
     {32, 8, 256, 6, true}, {16, 16, 256, 6, true}, {32, 16, 512, 3, true}, {32, 8, 256, 5, true},
     {16, 16, 256, 5, true},
-    {32, 8, 256, 6, true, true}, {16, 16, 256, 6, true, true}, {32, 8, 256, 6, false, true},
-    {32, 8, 256, 5, true, true},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
@@ -455,17 +464,13 @@ struct MixedBackend : Backend {
             case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, s);
             case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, s);
             case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, s);
-            case 14: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
-            case 15: return launch_mixed<32, 8, 256, 6, kOsherX2, false, true>(a, g, s);
-            case 16: return launch_mixed<16, 16, 256, 6, kOsherX2, false, true>(a, g, s);
-            case 17: return launch_mixed<32, 8, 256, 6, kOsherX2, false, false>(a, g, s);
-            default: return launch_mixed<32, 8, 256, 5, kOsherX2, false, true>(a, g, s);
+            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
         }
     }
 
-    // Autotuner: time stage 1 of every tile shape on this grid (it writes
-    // only scratch: a stage-1 output buffer and the residual partials, both
-    // rewritten by the real stage 1) and keep the fastest.
+    // Autotuner: time one pseudo-iteration's stages with every variant on
+    // this grid (they write only the two scratch buffers and the residual
+    // partials, all rewritten by the real iteration) and keep the fastest.
     int tune(ac_ctx *c, cudaStream_t s) override {
         if (variant >= 0) return AC_OK;
         // other solvers and BDF2/BDF3 run one compiled shape (32 x 8)
@@ -477,21 +482,33 @@ struct MixedBackend : Backend {
         }
         for (auto &kv : g_tuned)
             if (kv.first.nx == c->grid.nx && kv.first.ny == c->grid.ny) { set_variant(c, kv.second); return AC_OK; }
+        // the scratch buffers start as copies of the state, so that every
+        // timed stage sees real data
+        for (int b = 0; b < 3; ++b)
+            if (b != c->cur_host)
+                for (int f = 0; f < 4; ++f)
+                    CK(cudaMemcpyAsync(d[b][f], d[c->cur_host][f], c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                       s));
         int best = 0;
         float best_ms = 1e30f;
-        const int reps = c->N > (1u << 22) ? 3 : 8;
+        const int reps = c->N > (1u << 22) ? 2 : 5;
+        const int S = c->opt.rk_stages;
         for (int v = 0; v < kNumMixedVariants; ++v) {
             int rc;
-            for (int w = 0; w < 2; ++w)
-                if ((rc = launch(c, s, 1, v)) != AC_OK) return fail(rc, "tile variant %d failed to launch", v);
+            // every stage of one pseudo-iteration (stages write only the two
+            // scratch buffers; the level Q^m is untouched)
+            for (int st = 1; st <= S; ++st)
+                if ((rc = launch(c, s, st, v)) != AC_OK) return fail(rc, "tile variant %d failed to launch", v);
             CK(cudaEventRecord(c->ev[0], s));
             for (int r = 0; r < reps; ++r)
-                if ((rc = launch(c, s, 1, v)) != AC_OK) return fail(rc, "tile variant %d failed to launch", v);
+                for (int st = 1; st <= S; ++st)
+                    if ((rc = launch(c, s, st, v)) != AC_OK)
+                        return fail(rc, "tile variant %d failed to launch", v);
             CK(cudaEventRecord(c->ev[1], s));
             CK(cudaEventSynchronize(c->ev[1]));
             float ms = 0.0f;
             CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-            c->launches += 2 + reps;
+            c->launches += (1 + reps) * S;
             if (ms < best_ms) { best_ms = ms; best = v; }
         }
         set_variant(c, best);
@@ -556,10 +573,6 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<32, 16, 512, 3, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 5, kOsher, false, true>()));
         CK((allow_mixed_smem<16, 16, 256, 5, kOsher, false, true>()));
-        CK((allow_mixed_smem<32, 8, 256, 6, kOsherX2, false, true>()));
-        CK((allow_mixed_smem<16, 16, 256, 6, kOsherX2, false, true>()));
-        CK((allow_mixed_smem<32, 8, 256, 6, kOsherX2, false, false>()));
-        CK((allow_mixed_smem<32, 8, 256, 5, kOsherX2, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));

@@ -364,8 +364,8 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     return AC_OK;
 }
 
-// Autotuner for the batch: stage 1 of every tile shape over all tanks (it
-// writes only scratch), fastest kept.
+// Autotuner for the batch: one pseudo-iteration's stages with every variant
+// over all tanks (scratch buffers and partials only), fastest kept.
 int tune(ac_batch *b, cudaStream_t s) {
     if (b->variant >= 0) return AC_OK;
     if (b->opt.riemann != AC_RIEMANN_OSHER || b->opt.bdf_order > 1) return build_tiles(b, 0);
@@ -374,21 +374,33 @@ int tune(ac_batch *b, cudaStream_t s) {
         const int v = atoi(env);
         if (v >= 0 && v < kNumVariants) return build_tiles(b, v);
     }
+    // the scratch buffers start as copies of the state (every tank holds
+    // it in buffer 0 before its first step), so that every timed stage sees
+    // real data
+    bool all_first = true;
+    for (int k = 0; k < b->n; ++k) all_first = all_first && b->hctl[k].cur == 0;
+    if (all_first)
+        for (int x = 1; x < 3; ++x)
+            for (int f = 0; f < 4; ++f)
+                CK(cudaMemcpyAsync(b->d[x][f], b->d[0][f], b->total * sizeof(float), cudaMemcpyDeviceToDevice, s));
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumVariants; ++v) {
         int rc = build_tiles(b, v);
         if (rc != AC_OK) return rc;
-        for (int w = 0; w < 2; ++w)
-            if ((rc = stage_launch(b, s, 1, v)) != AC_OK) return rc;
+        // every stage of one pseudo-iteration (scratch buffers only)
+        const int S = b->opt.rk_stages;
+        for (int st = 1; st <= S; ++st)
+            if ((rc = stage_launch(b, s, st, v)) != AC_OK) return rc;
         CK(cudaEventRecord(b->ev[0], s));
-        for (int r = 0; r < 3; ++r)
-            if ((rc = stage_launch(b, s, 1, v)) != AC_OK) return rc;
+        for (int r = 0; r < 2; ++r)
+            for (int st = 1; st <= S; ++st)
+                if ((rc = stage_launch(b, s, st, v)) != AC_OK) return rc;
         CK(cudaEventRecord(b->ev[1], s));
         CK(cudaEventSynchronize(b->ev[1]));
         float ms = 0.0f;
         CK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
-        b->launches += 5;
+        b->launches += 3 * S;
         if (ms < best_ms) { best_ms = ms; best = v; }
     }
     return build_tiles(b, best);

@@ -6,6 +6,8 @@
 // memory, no library calls.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,7 +15,7 @@ namespace acgb {
 
 enum BcKind { kSlip = 0, kNoSlip = 1, kTransmissive = 2, kPeriodic = 3 };
 enum GradP { kGradNew = 0, kGradMinmod = 1, kGradSuperbee = 2, kGradSplitMinmod = 3, kGradSplitSuperbee = 4 };
-enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2, kOsherX2 = 3 };   // kOsherX2: FP32 Osher on packed FP32x2 (compile-time only)
+enum Riemann { kOsher = 0, kBassi = 1, kRoe = 2 };
 
 // ---------------------------------------------------------------------------
 // Arithmetic traits.  FP64 uses IEEE division and square root; FP32 uses
@@ -293,13 +295,15 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
 }
 
 // Face flux of the solver RS, chosen at compile time so that a kernel built
-// for one solver carries none of the others' registers.
+// for one solver carries none of the others' registers.  The FP32 Osher flux
+// is always the packed form, so every FP32 sweep (any tile shape, single tank
+// or batch) computes a face bit for bit the same way.
 template <int RS, typename T>
 __device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
                                              T inv_beta, T F[4]) {
     if constexpr (RS == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else if constexpr (RS == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
-    else if constexpr (RS == kOsherX2) osher_flux_x2(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else if constexpr (std::is_same<T, float>::value) osher_flux_x2(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
 }
 

@@ -335,3 +335,13 @@ def test_every_tile_variant(monkeypatch, v, bc):
     ref, *_ = oracle.physical_step(case, case.state(), tol=-1.0, max_iters=4)
     errs = rel_errors(got, ref)
     assert max(errs) <= TOL, errs
+
+
+def test_tile_shape_reported_after_the_first_step():
+    case = W.random_two_fluid(40, 24, ratio=10.0, c0=5.0)
+    t = ac.Tank.from_case(case)
+    assert t.tile_shape()[3] == -1          # not tuned yet (AC_ERR_STATE)
+    t.physical_step(case.dt, -1.0, 1)
+    tx, ty, nt, v = t.tile_shape()
+    assert v >= 0 and tx * ty >= nt > 0
+    t.close()

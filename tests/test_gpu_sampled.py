@@ -65,3 +65,30 @@ def test_rayleigh_taylor_full_grid_sampled_windows(rt_case, precision, tol):
         exp = tuple(r[cj, ci] for r in ref)
         errs = rel_errors(got, exp)
         assert max(errs) <= tol, ((i0, j0), errs)
+
+
+def test_batched_64_tanks_full_size():
+    """The batched benchmark's 64 tanks (64^2..1024^2, mixed form) in the
+    launch configuration the benchmark times, one physical step of one
+    pseudo-iteration: the three smallest tanks whole against the oracle, and
+    windows of the three largest (same dependency margin as above)."""
+    cases = W.batched_tanks(count=64, nmin=64, nmax=1024)
+    b = ac.Batch.from_cases(cases)
+    rc, its, st = b.physical_step([c.dt for c in cases], -1.0, 1)
+    assert its == [1] * len(cases)
+    order = sorted(range(len(cases)), key=lambda k: cases[k].cells)
+    for k in order[:3]:
+        c = cases[k]
+        ref, *_ = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=1)
+        errs = rel_errors(b.get_state(k), ref)
+        assert max(errs) <= 1e-5, (k, c.nx, errs)
+    for k in order[-3:]:
+        c = cases[k]
+        full = b.get_state(k)
+        for i0, j0 in [(0, 0), (c.nx - 48, c.ny - 48), (c.nx // 2, c.ny // 3)]:
+            sub, sl, (cj, ci) = window(c, i0, j0, 48, 48)
+            ref, *_ = oracle.physical_step(sub, sub.state(), tol=-1.0, max_iters=1)
+            got = tuple(f[sl][cj, ci] for f in full)
+            errs = rel_errors(got, tuple(r[cj, ci] for r in ref))
+            assert max(errs) <= 1e-5, (k, (i0, j0), errs)
+    b.close()
