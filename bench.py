@@ -343,7 +343,7 @@ def run_ours(args, ws, rank, local):
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
                               "traffic": MIXED_TRAFFIC_PER_CELL_STAGE * lc.cells,
                               "alu_frac": ops / FP32_PEAK_TOPS,
-                              "alu_note": f"{MIXED_FP32_OPS_PER_CELL_STAGE:.0f} FP32 arithmetic instructions per "
+                              "alu_note": f"{MIXED_FP32_OPS_PER_CELL_STAGE:.0f} FP32 arithmetic operations per "
                                           f"cell-stage (ncu) against {FP32_PEAK_TOPS:.1f} T/s (128 lanes/SM x 152 SMs "
                                           "x 2.07 GHz)"},
                  "error_vs_fp64_gpu": field_errors(lm_state, lf_state)}
@@ -464,11 +464,12 @@ BYTES_PER_CELL_ITER_F64 = 328.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, stage_kernel_mixed<32,8,256> prefetching variant, 2048x2048,
-# profiles/stage_kernel_mixed_rayleigh_taylor_2048.md): DRAM bytes and FP32
-# arithmetic thread-instructions (FFMA + FADD + FMUL) per cell of one stage launch
-MIXED_TRAFFIC_PER_CELL_STAGE = 64.2
-MIXED_FP32_OPS_PER_CELL_STAGE = 463.2
+# measured (ncu, stage_kernel_mixed<32,8,256> prefetching 5-CTA variant,
+# 2048x2048, profiles/stage_kernel_mixed_rayleigh_taylor_2048.md): DRAM bytes
+# and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2 forms
+# counted as two) per cell of one stage launch
+MIXED_TRAFFIC_PER_CELL_STAGE = 64.1
+MIXED_FP32_OPS_PER_CELL_STAGE = 482.6
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
