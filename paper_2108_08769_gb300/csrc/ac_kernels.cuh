@@ -216,7 +216,23 @@ stage_kernel(const SweepArgs<T> a) {
     __syncthreads();
 
     // ---- 3. face states and Osher fluxes ----
-    for (int k = tid; k < S::NXF + S::NYF; k += NT) {
+    // The faces are dealt out so that the four SM sub-partitions get equal
+    // numbers of warp-passes (the FP64 pipe, not issue, bounds this loop, and
+    // a pass costs the same with idle lanes).  The warps of a CTA sit on
+    // contiguous slots, so warps w and w + 4 share a sub-partition; group
+    // w mod 4 takes faces [32 P g, 32 P (g + 1)), P = ceil(F / 128), in
+    // passes of 32 shared round-robin by its warps.  The plain strided loop
+    // gives the first warps an extra pass when the warp count is not a
+    // multiple of 4 (32x14 tiles: 9 warp-passes on two sub-partitions
+    // against 8 here).
+    constexpr int NF = S::NXF + S::NYF, NW = NT / 32, FP = (NF + 127) / 128;
+    static_assert(NW >= 4, "face schedule needs four warps");
+    const int fw = tid >> 5, fgrp = fw & 3;
+    const int fwarps = (NW - fgrp + 3) >> 2;
+    const int fbeg = fgrp * 32 * FP, fend = min(NF, fbeg + 32 * FP);
+    for (int fq = fw >> 2; fbeg + 32 * fq < fend; fq += fwarps) {
+        const int k = fbeg + 32 * fq + (tid & 31);
+        if (k >= fend) continue;
         const bool isx = k < S::NXF;
         // face states: density, normal and tangential velocity (rotation,
         // Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure
