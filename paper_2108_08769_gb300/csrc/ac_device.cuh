@@ -122,12 +122,25 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
     //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
     T Sau = T(0), Se = T(0), Sue = T(0), Sve = T(0), Sg = T(0), Sh = T(0);
+    // the three densities' reciprocals from one reciprocal of their product
+    // (1 reciprocal + 6 products in place of 3 reciprocals)
+    T rq[3], irq[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rq[j] = rL + tq[j] * dr;
+    {
+        const T r01 = rq[0] * rq[1];
+        const T inv = Ar<T>::rcp(r01 * rq[2]);
+        const T inv01 = rq[2] * inv;   // 1 / (r0 r1)
+        irq[2] = r01 * inv;
+        irq[0] = rq[1] * inv01;
+        irq[1] = rq[0] * inv01;
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const T r = rL + tq[j] * dr;
+        const T r = rq[j];
         const T m = mL + tq[j] * dm;
         const T n = nL + tq[j] * dn;
-        const T ir = Ar<T>::rcp(r);
+        const T ir = irq[j];
         const T u = m * ir, v = n * ir;
         const T c2 = u * u + four_beta * ir;
         T c, ic;
