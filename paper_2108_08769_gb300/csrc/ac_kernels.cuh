@@ -313,14 +313,18 @@ stage_kernel(const SweepArgs<T> a) {
         if (a.local_dtau) {
             const T ir = Ar<T>::rcp(r0);
             const T u = m0 * ir, v = n0 * ir, fb = T(4) * a.beta * ir;
-            const T cx = Ar<T>::sqrt_(u * u + fb), cy = Ar<T>::sqrt_(v * v + fb);
+            // square roots as x / sqrt(x) and quotients as products with a
+            // rounded reciprocal: a few ulps, far inside the 1e-11 bar
+            T cx, cy, unused;
+            Ar<T>::sqrt_rsqrt(u * u + fb, cx, unused);
+            Ar<T>::sqrt_rsqrt(v * v + fb, cy, unused);
             const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
-            dtau = Ar<T>::div(a.cfl_area, den);
+            dtau = a.cfl_area * Ar<T>::rcp(den);
         } else {
             dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
         }
         const T api = T(1) + a.B[0] * a.alpha * dtau * inv_dt;   // Eq. point_implicit
-        const T coef = Ar<T>::div(a.alpha * dtau, api);
+        const T coef = (a.alpha * dtau) * Ar<T>::rcp(api);
         const T coef_p = a.alpha_pi_p_row ? coef : a.alpha * dtau;
         qout[0][g] = r0 + coef * b0;
         qout[1][g] = m0 + coef * b1;
