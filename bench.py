@@ -277,6 +277,11 @@ def run_ours(args, ws, rank, local):
                 "kernel": f"stage_kernel<double,{ftx},{fty}>", "tile_variant": fv, "launch_ms": per_launch_s * 1e3,
                 "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
                 "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM), not measured",
+                # the same launch counted in FP64 instructions against the pipe's
+                # issue rate (2 per SM per clock): DADD and DMUL take a pipe slot
+                # for one flop, so the flop fraction is at most ~0.71 of this one
+                "dp_instructions_per_cell_stage": FP64_INSTR_PER_CELL_STAGE,
+                "dp_pipe_frac": FP64_INSTR_PER_CELL_STAGE * case.cells / per_launch_s / FP64_PIPE_INSTR_PER_S,
                 "hbm_frac_of_measured": BYTES_PER_CELL_ITER_F64 / 3.0 * case.cells / per_launch_s / 1e9
                 / measured_hbm_gbs()}
     tank.close()
@@ -454,8 +459,11 @@ def run_batched(args, stream, flush, barrier):
 
 # FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
 # counted by ncu on stage_kernel<double,32,14> on this 256x256 tank
-# (profiles/stage_kernel_f64_hydrostatic_256.md)
-FP64_FLOPS_PER_CELL_STAGE = 851.1
+# (profiles/stage_kernel_f64_hydrostatic_256.md), and the FP64 instructions
+# (DFMA + DADD + DMUL) behind them
+FP64_FLOPS_PER_CELL_STAGE = 755.5
+FP64_INSTR_PER_CELL_STAGE = 533.0
+FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture (5.83 MB read,
 # the output stays in L2)
 FP64_TRAFFIC_PER_CELL_STAGE = 89.0
