@@ -112,6 +112,7 @@ struct ac_ctx {
     double stage_ms;
     long long stage_launches;
     unsigned long long *dt_word;   // device result of ac_realtime_dt
+    bool pdl;             // launch the loop's kernels with programmatic dependencies
     int nhist;            // older real-time levels held (0..2) before the next step
     int order_now;        // backward-difference order of the current step
     int graph_order;      // order the captured graph was built for
@@ -169,9 +170,9 @@ cudaError_t allow_f64_smem() {
 }
 
 template <int TX, int TY, int RS = kOsher>
-cudaError_t launch_f64(const SweepArgs<double> &a, dim3 g, cudaStream_t s) {
-    stage_kernel<double, TX, TY, RS><<<g, TX * TY, sizeof(StageSmem<double, TX, TY>), s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_f64(const SweepArgs<double> &a, dim3 g, bool pdl, cudaStream_t s) {
+    return launch_pdl(pdl, stage_kernel<double, TX, TY, RS>, g, dim3(TX * TY), sizeof(StageSmem<double, TX, TY>), s,
+                      a);
 }
 
 std::vector<std::pair<std::pair<int, int>, int>> g_tuned_f64;
@@ -203,17 +204,17 @@ struct F64Backend : Backend {
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
         cudaError_t e;
         // the Bassi and Roe fluxes are compiled for the first tile shape only
-        if (c->opt.riemann == AC_RIEMANN_BASSI) e = launch_f64<32, 8, kBassi>(a, g, s);
-        else if (c->opt.riemann == AC_RIEMANN_ROE) e = launch_f64<32, 8, kRoe>(a, g, s);
+        if (c->opt.riemann == AC_RIEMANN_BASSI) e = launch_f64<32, 8, kBassi>(a, g, c->pdl, s);
+        else if (c->opt.riemann == AC_RIEMANN_ROE) e = launch_f64<32, 8, kRoe>(a, g, c->pdl, s);
         else switch (v) {
-            case 0: e = launch_f64<32, 8>(a, g, s); break;
-            case 1: e = launch_f64<32, 7>(a, g, s); break;
-            case 2: e = launch_f64<32, 6>(a, g, s); break;
-            case 3: e = launch_f64<32, 4>(a, g, s); break;
-            case 4: e = launch_f64<16, 8>(a, g, s); break;
-            case 5: e = launch_f64<16, 16>(a, g, s); break;
-            case 6: e = launch_f64<32, 14>(a, g, s); break;
-            default: e = launch_f64<64, 7>(a, g, s); break;
+            case 0: e = launch_f64<32, 8>(a, g, c->pdl, s); break;
+            case 1: e = launch_f64<32, 7>(a, g, c->pdl, s); break;
+            case 2: e = launch_f64<32, 6>(a, g, c->pdl, s); break;
+            case 3: e = launch_f64<32, 4>(a, g, c->pdl, s); break;
+            case 4: e = launch_f64<16, 8>(a, g, c->pdl, s); break;
+            case 5: e = launch_f64<16, 16>(a, g, c->pdl, s); break;
+            case 6: e = launch_f64<32, 14>(a, g, c->pdl, s); break;
+            default: e = launch_f64<64, 7>(a, g, c->pdl, s); break;
         }
         if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stage sweep launch failed: %s", cudaGetErrorString(e));
         return AC_OK;
@@ -360,8 +361,7 @@ struct F64Backend : Backend {
         return AC_OK;
     }
     int dtau_min(ac_ctx *c, cudaStream_t s) override {
-        dtau_min_kernel<double><<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
-        CK(cudaGetLastError());
+        CK(launch_pdl(c->pdl, dtau_min_kernel<double>, dim3(grid_stride_blocks(c->N)), dim3(256), 0, s, args(c, 0)));
         return AC_OK;
     }
     int stage(ac_ctx *c, cudaStream_t s, int st) override { return launch(c, s, st, variant < 0 ? 0 : variant); }
@@ -398,9 +398,10 @@ constexpr MixedVariant kMixedVariants[] = {
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
 template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, bool PF = false>
-int launch_mixed(const MixedArgs &a, dim3 g, cudaStream_t s) {
-    stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF><<<g, NT, sizeof(MixedSmem<TX, TY>), s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? AC_OK : AC_ERR_CUDA;
+int launch_mixed(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
+    const cudaError_t e = launch_pdl(pdl, stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF>, g, dim3(NT),
+                                     sizeof(MixedSmem<TX, TY>), s, a);
+    return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
 template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, bool PF = false>
@@ -446,25 +447,25 @@ struct MixedBackend : Backend {
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
         // the Bassi and Roe fluxes are compiled for the first tile shape only
         const bool bdf = c->opt.bdf_order > 1;
-        if (c->opt.riemann == AC_RIEMANN_BASSI) return launch_mixed<32, 8, 256, 6, kBassi, true>(a, g, s);
-        if (c->opt.riemann == AC_RIEMANN_ROE) return launch_mixed<32, 8, 256, 6, kRoe, true>(a, g, s);
-        if (bdf) return launch_mixed<32, 8, 256, 6, kOsher, true>(a, g, s);
+        if (c->opt.riemann == AC_RIEMANN_BASSI) return launch_mixed<32, 8, 256, 6, kBassi, true>(a, g, c->pdl, s);
+        if (c->opt.riemann == AC_RIEMANN_ROE) return launch_mixed<32, 8, 256, 6, kRoe, true>(a, g, c->pdl, s);
+        if (bdf) return launch_mixed<32, 8, 256, 6, kOsher, true>(a, g, c->pdl, s);
         switch (v) {
-            case 0: return launch_mixed<32, 8, 256, 6>(a, g, s);
-            case 1: return launch_mixed<32, 16, 256, 6>(a, g, s);
-            case 2: return launch_mixed<32, 16, 512, 3>(a, g, s);
-            case 3: return launch_mixed<64, 8, 256, 6>(a, g, s);
-            case 4: return launch_mixed<64, 8, 512, 3>(a, g, s);
-            case 5: return launch_mixed<64, 16, 512, 3>(a, g, s);
-            case 6: return launch_mixed<16, 16, 256, 6>(a, g, s);
-            case 7: return launch_mixed<16, 16, 256, 7>(a, g, s);
-            case 8: return launch_mixed<32, 8, 256, 7>(a, g, s);
-            case 9: return launch_mixed<32, 16, 512, 1>(a, g, s);
-            case 10: return launch_mixed<32, 8, 256, 6, kOsher, false, true>(a, g, s);
-            case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, s);
-            case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, s);
-            case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, s);
-            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, s);
+            case 0: return launch_mixed<32, 8, 256, 6>(a, g, c->pdl, s);
+            case 1: return launch_mixed<32, 16, 256, 6>(a, g, c->pdl, s);
+            case 2: return launch_mixed<32, 16, 512, 3>(a, g, c->pdl, s);
+            case 3: return launch_mixed<64, 8, 256, 6>(a, g, c->pdl, s);
+            case 4: return launch_mixed<64, 8, 512, 3>(a, g, c->pdl, s);
+            case 5: return launch_mixed<64, 16, 512, 3>(a, g, c->pdl, s);
+            case 6: return launch_mixed<16, 16, 256, 6>(a, g, c->pdl, s);
+            case 7: return launch_mixed<16, 16, 256, 7>(a, g, c->pdl, s);
+            case 8: return launch_mixed<32, 8, 256, 7>(a, g, c->pdl, s);
+            case 9: return launch_mixed<32, 16, 512, 1>(a, g, c->pdl, s);
+            case 10: return launch_mixed<32, 8, 256, 6, kOsher, false, true>(a, g, c->pdl, s);
+            case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, c->pdl, s);
+            case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, c->pdl, s);
+            case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
+            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
         }
     }
 
@@ -683,8 +684,7 @@ struct MixedBackend : Backend {
         return AC_OK;
     }
     int dtau_min(ac_ctx *c, cudaStream_t s) override {
-        dtau_min_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
-        CK(cudaGetLastError());
+        CK(launch_pdl(c->pdl, dtau_min_kernel_mixed, dim3(grid_stride_blocks(c->N)), dim3(256), 0, s, args(c, 0)));
         return AC_OK;
     }
     int stage(ac_ctx *c, cudaStream_t s, int st) override {
@@ -717,9 +717,8 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
         if ((rc = c->be->stage(c, s, st)) != AC_OK) return rc;
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
-    end_iteration_kernel<kEndThreads><<<1, kEndThreads, 0, s>>>(
-        c->ctl, c->partials, c->be->nblocks, 1.0 / double(c->N), c->opt.rk_stages, cond, use_cond);
-    CK(cudaGetLastError());
+    CK(launch_pdl(c->pdl, end_iteration_kernel<kEndThreads>, dim3(1), dim3(kEndThreads), 0, s, c->ctl, c->partials,
+                  c->be->nblocks, 1.0 / double(c->N), c->opt.rk_stages, cond, use_cond));
     return AC_OK;
 }
 
@@ -947,7 +946,9 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
     c->order_now = c->opt.realtime ? std::min(c->opt.bdf_order, c->nhist + 1) : 1;
     if ((rc = c->be->begin(c, s, dt, tol, max_iters)) != AC_OK) return rc;
     c->launches += 1;
+    c->pdl = false;   // the tuner times launches one after another
     if ((rc = c->be->tune(c, s)) != AC_OK) return rc;
+    c->pdl = pdl_enabled() && !c->profiling;
     if (c->profiling) {
         // one iteration at a time, stage sweeps bracketed by events
         while (true) {

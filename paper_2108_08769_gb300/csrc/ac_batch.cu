@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 6)
 batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ tile_tank, int stage, float alpha,
                    int slot0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    pdl_wait();
     const int k = tile_tank[blockIdx.x];
     if constexpr (CD) {
         const BatchTank &t = c_tanks[slot0 + k];
@@ -132,6 +134,8 @@ __global__ void __launch_bounds__(NT)
 batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long long cond, int use_cond) {
     __shared__ double red[4][NT];
     const int tid = threadIdx.x;
+    pdl_trigger();
+    pdl_wait();
     const BatchTank &t = tanks[blockIdx.x];
     Ctl *ctl = t.a.ctl;
     const bool was_done = ctl->done != 0;
@@ -221,14 +225,12 @@ cudaError_t allow_smem() {
 // slot0 < 0: descriptors in global memory
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
 cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, float alpha, int slot0,
-                         cudaStream_t s) {
+                         bool pdl, cudaStream_t s) {
     if (slot0 >= 0)
-        batch_stage_kernel<TX, TY, NT, RS, BDF, true, PF>
-            <<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage, alpha, slot0);
-    else
-        batch_stage_kernel<TX, TY, NT, RS, BDF, false, PF>
-            <<<ntiles, NT, sizeof(MixedSmem<TX, TY>), s>>>(tanks, map, stage, alpha, 0);
-    return cudaGetLastError();
+        return launch_pdl(pdl, batch_stage_kernel<TX, TY, NT, RS, BDF, true, PF>, dim3(ntiles), dim3(NT),
+                          sizeof(MixedSmem<TX, TY>), s, tanks, map, stage, alpha, slot0);
+    return launch_pdl(pdl, batch_stage_kernel<TX, TY, NT, RS, BDF, false, PF>, dim3(ntiles), dim3(NT),
+                      sizeof(MixedSmem<TX, TY>), s, tanks, map, stage, alpha, 0);
 }
 
 // First-fit allocator over the constant descriptor table (process-wide).
@@ -281,6 +283,7 @@ struct ac_batch {
     double *dt_dev;
     std::vector<BatchTank> tanks_host;
     int slot0;                          // first constant-table slot, -1: descriptors in global memory
+    bool pdl;                           // launch the loop's kernels with programmatic dependencies
     std::vector<std::vector<double>> p_ref;
     std::vector<char> use_ref;
     Ctl *hctl;                          // pinned mirror of all control blocks
@@ -333,32 +336,38 @@ int build_tiles(ac_batch *b, int v) {
     return AC_OK;
 }
 
+// Launch arguments of one batch stage.
+struct StageLaunch {
+    const BatchTank *tanks;
+    const int *map;
+    int ntiles, stage;
+    float alpha;
+    int slot0;
+    bool pdl;
+    template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
+    cudaError_t go(cudaStream_t s) const {
+        return launch_stage<TX, TY, NT, RS, BDF, PF>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
+    }
+};
+
 int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     cudaError_t e;
     const float alpha = float(1.0 / double(b->opt.rk_stages - stage + 1));   // alpha_s
+    const StageLaunch L{b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, b->pdl};
     // the Bassi and Roe fluxes are compiled for the first tile shape only
-    if (b->opt.riemann == AC_RIEMANN_BASSI)
-        e = launch_stage<32, 8, 256, kBassi, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
-    else if (b->opt.riemann == AC_RIEMANN_ROE)
-        e = launch_stage<32, 8, 256, kRoe, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
-    else if (b->opt.bdf_order > 1)
-        e = launch_stage<32, 8, 256, kOsher, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s);
+    if (b->opt.riemann == AC_RIEMANN_BASSI) e = L.go<32, 8, 256, kBassi, true>(s);
+    else if (b->opt.riemann == AC_RIEMANN_ROE) e = L.go<32, 8, 256, kRoe, true>(s);
+    else if (b->opt.bdf_order > 1) e = L.go<32, 8, 256, kOsher, true>(s);
     else switch (v) {
-        case 0: e = launch_stage<32, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 1: e = launch_stage<32, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 2: e = launch_stage<32, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 3: e = launch_stage<64, 8, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 4: e = launch_stage<64, 8, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 5: e = launch_stage<64, 16, 512>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 6: e = launch_stage<16, 16, 256>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, s); break;
-        case 7:
-            e = launch_stage<32, 8, 256, kOsher, false, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha,
-                                                              b->slot0, s);
-            break;
-        default:
-            e = launch_stage<16, 16, 256, kOsher, false, true>(b->tanks_dev, b->tile_map, b->ntiles, stage, alpha,
-                                                               b->slot0, s);
-            break;
+        case 0: e = L.go<32, 8, 256>(s); break;
+        case 1: e = L.go<32, 16, 256>(s); break;
+        case 2: e = L.go<32, 16, 512>(s); break;
+        case 3: e = L.go<64, 8, 256>(s); break;
+        case 4: e = L.go<64, 8, 512>(s); break;
+        case 5: e = L.go<64, 16, 512>(s); break;
+        case 6: e = L.go<16, 16, 256>(s); break;
+        case 7: e = L.go<32, 8, 256, kOsher, false, true>(s); break;
+        default: e = L.go<16, 16, 256, kOsher, false, true>(s); break;
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
     return AC_OK;
@@ -413,7 +422,8 @@ int enqueue_iteration(ac_batch *b, cudaStream_t s, unsigned long long cond, int 
         if ((rc = stage_launch(b, s, st, b->variant)) != AC_OK) return rc;
         if (timed) CK(cudaEventRecord(b->ev[st], s));
     }
-    batch_end_kernel<256><<<b->n, 256, 0, s>>>(b->tanks_dev, b->sync, b->n, cond, use_cond);
+    CK(launch_pdl(b->pdl, batch_end_kernel<256>, dim3(b->n), dim3(256), 0, s, b->tanks_dev, b->sync, b->n, cond,
+                  use_cond));
     CK(cudaGetLastError());
     return AC_OK;
 }
@@ -742,8 +752,10 @@ int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_it
     batch_begin_kernel<<<bg, 256, 0, s>>>(b->tanks_dev, b->sync, b->dt_dev, tol, max_iters);
     CK(cudaGetLastError());
     b->launches += 1;
+    b->pdl = false;   // the tuner times launches one after another
     int rc = tune(b, s);
     if (rc != AC_OK) return rc;
+    b->pdl = pdl_enabled() && !b->profiling;
     long long iters_run = 0;
     if (b->profiling) {
         while (true) {

@@ -74,6 +74,13 @@ __device__ __forceinline__ T wall_ghost_sign(int gi, int gj, int nx, int ny, con
     return w ? T(-1) : T(1);
 }
 
+// Programmatic dependent launch: let the next kernel in the stream be
+// scheduled (its CTAs then wait in pdl_wait), and wait until the previous
+// kernel has finished and its writes are visible.  No-ops for a kernel
+// launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T, int TX, int TY>
 struct StageSmem {
     static constexpr int RW = TX + 4, RH = TY + 4;   // tile + 2-cell halo
@@ -98,6 +105,8 @@ stage_kernel(const SweepArgs<T> a) {
     constexpr int NT = TX * TY;
     constexpr int RW = S::RW, RH = S::RH, GW = S::GW, GH = S::GH;
 
+    pdl_trigger();
+    pdl_wait();
     const Ctl *ctl = a.ctl;
     if (ctl->done) return;
     int in, out;
@@ -360,6 +369,8 @@ stage_kernel(const SweepArgs<T> a) {
 // (Sec. 2.2.3), from Q^{m}.  Positive doubles order like their bit patterns.
 template <typename T>
 __global__ void dtau_min_kernel(const SweepArgs<T> a) {
+    pdl_trigger();
+    pdl_wait();
     const Ctl *ctl = a.ctl;
     if (ctl->done) return;
     const T *const *q = a.buf[ctl->cur];
@@ -436,6 +447,8 @@ end_iteration_kernel(Ctl *ctl, const double *partials, int nblocks, double inv_c
                      unsigned long long cond_handle, int use_cond) {
     __shared__ double red[4][NT];
     const int tid = threadIdx.x;
+    pdl_trigger();
+    pdl_wait();
     if (ctl->done) {
         if (use_cond && tid == 0) cudaGraphSetConditional(cond_handle, 0);
         return;

@@ -132,7 +132,7 @@ struct DirectSrc {
     const MixedArgs &a;
     const float *const *d0;
     __device__ __forceinline__ void prefetch(int, int) {}
-    __device__ __forceinline__ float jump(int k, int gi, int gj, bool per_x) const {
+    __device__ __forceinline__ float jump(int gi, int gj, bool per_x) const {
         float j = 0.0f;
         if (gj < a.ny) {
             if (gi < a.nx) j = __ldg(a.dref + gj * a.nx + gi);
@@ -166,7 +166,7 @@ struct PrefetchSrc {
             v[7] = __ldg(a.rho_ref + g);
         }
     }
-    __device__ __forceinline__ float jump(int, int, int, bool) const { return 0.0f; }
+    __device__ __forceinline__ float jump(int, int, bool) const { return 0.0f; }
     __device__ __forceinline__ void cell(int, int, float &e0, float &e1, float &e2, float &p0, float &q0,
                                          float &q1, float &q2, float &rr) const {
         e0 = v[0]; e1 = v[1]; e2 = v[2]; p0 = v[3]; q0 = v[4]; q1 = v[5]; q2 = v[6]; rr = v[7];
@@ -260,7 +260,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
             if constexpr (Src::kDxfStaged) {
                 jump = sm.dxf[k];
             } else {
-                jump = src.jump(k, x0 + fi, y0 + fj, per_x);
+                jump = src.jump(x0 + fi, y0 + fj, per_x);
                 sm.dxf[k] = jump;
             }
             const int ga = (fj + 1) * GW + fi;
@@ -508,6 +508,8 @@ template <int TX, int TY, int NT, int MINB = 1, int RS = kOsher, bool BDF = fals
 __global__ void __launch_bounds__(NT, MINB)
 stage_kernel_mixed(const MixedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    pdl_wait();
     if (a.ctl->done) return;
     mixed_tile<TX, TY, NT, RS, BDF, PF>(a, a.stage, a.alpha, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
@@ -515,6 +517,8 @@ stage_kernel_mixed(const MixedArgs a) {
 
 // Global pseudo-time step option for the mixed form.
 static __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
+    pdl_trigger();
+    pdl_wait();
     const Ctl *ctl = a.ctl;
     if (ctl->done) return;
     const float *const *d = a.d[ctl->cur];
