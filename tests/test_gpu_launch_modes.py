@@ -1,0 +1,76 @@
+"""The launch mode does not change a number.
+
+A physical step runs as one graph launch (device-driven WHILE loop, kernels
+with programmatic dependencies), as a host-driven loop (AC_LAUNCH=host), with
+plain launches (AC_PDL=0), or one iteration at a time with per-stage events
+(profiling).  All four give bit-identical states, iteration counts and
+residual norms, in both precisions and for the batch.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2108_08769_gb300 import ac
+from paper_2108_08769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r'''
+import json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2108_08769_gb300 import ac, workloads as W
+out = {}
+for prec in ("fp64", "mixed"):
+    case = W.random_two_fluid(70, 45, ratio=1000.0, c0=20.0)
+    t = ac.Tank.from_case(case, precision=prec)
+    rc, its = t.physical_step(case.dt, 1e-3, 40)
+    R, R0 = t.residual_norms()
+    out[prec] = {"its": its, "R": list(R), "state": [a.tolist() for a in t.get_state()]}
+    t.close()
+cases = W.batched_tanks(count=4, nmin=20, nmax=60, seed=7)
+b = ac.Batch.from_cases(cases)
+rc, its, st = b.physical_step(1e-3, -1.0, 6)
+out["batch"] = {"its": its, "state": [[a.tolist() for a in b.get_state(k)] for k in range(len(cases))]}
+b.close()
+json.dump(out, open(sys.argv[2], "w"))
+'''
+
+
+def run_child(tmp_path, name, env_extra):
+    script = tmp_path / "child.py"
+    script.write_text(CHILD)
+    out = tmp_path / f"{name}.json"
+    env = dict(os.environ)
+    env.update(env_extra)
+    subprocess.run([sys.executable, str(script), ROOT, str(out)], env=env, check=True, timeout=600)
+    return json.load(open(out))
+
+
+def test_graph_host_loop_and_plain_launches_agree(tmp_path):
+    base = run_child(tmp_path, "graph", {})
+    for name, extra in [("host", {"AC_LAUNCH": "host"}), ("nopdl", {"AC_PDL": "0"})]:
+        other = run_child(tmp_path, name, extra)
+        assert other == base, name
+
+
+def test_profiling_mode_agrees_with_the_graph():
+    case = W.random_two_fluid(70, 45, ratio=1000.0, c0=20.0)
+    results = []
+    for prof in (False, True):
+        t = ac.Tank.from_case(case, precision="mixed")
+        t.set_profiling(prof)
+        rc, its = t.physical_step(case.dt, 1e-3, 40)
+        R, _ = t.residual_norms()
+        results.append((its, R, t.get_state()))
+        t.close()
+    (i0, r0, s0), (i1, r1, s1) = results
+    assert i0 == i1 and np.array_equal(r0, r1)
+    for x, y in zip(s0, s1):
+        assert np.array_equal(x, y)
