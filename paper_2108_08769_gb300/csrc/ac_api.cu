@@ -385,7 +385,8 @@ struct F64Backend : Backend {
 // the CTAs per SM the register allocation is asked to allow (1 = no limit).
 struct MixedVariant {
     int tx, ty, nt, minb;
-    bool pf;   // ring terms and update inputs prefetched (cp.async / early loads)
+    bool pf;      // ring terms and update inputs prefetched (cp.async / early loads)
+    bool sweep;   // column-strip sweep: tx = 28 output columns per warp, ty = rows per strip
 };
 // (Without a CTAs-per-SM hint the compiler spends ~63 registers on this
 // sweep; 6 x 256 or 3 x 512 threads per SM hold it at 40 without spills.)
@@ -394,6 +395,10 @@ constexpr MixedVariant kMixedVariants[] = {
     {16, 16, 256, 6}, {16, 16, 256, 7}, {32, 8, 256, 7}, {32, 16, 512, 1},
     {32, 8, 256, 6, true}, {16, 16, 256, 6, true}, {32, 16, 512, 3, true}, {32, 8, 256, 5, true},
     {16, 16, 256, 5, true},
+    // column-strip sweeps (new pressure gradient only): 28 columns x H rows per warp, 4 warps per CTA,
+    // 4 CTAs per SM (127 registers, no spills; tighter hints spill and lose)
+    {28, 32, 128, 4, false, true}, {28, 64, 128, 4, false, true}, {28, 128, 128, 4, false, true},
+    {28, 256, 128, 4, false, true}, {28, 64, 256, 2, false, true},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
@@ -401,6 +406,14 @@ template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, b
 int launch_mixed(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
     const cudaError_t e = launch_pdl(pdl, stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF>, g, dim3(NT),
                                      sizeof(MixedSmem<TX, TY>), s, a);
+    return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
+}
+
+template <int H, int WPC, int MINB>
+int launch_sweep(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
+    const int nstrips = (int)(g.x * g.y);
+    const cudaError_t e = launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB>, dim3((nstrips + WPC - 1) / WPC),
+                                     dim3(WPC * 32), 0, s, a, (int)g.x, nstrips);
     return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
@@ -465,7 +478,12 @@ struct MixedBackend : Backend {
             case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, c->pdl, s);
             case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, c->pdl, s);
             case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
-            default: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
+            case 14: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
+            case 15: return launch_sweep<32, 4, 4>(a, g, c->pdl, s);
+            case 16: return launch_sweep<64, 4, 4>(a, g, c->pdl, s);
+            case 17: return launch_sweep<128, 4, 4>(a, g, c->pdl, s);
+            case 18: return launch_sweep<256, 4, 4>(a, g, c->pdl, s);
+            default: return launch_sweep<64, 8, 2>(a, g, c->pdl, s);
         }
     }
 
@@ -476,13 +494,21 @@ struct MixedBackend : Backend {
         if (variant >= 0) return AC_OK;
         // other solvers and BDF2/BDF3 run one compiled shape (32 x 8)
         if (c->opt.riemann != AC_RIEMANN_OSHER || c->opt.bdf_order > 1) { set_variant(c, 0); return AC_OK; }
+        // the column-strip sweeps implement the new pressure gradient only
+        const bool sweep_ok = c->opt.gradp == AC_GRADP_NEW;
         const char *env = getenv("AC_TILE");
         if (env) {
             int v = atoi(env);
-            if (v >= 0 && v < kNumMixedVariants) { set_variant(c, v); return AC_OK; }
+            if (v >= 0 && v < kNumMixedVariants) {
+                set_variant(c, kMixedVariants[v].sweep && !sweep_ok ? 0 : v);
+                return AC_OK;
+            }
         }
         for (auto &kv : g_tuned)
-            if (kv.first.nx == c->grid.nx && kv.first.ny == c->grid.ny) { set_variant(c, kv.second); return AC_OK; }
+            if (kv.first.nx == c->grid.nx && kv.first.ny == c->grid.ny && (sweep_ok || !kMixedVariants[kv.second].sweep)) {
+                set_variant(c, kv.second);
+                return AC_OK;
+            }
         // the scratch buffers start as copies of the state, so that every
         // timed stage sees real data
         for (int b = 0; b < 3; ++b)
@@ -495,6 +521,7 @@ struct MixedBackend : Backend {
         const int reps = c->N > (1u << 22) ? 2 : 5;
         const int S = c->opt.rk_stages;
         for (int v = 0; v < kNumMixedVariants; ++v) {
+            if (kMixedVariants[v].sweep && !sweep_ok) continue;
             int rc;
             // every stage of one pseudo-iteration (stages write only the two
             // scratch buffers; the level Q^m is untouched)

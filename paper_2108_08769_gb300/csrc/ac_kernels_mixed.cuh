@@ -117,6 +117,116 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-cell and per-face arithmetic shared by the tile sweep and the
+// column-strip sweep, so that both compute every value the same way.
+// ---------------------------------------------------------------------------
+
+// Half slope of p' from the new pressure gradient (Eq. new_gradp) at a cell
+// with W = Wc, the half slopes of rho, u, v, the frozen real-time terms of
+// rho u, rho v (rtx, rty), the reference density and the ghost gravity sign.
+__device__ __forceinline__ void new_gradp_half_slopes(const MixedArgs &a, const float4 &Wc, float hrx, float hry,
+                                                      float hux, float huy, float hvx, float hvy, float rtx,
+                                                      float rty, float rref, float sg, float &hpx, float &hpy) {
+    const float rho = Wc.x, u = Wc.y, v = Wc.z;
+    const float ru = rho * u, rv = rho * v, uv = u * v;
+    hpx = -a.half_dx * rtx - (u * u * hrx + 2.0f * ru * hux) -
+          a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
+    // slope of p - p_ref: the reference slope rho_ref g_y is removed
+    hpy = -a.half_dy * rty - (v * v * hry + 2.0f * rv * hvy) -
+          a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - rref) * a.gy * sg;
+}
+
+// Face states between cells A (left/below) and B with half slopes SA, SB
+// along the face normal: density, normal and tangential velocity (rotation,
+// Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure; jump = reference
+// jump across an x-face.
+struct FaceStates {
+    float rL, nL, tL, pL, rR, nR, tR, pR;
+};
+__device__ __forceinline__ void x_face_states(const float4 &A, const float4 &B, const float4 &SA, const float4 &SB,
+                                              float jump, FaceStates &f) {
+    f.rL = A.x + SA.x; f.nL = A.y + SA.y; f.tL = A.z + SA.z; f.pL = A.w + SA.w - 0.5f * jump;
+    f.rR = B.x - SB.x; f.nR = B.y - SB.y; f.tR = B.z - SB.z; f.pR = B.w - SB.w + 0.5f * jump;
+}
+__device__ __forceinline__ void y_face_states(const float4 &A, const float4 &B, const float4 &SA, const float4 &SB,
+                                              FaceStates &f) {
+    f.rL = A.x + SA.x; f.nL = A.z + SA.z; f.tL = A.y + SA.y; f.pL = A.w + SA.w;
+    f.rR = B.x - SB.x; f.nR = B.z - SB.z; f.tR = B.y - SB.y; f.pR = B.w - SB.w;
+}
+// The face flux from its states: (mass, x-momentum, y-momentum, p/beta).
+template <int RS>
+__device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const FaceStates &f) {
+    float F[4];
+    riemann_flux<RS, float>(f.rL, f.nL, f.tL, f.pL, f.rR, f.nR, f.tR, f.pR, a.beta, a.inv_beta, F);
+    return make_float4(F[0], isx ? F[1] : F[2], isx ? F[2] : F[1], F[3]);
+}
+
+// Divergence, sources and the point-implicit update of one cell (Eqs. RK2,
+// point_implicit): writes dQ^s and p'^s at g and adds the stage-1 squared
+// bracket to sq.  Fw, Fe, Fs, Fn: face fluxes; jw, je: reference jumps of
+// the west and east faces; src.cell(cell, g, ...) gives dQ^{m}, p'^{m}, Q^n
+// and rho_ref of the cell.
+template <bool BDF, typename Src>
+__device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
+                                            float *const *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
+                                            const float4 &Fs, const float4 &Fn, float jw, float je, const Src &src,
+                                            float4 &sq) {
+    const float div0 = (Fe.x - Fw.x) * a.inv_dx + (Fn.x - Fs.x) * a.inv_dy;
+    const float div1 = (Fe.y - Fw.y) * a.inv_dx + (Fn.y - Fs.y) * a.inv_dy;
+    const float div2 = (Fe.z - Fw.z) * a.inv_dx + (Fn.z - Fs.z) * a.inv_dy;
+    const float div3 = (Fe.w - Fw.w) * a.inv_dx + (Fn.w - Fs.w) * a.inv_dy;
+    float e0, e1, e2, p0, q0, q1, q2, rref;
+    src.cell(cell, g, e0, e1, e2, p0, q0, q1, q2, rref);
+    const float r0 = q0 + e0;
+    const float m0 = q1 + e1;
+    const float n0 = q2 + e2;
+    float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
+    if constexpr (BDF) {
+        if (a.order >= 2) {
+            rt0 -= a.B2 * a.D1[0][g];
+            rt1 -= a.B2 * a.D1[1][g];
+            rt2 -= a.B2 * a.D1[2][g];
+        }
+        if (a.order >= 3) {
+            rt0 -= a.B3 * a.D2[0][g];
+            rt1 -= a.B3 * a.D2[1][g];
+            rt2 -= a.B3 * a.D2[2][g];
+        }
+    }
+    rt0 *= inv_dt;
+    rt1 *= inv_dt;
+    rt2 *= inv_dt;
+    // reference force: -(divergence of the x-face reference means)
+    const float sref = -0.5f * (je + jw) * a.inv_dx;
+    const float b0 = -div0 - rt0;
+    const float b1 = -div1 - rt1 + r0 * a.gx + sref;
+    const float b2 = -div2 - rt2 + (r0 - rref) * a.gy;
+    const float b3 = -div3;
+    float dtau;
+    if (a.local_dtau) {
+        const float ir = Ar<float>::rcp(r0);
+        const float u = m0 * ir, v = n0 * ir, fb = 4.0f * a.beta * ir;
+        const float u2 = u * u + fb, v2 = v * v + fb;
+        const float cx = u2 * rsqrtf(u2), cy = v2 * rsqrtf(v2);
+        const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
+        dtau = __fdividef(a.cfl_area, den);
+    } else {
+        dtau = float(__longlong_as_double((long long)a.ctl->dtau_bits));
+    }
+    const float adt = alpha * dtau;
+    const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
+    const float coef_p = a.alpha_pi_p_row ? coef : adt;
+    dout[0][g] = e0 + coef * b0;
+    dout[1][g] = e1 + coef * b1;
+    dout[2][g] = e2 + coef * b2;
+    dout[3][g] = p0 + a.beta * coef_p * b3;
+    if (stage1) {
+        const float pb = a.beta * b3;
+        sq.x += b0 * b0; sq.y += b1 * b1; sq.z += b2 * b2; sq.w += pb * pb;
+    }
+}
+
 // 4-byte global -> shared copy that completes asynchronously (cp.async);
 // cp_async_wait_all() makes this thread's copies visible to itself, a
 // barrier after it to the block.
@@ -220,13 +330,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
                 ax.x = rx;
                 ax.y = ry;
             }
-            const float rho = Wc.x, u = Wc.y, v = Wc.z;
-            const float ru = rho * u, rv = rho * v, uv = u * v;
-            hpx = -a.half_dx * ax.x - (u * u * hrx + 2.0f * ru * hux) -
-                  a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
-            // slope of p - p_ref: the reference slope rho_ref g_y is removed
-            hpy = -a.half_dy * ax.y - (v * v * hry + 2.0f * rv * hvy) -
-                  a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - ax.z) * a.gy * sg;
+            new_gradp_half_slopes(a, Wc, hrx, hry, hux, huy, hvx, hvy, ax.x, ax.y, ax.z, sg, hpx, hpy);
         } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
             // Qian et al. split (Sec. 2.3.2); p' = p here (no reference)
             float sg = 1.0f;
@@ -250,9 +354,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
     src.prefetch(x0 + tid % TX, y0 + tid / TX);
     for (int k = tid; k < S::NXF + S::NYF; k += NT) {
         const bool isx = k < S::NXF;
-        // face states: density, normal and tangential velocity (rotation,
-        // Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure
-        float rL, nL, tL, pL, rR, nR, tR, pR;
+        FaceStates f;
         float4 *dst;
         if (isx) {
             const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
@@ -265,29 +367,23 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
             }
             const int ga = (fj + 1) * GW + fi;
             const int ca = (fj + 2) * RW + fi + 1;
-            const float4 A = sm.w[ca], B = sm.w[ca + 1], SA = sm.gx[ga], SB = sm.gx[ga + 1];
-            rL = A.x + SA.x; nL = A.y + SA.y; tL = A.z + SA.z; pL = A.w + SA.w - 0.5f * jump;
-            rR = B.x - SB.x; nR = B.y - SB.y; tR = B.z - SB.z; pR = B.w - SB.w + 0.5f * jump;
+            x_face_states(sm.w[ca], sm.w[ca + 1], sm.gx[ga], sm.gx[ga + 1], jump, f);
             dst = &sm.fx[k];
         } else {
             const int kk = k - S::NXF;
             const int fj = kk / TX, fi = kk - fj * TX;
             const int ga = fj * GW + fi + 1;
             const int ca = (fj + 1) * RW + fi + 2;
-            const float4 A = sm.w[ca], B = sm.w[ca + RW], SA = sm.gy[ga], SB = sm.gy[ga + GW];
-            rL = A.x + SA.x; nL = A.z + SA.z; tL = A.y + SA.y; pL = A.w + SA.w;
-            rR = B.x - SB.x; nR = B.z - SB.z; tR = B.y - SB.y; pR = B.w - SB.w;
+            y_face_states(sm.w[ca], sm.w[ca + RW], sm.gy[ga], sm.gy[ga + GW], f);
             dst = &sm.fy[kk];
         }
         // one flux call for both kinds: no divergence where a warp holds both
-        float F[4];
-        riemann_flux<RS, float>(rL, nL, tL, pL, rR, nR, tR, pR, a.beta, a.inv_beta, F);
-        *dst = make_float4(F[0], isx ? F[1] : F[2], isx ? F[2] : F[1], F[3]);
+        *dst = face_flux<RS>(a, isx, f);
     }
     __syncthreads();
 
     // ---- 4. divergence + sources + point-implicit update of dQ and p' ----
-    float sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float4 sq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
     for (int cell = tid; cell < TX * TY; cell += NT) {
         const int lj = cell / TX, li = cell - lj * TX;
@@ -295,66 +391,14 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         if (gi >= nx || gj >= ny) continue;
         const int g = gj * nx + gi;
         const int fw = lj * (TX + 1) + li;
-        const float4 Fw = sm.fx[fw], Fe = sm.fx[fw + 1], Fs = sm.fy[cell], Fn = sm.fy[cell + TX];
-        const float div0 = (Fe.x - Fw.x) * a.inv_dx + (Fn.x - Fs.x) * a.inv_dy;
-        const float div1 = (Fe.y - Fw.y) * a.inv_dx + (Fn.y - Fs.y) * a.inv_dy;
-        const float div2 = (Fe.z - Fw.z) * a.inv_dx + (Fn.z - Fs.z) * a.inv_dy;
-        const float div3 = (Fe.w - Fw.w) * a.inv_dx + (Fn.w - Fs.w) * a.inv_dy;
-        float e0, e1, e2, p0, q0, q1, q2, rref;
-        src.cell(cell, g, e0, e1, e2, p0, q0, q1, q2, rref);
-        const float r0 = q0 + e0;
-        const float m0 = q1 + e1;
-        const float n0 = q2 + e2;
-        float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
-        if constexpr (BDF) {
-            if (a.order >= 2) {
-                rt0 -= a.B2 * a.D1[0][g];
-                rt1 -= a.B2 * a.D1[1][g];
-                rt2 -= a.B2 * a.D1[2][g];
-            }
-            if (a.order >= 3) {
-                rt0 -= a.B3 * a.D2[0][g];
-                rt1 -= a.B3 * a.D2[1][g];
-                rt2 -= a.B3 * a.D2[2][g];
-            }
-        }
-        rt0 *= inv_dt;
-        rt1 *= inv_dt;
-        rt2 *= inv_dt;
-        // reference force: -(divergence of the x-face reference means)
-        const float sref = -0.5f * (sm.dxf[fw + 1] + sm.dxf[fw]) * a.inv_dx;
-        const float b0 = -div0 - rt0;
-        const float b1 = -div1 - rt1 + r0 * a.gx + sref;
-        const float b2 = -div2 - rt2 + (r0 - rref) * a.gy;
-        const float b3 = -div3;
-        float dtau;
-        if (a.local_dtau) {
-            const float ir = Ar<float>::rcp(r0);
-            const float u = m0 * ir, v = n0 * ir, fb = 4.0f * a.beta * ir;
-            const float u2 = u * u + fb, v2 = v * v + fb;
-            const float cx = u2 * rsqrtf(u2), cy = v2 * rsqrtf(v2);
-            const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
-            dtau = __fdividef(a.cfl_area, den);
-        } else {
-            dtau = float(__longlong_as_double((long long)ctl->dtau_bits));
-        }
-        const float adt = alpha * dtau;
-        const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
-        const float coef_p = a.alpha_pi_p_row ? coef : adt;
-        dout[0][g] = e0 + coef * b0;
-        dout[1][g] = e1 + coef * b1;
-        dout[2][g] = e2 + coef * b2;
-        dout[3][g] = p0 + a.beta * coef_p * b3;
-        if (stage == 1) {
-            const float pb = a.beta * b3;
-            sq[0] += b0 * b0; sq[1] += b1 * b1; sq[2] += b2 * b2; sq[3] += pb * pb;
-        }
+        cell_update<BDF>(a, alpha, inv_dt, stage == 1, dout, cell, g, sm.fx[fw], sm.fx[fw + 1], sm.fy[cell],
+                         sm.fy[cell + TX], sm.dxf[fw], sm.dxf[fw + 1], src, sq);
     }
     if (stage == 1) {
         // per-warp sums in FP32, block and grid sums in FP64
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            float v = sq[f];
+            float v = f == 0 ? sq.x : f == 1 ? sq.y : f == 2 ? sq.z : sq.w;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if ((tid & 31) == 0) sm.red[f][tid >> 5] = double(v);
@@ -513,6 +557,201 @@ stage_kernel_mixed(const MixedArgs a) {
     if (a.ctl->done) return;
     mixed_tile<TX, TY, NT, RS, BDF, PF>(a, a.stage, a.alpha, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Column-strip form of the stage sweep (Osher flux, Backward-Euler, the new
+// pressure gradient; either limiter).  Each warp owns 32 adjacent columns, of which the middle 28 are
+// output, and walks up a strip of H rows with a rolling window in registers:
+// the y-direction stencil lives in each lane's registers, x-neighbours come
+// from warp shuffles, so there is no shared memory and no block barrier.  At
+// the row it ingests, k, the warp forms W(k); with W(k-2..k) it forms the
+// slopes and pressure gradient of row k-1, the x-face fluxes of row k-1 and
+// the y-face flux between rows k-2 and k-1, and it updates row k-2.  Lanes
+// 0, 1, 30, 31 are halo (their slopes or fluxes feed the output lanes'
+// faces).  Every per-cell and per-face value uses the same functions as the
+// tile sweep.
+// ---------------------------------------------------------------------------
+struct GlobalSrc {
+    const MixedArgs &a;
+    const float *const *d0;
+    __device__ __forceinline__ void cell(int, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
+                                         float &q1, float &q2, float &rr) const {
+        e0 = d0[0][g]; e1 = d0[1][g]; e2 = d0[2][g]; p0 = d0[3][g];
+        q0 = __ldg(a.qn32[0] + g); q1 = __ldg(a.qn32[1] + g); q2 = __ldg(a.qn32[2] + g);
+        rr = __ldg(a.rho_ref + g);
+    }
+};
+
+__device__ __forceinline__ float4 shfl_down4(const float4 &v, int d) {
+    return make_float4(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
+                       __shfl_down_sync(0xffffffffu, v.z, d), __shfl_down_sync(0xffffffffu, v.w, d));
+}
+__device__ __forceinline__ float4 shfl_up4(const float4 &v, int d) {
+    return make_float4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
+                       __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
+}
+
+constexpr int kStripOut = 28;   // output columns per warp
+
+// The update's inputs of one cell, held in registers (loaded a row ahead).
+struct HeldSrc {
+    float e0, e1, e2, p0, q0, q1, q2, rr;
+    __device__ __forceinline__ void cell(int, int, float &a0, float &a1, float &a2, float &a3, float &b0,
+                                         float &b1, float &b2, float &c0) const {
+        a0 = e0; a1 = e1; a2 = e2; a3 = p0; b0 = q0; b1 = q1; b2 = q2; c0 = rr;
+    }
+};
+
+template <int H, int WPC, int MINB>
+__global__ void __launch_bounds__(WPC * 32, MINB)
+sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
+    pdl_trigger();
+    pdl_wait();
+    const Ctl *ctl = a.ctl;
+    if (ctl->done) return;
+    const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
+    if (warp >= nstrips) return;   // whole warps only
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx, ny = a.ny;
+    const int sy = warp / strips_x, sx = warp - sy * strips_x;
+    const int c = sx * kStripOut + lane - 2;   // this lane's column
+    const int y0 = sy * H, y1 = min(y0 + H, ny);
+    const int stage = a.stage;
+    int in, out;
+    const int cur = ctl->cur;
+    stage_buffers(cur, stage, in, out);
+    const float *const *din = a.d[in];
+    const float *const *d0 = a.d[cur];
+    float *const *dout = a.d[out];
+    const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
+    const bool need_rt = a.realtime != 0;
+    const bool per_x = (a.bc[0] == kPeriodic);
+    // the column's source (ghost columns fold onto interior ones)
+    int nfx, tfx;
+    const int scol = fold_axis(c, nx, a.bc[0], a.bc[1], nfx, tfx);
+    const bool out_lane = lane >= 2 && lane < 30 && c < nx;
+    const int ucol = min(max(c, 0), nx - 1);   // in-bounds column for the prefetch of non-output lanes
+
+    // raw inputs of a row, loaded one row ahead of use
+    struct Raw {
+        float q0, q1, q2, d0, d1, d2, d3;   // Q^n and dQ^{s-1} (+ p')
+        float e1, e2, rr;                   // ring terms: dQ^{m} of rho u, rho v; rho_ref
+        int fl;                             // fold bits
+    };
+    auto load_raw = [&](int k, Raw &R, int &srow) {
+        int nfy, tfy;
+        srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+        const int s = srow * nx + scol;
+        R.q0 = __ldg(a.qn32[0] + s); R.q1 = __ldg(a.qn32[1] + s); R.q2 = __ldg(a.qn32[2] + s);
+        R.d0 = din[0][s]; R.d1 = din[1][s]; R.d2 = din[2][s]; R.d3 = din[3][s];
+        R.e1 = need_rt ? d0[1][s] : 0.0f;
+        R.e2 = need_rt ? d0[2][s] : 0.0f;
+        R.rr = __ldg(a.rho_ref + s);
+        R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
+    };
+    auto load_upd = [&](int row, HeldSrc &U) {
+        const int g = min(max(row, 0), ny - 1) * nx + ucol;
+        U.e0 = d0[0][g]; U.e1 = d0[1][g]; U.e2 = d0[2][g]; U.p0 = d0[3][g];
+        U.q0 = __ldg(a.qn32[0] + g); U.q1 = __ldg(a.qn32[1] + g); U.q2 = __ldg(a.qn32[2] + g);
+        U.rr = __ldg(a.rho_ref + g);
+    };
+
+    float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
+    float4 Sym2 = Wm2;                                       // y half slopes of row k-2
+    float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
+    float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
+    float Jm2 = 0.0f;                                        // east x-face reference jump of row k-2
+    Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
+    int srk, srn;
+    HeldSrc Uk, Un;                                          // update inputs of rows k-2, k-1
+    float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
+    load_raw(y0 - 2, Rk, srk);
+    load_upd(y0 - 2, Uk);
+    for (int k = y0 - 2; k <= y1 + 1; ++k) {
+        // prefetch: the next row's raw inputs and the next updated row's inputs
+        load_raw(k + 1, Rn, srn);
+        load_upd(k - 1, Un);
+        // ---- W = (rho, u, v, p') of Q^{s-1} at row k ----
+        float4 W0;
+        {
+            const float r = Rk.q0 + Rk.d0;
+            float mm = Rk.q1 + Rk.d1;
+            float nn = Rk.q2 + Rk.d2;
+            mm = (Rk.fl & 1) ? -mm : mm;
+            nn = (Rk.fl & 2) ? -nn : nn;
+            const float ir = Ar<float>::rcp(r);
+            W0 = make_float4(r, mm * ir, nn * ir, Rk.d3);
+        }
+        if (k >= y0) {
+            // ---- slopes and pressure gradient of row r = k-1 ----
+            const int r = k - 1;
+            const float4 We = shfl_down4(Wm1, 1), Ww = shfl_up4(Wm1, 1);
+            float hrx, hry, hux, huy, hvx, hvy;
+            limit_slopes(Wm1, We, Ww, W0, Wm2, a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
+            float rx = 0.0f, ry = 0.0f;
+            if (need_rt) {
+                rx = (a.B0 * Rm1.e1) * inv_dt;
+                ry = (a.B0 * Rm1.e2) * inv_dt;
+                rx = (Rm1.fl & 1) ? -rx : rx;
+                ry = (Rm1.fl & 2) ? -ry : ry;
+            }
+            const float sg = wall_ghost_sign<float>(c, r, nx, ny, a.bc);
+            float hpx, hpy;
+            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.rr, sg, hpx, hpy);
+            const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
+            // ---- east x-face of row r (between columns c and c + 1) ----
+            const float4 Wn = shfl_down4(Wm1, 1), Sn = shfl_down4(Sx, 1);
+            float jump = 0.0f;
+            const int gi = c + 1;
+            if (r >= 0 && r < ny && gi >= 0) {
+                if (gi < nx) jump = __ldg(a.dref + r * nx + gi);
+                else if (gi == nx && per_x) jump = __ldg(a.dref + r * nx);
+            }
+            FaceStates f;
+            x_face_states(Wm1, Wn, Sx, Sn, jump, f);
+            const float4 Fx = face_flux<kOsher>(a, true, f);
+            if (k >= y0 + 1) {
+                // ---- y-face between rows r - 1 and r ----
+                FaceStates fy;
+                y_face_states(Wm2, Wm1, Sym2, Sy, fy);
+                const float4 Fy = face_flux<kOsher>(a, false, fy);
+                if (k >= y0 + 2) {
+                    // ---- update of row k - 2 ----
+                    const float4 Fw = shfl_up4(Fxm2, 1);
+                    const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
+                    if (out_lane)
+                        cell_update<false>(a, a.alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
+                                           Fy, jw, Jm2, Uk, sq);
+                }
+                Fyp = Fy;
+            }
+            Fxm2 = Fx;
+            Jm2 = jump;
+            Sym2 = Sy;
+        }
+        Wm2 = Wm1;
+        Wm1 = W0;
+        Rm1 = Rk;
+        Rk = Rn;
+        srk = srn;
+        Uk = Un;
+    }
+    if (stage == 1) {
+        // per-warp sums in FP32, one FP64 partial per strip
+        float v0 = sq.x, v1 = sq.y, v2 = sq.z, v3 = sq.w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, o);
+            v1 += __shfl_down_sync(0xffffffffu, v1, o);
+            v2 += __shfl_down_sync(0xffffffffu, v2, o);
+            v3 += __shfl_down_sync(0xffffffffu, v3, o);
+        }
+        if (lane == 0) {
+            double *p = a.partials + (size_t)warp * 4;
+            p[0] = v0; p[1] = v1; p[2] = v2; p[3] = v3;
+        }
+    }
 }
 
 // Global pseudo-time step option for the mixed form.
