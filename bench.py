@@ -343,7 +343,8 @@ def run_ours(args, ws, rank, local):
                  "pseudo_iters_per_step": statistics.mean(l_iters), "gpu_launches": l_launches,
                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": measured_hbm_gbs(), "unit": "GB/s",
                               "frac": gbs / measured_hbm_gbs(), "frac_of_nominal_8tbs": gbs / 8000.0,
-                              "kernel": f"stage_kernel_mixed<{ltx},{lty},{lnt}>", "tile_variant": lv,
+                              "kernel": (f"sweep_kernel_mixed<{lty},{lnt // 32}> (28-column strips)" if ltx == 28
+                                         else f"stage_kernel_mixed<{ltx},{lty},{lnt}>"), "tile_variant": lv,
                               "launch_ms": l_launch_s * 1e3,
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
                               "traffic": MIXED_TRAFFIC_PER_CELL_STAGE * lc.cells,
@@ -472,12 +473,12 @@ BYTES_PER_CELL_ITER_F64 = 328.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, stage_kernel_mixed<32,8,256> prefetching 5-CTA variant,
-# 2048x2048, profiles/stage_kernel_mixed_rayleigh_taylor_2048.md): DRAM bytes
-# and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2 forms
-# counted as two) per cell of one stage launch
-MIXED_TRAFFIC_PER_CELL_STAGE = 64.1
-MIXED_FP32_OPS_PER_CELL_STAGE = 482.6
+# measured (ncu, sweep_kernel_mixed<256,4>, the tuned kernel on this
+# 2048x8192 tank, profiles/sweep_kernel_mixed_rayleigh_taylor_2048x8192.md):
+# DRAM bytes and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2
+# forms counted as two) per cell of one stage launch
+MIXED_TRAFFIC_PER_CELL_STAGE = 68.0
+MIXED_FP32_OPS_PER_CELL_STAGE = 492.3
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
