@@ -87,6 +87,32 @@ batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
     }
 }
 
+// Column-strip form over the flattened strips of all tanks: warp w takes
+// strip w (see mixed_strip); CD as above.
+template <int H, int WPC, int MINB, bool CD>
+__global__ void __launch_bounds__(WPC * 32, MINB)
+batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ strip_tank, int nstrips, int stage,
+                   float alpha, int slot0) {
+    pdl_trigger();
+    pdl_wait();
+    const int w = blockIdx.x * WPC + (threadIdx.x >> 5);
+    if (w >= nstrips) return;   // whole warps only
+    const int k = strip_tank[w];
+    if constexpr (CD) {
+        const BatchTank &t = c_tanks[slot0 + k];
+        if (t.a.ctl->done) return;
+        const int local = w - t.tile0;
+        const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+    } else {
+        const BatchTank &t = tanks[k];
+        if (t.a.ctl->done) return;
+        const int local = w - t.tile0;
+        const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+    }
+}
+
 // Start of a physical step for every tank (blockIdx.y = tank): level shift
 // in FP64 and control-block reset (Alg. 1).
 __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const double *dt, double tol,
@@ -205,11 +231,13 @@ __global__ void batch_restore_kernel(BatchTank *tanks) {
 
 struct Variant {
     int tx, ty, nt;
-    bool pf;   // prefetching tile sweep
+    bool pf;      // prefetching tile sweep
+    bool sweep;   // column-strip sweep: 28 columns x ty rows per warp (new pressure gradient only)
 };
 constexpr Variant kVariants[] = {
-    {32, 8, 256}, {32, 16, 256}, {32, 16, 512}, {64, 8, 256},       {64, 8, 512},
+    {32, 8, 256},  {32, 16, 256}, {32, 16, 512}, {64, 8, 256},        {64, 8, 512},
     {64, 16, 512}, {16, 16, 256}, {32, 8, 256, true}, {16, 16, 256, true},
+    {28, 32, 128, false, true}, {28, 64, 128, false, true}, {28, 128, 128, false, true},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -223,6 +251,17 @@ cudaError_t allow_smem() {
 }
 
 // slot0 < 0: descriptors in global memory
+template <int H, int WPC, int MINB>
+cudaError_t launch_sweep(const BatchTank *tanks, const int *map, int nstrips, int stage, float alpha, int slot0,
+                         bool pdl, cudaStream_t s) {
+    const dim3 g((nstrips + WPC - 1) / WPC);
+    if (slot0 >= 0)
+        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true>, g, dim3(WPC * 32), 0, s, tanks, map, nstrips,
+                          stage, alpha, slot0);
+    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false>, g, dim3(WPC * 32), 0, s, tanks, map, nstrips,
+                      stage, alpha, 0);
+}
+
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
 cudaError_t launch_stage(const BatchTank *tanks, const int *map, int ntiles, int stage, float alpha, int slot0,
                          bool pdl, cudaStream_t s) {
@@ -348,6 +387,10 @@ struct StageLaunch {
     cudaError_t go(cudaStream_t s) const {
         return launch_stage<TX, TY, NT, RS, BDF, PF>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
     }
+    template <int H>
+    cudaError_t strips(cudaStream_t s) const {
+        return launch_sweep<H, 4, 4>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
+    }
 };
 
 int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
@@ -367,7 +410,10 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
         case 5: e = L.go<64, 16, 512>(s); break;
         case 6: e = L.go<16, 16, 256>(s); break;
         case 7: e = L.go<32, 8, 256, kOsher, false, true>(s); break;
-        default: e = L.go<16, 16, 256, kOsher, false, true>(s); break;
+        case 8: e = L.go<16, 16, 256, kOsher, false, true>(s); break;
+        case 9: e = L.strips<32>(s); break;
+        case 10: e = L.strips<64>(s); break;
+        default: e = L.strips<128>(s); break;
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
     return AC_OK;
@@ -378,10 +424,12 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
 int tune(ac_batch *b, cudaStream_t s) {
     if (b->variant >= 0) return AC_OK;
     if (b->opt.riemann != AC_RIEMANN_OSHER || b->opt.bdf_order > 1) return build_tiles(b, 0);
+    // the column-strip sweeps implement the new pressure gradient only
+    const bool sweep_ok = b->opt.gradp == AC_GRADP_NEW;
     const char *env = getenv("AC_BATCH_TILE");
     if (env) {
         const int v = atoi(env);
-        if (v >= 0 && v < kNumVariants) return build_tiles(b, v);
+        if (v >= 0 && v < kNumVariants) return build_tiles(b, kVariants[v].sweep && !sweep_ok ? 0 : v);
     }
     // the scratch buffers start as copies of the state (every tank holds
     // it in buffer 0 before its first step), so that every timed stage sees
@@ -395,6 +443,7 @@ int tune(ac_batch *b, cudaStream_t s) {
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumVariants; ++v) {
+        if (kVariants[v].sweep && !sweep_ok) continue;
         int rc = build_tiles(b, v);
         if (rc != AC_OK) return rc;
         // every stage of one pseudo-iteration (scratch buffers only)

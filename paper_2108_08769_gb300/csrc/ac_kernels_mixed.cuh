@@ -603,21 +603,17 @@ struct HeldSrc {
     }
 };
 
-template <int H, int WPC, int MINB>
-__global__ void __launch_bounds__(WPC * 32, MINB)
-sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
-    pdl_trigger();
-    pdl_wait();
+// One strip (strip coordinates sx, sy) of stage `stage` (coefficient alpha)
+// of one tank, by one warp; `partial` receives the strip's four residual
+// partial sums at stage 1.  Shared by the single-tank and batched kernels.
+template <int H>
+__device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
+                                            double *partial) {
     const Ctl *ctl = a.ctl;
-    if (ctl->done) return;
-    const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
-    if (warp >= nstrips) return;   // whole warps only
     const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
-    const int sy = warp / strips_x, sx = warp - sy * strips_x;
     const int c = sx * kStripOut + lane - 2;   // this lane's column
     const int y0 = sy * H, y1 = min(y0 + H, ny);
-    const int stage = a.stage;
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, stage, in, out);
@@ -721,7 +717,7 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
                     if (out_lane)
-                        cell_update<false>(a, a.alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
+                        cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
                                            Fy, jw, Jm2, Uk, sq);
                 }
                 Fyp = Fy;
@@ -748,10 +744,21 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
             v3 += __shfl_down_sync(0xffffffffu, v3, o);
         }
         if (lane == 0) {
-            double *p = a.partials + (size_t)warp * 4;
-            p[0] = v0; p[1] = v1; p[2] = v2; p[3] = v3;
+            partial[0] = v0; partial[1] = v1; partial[2] = v2; partial[3] = v3;
         }
     }
+}
+
+template <int H, int WPC, int MINB>
+__global__ void __launch_bounds__(WPC * 32, MINB)
+sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
+    pdl_trigger();
+    pdl_wait();
+    if (a.ctl->done) return;
+    const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
+    if (warp >= nstrips) return;   // whole warps only
+    const int sy = warp / strips_x, sx = warp - sy * strips_x;
+    mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4);
 }
 
 // Global pseudo-time step option for the mixed form.

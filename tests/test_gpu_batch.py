@@ -2,10 +2,14 @@
 
 A tank's numbers must not depend on the rest of the batch: with a fixed
 number of pseudo-iterations every tank equals a single-tank context in the
-mixed form bit for bit (whatever tile shapes the two autotuners pick), and
-with the stopping test on every tank stops at its own iteration count, the
-same as alone when both use one tile shape.  Against the FP64 oracle each
-tank stays within the mixed form's 1e-5 relative field error.
+mixed form bit for bit when both run the same form of the sweep (any tile
+shape of the tile sweep, or the column-strip sweep), and with the stopping
+test on every tank stops at its own iteration count, the same as alone when
+both use one tile shape.  The two forms share their arithmetic but not
+their compiled code: the compiler may fuse a product and a sum into one
+FMA in one kernel and not in the other, so across forms a tank agrees to
+round-off.  Against the FP64 oracle each tank stays within the mixed form's
+1e-5 relative field error.
 """
 import numpy as np
 import pytest
@@ -38,7 +42,15 @@ def single_mixed(case, dt, tol, iters):
     return s, n, R
 
 
-def test_batch_equals_single_tanks_bitwise_fixed_iterations():
+# single-tank variant of the same form as each batch variant: the tile
+# sweep (32x8) for the tile variants, the strip sweep of the same strip
+# height (32, 64, 128 rows) for the strip variants
+SINGLE_OF_BATCH = {9: 15, 10: 16, 11: 17}
+
+
+def test_batch_equals_single_tanks_bitwise_fixed_iterations(monkeypatch):
+    monkeypatch.setenv("AC_BATCH_TILE", "0")
+    monkeypatch.setenv("AC_TILE", "0")
     cases = uneven_cases()
     b = ac.Batch.from_cases(cases)
     rc, its, st = b.physical_step(1e-3, -1.0, 7)
@@ -52,14 +64,16 @@ def test_batch_equals_single_tanks_bitwise_fixed_iterations():
     b.close()
 
 
-N_BATCH_VARIANTS = 9
+N_BATCH_VARIANTS = 12
 
 
 @pytest.mark.parametrize("v", range(N_BATCH_VARIANTS))
 def test_every_batch_variant_equals_single_tanks_bitwise(monkeypatch, v):
     """Each compiled batch variant (tile shape, direct or prefetching
-    loads), forced in place of the autotuner's pick."""
+    loads, column strips), forced in place of the autotuner's pick, against
+    single tanks run with the same form."""
     monkeypatch.setenv("AC_BATCH_TILE", str(v))
+    monkeypatch.setenv("AC_TILE", str(SINGLE_OF_BATCH.get(v, 0)))
     cases = uneven_cases()
     b = ac.Batch.from_cases(cases)
     b.physical_step(1e-3, -1.0, 5)
@@ -158,9 +172,11 @@ def test_bdf2_batch_equals_single_tanks():
     b.close()
 
 
-def test_two_batches_alive_at_once():
+def test_two_batches_alive_at_once(monkeypatch):
     """Two batches hold separate ranges of the constant descriptor table;
     stepping them in turn leaves each equal to its tanks run alone."""
+    monkeypatch.setenv("AC_BATCH_TILE", "0")
+    monkeypatch.setenv("AC_TILE", "0")
     ca = uneven_cases()[:4]
     cb = W.batched_tanks(count=5, nmin=24, nmax=70, seed=31)
     a = ac.Batch.from_cases(ca)
@@ -181,9 +197,11 @@ def test_two_batches_alive_at_once():
     b.close()
 
 
-def test_batch_larger_than_the_constant_table():
+def test_batch_larger_than_the_constant_table(monkeypatch):
     """170 small tanks do not fit the 160-slot constant table: the batch
     reads its descriptors from global memory, with the same results."""
+    monkeypatch.setenv("AC_BATCH_TILE", "0")
+    monkeypatch.setenv("AC_TILE", "0")
     cases = W.batched_tanks(count=170, nmin=8, nmax=20, seed=41)
     b = ac.Batch.from_cases(cases)
     b.physical_step(1e-3, -1.0, 3)

@@ -48,6 +48,9 @@ def run_child(tmp_path, name, env_extra):
     script.write_text(CHILD)
     out = tmp_path / f"{name}.json"
     env = dict(os.environ)
+    # every process tunes on its own: pin the variants so that all modes run
+    # the same kernels
+    env.update({"AC_TILE": "0", "AC_TILE_F64": "0", "AC_BATCH_TILE": "0"})
     env.update(env_extra)
     subprocess.run([sys.executable, str(script), ROOT, str(out)], env=env, check=True, timeout=600)
     return json.load(open(out))
@@ -60,7 +63,8 @@ def test_graph_host_loop_and_plain_launches_agree(tmp_path):
         assert other == base, name
 
 
-def test_profiling_mode_agrees_with_the_graph():
+def test_profiling_mode_agrees_with_the_graph(monkeypatch):
+    monkeypatch.setenv("AC_TILE", "0")
     case = W.random_two_fluid(70, 45, ratio=1000.0, c0=20.0)
     results = []
     for prof in (False, True):
