@@ -307,10 +307,81 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
     F[3] = 0.5f * ((uL + uR) - (dq * Sau - Sh));
 }
 
+// Osher fluxes of two faces at once (Sec. 2.4.3), for a thread that owns an
+// x-face and a y-face: lane x of every packed FP32x2 instruction carries one
+// face and lane y the other, and each lane takes the three Gauss points in
+// turn.  Every operation of the flux is then a packed one (the reciprocal
+// and reciprocal square root excepted) and no lane sums are needed.  Same
+// quadrature and terms as osher_flux, per lane; the weight of a point rides
+// on k = w rho / c.  Inputs are (rho, un, ut, p) per lane, output as
+// osher_flux per lane.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+__device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL, float2 pL, float2 rR, float2 uR,
+                                                float2 vR, float2 pR, float beta, float inv_beta, float2 F[4]) {
+    const float2 ib = dup2(inv_beta);
+    const float2 mL = __fmul2_rn(rL, uL), nL = __fmul2_rn(rL, vL), qL = __fmul2_rn(pL, ib);
+    const float2 mR = __fmul2_rn(rR, uR), nR = __fmul2_rn(rR, vR), qR = __fmul2_rn(pR, ib);
+    const float2 dr = sub2(rR, rL), dm = sub2(mR, mL), dn = sub2(nR, nL), dq = sub2(qR, qL);
+    const float2 ndr = neg2(dr);
+    // central parts F(Q_L) + F(Q_R) first, so that the face states die here
+    const float2 c0 = __fadd2_rn(mL, mR);
+    const float2 c1 = __fadd2_rn(__ffma2_rn(mR, uR, __ffma2_rn(mL, uL, pL)), pR);
+    const float2 c2c = __ffma2_rn(mR, vR, __fmul2_rn(mL, vL));
+    const float2 c3 = __fadd2_rn(uL, uR);
+    const float2 fb = dup2(4.0f * beta);
+    const float tq[3] = {0.11270166537925831148f, 0.5f, 0.88729833462074168852f};
+    const float wq[3] = {5.0f / 18.0f, 8.0f / 18.0f, 5.0f / 18.0f};
+    float2 Sau, Se, Sue, Sve, Sg, Sh;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 t = dup2(tq[j]), w = dup2(wq[j]);
+        const float2 r = __ffma2_rn(t, dr, rL), m = __ffma2_rn(t, dm, mL), n = __ffma2_rn(t, dn, nL);
+        const float2 ir = make_float2(Ar<float>::rcp(r.x), Ar<float>::rcp(r.y));
+        const float2 u = __fmul2_rn(m, ir), v = __fmul2_rn(n, ir);
+        const float2 c2 = __ffma2_rn(u, u, __fmul2_rn(fb, ir));
+        const float2 ic = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
+        const float2 c = __fmul2_rn(c2, ic);
+        // l4 = u/2 + c/2, l5 = u/2 - c/2 (c/2 is exact, so one rounding each)
+        const float2 hu = __fmul2_rn(dup2(0.5f), u);
+        const float2 l4 = __ffma2_rn(dup2(0.5f), c, hu), l5 = __ffma2_rn(dup2(-0.5f), c, hu);
+        const float2 au = make_float2(fabsf(u.x), fabsf(u.y)), nau = make_float2(-au.x, -au.y);
+        const float2 a = __fmul2_rn(__ffma2_rn(u, ndr, dm), ib);
+        const float2 k = __fmul2_rn(__fmul2_rn(w, r), ic);
+        const float2 g4 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l4, nau), k), __ffma2_rn(l4, a, dq));
+        const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dq));
+        const float2 e = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
+        const float2 gs = __fmul2_rn(ir, __fadd2_rn(g4, g5));
+        const float2 h = __fmul2_rn(ir, __ffma2_rn(g5, l4, __fmul2_rn(g4, l5)));
+        if (j == 0) {
+            Sau = __fmul2_rn(w, au);
+            Se = e;
+            Sue = __fmul2_rn(u, e);
+            Sve = __fmul2_rn(v, e);
+            Sg = gs;
+            Sh = h;
+        } else {
+            Sau = __ffma2_rn(w, au, Sau);
+            Se = __fadd2_rn(Se, e);
+            Sue = __ffma2_rn(u, e, Sue);
+            Sve = __ffma2_rn(v, e, Sve);
+            Sg = __fadd2_rn(Sg, gs);
+            Sh = __fadd2_rn(Sh, h);
+        }
+    }
+    const float2 half = dup2(0.5f);
+    // F = 1/2 (F(Q_L) + F(Q_R) - D), D as in osher_flux
+    F[0] = __fmul2_rn(half, sub2(c0, __ffma2_rn(dr, Sau, Se)));
+    F[1] = __fmul2_rn(half, sub2(c1, __ffma2_rn(dup2(beta), Sg, __ffma2_rn(dm, Sau, Sue))));
+    F[2] = __fmul2_rn(half, sub2(c2c, __ffma2_rn(dn, Sau, Sve)));
+    F[3] = __fmul2_rn(half, sub2(c3, sub2(__fmul2_rn(dq, Sau), Sh)));
+}
+
 // Face flux of the solver RS, chosen at compile time so that a kernel built
 // for one solver carries none of the others' registers.  The FP32 Osher flux
-// is always the packed form, so every FP32 sweep (any tile shape, single tank
-// or batch) computes a face bit for bit the same way.
+// of one face is always the packed form above, so every FP32 tile sweep (any
+// tile shape, single tank or batch) computes a face bit for bit the same way;
+// the column-strip sweep takes its faces in pairs (osher_flux_pair).
 template <int RS, typename T>
 __device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
                                              T inv_beta, T F[4]) {

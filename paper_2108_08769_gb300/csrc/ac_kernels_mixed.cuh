@@ -704,14 +704,19 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 if (gi < nx) jump = __ldg(a.dref + r * nx + gi);
                 else if (gi == nx && per_x) jump = __ldg(a.dref + r * nx);
             }
-            FaceStates f;
+            // ---- and the y-face between rows r - 1 and r (not needed, but
+            // harmless, on the first row): both fluxes as one packed pair ----
+            FaceStates f, fy;
             x_face_states(Wm1, Wn, Sx, Sn, jump, f);
-            const float4 Fx = face_flux<kOsher>(a, true, f);
+            y_face_states(Wm2, Wm1, Sym2, Sy, fy);
+            float2 Fp[4];
+            osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
+                            make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
+                            make_float2(f.tR, fy.tR), make_float2(f.pR, fy.pR), a.beta, a.inv_beta, Fp);
+            const float4 Fx = make_float4(Fp[0].x, Fp[1].x, Fp[2].x, Fp[3].x);
             if (k >= y0 + 1) {
-                // ---- y-face between rows r - 1 and r ----
-                FaceStates fy;
-                y_face_states(Wm2, Wm1, Sym2, Sy, fy);
-                const float4 Fy = face_flux<kOsher>(a, false, fy);
+                // the y-face's normal momentum is rho v
+                const float4 Fy = make_float4(Fp[0].y, Fp[2].y, Fp[1].y, Fp[3].y);
                 if (k >= y0 + 2) {
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
