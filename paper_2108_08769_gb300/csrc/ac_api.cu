@@ -182,6 +182,7 @@ struct F64Backend : Backend {
     double *buf[3][4] = {};
     double *lev[4] = {};
     double *lev1[3] = {}, *lev2[3] = {};   // Q^{n-1}, Q^{n-2} (BDF2, BDF3)
+    double *aux[4] = {};                    // dtau and real-time terms kept from stage 1
 
     int shape(int &tx, int &ty, int &nt) const override {
         const F64Variant &m = kF64Variants[variant < 0 ? 0 : variant];
@@ -291,6 +292,8 @@ struct F64Backend : Backend {
         for (int q = 0; q < 4; ++q) a.B[q] = kBDF[c->order_now][q];
         a.partials = c->partials;
         a.ctl = c->ctl;
+        for (int f = 0; f < 4; ++f) a.aux[f] = aux[f];
+        a.reuse = (aux[0] != nullptr && c->opt.rk_stages > 1) ? 1 : 0;
         return a;
     }
     int alloc(ac_ctx *c) override {
@@ -300,6 +303,8 @@ struct F64Backend : Backend {
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) CK(cudaMalloc(&buf[b][f], bytes));
         for (int f = 0; f < 4; ++f) CK(cudaMalloc(&lev[f], bytes));
+        if (c->opt.rk_stages > 1)
+            for (int f = 0; f < 4; ++f) CK(cudaMalloc(&aux[f], bytes));
         for (int f = 0; f < 3; ++f) {
             if (c->opt.bdf_order >= 2) CK(cudaMalloc(&lev1[f], bytes));
             if (c->opt.bdf_order >= 3) CK(cudaMalloc(&lev2[f], bytes));
@@ -319,7 +324,7 @@ struct F64Backend : Backend {
     void release() override {
         for (int b = 0; b < 3; ++b)
             for (int f = 0; f < 4; ++f) cudaFree(buf[b][f]);
-        for (int f = 0; f < 4; ++f) cudaFree(lev[f]);
+        for (int f = 0; f < 4; ++f) { cudaFree(lev[f]); cudaFree(aux[f]); }
         for (int f = 0; f < 3; ++f) { cudaFree(lev1[f]); cudaFree(lev2[f]); }
     }
     int set_state(ac_ctx *c, const double *const f[4]) override {

@@ -94,6 +94,19 @@ __device__ __forceinline__ T half_minmod(T a, T b) {
     return (copysign(T(0.25), a) + copysign(T(0.25), b)) * fmin(fabs(a), fabs(b));
 }
 
+// The whole k = 1 limiter, G(a, b) = 2 half_minmod(a, b), from the bit
+// patterns: zero where the sign bits differ, else the argument of smaller
+// magnitude (finite magnitudes order like their patterns with the sign bit
+// cleared).  Integer instructions only, for sweeps that the FP64 pipe
+// bounds; the same value, signed zeros included, and, like fmin, the other
+// argument in place of a NaN.
+__device__ __forceinline__ double minmod_bits(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    const long long m = (ma < mb) ? ia : ib;
+    return ((ia ^ ib) < 0) ? 0.0 : __longlong_as_double(m);
+}
+
 // ---------------------------------------------------------------------------
 // Osher flux of Dumbser & Toro along the straight path in Q, 3-point
 // Gauss-Legendre (Sec. 2.4.3), in the face-normal frame.  States are given
@@ -106,9 +119,11 @@ __device__ __forceinline__ T half_minmod(T a, T b) {
 // Writing a = (d(rho un) - un d(rho))/beta and dq = d(p/beta):
 //   l4.dQ =  (rho/c)(l4 a + dq),   l5.dQ = -(rho/c)(l5 a + dq),
 // and since l4 > 0 > l5: |l4| - |u| = l4 - |u|, |l5| - |u| = -l5 - |u|.
-// Output F = (mass, normal momentum, tangential momentum, p/beta flux).
+// Output F = (mass, normal momentum, tangential momentum, p/beta flux), or
+// 2F with TWICE (the caller folds the 1/2 into its divergence; a factor of
+// two is exact, so the divergence is the same to the last bit).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool TWICE = false>
 __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR,
                                            T beta, T inv_beta, T F[4]) {
     const T mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
@@ -121,7 +136,8 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     // D = sum_j w_j |A_j| dQ, accumulated as
     //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
     //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
-    T Sau = T(0), Se = T(0), Sue = T(0), Sve = T(0), Sg = T(0), Sh = T(0);
+    // (the weight w_j rides on k = w_j rho / c)
+    T Sau, Se, Sue, Sve, Sg, Sh;
     // the three densities' reciprocals from one reciprocal of their product
     // (1 reciprocal + 6 products in place of 3 reciprocals)
     T rq[3], irq[3];
@@ -145,29 +161,30 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T c2 = u * u + four_beta * ir;
         T c, ic;
         Ar<T>::sqrt_rsqrt(c2, c, ic);
-        const T hu = T(0.5) * u, hc = T(0.5) * c;
-        const T l4 = hu + hc, l5 = hu - hc;
+        // l4 = u/2 + c/2, l5 = u/2 - c/2 (c/2 is exact: one rounding each)
+        const T hu = T(0.5) * u;
+        const T l4 = fma(T(0.5), c, hu), l5 = fma(T(-0.5), c, hu);
         const T au = fabs(u);
         const T a = (dm - u * dr) * inv_beta;
-        const T k = r * ic;
+        const T w = wq[j];
+        const T k = (w * r) * ic;
         const T g4 = (l4 - au) * k * (l4 * a + dq);
         const T g5 = (l5 + au) * k * (l5 * a + dq);
-        const T w = wq[j];
-        const T we = w * (g4 * l4 + g5 * l5);
-        const T wir = w * ir;
-        Sau += w * au;
-        Se += we;
-        Sue += u * we;
-        Sve += v * we;
-        Sg += wir * (g4 + g5);
-        Sh += wir * (g4 * l5 + g5 * l4);
+        const T e = g4 * l4 + g5 * l5;
+        const T gs = ir * (g4 + g5), h = ir * (g4 * l5 + g5 * l4);
+        if (j == 0) {
+            Sau = w * au; Se = e; Sue = u * e; Sve = v * e; Sg = gs; Sh = h;
+        } else {
+            Sau += w * au; Se += e; Sue += u * e; Sve += v * e; Sg += gs; Sh += h;
+        }
     }
     // central part 1/2 (F(Q_L) + F(Q_R)); dissipation 1/2 * D (D already
     // carries the 1/2 of the [0,1] quadrature)
-    F[0] = T(0.5) * ((mL + mR) - (dr * Sau + Se));
-    F[1] = T(0.5) * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
-    F[2] = T(0.5) * ((mL * vL + mR * vR) - (dn * Sau + Sve));
-    F[3] = T(0.5) * ((uL + uR) - (dq * Sau - Sh));
+    const T hf = TWICE ? T(1) : T(0.5);
+    F[0] = hf * ((mL + mR) - (dr * Sau + Se));
+    F[1] = hf * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
+    F[2] = hf * ((mL * vL + mR * vR) - (dn * Sau + Sve));
+    F[3] = hf * ((uL + uR) - (dq * Sau - Sh));
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +192,7 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
 // needed here): F = 1/2 (F(Q_L) + F(Q_R) - |A(Q~)| dQ), |A| dQ in the same
 // rank-2 form as one Osher quadrature point with weight 1.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool TWICE = false>
 __device__ __forceinline__ void roe_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta, T inv_beta,
                                          T F[4]) {
     const T mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
@@ -197,10 +214,11 @@ __device__ __forceinline__ void roe_flux(T rL, T uL, T vL, T pL, T rR, T uR, T v
     const T g4 = (l4 - au) * k * (l4 * a + dq);
     const T g5 = (l5 + au) * k * (l5 * a + dq);
     const T e = g4 * l4 + g5 * l5;
-    F[0] = T(0.5) * ((mL + mR) - (au * dr + e));
-    F[1] = T(0.5) * ((mL * uL + pL + mR * uR + pR) - (au * dm + u * e + beta * ir * (g4 + g5)));
-    F[2] = T(0.5) * ((mL * vL + mR * vR) - (au * dn + v * e));
-    F[3] = T(0.5) * ((uL + uR) - (au * dq - (g4 * l5 + g5 * l4) * ir));
+    const T hf = TWICE ? T(1) : T(0.5);   // 2F with TWICE, as osher_flux
+    F[0] = hf * ((mL + mR) - (au * dr + e));
+    F[1] = hf * ((mL * uL + pL + mR * uR + pR) - (au * dm + u * e + beta * ir * (g4 + g5)));
+    F[2] = hf * ((mL * vL + mR * vR) - (au * dn + v * e));
+    F[3] = hf * ((uL + uR) - (au * dq - (g4 * l5 + g5 * l4) * ir));
 }
 
 // ---------------------------------------------------------------------------
@@ -209,7 +227,7 @@ __device__ __forceinline__ void roe_flux(T rL, T uL, T vL, T pL, T rR, T uR, T v
 // star values u*, p*, rho*_L, rho*_R, and the state at x/tau = 0 sampled as
 // left (0 <= S_L), left star (0 <= u*), right star (0 <= S_R) or right.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool TWICE = false>
 __device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta, T inv_beta,
                                            T F[4]) {
     const T cL = Ar<T>::sqrt_(uL * uL + T(4) * beta * Ar<T>::rcp(rL));
@@ -232,10 +250,11 @@ __device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         }
     }
     const T m = r * u;
-    F[0] = m;
-    F[1] = m * u + p;
-    F[2] = m * v;
-    F[3] = u;
+    const T s = TWICE ? T(2) : T(1);   // 2F with TWICE, as osher_flux
+    F[0] = s * m;
+    F[1] = s * (m * u + p);
+    F[2] = s * (m * v);
+    F[3] = s * u;
 }
 
 // FP32 form of osher_flux for sm_100-class parts: the two outer Gauss points
@@ -382,13 +401,15 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
 // of one face is always the packed form above, so every FP32 tile sweep (any
 // tile shape, single tank or batch) computes a face bit for bit the same way;
 // the column-strip sweep takes its faces in pairs (osher_flux_pair).
-template <int RS, typename T>
+// With TWICE (FP64 only) every solver returns 2F.
+template <int RS, typename T, bool TWICE = false>
 __device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
                                              T inv_beta, T F[4]) {
-    if constexpr (RS == kRoe) roe_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
-    else if constexpr (RS == kBassi) bassi_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    static_assert(!TWICE || std::is_same<T, double>::value, "2F form is FP64 only");
+    if constexpr (RS == kRoe) roe_flux<T, TWICE>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else if constexpr (RS == kBassi) bassi_flux<T, TWICE>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
     else if constexpr (std::is_same<T, float>::value) osher_flux_x2(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
-    else osher_flux<T>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
+    else osher_flux<T, TWICE>(rL, uL, vL, pL, rR, uR, vR, pR, beta, inv_beta, F);
 }
 
 }  // namespace acgb

@@ -54,7 +54,23 @@ struct SweepArgs {
     T B[4];                        // its coefficients B0..B3 (Table BDF)
     double *partials;              // per-CTA residual partial sums [nblocks][4]
     Ctl *ctl;
+    // Per-cell values that stay fixed through a pseudo-iteration (they come
+    // from Q^{m} and the real-time levels): local dtau and the real-time
+    // terms of rho, rho u, rho v.  With reuse set, stage 1 writes them and
+    // later stages read them back instead of recomputing; null otherwise.
+    T *aux[4];
+    int reuse;
 };
+
+// Frozen real-time term (Eq. bdf) of field f at index s, Q^{m} value qm:
+// (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} + B3 Q^{n-2}) / dt, always in this order.
+template <typename T>
+__device__ __forceinline__ T realtime_term(const SweepArgs<T> &a, T qm, int f, size_t s, T inv_dt) {
+    T r = fma(a.B[1], a.lev[f][s], a.B[0] * qm);
+    if (a.order >= 2) r = fma(a.B[2], a.lev1[f][s], r);
+    if (a.order >= 3) r = fma(a.B[3], a.lev2[f][s], r);
+    return r * inv_dt;
+}
 
 // Buffer roles within a pseudo-iteration: stage s reads `in` and writes
 // `out`; Q^{m} (stage 0) stays in `cur` until the iteration ends.
@@ -140,6 +156,7 @@ stage_kernel(const SweepArgs<T> a) {
     }
     // ---- frozen real-time term of the momenta on the ring (Eq. bdf, BE) ----
     const bool need_rt = (a.gradp == kGradNew) && a.realtime;
+    const bool reuse_now = a.reuse && a.stage > 1;   // fixed per-cell values from stage 1
     if (need_rt) {
         for (int k = tid; k < GW * GH; k += NT) {
             const int gi = x0 + (k % GW) - 1, gj = y0 + (k / GW) - 1;
@@ -147,18 +164,14 @@ stage_kernel(const SweepArgs<T> a) {
             const int si = fold_axis(gi, nx, a.bc[0], a.bc[1], nfx, tfx);
             const int sj = fold_axis(gj, ny, a.bc[2], a.bc[3], nfy, tfy);
             const size_t s = (size_t)sj * nx + si;
-            T rx = a.B[0] * q0[1][s] + a.B[1] * a.lev[1][s];
-            T ry = a.B[0] * q0[2][s] + a.B[1] * a.lev[2][s];
-            if (a.order >= 2) {
-                rx += a.B[2] * a.lev1[1][s];
-                ry += a.B[2] * a.lev1[2][s];
+            T rx, ry;
+            if (reuse_now) {
+                rx = a.aux[2][s];
+                ry = a.aux[3][s];
+            } else {
+                rx = realtime_term(a, q0[1][s], 1, s, inv_dt);
+                ry = realtime_term(a, q0[2][s], 2, s, inv_dt);
             }
-            if (a.order >= 3) {
-                rx += a.B[3] * a.lev2[1][s];
-                ry += a.B[3] * a.lev2[2][s];
-            }
-            rx *= inv_dt;
-            ry *= inv_dt;
             if ((nfx + tfy) & 1) rx = -rx;
             if ((nfy + tfx) & 1) ry = -ry;
             sm.rt[0][k] = rx;
@@ -167,7 +180,11 @@ stage_kernel(const SweepArgs<T> a) {
     }
     __syncthreads();
 
-    // ---- 2. limited half slopes and pressure gradient on the ring ----
+    // ---- 2. limited slopes and pressure gradient on the ring ----
+    // Whole slopes (the limited difference across one cell, dx d_x rho and
+    // so on); the face states take half of each with one FMA.  Halving is
+    // exact, so these are the half slopes of the limiter's definition to
+    // the last bit, formed with fewer FP64 instructions.
     const T klim = T(a.limiter_k);
     const T kp = (a.gradp == kGradSuperbee || a.gradp == kGradSplitSuperbee) ? T(2) : T(1);
     for (int k = tid; k < GW * GH; k += NT) {
@@ -175,35 +192,35 @@ stage_kernel(const SweepArgs<T> a) {
         const int c = (lj + 1) * RW + (li + 1);
         const int e = c + 1, wv = c - 1, nn = c + RW, ss = c - RW;
         const T *R = sm.w[0], *U = sm.w[1], *V = sm.w[2], *P = sm.w[3];
-        T hrx, hry, hux, huy, hvx, hvy;
+        T srx, sry, sux, suy, svx, svy;
         if (a.limiter_k == 1) {
-            hrx = half_minmod(R[e] - R[c], R[c] - R[wv]);
-            hry = half_minmod(R[nn] - R[c], R[c] - R[ss]);
-            hux = half_minmod(U[e] - U[c], U[c] - U[wv]);
-            huy = half_minmod(U[nn] - U[c], U[c] - U[ss]);
-            hvx = half_minmod(V[e] - V[c], V[c] - V[wv]);
-            hvy = half_minmod(V[nn] - V[c], V[c] - V[ss]);
+            srx = minmod_bits(R[e] - R[c], R[c] - R[wv]);
+            sry = minmod_bits(R[nn] - R[c], R[c] - R[ss]);
+            sux = minmod_bits(U[e] - U[c], U[c] - U[wv]);
+            suy = minmod_bits(U[nn] - U[c], U[c] - U[ss]);
+            svx = minmod_bits(V[e] - V[c], V[c] - V[wv]);
+            svy = minmod_bits(V[nn] - V[c], V[c] - V[ss]);
         } else {
-            hrx = T(0.5) * limiter(R[e] - R[c], R[c] - R[wv], klim);
-            hry = T(0.5) * limiter(R[nn] - R[c], R[c] - R[ss], klim);
-            hux = T(0.5) * limiter(U[e] - U[c], U[c] - U[wv], klim);
-            huy = T(0.5) * limiter(U[nn] - U[c], U[c] - U[ss], klim);
-            hvx = T(0.5) * limiter(V[e] - V[c], V[c] - V[wv], klim);
-            hvy = T(0.5) * limiter(V[nn] - V[c], V[c] - V[ss], klim);
+            srx = limiter(R[e] - R[c], R[c] - R[wv], klim);
+            sry = limiter(R[nn] - R[c], R[c] - R[ss], klim);
+            sux = limiter(U[e] - U[c], U[c] - U[wv], klim);
+            suy = limiter(U[nn] - U[c], U[c] - U[ss], klim);
+            svx = limiter(V[e] - V[c], V[c] - V[wv], klim);
+            svy = limiter(V[nn] - V[c], V[c] - V[ss], klim);
         }
-        T hpx, hpy;
+        T spx, spy;
         if (a.gradp == kGradNew) {
-            // Eq. new_gradp times dx/2, with dx/2 * d_x rho = hrx etc.
+            // Eq. new_gradp times dx, with dx d_x rho = srx etc.
             const int gi = x0 + li - 1, gj = y0 + lj - 1;
             const T sg = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc);
             const T rho = R[c], u = U[c], v = V[c];
             const T rtx = need_rt ? sm.rt[0][k] : T(0);
             const T rty = need_rt ? sm.rt[1][k] : T(0);
             const T ru = rho * u, rv = rho * v, uv = u * v;
-            hpx = -a.half_dx * rtx - (u * u * hrx + T(2) * ru * hux) -
-                  a.dx_over_dy * (uv * hry + ru * hvy + rv * huy) + a.half_dx * rho * a.gx * sg;
-            hpy = -a.half_dy * rty - (v * v * hry + T(2) * rv * hvy) -
-                  a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * rho * a.gy * sg;
+            spx = -a.dx * rtx - (u * u * srx + T(2) * ru * sux) -
+                  a.dx_over_dy * (uv * sry + ru * svy + rv * suy) + a.dx * rho * a.gx * sg;
+            spy = -a.dy * rty - (v * v * sry + T(2) * rv * svy) -
+                  a.dy_over_dx * (uv * srx + rv * sux + ru * svx) + a.dy * rho * a.gy * sg;
         } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
             // Qian et al. split (Sec. 2.3.2): limit the kinematic part of the
             // one-sided pressure differences, add the cell's hydrostatic
@@ -211,16 +228,16 @@ stage_kernel(const SweepArgs<T> a) {
             const int gi = x0 + li - 1, gj = y0 + lj - 1;
             const T sg = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc);
             const T gxs = a.gx * sg, gys = a.gy * sg;
-            hpx = T(0.5) * limiter(P[e] - P[c] - a.half_dx * (R[c] + R[e]) * gxs,
-                                   P[c] - P[wv] - a.half_dx * (R[wv] + R[c]) * gxs, kp) + a.half_dx * R[c] * gxs;
-            hpy = T(0.5) * limiter(P[nn] - P[c] - a.half_dy * (R[c] + R[nn]) * gys,
-                                   P[c] - P[ss] - a.half_dy * (R[ss] + R[c]) * gys, kp) + a.half_dy * R[c] * gys;
+            spx = limiter(P[e] - P[c] - a.half_dx * (R[c] + R[e]) * gxs,
+                          P[c] - P[wv] - a.half_dx * (R[wv] + R[c]) * gxs, kp) + a.dx * R[c] * gxs;
+            spy = limiter(P[nn] - P[c] - a.half_dy * (R[c] + R[nn]) * gys,
+                          P[c] - P[ss] - a.half_dy * (R[ss] + R[c]) * gys, kp) + a.dy * R[c] * gys;
         } else {
-            hpx = T(0.5) * limiter(P[e] - P[c], P[c] - P[wv], kp);
-            hpy = T(0.5) * limiter(P[nn] - P[c], P[c] - P[ss], kp);
+            spx = limiter(P[e] - P[c], P[c] - P[wv], kp);
+            spy = limiter(P[nn] - P[c], P[c] - P[ss], kp);
         }
-        sm.gx[0][k] = hrx; sm.gx[1][k] = hux; sm.gx[2][k] = hvx; sm.gx[3][k] = hpx;
-        sm.gy[0][k] = hry; sm.gy[1][k] = huy; sm.gy[2][k] = hvy; sm.gy[3][k] = hpy;
+        sm.gx[0][k] = srx; sm.gx[1][k] = sux; sm.gx[2][k] = svx; sm.gx[3][k] = spx;
+        sm.gy[0][k] = sry; sm.gy[1][k] = suy; sm.gy[2][k] = svy; sm.gy[3][k] = spy;
     }
     __syncthreads();
 
@@ -251,25 +268,26 @@ stage_kernel(const SweepArgs<T> a) {
             const int fi = k % (TX + 1), fj = k / (TX + 1);  // face between cells fi-1 and fi
             const int ga = (fj + 1) * GW + fi, gb = ga + 1;
             const int ca = (fj + 2) * RW + fi + 1, cb = ca + 1;
-            rL = sm.w[0][ca] + sm.gx[0][ga]; rR = sm.w[0][cb] - sm.gx[0][gb];
-            nL = sm.w[1][ca] + sm.gx[1][ga]; nR = sm.w[1][cb] - sm.gx[1][gb];
-            tL = sm.w[2][ca] + sm.gx[2][ga]; tR = sm.w[2][cb] - sm.gx[2][gb];
-            pL = sm.w[3][ca] + sm.gx[3][ga]; pR = sm.w[3][cb] - sm.gx[3][gb];
+            rL = fma(T(0.5), sm.gx[0][ga], sm.w[0][ca]); rR = fma(T(-0.5), sm.gx[0][gb], sm.w[0][cb]);
+            nL = fma(T(0.5), sm.gx[1][ga], sm.w[1][ca]); nR = fma(T(-0.5), sm.gx[1][gb], sm.w[1][cb]);
+            tL = fma(T(0.5), sm.gx[2][ga], sm.w[2][ca]); tR = fma(T(-0.5), sm.gx[2][gb], sm.w[2][cb]);
+            pL = fma(T(0.5), sm.gx[3][ga], sm.w[3][ca]); pR = fma(T(-0.5), sm.gx[3][gb], sm.w[3][cb]);
             fo = k;
         } else {
             const int kk = k - S::NXF;
             const int fi = kk % TX, fj = kk / TX;            // face between cells fj-1 and fj
             const int ga = fj * GW + fi + 1, gb = ga + GW;
             const int ca = (fj + 1) * RW + fi + 2, cb = ca + RW;
-            rL = sm.w[0][ca] + sm.gy[0][ga]; rR = sm.w[0][cb] - sm.gy[0][gb];
-            tL = sm.w[1][ca] + sm.gy[1][ga]; tR = sm.w[1][cb] - sm.gy[1][gb];
-            nL = sm.w[2][ca] + sm.gy[2][ga]; nR = sm.w[2][cb] - sm.gy[2][gb];
-            pL = sm.w[3][ca] + sm.gy[3][ga]; pR = sm.w[3][cb] - sm.gy[3][gb];
+            rL = fma(T(0.5), sm.gy[0][ga], sm.w[0][ca]); rR = fma(T(-0.5), sm.gy[0][gb], sm.w[0][cb]);
+            tL = fma(T(0.5), sm.gy[1][ga], sm.w[1][ca]); tR = fma(T(-0.5), sm.gy[1][gb], sm.w[1][cb]);
+            nL = fma(T(0.5), sm.gy[2][ga], sm.w[2][ca]); nR = fma(T(-0.5), sm.gy[2][gb], sm.w[2][cb]);
+            pL = fma(T(0.5), sm.gy[3][ga], sm.w[3][ca]); pR = fma(T(-0.5), sm.gy[3][gb], sm.w[3][cb]);
             fo = kk;
         }
         // one flux call for both kinds: no divergence where a warp holds both
+        // (2F: the divergence below takes the 1/2)
         T F[4];
-        riemann_flux<RS, T>(rL, nL, tL, pL, rR, nR, tR, pR, a.beta, a.inv_beta, F);
+        riemann_flux<RS, T, true>(rL, nL, tL, pL, rR, nR, tR, pR, a.beta, a.inv_beta, F);
         T *fd = isx ? &sm.fx[0][fo] : &sm.fy[0][fo];
         const int fs = isx ? S::NXF : S::NYF;
         fd[0] = F[0];
@@ -288,30 +306,29 @@ stage_kernel(const SweepArgs<T> a) {
         const size_t g = (size_t)gj * nx + gi;
         const int fw = lj * (TX + 1) + li, fe = fw + 1;
         const int fs = lj * TX + li, fn = fs + TX;
+        // fluxes are stored doubled: (2Fe - 2Fw) (1/(2 dx)) is (Fe - Fw)/dx exactly
+        const T hidx = T(0.5) * a.inv_dx, hidy = T(0.5) * a.inv_dy;
         T div[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f)
-            div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * a.inv_dx + (sm.fy[f][fn] - sm.fy[f][fs]) * a.inv_dy;
+            div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * hidx + (sm.fy[f][fn] - sm.fy[f][fs]) * hidy;
         const T r0 = q0[0][g], m0 = q0[1][g], n0 = q0[2][g], p0 = q0[3][g];
         T rt0 = T(0), rt1 = T(0), rt2 = T(0);
         if (a.realtime) {
-            // Eq. bdf: (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} + B3 Q^{n-2}) / dt
-            rt0 = a.B[0] * r0 + a.B[1] * a.lev[0][g];
-            rt1 = a.B[0] * m0 + a.B[1] * a.lev[1][g];
-            rt2 = a.B[0] * n0 + a.B[1] * a.lev[2][g];
-            if (a.order >= 2) {
-                rt0 += a.B[2] * a.lev1[0][g];
-                rt1 += a.B[2] * a.lev1[1][g];
-                rt2 += a.B[2] * a.lev1[2][g];
+            if (reuse_now) {
+                rt0 = a.aux[1][g];
+                rt1 = a.aux[2][g];
+                rt2 = a.aux[3][g];
+            } else {
+                rt0 = realtime_term(a, r0, 0, g, inv_dt);
+                rt1 = realtime_term(a, m0, 1, g, inv_dt);
+                rt2 = realtime_term(a, n0, 2, g, inv_dt);
+                if (a.reuse) {
+                    a.aux[1][g] = rt0;
+                    a.aux[2][g] = rt1;
+                    a.aux[3][g] = rt2;
+                }
             }
-            if (a.order >= 3) {
-                rt0 += a.B[3] * a.lev2[0][g];
-                rt1 += a.B[3] * a.lev2[1][g];
-                rt2 += a.B[3] * a.lev2[2][g];
-            }
-            rt0 *= inv_dt;
-            rt1 *= inv_dt;
-            rt2 *= inv_dt;
         }
         const T b0 = -div[0] - rt0;
         const T b1 = -div[1] - rt1 + r0 * a.gx;
@@ -319,7 +336,9 @@ stage_kernel(const SweepArgs<T> a) {
         const T b3 = -div[3];
         // pseudo-time step from Q^{m} (Sec. 2.2.3)
         T dtau;
-        if (a.local_dtau) {
+        if (a.local_dtau && reuse_now) {
+            dtau = a.aux[0][g];
+        } else if (a.local_dtau) {
             const T ir = Ar<T>::rcp(r0);
             const T u = m0 * ir, v = n0 * ir, fb = T(4) * a.beta * ir;
             // square roots as x / sqrt(x) and quotients as products with a
@@ -329,6 +348,7 @@ stage_kernel(const SweepArgs<T> a) {
             Ar<T>::sqrt_rsqrt(v * v + fb, cy, unused);
             const T den = T(0.5) * (fabs(u) + cx) * a.dy + T(0.5) * (fabs(v) + cy) * a.dx;
             dtau = a.cfl_area * Ar<T>::rcp(den);
+            if (a.reuse) a.aux[0][g] = dtau;
         } else {
             dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
         }

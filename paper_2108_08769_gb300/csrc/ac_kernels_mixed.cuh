@@ -697,7 +697,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.rr, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
             // ---- east x-face of row r (between columns c and c + 1) ----
-            const float4 Wn = shfl_down4(Wm1, 1), Sn = shfl_down4(Sx, 1);
+            const float4 &Wn = We;
+            const float4 Sn = shfl_down4(Sx, 1);
             float jump = 0.0f;
             const int gi = c + 1;
             if (r >= 0 && r < ny && gi >= 0) {
