@@ -153,33 +153,21 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
 }
 
 // End of a pseudo-iteration for every tank (blockIdx.x = tank): its norms
-// from its own tiles' partial sums (fixed order), its stopping test and
-// buffer rotation; the last CTA sets the WHILE condition.
+// from its own tiles' partial sums (the fixed order of sum_partials_fixed,
+// as for a tank run alone), its stopping test and buffer rotation; the last
+// CTA sets the WHILE condition.
 template <int NT>
 __global__ void __launch_bounds__(NT)
 batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long long cond, int use_cond) {
-    __shared__ double red[4][NT];
+    static_assert(NT >= kEndLanes, "sum_partials_fixed needs kEndLanes threads");
     const int tid = threadIdx.x;
     pdl_trigger();
     pdl_wait();
     const BatchTank &t = tanks[blockIdx.x];
     Ctl *ctl = t.a.ctl;
     const bool was_done = ctl->done != 0;
-    if (!was_done) {
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int b = tid; b < t.ntiles; b += NT)
-#pragma unroll
-            for (int f = 0; f < 4; ++f) s[f] += t.a.partials[(size_t)b * 4 + f];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) red[f][tid] = s[f];
-        __syncthreads();
-        for (int w = NT / 2; w > 0; w >>= 1) {
-            if (tid < w)
-#pragma unroll
-                for (int f = 0; f < 4; ++f) red[f][tid] += red[f][tid + w];
-            __syncthreads();
-        }
-    }
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!was_done) sum_partials_fixed(t.a.partials, t.ntiles, sums);
     if (tid == 0) {
         int active = 0;
         if (!was_done) {
@@ -188,7 +176,7 @@ batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long lo
             ctl->iter = it;
             bool finite = true, conv = true;
             for (int f = 0; f < 4; ++f) {
-                const double R = sqrt(red[f][0] * inv_cells);
+                const double R = sqrt(sums[f] * inv_cells);
                 ctl->R[f] = R;
                 if (it == 1) ctl->R0[f] = R;
                 if (!isfinite(R)) finite = false;

@@ -34,7 +34,21 @@ struct Ctl {
     double R[4], R0[4];
     double abs_tol[4];
     unsigned long long dtau_bits;  // global pseudo-time step (bit pattern of a positive double)
+    int arrive;      // CTAs of the last stage that have finished (fused end of iteration)
 };
+
+// What the end of a pseudo-iteration needs (see end_iteration).  `fused` is
+// set only for the launch of the last stage when that stage's last CTA runs
+// it; every other launch gets a zeroed IterEnd.
+struct IterEnd {
+    int fused;
+    int nparts;                // residual partial slots written by stage 1
+    int s_max;
+    int use_cond;              // set the graph's while-condition
+    double inv_cells;
+    unsigned long long cond;   // its handle
+};
+constexpr int kEndLanes = 128;  // threads that take part in end_iteration
 
 template <typename T>
 struct SweepArgs {
@@ -83,6 +97,103 @@ __host__ __device__ __forceinline__ int final_buffer(int cur, int s_max) {
     return (s_max & 1) ? (cur + 1) % 3 : (cur + 2) % 3;
 }
 
+// Sum of the stage-1 residual partials (4 per slot, nparts slots) in a fixed
+// order: 128 strided sums, a shuffle tree in each of four warps, the four
+// warp sums left to right.  Called by every thread of a CTA of at least
+// kEndLanes threads; the sums are valid in thread 0.  The single-tank end of
+// iteration and the batch's per-tank end both use it, so a tank's norms do
+// not depend on which of them ran.
+__device__ __forceinline__ void sum_partials_fixed(const double *partials, int nparts, double out[4]) {
+    __shared__ double wsum[kEndLanes / 32][4];
+    const int tid = threadIdx.x;
+    if (tid < kEndLanes) {
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = tid; b < nparts; b += kEndLanes) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s[f] += partials[(size_t)b * 4 + f];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s[f] += __shfl_down_sync(0xffffffffu, s[f], o);
+        }
+        if ((tid & 31) == 0) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) wsum[tid >> 5][f] = s[f];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int f = 0; f < 4; ++f) {
+            double sum = wsum[0][f];
+            for (int w = 1; w < kEndLanes / 32; ++w) sum += wsum[w][f];
+            out[f] = sum;
+        }
+    }
+}
+
+// End of a pseudo-iteration: the residual norms from the stage-1 partials,
+// the stopping test (Alg. 1), the buffer rotation and, inside a captured
+// loop, the while-condition.  Called by every thread of one CTA of at least
+// kEndLanes threads.
+__device__ __forceinline__ void end_iteration(Ctl *ctl, const double *partials, const IterEnd &e) {
+    double sums[4];
+    sum_partials_fixed(partials, e.nparts, sums);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const int it = ctl->iter + 1;
+        ctl->iter = it;
+        bool finite = true, conv = true;
+        for (int f = 0; f < 4; ++f) {
+            const double R = sqrt(sums[f] * e.inv_cells);
+            ctl->R[f] = R;
+            if (it == 1) ctl->R0[f] = R;
+            if (!isfinite(R)) finite = false;
+            const double thr = fmax(ctl->tol * ctl->R0[f], ctl->abs_tol[f]);
+            if (!(R <= thr)) conv = false;
+        }
+        ctl->cur = final_buffer(ctl->cur, e.s_max);
+        int done = 0;
+        if (!finite) { ctl->status = -3; done = 1; }
+        else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
+        else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
+        ctl->done = done;
+        ctl->dtau_bits = 0x7ff0000000000000ull;
+        ctl->arrive = 0;
+        if (e.use_cond) cudaGraphSetConditional(e.cond, done ? 0u : 1u);
+    }
+}
+
+// A stage kernel that found the iteration already finished: its launch of
+// the last stage still ends the captured loop (one thread of the grid).
+static __device__ __noinline__ void end_skipped_call(const IterEnd e) { cudaGraphSetConditional(e.cond, 0); }
+__device__ __forceinline__ void end_skipped(const IterEnd &e) {
+    if (e.fused && e.use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) end_skipped_call(e);
+}
+
+// Tail of the last stage's kernel with the end of the iteration fused in:
+// every CTA counts itself on ctl->arrive after its writes; the CTA that
+// arrives last runs end_iteration.  No CTA waits for another (the count
+// only chooses which one does the work), and that CTA resets the count.
+// Every thread of every CTA that passed the entry test must call this.  It
+// stays out of line so that the stage sweep before it compiles the same
+// with or without it (the batch kernels, which have no such tail, compute a
+// tank bit for bit as the single-tank kernels do).
+static __device__ __noinline__ void fused_iteration_end_body(Ctl *ctl, const double *partials, const IterEnd e) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&ctl->arrive, 1) == (int)(gridDim.x * gridDim.y) - 1);
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        end_iteration(ctl, partials, e);
+    }
+}
+__device__ __forceinline__ void fused_iteration_end(Ctl *ctl, const double *partials, const IterEnd &e) {
+    if (e.fused) fused_iteration_end_body(ctl, partials, e);
+}
+
 template <typename T>
 __device__ __forceinline__ T wall_ghost_sign(int gi, int gj, int nx, int ny, const int bc[4]) {
     const bool w = (gi < 0 && is_wall(bc[0])) || (gi >= nx && is_wall(bc[1])) ||
@@ -112,9 +223,14 @@ struct StageSmem {
     double red[4][TX * TY / 32];
 };
 
+// Tiles of 448 cells are sized to run one per SM: they may take the whole
+// register file (ptxas otherwise budgets for two CTAs per SM and recomputes
+// products to stay inside it).  Other shapes keep the compiler's choice.
+constexpr int f64_min_blocks(int nt) { return nt >= 448 ? 1 : 0; }
+
 template <typename T, int TX, int TY, int RS = kOsher>
-__global__ void __launch_bounds__(TX * TY)
-stage_kernel(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(TX * TY, f64_min_blocks(TX * TY))
+stage_kernel(const SweepArgs<T> a, const IterEnd iend) {
     using S = StageSmem<T, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
@@ -123,8 +239,11 @@ stage_kernel(const SweepArgs<T> a) {
 
     pdl_trigger();
     pdl_wait();
-    const Ctl *ctl = a.ctl;
-    if (ctl->done) return;
+    Ctl *ctl = a.ctl;
+    if (ctl->done) {
+        end_skipped(iend);
+        return;
+    }
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, a.stage, in, out);
@@ -253,6 +372,7 @@ stage_kernel(const SweepArgs<T> a) {
     // against 8 here).
     constexpr int NF = S::NXF + S::NYF, NW = NT / 32, FP = (NF + 127) / 128;
     static_assert(NW >= 4, "face schedule needs four warps");
+    static_assert(NT >= kEndLanes, "the fused end of iteration needs kEndLanes threads");
     const int fw = tid >> 5, fgrp = fw & 3;
     const int fwarps = (NW - fgrp + 3) >> 2;
     const int fbeg = fgrp * 32 * FP, fend = min(NF, fbeg + 32 * FP);
@@ -383,6 +503,7 @@ stage_kernel(const SweepArgs<T> a) {
             a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = s;
         }
     }
+    fused_iteration_end(ctl, a.partials, iend);
 }
 
 // Global pseudo-time step option: min over cells of the local step
@@ -455,60 +576,21 @@ __global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, i
         ctl->dt = dt;
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;  // +inf
+        ctl->arrive = 0;
     }
 }
 
-// End of a pseudo-iteration: residual norms from the stage-1 partials (fixed
-// summation order), the stopping test (Alg. 1), and the buffer rotation.
-// Sets the graph's while-condition when launched inside a captured loop.
-template <int NT>
-__global__ void __launch_bounds__(NT)
-end_iteration_kernel(Ctl *ctl, const double *partials, int nblocks, double inv_cells, int s_max,
-                     unsigned long long cond_handle, int use_cond) {
-    __shared__ double red[4][NT];
-    const int tid = threadIdx.x;
+// End of a pseudo-iteration as a kernel of its own (kEndLanes threads, one
+// CTA): used where the stages are timed one by one.
+static __global__ void __launch_bounds__(kEndLanes)
+end_iteration_kernel(Ctl *ctl, const double *partials, const IterEnd e) {
     pdl_trigger();
     pdl_wait();
     if (ctl->done) {
-        if (use_cond && tid == 0) cudaGraphSetConditional(cond_handle, 0);
+        if (e.use_cond && threadIdx.x == 0) cudaGraphSetConditional(e.cond, 0);
         return;
     }
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblocks; b += NT) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) s[f] += partials[(size_t)b * 4 + f];
-    }
-#pragma unroll
-    for (int f = 0; f < 4; ++f) red[f][tid] = s[f];
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if (tid < w) {
-#pragma unroll
-            for (int f = 0; f < 4; ++f) red[f][tid] += red[f][tid + w];
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        const int it = ctl->iter + 1;
-        ctl->iter = it;
-        bool finite = true, conv = true;
-        for (int f = 0; f < 4; ++f) {
-            const double R = sqrt(red[f][0] * inv_cells);
-            ctl->R[f] = R;
-            if (it == 1) ctl->R0[f] = R;
-            if (!isfinite(R)) finite = false;
-            const double thr = fmax(ctl->tol * ctl->R0[f], ctl->abs_tol[f]);
-            if (!(R <= thr)) conv = false;
-        }
-        ctl->cur = final_buffer(ctl->cur, s_max);
-        int done = 0;
-        if (!finite) { ctl->status = -3; done = 1; }
-        else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
-        else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
-        ctl->done = done;
-        ctl->dtau_bits = 0x7ff0000000000000ull;
-        if (use_cond) cudaGraphSetConditional(cond_handle, done ? 0u : 1u);
-    }
+    end_iteration(ctl, partials, e);
 }
 
 }  // namespace acgb
