@@ -460,16 +460,21 @@ def run_batched(args, stream, flush, barrier):
 
 # FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
 # counted by ncu on stage_kernel<double,32,14> on this 256x256 tank
-# (profiles/stage_kernel_f64_hydrostatic_256.md), and the FP64 instructions
-# (DFMA + DADD + DMUL) behind them
-FP64_FLOPS_PER_CELL_STAGE = 755.5
-FP64_INSTR_PER_CELL_STAGE = 533.0
+# (profiles/stage_kernel_f64_hydrostatic_256.md), averaged over the three
+# stages of a pseudo-iteration (stage 1 also forms the local dtau and the
+# real-time terms that stages 2 and 3 read back: 771.3, 669.3, 669.3), and
+# the FP64 instructions (DFMA + DADD + DMUL) behind them (542.3, 466.8, 466.8)
+FP64_FLOPS_PER_CELL_STAGE = 703.4
+FP64_INSTR_PER_CELL_STAGE = 492.0
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
-# DRAM bytes per cell of one FP64 stage launch, same capture (5.83 MB read,
-# the output stays in L2)
-FP64_TRAFFIC_PER_CELL_STAGE = 89.0
-# algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3)
-BYTES_PER_CELL_ITER_F64 = 328.0
+# DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
+# the three stages (3.74, 6.36, 6.36 MB read; the output stays in L2)
+FP64_TRAFFIC_PER_CELL_STAGE = 83.7
+# algorithmic HBM bytes per cell-iteration of the FP64 sweep (s_max = 3):
+# stage 1 reads Q^{m} (32 B) and Q^n (24 B), writes Q^1 (32 B) and the four
+# per-cell values kept for the later stages (32 B); stages 2 and 3 read
+# Q^{s-1}, Q^{m} and those values and write Q^s (4 x 32 B each)
+BYTES_PER_CELL_ITER_F64 = 376.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
@@ -478,7 +483,7 @@ MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
 # DRAM bytes and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2
 # forms counted as two) per cell of one stage launch
 MIXED_TRAFFIC_PER_CELL_STAGE = 68.0
-MIXED_FP32_OPS_PER_CELL_STAGE = 492.3
+MIXED_FP32_OPS_PER_CELL_STAGE = 473.2
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 

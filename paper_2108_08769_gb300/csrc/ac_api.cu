@@ -5,11 +5,9 @@
 //   begin-step kernel            Q^n <- Q, control block reset
 //   graph: WHILE (not done) {    one pseudo-iteration per body execution
 //     [global dtau kernel]       global pseudo-time step option
-//     stage sweep  x s_max       fused stage sweeps (Eq. RK2); the last CTA of
-//                                the last stage runs the end of the iteration:
-//                                norms, stopping test, buffer rotation, and
+//     stage sweep  x s_max       fused stage sweeps (Eq. RK2)
+//     end_iteration_kernel       norms, stopping test, buffer rotation;
 //   }                            sets the WHILE condition on the device
-//   (timed stages: the end of the iteration is end_iteration_kernel instead)
 //   one device->host read of the control block.
 // The loop runs without host round trips; the host waits once per step.
 //
@@ -117,27 +115,11 @@ struct ac_ctx {
     int nhist;            // older real-time levels held (0..2) before the next step
     int order_now;        // backward-difference order of the current step
     int graph_order;      // order the captured graph was built for
-    IterEnd end_now;      // end of iteration fused into the next last-stage launch (fused = 1), else zero
 };
 
 namespace {
 
 int grid_stride_blocks(size_t N) { return (int)std::min<size_t>((N + 255) / 256, kGridStrideBlocks); }
-
-// The end of iteration that a launch of stage st carries: only the launch of
-// the last stage that enqueue_iteration marks, never a tuner's launch.
-IterEnd stage_end(const ac_ctx *c, int st) {
-    return (c->end_now.fused && st == c->opt.rk_stages) ? c->end_now : IterEnd{};
-}
-
-// AC_FUSE_END=0 keeps the end of iteration as a kernel of its own.
-bool fuse_end_enabled() {
-    static const bool on = [] {
-        const char *e = getenv("AC_FUSE_END");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
 
 struct Backend {
     dim3 grid;        // stage-sweep grid of the chosen tile shape
@@ -187,9 +169,9 @@ cudaError_t allow_f64_smem() {
 }
 
 template <int TX, int TY, int RS = kOsher>
-cudaError_t launch_f64(const SweepArgs<double> &a, const IterEnd &e, dim3 g, bool pdl, cudaStream_t s) {
+cudaError_t launch_f64(const SweepArgs<double> &a, dim3 g, bool pdl, cudaStream_t s) {
     return launch_pdl(pdl, stage_kernel<double, TX, TY, RS>, g, dim3(TX * TY), sizeof(StageSmem<double, TX, TY>), s,
-                      a, e);
+                      a);
 }
 
 std::vector<std::pair<std::pair<int, int>, int>> g_tuned_f64;
@@ -218,22 +200,21 @@ struct F64Backend : Backend {
 
     int launch(const ac_ctx *c, cudaStream_t s, int st, int v) const {
         const SweepArgs<double> a = args(c, st);
-        const IterEnd ie = stage_end(c, st);
         const F64Variant &m = kF64Variants[v];
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
         cudaError_t e;
         // the Bassi and Roe fluxes are compiled for the first tile shape only
-        if (c->opt.riemann == AC_RIEMANN_BASSI) e = launch_f64<32, 8, kBassi>(a, ie, g, c->pdl, s);
-        else if (c->opt.riemann == AC_RIEMANN_ROE) e = launch_f64<32, 8, kRoe>(a, ie, g, c->pdl, s);
+        if (c->opt.riemann == AC_RIEMANN_BASSI) e = launch_f64<32, 8, kBassi>(a, g, c->pdl, s);
+        else if (c->opt.riemann == AC_RIEMANN_ROE) e = launch_f64<32, 8, kRoe>(a, g, c->pdl, s);
         else switch (v) {
-            case 0: e = launch_f64<32, 8>(a, ie, g, c->pdl, s); break;
-            case 1: e = launch_f64<32, 7>(a, ie, g, c->pdl, s); break;
-            case 2: e = launch_f64<32, 6>(a, ie, g, c->pdl, s); break;
-            case 3: e = launch_f64<32, 4>(a, ie, g, c->pdl, s); break;
-            case 4: e = launch_f64<16, 8>(a, ie, g, c->pdl, s); break;
-            case 5: e = launch_f64<16, 16>(a, ie, g, c->pdl, s); break;
-            case 6: e = launch_f64<32, 14>(a, ie, g, c->pdl, s); break;
-            default: e = launch_f64<64, 7>(a, ie, g, c->pdl, s); break;
+            case 0: e = launch_f64<32, 8>(a, g, c->pdl, s); break;
+            case 1: e = launch_f64<32, 7>(a, g, c->pdl, s); break;
+            case 2: e = launch_f64<32, 6>(a, g, c->pdl, s); break;
+            case 3: e = launch_f64<32, 4>(a, g, c->pdl, s); break;
+            case 4: e = launch_f64<16, 8>(a, g, c->pdl, s); break;
+            case 5: e = launch_f64<16, 16>(a, g, c->pdl, s); break;
+            case 6: e = launch_f64<32, 14>(a, g, c->pdl, s); break;
+            default: e = launch_f64<64, 7>(a, g, c->pdl, s); break;
         }
         if (e != cudaSuccess) return fail(AC_ERR_CUDA, "stage sweep launch failed: %s", cudaGetErrorString(e));
         return AC_OK;
@@ -426,17 +407,17 @@ constexpr MixedVariant kMixedVariants[] = {
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
 template <int TX, int TY, int NT, int MINB, int RS = kOsher, bool BDF = false, bool PF = false>
-int launch_mixed(const MixedArgs &a, const IterEnd &ie, dim3 g, bool pdl, cudaStream_t s) {
+int launch_mixed(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
     const cudaError_t e = launch_pdl(pdl, stage_kernel_mixed<TX, TY, NT, MINB, RS, BDF, PF>, g, dim3(NT),
-                                     sizeof(MixedSmem<TX, TY>), s, a, ie);
+                                     sizeof(MixedSmem<TX, TY>), s, a);
     return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
 template <int H, int WPC, int MINB>
-int launch_sweep(const MixedArgs &a, const IterEnd &ie, dim3 g, bool pdl, cudaStream_t s) {
+int launch_sweep(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
     const int nstrips = (int)(g.x * g.y);
     const cudaError_t e = launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB>, dim3((nstrips + WPC - 1) / WPC),
-                                     dim3(WPC * 32), 0, s, a, (int)g.x, nstrips, ie);
+                                     dim3(WPC * 32), 0, s, a, (int)g.x, nstrips);
     return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
@@ -479,35 +460,34 @@ struct MixedBackend : Backend {
 
     int launch(const ac_ctx *c, cudaStream_t s, int st, int v) const {
         const MixedArgs a = args(c, st);
-        const IterEnd ie = stage_end(c, st);
         const MixedVariant &m = kMixedVariants[v];
         const dim3 g((c->grid.nx + m.tx - 1) / m.tx, (c->grid.ny + m.ty - 1) / m.ty);
         // the Bassi and Roe fluxes are compiled for the first tile shape only
         const bool bdf = c->opt.bdf_order > 1;
-        if (c->opt.riemann == AC_RIEMANN_BASSI) return launch_mixed<32, 8, 256, 6, kBassi, true>(a, ie, g, c->pdl, s);
-        if (c->opt.riemann == AC_RIEMANN_ROE) return launch_mixed<32, 8, 256, 6, kRoe, true>(a, ie, g, c->pdl, s);
-        if (bdf) return launch_mixed<32, 8, 256, 6, kOsher, true>(a, ie, g, c->pdl, s);
+        if (c->opt.riemann == AC_RIEMANN_BASSI) return launch_mixed<32, 8, 256, 6, kBassi, true>(a, g, c->pdl, s);
+        if (c->opt.riemann == AC_RIEMANN_ROE) return launch_mixed<32, 8, 256, 6, kRoe, true>(a, g, c->pdl, s);
+        if (bdf) return launch_mixed<32, 8, 256, 6, kOsher, true>(a, g, c->pdl, s);
         switch (v) {
-            case 0: return launch_mixed<32, 8, 256, 6>(a, ie, g, c->pdl, s);
-            case 1: return launch_mixed<32, 16, 256, 6>(a, ie, g, c->pdl, s);
-            case 2: return launch_mixed<32, 16, 512, 3>(a, ie, g, c->pdl, s);
-            case 3: return launch_mixed<64, 8, 256, 6>(a, ie, g, c->pdl, s);
-            case 4: return launch_mixed<64, 8, 512, 3>(a, ie, g, c->pdl, s);
-            case 5: return launch_mixed<64, 16, 512, 3>(a, ie, g, c->pdl, s);
-            case 6: return launch_mixed<16, 16, 256, 6>(a, ie, g, c->pdl, s);
-            case 7: return launch_mixed<16, 16, 256, 7>(a, ie, g, c->pdl, s);
-            case 8: return launch_mixed<32, 8, 256, 7>(a, ie, g, c->pdl, s);
-            case 9: return launch_mixed<32, 16, 512, 1>(a, ie, g, c->pdl, s);
-            case 10: return launch_mixed<32, 8, 256, 6, kOsher, false, true>(a, ie, g, c->pdl, s);
-            case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, ie, g, c->pdl, s);
-            case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, ie, g, c->pdl, s);
-            case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, ie, g, c->pdl, s);
-            case 14: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, ie, g, c->pdl, s);
-            case 15: return launch_sweep<32, 4, 4>(a, ie, g, c->pdl, s);
-            case 16: return launch_sweep<64, 4, 4>(a, ie, g, c->pdl, s);
-            case 17: return launch_sweep<128, 4, 4>(a, ie, g, c->pdl, s);
-            case 18: return launch_sweep<256, 4, 4>(a, ie, g, c->pdl, s);
-            default: return launch_sweep<64, 8, 2>(a, ie, g, c->pdl, s);
+            case 0: return launch_mixed<32, 8, 256, 6>(a, g, c->pdl, s);
+            case 1: return launch_mixed<32, 16, 256, 6>(a, g, c->pdl, s);
+            case 2: return launch_mixed<32, 16, 512, 3>(a, g, c->pdl, s);
+            case 3: return launch_mixed<64, 8, 256, 6>(a, g, c->pdl, s);
+            case 4: return launch_mixed<64, 8, 512, 3>(a, g, c->pdl, s);
+            case 5: return launch_mixed<64, 16, 512, 3>(a, g, c->pdl, s);
+            case 6: return launch_mixed<16, 16, 256, 6>(a, g, c->pdl, s);
+            case 7: return launch_mixed<16, 16, 256, 7>(a, g, c->pdl, s);
+            case 8: return launch_mixed<32, 8, 256, 7>(a, g, c->pdl, s);
+            case 9: return launch_mixed<32, 16, 512, 1>(a, g, c->pdl, s);
+            case 10: return launch_mixed<32, 8, 256, 6, kOsher, false, true>(a, g, c->pdl, s);
+            case 11: return launch_mixed<16, 16, 256, 6, kOsher, false, true>(a, g, c->pdl, s);
+            case 12: return launch_mixed<32, 16, 512, 3, kOsher, false, true>(a, g, c->pdl, s);
+            case 13: return launch_mixed<32, 8, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
+            case 14: return launch_mixed<16, 16, 256, 5, kOsher, false, true>(a, g, c->pdl, s);
+            case 15: return launch_sweep<32, 4, 4>(a, g, c->pdl, s);
+            case 16: return launch_sweep<64, 4, 4>(a, g, c->pdl, s);
+            case 17: return launch_sweep<128, 4, 4>(a, g, c->pdl, s);
+            case 18: return launch_sweep<256, 4, 4>(a, g, c->pdl, s);
+            default: return launch_sweep<64, 8, 2>(a, g, c->pdl, s);
         }
     }
 
@@ -760,11 +740,8 @@ struct MixedBackend : Backend {
 
 // Enqueue one pseudo-iteration on stream s (events around the stage sweeps
 // when `timed`).
-// The end of the iteration (norms, stopping test, rotation) runs in the last
-// CTA of the last stage sweep, except when the stages are timed one by one.
 int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false) {
     int rc;
-    const bool fuse = !timed && fuse_end_enabled();
     IterEnd e{};
     e.nparts = c->be->nblocks;
     e.s_max = c->opt.rk_stages;
@@ -774,24 +751,14 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
     if (!c->opt.local_dtau && (rc = c->be->dtau_min(c, s)) != AC_OK) return rc;
     if (timed) CK(cudaEventRecord(c->ev[0], s));
     for (int st = 1; st <= c->opt.rk_stages; ++st) {
-        if (fuse && st == c->opt.rk_stages) {
-            c->end_now = e;
-            c->end_now.fused = 1;
-        }
-        rc = c->be->stage(c, s, st);
-        c->end_now = IterEnd{};
-        if (rc != AC_OK) return rc;
+        if ((rc = c->be->stage(c, s, st)) != AC_OK) return rc;
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
-    if (!fuse)
-        CK(launch_pdl(c->pdl, end_iteration_kernel, dim3(1), dim3(kEndLanes), 0, s, c->ctl, c->partials, e));
+    CK(launch_pdl(c->pdl, end_iteration_kernel, dim3(1), dim3(kEndLanes), 0, s, c->ctl, c->partials, e));
     return AC_OK;
 }
 
-int kernels_per_iteration(const ac_ctx *c, bool timed = false) {
-    const bool fuse = !timed && fuse_end_enabled();
-    return c->opt.rk_stages + (fuse ? 0 : 1) + (c->opt.local_dtau ? 0 : 1);
-}
+int kernels_per_iteration(const ac_ctx *c) { return c->opt.rk_stages + 1 + (c->opt.local_dtau ? 0 : 1); }
 
 int build_graph(ac_ctx *c) {
     if (c->exec && c->graph_order == c->order_now) return AC_OK;
@@ -1030,7 +997,7 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
                 c->stage_ms += ms;
             }
             c->stage_launches += c->opt.rk_stages;
-            c->launches += kernels_per_iteration(c, true);
+            c->launches += kernels_per_iteration(c);
             if (c->hctl->done) break;
         }
     } else if (use_host_loop()) {

@@ -34,14 +34,10 @@ struct Ctl {
     double R[4], R0[4];
     double abs_tol[4];
     unsigned long long dtau_bits;  // global pseudo-time step (bit pattern of a positive double)
-    int arrive;      // CTAs of the last stage that have finished (fused end of iteration)
 };
 
-// What the end of a pseudo-iteration needs (see end_iteration).  `fused` is
-// set only for the launch of the last stage when that stage's last CTA runs
-// it; every other launch gets a zeroed IterEnd.
+// What the end of a pseudo-iteration needs (see end_iteration).
 struct IterEnd {
-    int fused;
     int nparts;                // residual partial slots written by stage 1
     int s_max;
     int use_cond;              // set the graph's while-condition
@@ -159,39 +155,8 @@ __device__ __forceinline__ void end_iteration(Ctl *ctl, const double *partials, 
         else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
         ctl->done = done;
         ctl->dtau_bits = 0x7ff0000000000000ull;
-        ctl->arrive = 0;
         if (e.use_cond) cudaGraphSetConditional(e.cond, done ? 0u : 1u);
     }
-}
-
-// A stage kernel that found the iteration already finished: its launch of
-// the last stage still ends the captured loop (one thread of the grid).
-static __device__ __noinline__ void end_skipped_call(const IterEnd e) { cudaGraphSetConditional(e.cond, 0); }
-__device__ __forceinline__ void end_skipped(const IterEnd &e) {
-    if (e.fused && e.use_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) end_skipped_call(e);
-}
-
-// Tail of the last stage's kernel with the end of the iteration fused in:
-// every CTA counts itself on ctl->arrive after its writes; the CTA that
-// arrives last runs end_iteration.  No CTA waits for another (the count
-// only chooses which one does the work), and that CTA resets the count.
-// Every thread of every CTA that passed the entry test must call this.  It
-// stays out of line so that the stage sweep before it compiles the same
-// with or without it (the batch kernels, which have no such tail, compute a
-// tank bit for bit as the single-tank kernels do).
-static __device__ __noinline__ void fused_iteration_end_body(Ctl *ctl, const double *partials, const IterEnd e) {
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(&ctl->arrive, 1) == (int)(gridDim.x * gridDim.y) - 1);
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        end_iteration(ctl, partials, e);
-    }
-}
-__device__ __forceinline__ void fused_iteration_end(Ctl *ctl, const double *partials, const IterEnd &e) {
-    if (e.fused) fused_iteration_end_body(ctl, partials, e);
 }
 
 template <typename T>
@@ -230,7 +195,7 @@ constexpr int f64_min_blocks(int nt) { return nt >= 448 ? 1 : 0; }
 
 template <typename T, int TX, int TY, int RS = kOsher>
 __global__ void __launch_bounds__(TX * TY, f64_min_blocks(TX * TY))
-stage_kernel(const SweepArgs<T> a, const IterEnd iend) {
+stage_kernel(const SweepArgs<T> a) {
     using S = StageSmem<T, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
@@ -239,11 +204,8 @@ stage_kernel(const SweepArgs<T> a, const IterEnd iend) {
 
     pdl_trigger();
     pdl_wait();
-    Ctl *ctl = a.ctl;
-    if (ctl->done) {
-        end_skipped(iend);
-        return;
-    }
+    const Ctl *ctl = a.ctl;
+    if (ctl->done) return;
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, a.stage, in, out);
@@ -372,7 +334,6 @@ stage_kernel(const SweepArgs<T> a, const IterEnd iend) {
     // against 8 here).
     constexpr int NF = S::NXF + S::NYF, NW = NT / 32, FP = (NF + 127) / 128;
     static_assert(NW >= 4, "face schedule needs four warps");
-    static_assert(NT >= kEndLanes, "the fused end of iteration needs kEndLanes threads");
     const int fw = tid >> 5, fgrp = fw & 3;
     const int fwarps = (NW - fgrp + 3) >> 2;
     const int fbeg = fgrp * 32 * FP, fend = min(NF, fbeg + 32 * FP);
@@ -503,7 +464,6 @@ stage_kernel(const SweepArgs<T> a, const IterEnd iend) {
             a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = s;
         }
     }
-    fused_iteration_end(ctl, a.partials, iend);
 }
 
 // Global pseudo-time step option: min over cells of the local step
@@ -576,12 +536,11 @@ __global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, i
         ctl->dt = dt;
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;  // +inf
-        ctl->arrive = 0;
     }
 }
 
-// End of a pseudo-iteration as a kernel of its own (kEndLanes threads, one
-// CTA): used where the stages are timed one by one.
+// End of a pseudo-iteration (kEndLanes threads, one CTA).  Sets the graph's
+// while-condition when launched inside a captured loop.
 static __global__ void __launch_bounds__(kEndLanes)
 end_iteration_kernel(Ctl *ctl, const double *partials, const IterEnd e) {
     pdl_trigger();

@@ -550,18 +550,13 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
 
 template <int TX, int TY, int NT, int MINB = 1, int RS = kOsher, bool BDF = false, bool PF = false>
 __global__ void __launch_bounds__(NT, MINB)
-stage_kernel_mixed(const MixedArgs a, const IterEnd iend) {
-    static_assert(NT >= kEndLanes, "the fused end of iteration needs kEndLanes threads");
+stage_kernel_mixed(const MixedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_trigger();
     pdl_wait();
-    if (a.ctl->done) {
-        end_skipped(iend);
-        return;
-    }
+    if (a.ctl->done) return;
     mixed_tile<TX, TY, NT, RS, BDF, PF>(a, a.stage, a.alpha, blockIdx.x, blockIdx.y,
                            a.partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4, smem_raw);
-    fused_iteration_end(a.ctl, a.partials, iend);
 }
 
 // ---------------------------------------------------------------------------
@@ -762,20 +757,14 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
 
 template <int H, int WPC, int MINB>
 __global__ void __launch_bounds__(WPC * 32, MINB)
-sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips, const IterEnd iend) {
-    static_assert(WPC * 32 >= kEndLanes, "the fused end of iteration needs kEndLanes threads");
+sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     pdl_trigger();
     pdl_wait();
-    if (a.ctl->done) {
-        end_skipped(iend);
-        return;
-    }
+    if (a.ctl->done) return;
     const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
-    if (warp < nstrips) {   // whole warps
-        const int sy = warp / strips_x, sx = warp - sy * strips_x;
-        mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4);
-    }
-    fused_iteration_end(a.ctl, a.partials, iend);
+    if (warp >= nstrips) return;   // whole warps only
+    const int sy = warp / strips_x, sx = warp - sy * strips_x;
+    mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4);
 }
 
 // Global pseudo-time step option for the mixed form.
@@ -850,7 +839,6 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
         ctl->dt = dt;
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;
-        ctl->arrive = 0;
     }
 }
 

@@ -184,10 +184,9 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(AC_ERR_CUDA, "dtau launch: %s", cudaGetErrorString(e));
     }
     const size_t smem = sizeof(StageSmem<double, kTX, kTY>);
-    const IterEnd no_end{};   // a single stage: no end of iteration here
-    if (opt->riemann == AC_RIEMANN_BASSI) stage_kernel<double, kTX, kTY, kBassi><<<g, kTX * kTY, smem, s>>>(a, no_end);
-    else if (opt->riemann == AC_RIEMANN_ROE) stage_kernel<double, kTX, kTY, kRoe><<<g, kTX * kTY, smem, s>>>(a, no_end);
-    else stage_kernel<double, kTX, kTY, kOsher><<<g, kTX * kTY, smem, s>>>(a, no_end);
+    if (opt->riemann == AC_RIEMANN_BASSI) stage_kernel<double, kTX, kTY, kBassi><<<g, kTX * kTY, smem, s>>>(a);
+    else if (opt->riemann == AC_RIEMANN_ROE) stage_kernel<double, kTX, kTY, kRoe><<<g, kTX * kTY, smem, s>>>(a);
+    else stage_kernel<double, kTX, kTY, kOsher><<<g, kTX * kTY, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(AC_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(e));
     if (stage == 1 && norms) {
         noalloc_norms_kernel<<<1, 256, 0, s>>>(partials, (int)tiles, 1.0 / ((double)grid->nx * grid->ny), norms);

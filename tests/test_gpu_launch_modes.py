@@ -1,12 +1,10 @@
 """The launch mode does not change a number.
 
 A physical step runs as one graph launch (device-driven WHILE loop, kernels
-with programmatic dependencies, the end of each iteration in the last CTA of
-the last stage), as a host-driven loop (AC_LAUNCH=host), with plain launches
-(AC_PDL=0), with the end of each iteration as a kernel of its own
-(AC_FUSE_END=0), or one iteration at a time with per-stage events
-(profiling).  All give bit-identical states, iteration counts and residual
-norms, in both precisions and for the batch.
+with programmatic dependencies), as a host-driven loop (AC_LAUNCH=host), with
+plain launches (AC_PDL=0), or one iteration at a time with per-stage events
+(profiling).  All four give bit-identical states, iteration counts and
+residual norms, in both precisions and for the batch.
 """
 import json
 import os
@@ -60,8 +58,7 @@ def run_child(tmp_path, name, env_extra):
 
 def test_graph_host_loop_and_plain_launches_agree(tmp_path):
     base = run_child(tmp_path, "graph", {})
-    for name, extra in [("host", {"AC_LAUNCH": "host"}), ("nopdl", {"AC_PDL": "0"}),
-                        ("sepend", {"AC_FUSE_END": "0"}), ("host_sepend", {"AC_LAUNCH": "host", "AC_FUSE_END": "0"})]:
+    for name, extra in [("host", {"AC_LAUNCH": "host"}), ("nopdl", {"AC_PDL": "0"})]:
         other = run_child(tmp_path, name, extra)
         assert other == base, name
 

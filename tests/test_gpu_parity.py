@@ -222,11 +222,10 @@ def test_runs_on_a_torch_stream():
     got = t.get_state()
     ref, *_ = oracle.physical_step(case, case.state(), tol=-1.0, max_iters=4)
     assert max(rel_errors(got, ref)) <= TOL
-    # a step of 4 pseudo-iterations: 1 begin kernel + 4 x 3 stage sweeps (the
-    # last stage's last CTA ends each iteration)
+    # a step of 4 pseudo-iterations: 1 begin kernel + 4 x (3 stage sweeps + 1 end kernel)
     n0 = t.kernel_launches()
     t.physical_step(case.dt, -1.0, 4)
-    assert t.kernel_launches() - n0 == 1 + 4 * 3
+    assert t.kernel_launches() - n0 == 1 + 4 * 4
     t.close()
 
 
