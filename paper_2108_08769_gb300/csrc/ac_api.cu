@@ -403,6 +403,8 @@ constexpr MixedVariant kMixedVariants[] = {
     // 4 CTAs per SM (127 registers, no spills; tighter hints spill and lose)
     {28, 32, 128, 4, false, true}, {28, 64, 128, 4, false, true}, {28, 128, 128, 4, false, true},
     {28, 256, 128, 4, false, true}, {28, 64, 256, 2, false, true},
+    // one 448-cell tile per SM on a 256x256 grid (a single wave of CTAs), with and without prefetching
+    {32, 14, 448, 1, true}, {32, 14, 448, 1},
 };
 constexpr int kNumMixedVariants = sizeof(kMixedVariants) / sizeof(kMixedVariants[0]);
 
@@ -487,7 +489,9 @@ struct MixedBackend : Backend {
             case 16: return launch_sweep<64, 4, 4>(a, g, c->pdl, s);
             case 17: return launch_sweep<128, 4, 4>(a, g, c->pdl, s);
             case 18: return launch_sweep<256, 4, 4>(a, g, c->pdl, s);
-            default: return launch_sweep<64, 8, 2>(a, g, c->pdl, s);
+            case 19: return launch_sweep<64, 8, 2>(a, g, c->pdl, s);
+            case 20: return launch_mixed<32, 14, 448, 1, kOsher, false, true>(a, g, c->pdl, s);
+            default: return launch_mixed<32, 14, 448, 1>(a, g, c->pdl, s);
         }
     }
 
@@ -605,6 +609,8 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<32, 16, 512, 3, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 8, 256, 5, kOsher, false, true>()));
         CK((allow_mixed_smem<16, 16, 256, 5, kOsher, false, true>()));
+        CK((allow_mixed_smem<32, 14, 448, 1, kOsher, false, true>()));
+        CK((allow_mixed_smem<32, 14, 448, 1>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));

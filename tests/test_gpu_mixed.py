@@ -173,7 +173,7 @@ def test_bdf_levels_against_oracle(order):
     t.close()
 
 
-N_MIXED_VARIANTS = 20
+N_MIXED_VARIANTS = 22
 
 
 @pytest.mark.parametrize("v", range(N_MIXED_VARIANTS))
