@@ -633,8 +633,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     struct Raw {
         float q0, q1, q2, d0, d1, d2, d3;   // Q^n and dQ^{s-1} (+ p')
         float e1, e2, rr;                   // ring terms: dQ^{m} of rho u, rho v; rho_ref
+        float jump;                         // reference jump across the east x-face (0 off the tank's rows)
         int fl;                             // fold bits
     };
+    const int gi = c + 1;   // the east x-face's column
     auto load_raw = [&](int k, Raw &R, int &srow) {
         int nfy, tfy;
         srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
@@ -644,6 +646,11 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         R.e1 = need_rt ? d0[1][s] : 0.0f;
         R.e2 = need_rt ? d0[2][s] : 0.0f;
         R.rr = __ldg(a.rho_ref + s);
+        R.jump = 0.0f;
+        if (k >= 0 && k < ny && gi >= 0) {
+            if (gi < nx) R.jump = __ldg(a.dref + k * nx + gi);
+            else if (gi == nx && per_x) R.jump = __ldg(a.dref + k * nx);
+        }
         R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
     };
     auto load_upd = [&](int row, HeldSrc &U) {
@@ -699,12 +706,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             // ---- east x-face of row r (between columns c and c + 1) ----
             const float4 &Wn = We;
             const float4 Sn = shfl_down4(Sx, 1);
-            float jump = 0.0f;
-            const int gi = c + 1;
-            if (r >= 0 && r < ny && gi >= 0) {
-                if (gi < nx) jump = __ldg(a.dref + r * nx + gi);
-                else if (gi == nx && per_x) jump = __ldg(a.dref + r * nx);
-            }
+            const float jump = Rm1.jump;
             // ---- and the y-face between rows r - 1 and r (not needed, but
             // harmless, on the first row): both fluxes as one packed pair ----
             FaceStates f, fy;
