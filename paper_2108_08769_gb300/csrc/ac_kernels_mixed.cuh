@@ -606,7 +606,17 @@ struct HeldSrc {
 // One strip (strip coordinates sx, sy) of stage `stage` (coefficient alpha)
 // of one tank, by one warp; `partial` receives the strip's four residual
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
-template <int H>
+// ONE_TANK (the single-tank kernel): the per-column parts of the boundary
+// logic are formed once per strip and interior rows skip the fold, and the
+// update takes Q^n, rho_ref and the ring terms of its row from the row loads
+// of two rows before (an output cell is an interior cell, so they are its
+// own values) instead of loading them again.  Otherwise (the batch kernel)
+// every row forms the boundary logic again and the update loads its inputs.
+// Both give the same values.  The first form holds more values across rows,
+// which pays where the tank's fields are constant-bank operands and not in
+// the batch kernel, whose tank fields are dynamically indexed constant loads
+// and whose registers already spill.
+template <int H, bool ONE_TANK = true>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial) {
     const Ctl *ctl = a.ctl;
@@ -636,28 +646,56 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         float jump;                         // reference jump across the east x-face (0 off the tank's rows)
         int fl;                             // fold bits
     };
+    // Per-column parts of the boundary logic, fixed for the whole strip, in
+    // one word: the fold bits of an interior row (bits 0-1), whether the
+    // column is a wall ghost (bit 2), whether the low and high y sides are
+    // walls (bits 3, 4); and the column of the east x-face's reference jump
+    // (-1: none).
     const int gi = c + 1;   // the east x-face's column
+    const int jcol = (gi >= 0 && gi < nx) ? gi : ((gi == nx && per_x) ? 0 : -1);
+    const int colbits = (nfx & 1) | ((tfx & 1) << 1) |
+                        (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
+                        (is_wall(a.bc[2]) ? 8 : 0) | (is_wall(a.bc[3]) ? 16 : 0);
     auto load_raw = [&](int k, Raw &R, int &srow) {
-        int nfy, tfy;
-        srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+        if constexpr (ONE_TANK) {
+            R.fl = colbits & 3;
+            if (k >= 0 && k < ny) {   // the same for the whole warp
+                srow = k;
+            } else {
+                int nfy, tfy;
+                srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+                R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
+            }
+        } else {
+            int nfy, tfy;
+            srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+            R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
+        }
         const int s = srow * nx + scol;
         R.q0 = __ldg(a.qn32[0] + s); R.q1 = __ldg(a.qn32[1] + s); R.q2 = __ldg(a.qn32[2] + s);
         R.d0 = din[0][s]; R.d1 = din[1][s]; R.d2 = din[2][s]; R.d3 = din[3][s];
-        R.e1 = need_rt ? d0[1][s] : 0.0f;
-        R.e2 = need_rt ? d0[2][s] : 0.0f;
+        R.e1 = (ONE_TANK || need_rt) ? d0[1][s] : 0.0f;
+        R.e2 = (ONE_TANK || need_rt) ? d0[2][s] : 0.0f;
         R.rr = __ldg(a.rho_ref + s);
-        R.jump = 0.0f;
-        if (k >= 0 && k < ny && gi >= 0) {
-            if (gi < nx) R.jump = __ldg(a.dref + k * nx + gi);
-            else if (gi == nx && per_x) R.jump = __ldg(a.dref + k * nx);
+        if constexpr (ONE_TANK) {
+            R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.dref + k * nx + jcol) : 0.0f;
+        } else {
+            R.jump = 0.0f;
+            if (k >= 0 && k < ny && gi >= 0) {
+                if (gi < nx) R.jump = __ldg(a.dref + k * nx + gi);
+                else if (gi == nx && per_x) R.jump = __ldg(a.dref + k * nx);
+            }
         }
-        R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
     };
+    // the update's own inputs of a row (ONE_TANK: those the row loads do not hold)
     auto load_upd = [&](int row, HeldSrc &U) {
         const int g = min(max(row, 0), ny - 1) * nx + ucol;
-        U.e0 = d0[0][g]; U.e1 = d0[1][g]; U.e2 = d0[2][g]; U.p0 = d0[3][g];
-        U.q0 = __ldg(a.qn32[0] + g); U.q1 = __ldg(a.qn32[1] + g); U.q2 = __ldg(a.qn32[2] + g);
-        U.rr = __ldg(a.rho_ref + g);
+        U.e0 = d0[0][g]; U.p0 = d0[3][g];
+        if constexpr (!ONE_TANK) {
+            U.e1 = d0[1][g]; U.e2 = d0[2][g];
+            U.q0 = __ldg(a.qn32[0] + g); U.q1 = __ldg(a.qn32[1] + g); U.q2 = __ldg(a.qn32[2] + g);
+            U.rr = __ldg(a.rho_ref + g);
+        }
     };
 
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
@@ -665,7 +703,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
     float Jm2 = 0.0f;                                        // east x-face reference jump of row k-2
-    Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
+    Raw Rm2 = {}, Rm1 = {}, Rk, Rn;                          // raw rows k-2, k-1, k, k+1
     int srk, srn;
     HeldSrc Uk, Un;                                          // update inputs of rows k-2, k-1
     float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -699,7 +737,14 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 rx = (Rm1.fl & 1) ? -rx : rx;
                 ry = (Rm1.fl & 2) ? -ry : ry;
             }
-            const float sg = wall_ghost_sign<float>(c, r, nx, ny, a.bc);
+            // gravity reversed in wall ghosts (as wall_ghost_sign)
+            float sg;
+            if constexpr (ONE_TANK) {
+                const bool wall_ghost = (colbits & 4) || (r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16));
+                sg = wall_ghost ? -1.0f : 1.0f;
+            } else {
+                sg = wall_ghost_sign<float>(c, r, nx, ny, a.bc);
+            }
             float hpx, hpy;
             new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.rr, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
@@ -724,6 +769,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
+                    if constexpr (ONE_TANK) {
+                        Uk.e1 = Rm2.e1; Uk.e2 = Rm2.e2;
+                        Uk.q0 = Rm2.q0; Uk.q1 = Rm2.q1; Uk.q2 = Rm2.q2; Uk.rr = Rm2.rr;
+                    }
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
                                            Fy, jw, Jm2, Uk, sq);
@@ -736,6 +785,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         }
         Wm2 = Wm1;
         Wm1 = W0;
+        if constexpr (ONE_TANK) Rm2 = Rm1;
         Rm1 = Rk;
         Rk = Rn;
         srk = srn;
