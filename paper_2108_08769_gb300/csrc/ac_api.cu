@@ -437,9 +437,9 @@ std::vector<std::pair<TuneKey, int>> g_tuned;
 
 struct MixedBackend : Backend {
     int variant = -1;
-    float *d[3][4] = {};
-    float *qn32[3] = {};
-    float *rho_ref = nullptr, *dref = nullptr, *lev_p = nullptr;
+    float4 *d[3] = {};   // per cell (dQ of rho, rho u, rho v; p'), three rotating buffers
+    float4 *qn = nullptr;  // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
+    float *dref = nullptr, *lev_p = nullptr;
     float *D1[3] = {}, *D2[3] = {};   // Q^n - Q^{n-1}, Q^n - Q^{n-2} (BDF2, BDF3)
     double *q64[3] = {};
     std::vector<double> p_ref;   // FP64 reference pressure (host copy)
@@ -521,9 +521,7 @@ struct MixedBackend : Backend {
         // timed stage sees real data
         for (int b = 0; b < 3; ++b)
             if (b != c->cur_host)
-                for (int f = 0; f < 4; ++f)
-                    CK(cudaMemcpyAsync(d[b][f], d[c->cur_host][f], c->N * sizeof(float), cudaMemcpyDeviceToDevice,
-                                       s));
+                CK(cudaMemcpyAsync(d[b], d[c->cur_host], c->N * sizeof(float4), cudaMemcpyDeviceToDevice, s));
         int best = 0;
         float best_ms = 1e30f;
         const int reps = c->N > (1u << 22) ? 2 : 5;
@@ -569,10 +567,10 @@ struct MixedBackend : Backend {
         a.beta = float(c->beta); a.inv_beta = float(1.0 / c->beta);
         a.gx = float(c->grid.gx); a.gy = float(c->grid.gy);
         a.cfl_area = float(c->opt.cfl_tau * dx * dy);
-        for (int b = 0; b < 3; ++b)
-            for (int f = 0; f < 4; ++f) a.d[b][f] = d[b][f];
-        for (int f = 0; f < 3; ++f) { a.qn32[f] = qn32[f]; a.q64[f] = q64[f]; }
-        a.rho_ref = rho_ref; a.dref = dref; a.lev_p = lev_p;
+        for (int b = 0; b < 3; ++b) a.d[b] = d[b];
+        a.qn = qn;
+        for (int f = 0; f < 3; ++f) a.q64[f] = q64[f];
+        a.dref = dref; a.lev_p = lev_p;
         for (int f = 0; f < 3; ++f) { a.D1[f] = D1[f]; a.D2[f] = D2[f]; }
         a.order = c->order_now;
         a.B0 = float(kBDF[c->order_now][0]);
@@ -583,11 +581,10 @@ struct MixedBackend : Backend {
         return a;
     }
     int alloc(ac_ctx *c) override {
-        const size_t fb = c->N * sizeof(float), db = c->N * sizeof(double);
-        for (int b = 0; b < 3; ++b)
-            for (int f = 0; f < 4; ++f) CK(cudaMalloc(&d[b][f], fb));
-        for (int f = 0; f < 3; ++f) { CK(cudaMalloc(&qn32[f], fb)); CK(cudaMalloc(&q64[f], db)); }
-        CK(cudaMalloc(&rho_ref, fb));
+        const size_t fb = c->N * sizeof(float), db = c->N * sizeof(double), f4 = c->N * sizeof(float4);
+        for (int b = 0; b < 3; ++b) CK(cudaMalloc(&d[b], f4));
+        CK(cudaMalloc(&qn, f4));
+        for (int f = 0; f < 3; ++f) CK(cudaMalloc(&q64[f], db));
         CK(cudaMalloc(&dref, fb));
         CK(cudaMalloc(&lev_p, fb));
         for (int f = 0; f < 3; ++f) {
@@ -622,10 +619,9 @@ struct MixedBackend : Backend {
         return AC_OK;
     }
     void release() override {
-        for (int b = 0; b < 3; ++b)
-            for (int f = 0; f < 4; ++f) cudaFree(d[b][f]);
-        for (int f = 0; f < 3; ++f) { cudaFree(qn32[f]); cudaFree(q64[f]); }
-        cudaFree(rho_ref);
+        for (int b = 0; b < 3; ++b) cudaFree(d[b]);
+        cudaFree(qn);
+        for (int f = 0; f < 3; ++f) cudaFree(q64[f]);
         cudaFree(dref);
         cudaFree(lev_p);
         for (int f = 0; f < 3; ++f) { cudaFree(D1[f]); cudaFree(D2[f]); }
@@ -639,39 +635,34 @@ struct MixedBackend : Backend {
         MixedReference ref;
         build_mixed_reference(c->grid.nx, c->grid.ny, c->dy, c->grid.gy, c->bc, use_ref, f, ref);
         p_ref = ref.p_ref;
-        std::vector<float> h32(N);
         cudaStream_t s = c->stream;
         const size_t fb = N * sizeof(float);
-        for (int k = 0; k < 3; ++k) {
-            CK(cudaMemcpyAsync(q64[k], f[k], N * sizeof(double), cudaMemcpyHostToDevice, s));
-            for (size_t q = 0; q < N; ++q) h32[q] = float(f[k][q]);
-            CK(cudaMemcpyAsync(qn32[k], h32.data(), fb, cudaMemcpyHostToDevice, s));
-            CK(cudaStreamSynchronize(s));   // h32 is reused
-            CK(cudaMemsetAsync(d[0][k], 0, fb, s));
+        // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, p')
+        std::vector<float4> hq(N), hd(N);
+        for (size_t q = 0; q < N; ++q) {
+            hq[q] = make_float4(float(f[0][q]), float(f[1][q]), float(f[2][q]), ref.rho_ref[q]);
+            hd[q] = make_float4(0.0f, 0.0f, 0.0f, ref.p_prime[q]);
         }
-        CK(cudaMemcpyAsync(d[0][3], ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
+        for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(q64[k], f[k], N * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(qn, hq.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d[0], hd.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(lev_p, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(rho_ref, ref.rho_ref.data(), fb, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(dref, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         return AC_OK;
     }
     int get_state(const ac_ctx *c, double *const out[4]) override {
         const size_t N = c->N;
-        std::vector<float> h(N);
+        std::vector<float4> h(N);
         const int cur = c->cur_host;
-        for (int k = 0; k < 3; ++k) {
-            if (!out[k]) continue;
-            CK(cudaMemcpyAsync(out[k], q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaMemcpyAsync(h.data(), d[cur][k], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            for (size_t q = 0; q < N; ++q) out[k][q] += double(h[q]);
-        }
-        if (out[3]) {
-            CK(cudaMemcpyAsync(h.data(), d[cur][3], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            for (size_t q = 0; q < N; ++q) out[3][q] = p_ref[q] + double(h[q]);
-        }
+        CK(cudaMemcpyAsync(h.data(), d[cur], N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        for (int k = 0; k < 3; ++k)
+            if (out[k]) CK(cudaMemcpyAsync(out[k], q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (out[0]) for (size_t q = 0; q < N; ++q) out[0][q] += double(h[q].x);
+        if (out[1]) for (size_t q = 0; q < N; ++q) out[1][q] += double(h[q].y);
+        if (out[2]) for (size_t q = 0; q < N; ++q) out[2][q] += double(h[q].z);
+        if (out[3]) for (size_t q = 0; q < N; ++q) out[3][q] = p_ref[q] + double(h[q].w);
         return AC_OK;
     }
     // Between steps, history 1 is the FP64 level q64 and history 2 is
@@ -692,25 +683,35 @@ struct MixedBackend : Backend {
     int set_history(ac_ctx *c, int k, const double *const in[3]) override {
         const size_t N = c->N;
         std::vector<double> old(N);
-        std::vector<float> h(N), h32(N);
+        std::vector<float> h(N);
+        std::vector<float4> hd, hq;   // the per-cell records (k == 1)
         const int cur = c->cur_host;
+        if (k == 1) {
+            hd.resize(N);
+            hq.resize(N);
+            CK(cudaMemcpyAsync(hd.data(), d[cur], N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(hq.data(), qn, N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+        }
         for (int f = 0; f < 3; ++f) {
             CK(cudaMemcpyAsync(old.data(), q64[f], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            if (k == 1) CK(cudaMemcpyAsync(h.data(), d[cur][f], N * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             if (k == 1) {
                 // the state Q = q64 + dQ stays; the level and dQ change
+                auto at = [f](float4 &v) -> float & { return f == 0 ? v.x : (f == 1 ? v.y : v.z); };
                 for (size_t q = 0; q < N; ++q) {
-                    h[q] = float((old[q] - in[f][q]) + double(h[q]));
-                    h32[q] = float(in[f][q]);
+                    at(hd[q]) = float((old[q] - in[f][q]) + double(at(hd[q])));
+                    at(hq[q]) = float(in[f][q]);
                 }
                 CK(cudaMemcpyAsync(q64[f], in[f], N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-                CK(cudaMemcpyAsync(qn32[f], h32.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-                CK(cudaMemcpyAsync(d[cur][f], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             } else {
                 for (size_t q = 0; q < N; ++q) h[q] = float(old[q] - in[f][q]);
                 CK(cudaMemcpyAsync(D1[f], h.data(), N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             }
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        if (k == 1) {
+            CK(cudaMemcpyAsync(d[cur], hd.data(), N * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(qn, hq.data(), N * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
             CK(cudaStreamSynchronize(c->stream));
         }
         return AC_OK;

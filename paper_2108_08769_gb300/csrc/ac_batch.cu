@@ -122,17 +122,23 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        const float4 e = a.d[cur][g];
+        float4 q4 = a.qn[g];   // .w (rho_ref) stays
+        const float dqs[3] = {e.x, e.y, e.z};
+        float qs[3];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const float dq = a.d[cur][f][g];
+            const float dq = dqs[f];
             const double q = a.q64[f][g] + double(dq);
             if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
             if (a.D1[0]) a.D1[f][g] = dq;
             a.q64[f][g] = q;
-            a.qn32[f][g] = float(q);
-            a.d[cur][f][g] = 0.0f;
+            qs[f] = float(q);
         }
-        a.lev_p[g] = a.d[cur][3][g];
+        q4.x = qs[0]; q4.y = qs[1]; q4.z = qs[2];
+        a.qn[g] = q4;
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, e.w);
+        a.lev_p[g] = e.w;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double h = dt[blockIdx.y];
@@ -209,12 +215,8 @@ __global__ void batch_restore_kernel(BatchTank *tanks) {
     if (a.ctl->status != -3) return;
     const int cur = a.ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
-    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        a.d[cur][0][g] = 0.0f;
-        a.d[cur][1][g] = 0.0f;
-        a.d[cur][2][g] = 0.0f;
-        a.d[cur][3][g] = a.lev_p[g];
-    }
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, a.lev_p[g]);
 }
 
 struct Variant {
@@ -297,9 +299,9 @@ struct ac_batch {
     std::vector<size_t> off;            // first cell of each tank in the pooled arrays
     size_t total;                       // pooled cells (with alignment padding)
     // pooled device arrays
-    float *d[3][4];
-    float *qn32[3];
-    float *rho_ref, *dref, *lev_p;
+    float4 *d[3];                       // per cell (dQ of rho, rho u, rho v; p'), three rotating pools
+    float4 *qn;                         // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
+    float *dref, *lev_p;
     float *D1[3], *D2[3];               // BDF2/BDF3 level differences (pools)
     double *q64[3];
     double *partials;
@@ -426,8 +428,7 @@ int tune(ac_batch *b, cudaStream_t s) {
     for (int k = 0; k < b->n; ++k) all_first = all_first && b->hctl[k].cur == 0;
     if (all_first)
         for (int x = 1; x < 3; ++x)
-            for (int f = 0; f < 4; ++f)
-                CK(cudaMemcpyAsync(b->d[x][f], b->d[0][f], b->total * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(b->d[x], b->d[0], b->total * sizeof(float4), cudaMemcpyDeviceToDevice, s));
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumVariants; ++v) {
@@ -511,10 +512,9 @@ void ac_batch_destroy(ac_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    for (int x = 0; x < 3; ++x)
-        for (int f = 0; f < 4; ++f) cudaFree(b->d[x][f]);
-    for (int f = 0; f < 3; ++f) { cudaFree(b->qn32[f]); cudaFree(b->q64[f]); cudaFree(b->D1[f]); cudaFree(b->D2[f]); }
-    cudaFree(b->rho_ref);
+    for (int x = 0; x < 3; ++x) cudaFree(b->d[x]);
+    cudaFree(b->qn);
+    for (int f = 0; f < 3; ++f) { cudaFree(b->q64[f]); cudaFree(b->D1[f]); cudaFree(b->D2[f]); }
     cudaFree(b->dref);
     cudaFree(b->lev_p);
     cudaFree(b->partials);
@@ -589,11 +589,10 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
             return c_;                                                                                   \
         }                                                                                                \
     } while (0)
-    const size_t fb = total * sizeof(float), db = total * sizeof(double);
-    for (int x = 0; x < 3; ++x)
-        for (int f = 0; f < 4; ++f) CKB(cudaMalloc(&b->d[x][f], fb));
-    for (int f = 0; f < 3; ++f) { CKB(cudaMalloc(&b->qn32[f], fb)); CKB(cudaMalloc(&b->q64[f], db)); }
-    CKB(cudaMalloc(&b->rho_ref, fb));
+    const size_t fb = total * sizeof(float), db = total * sizeof(double), f4 = total * sizeof(float4);
+    for (int x = 0; x < 3; ++x) CKB(cudaMalloc(&b->d[x], f4));
+    CKB(cudaMalloc(&b->qn, f4));
+    for (int f = 0; f < 3; ++f) CKB(cudaMalloc(&b->q64[f], db));
     CKB(cudaMalloc(&b->dref, fb));
     CKB(cudaMalloc(&b->lev_p, fb));
     for (int f = 0; f < 3; ++f) {
@@ -646,10 +645,9 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.beta = float(beta[k]); a.inv_beta = float(1.0 / beta[k]);
         a.gx = float(g.gx); a.gy = float(g.gy);
         a.cfl_area = float(o.cfl_tau * dx * dy);
-        for (int x = 0; x < 3; ++x)
-            for (int f = 0; f < 4; ++f) a.d[x][f] = b->d[x][f] + pos;
-        for (int f = 0; f < 3; ++f) { a.qn32[f] = b->qn32[f] + pos; a.q64[f] = b->q64[f] + pos; }
-        a.rho_ref = b->rho_ref + pos;
+        for (int x = 0; x < 3; ++x) a.d[x] = b->d[x] + pos;
+        a.qn = b->qn + pos;
+        for (int f = 0; f < 3; ++f) a.q64[f] = b->q64[f] + pos;
         a.dref = b->dref + pos;
         a.lev_p = b->lev_p + pos;
         for (int f = 0; f < 3; ++f) {
@@ -705,21 +703,20 @@ int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou
     hc.done = 1;
     hc.iter = 0;
     const size_t o = b->off[k], fb = N * sizeof(float);
-    std::vector<float> h32(N);
-    for (int q = 0; q < 3; ++q) {
-        CK(cudaMemcpyAsync(b->q64[q] + o, f[q], N * sizeof(double), cudaMemcpyHostToDevice, s));
-        for (size_t i = 0; i < N; ++i) h32[i] = float(f[q][i]);
-        CK(cudaMemcpyAsync(b->qn32[q] + o, h32.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-        CK(cudaMemsetAsync(b->d[0][q] + o, 0, fb, s));
+    // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, p')
+    std::vector<float4> hq(N), hd(N);
+    for (size_t i = 0; i < N; ++i) {
+        hq[i] = make_float4(float(f[0][i]), float(f[1][i]), float(f[2][i]), ref.rho_ref[i]);
+        hd[i] = make_float4(0.0f, 0.0f, 0.0f, ref.p_prime[i]);
     }
+    for (int q = 0; q < 3; ++q) CK(cudaMemcpyAsync(b->q64[q] + o, f[q], N * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->qn + o, hq.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->d[0] + o, hd.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
     for (int q = 0; q < 3; ++q) {
         if (b->D1[q]) CK(cudaMemsetAsync(b->D1[q] + o, 0, fb, s));
         if (b->D2[q]) CK(cudaMemsetAsync(b->D2[q] + o, 0, fb, s));
     }
-    CK(cudaMemcpyAsync(b->d[0][3] + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->lev_p + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(b->rho_ref + o, ref.rho_ref.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->dref + o, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->ctl + k, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -735,19 +732,15 @@ int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, doub
     const size_t N = (size_t)b->grids[k].nx * b->grids[k].ny, o = b->off[k];
     const int cur = b->hctl[k].cur;
     double *out[4] = {rho, rhou, rhov, p};
-    std::vector<float> h(N);
-    for (int q = 0; q < 3; ++q) {
-        if (!out[q]) continue;
-        CK(cudaMemcpyAsync(out[q], b->q64[q] + o, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-        CK(cudaMemcpyAsync(h.data(), b->d[cur][q] + o, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
-        CK(cudaStreamSynchronize(b->stream));
-        for (size_t i = 0; i < N; ++i) out[q][i] += double(h[i]);
-    }
-    if (p) {
-        CK(cudaMemcpyAsync(h.data(), b->d[cur][3] + o, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
-        CK(cudaStreamSynchronize(b->stream));
-        for (size_t i = 0; i < N; ++i) p[i] = b->p_ref[k][i] + double(h[i]);
-    }
+    std::vector<float4> h(N);
+    CK(cudaMemcpyAsync(h.data(), b->d[cur] + o, N * sizeof(float4), cudaMemcpyDeviceToHost, b->stream));
+    for (int q = 0; q < 3; ++q)
+        if (out[q]) CK(cudaMemcpyAsync(out[q], b->q64[q] + o, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (rho) for (size_t i = 0; i < N; ++i) rho[i] += double(h[i].x);
+    if (rhou) for (size_t i = 0; i < N; ++i) rhou[i] += double(h[i].y);
+    if (rhov) for (size_t i = 0; i < N; ++i) rhov[i] += double(h[i].z);
+    if (p) for (size_t i = 0; i < N; ++i) p[i] = b->p_ref[k][i] + double(h[i].w);
     return AC_OK;
 }
 

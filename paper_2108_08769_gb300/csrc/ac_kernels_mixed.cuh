@@ -2,12 +2,12 @@
 // FP32 flux, reconstruction and update arithmetic; FP64 real-time level,
 // hydrostatic reference pressure and residual sums.
 //
-// Storage (per cell):
-//   qn32[3]   FP32 copy of the real-time level Q^n = (rho, rho u, rho v)
-//   d[b][4]   three rotating FP32 buffers: dQ = Q - Q^n for rho, rho u, rho v
-//             and p' = p - p_ref
-//   rho_ref   FP32 reference density; p_ref (FP64, host side) is its discrete
-//             hydrostatic column integral along y
+// Storage (per cell; the two 16-byte records are read with one vector load):
+//   qn        (FP32 copy of the real-time level Q^n = (rho, rho u, rho v),
+//             reference density rho_ref); p_ref (FP64, host side) is the
+//             discrete hydrostatic column integral of rho_ref along y
+//   d[b]      three rotating buffers of (dQ = Q - Q^n for rho, rho u, rho v,
+//             p' = p - p_ref), FP32
 //   dref      FP32 jump p_ref(i) - p_ref(i-1) across the west x-face
 //   q64[3]    FP64 real-time level, advanced once per physical step
 //             (Q^{n+1} = Q^n + dQ in FP64: the level accumulation)
@@ -49,9 +49,8 @@ struct MixedArgs {
     float dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
     float beta, inv_beta, gx, gy;
     float cfl_area;
-    float *d[3][4];        // dQ (rho, rho u, rho v) and p'
-    float *qn32[3];        // FP32 copy of Q^n
-    const float *rho_ref;  // reference density
+    float4 *d[3];          // per cell (dQ of rho, rho u, rho v; p'), three rotating buffers
+    float4 *qn;            // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
     const float *dref;     // reference jump across the west x-face
     float *lev_p;          // p' at the start of the physical step
     float *D1[3], *D2[3];  // Q^n - Q^{n-1}, Q^n - Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
@@ -84,16 +83,17 @@ struct MixedSmem {
 
 // Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell as W = (rho, u, v, p').
 struct CellLoad {
-    const float *__restrict__ qn0, *__restrict__ qn1, *__restrict__ qn2;
-    const float *__restrict__ d0, *__restrict__ d1, *__restrict__ d2, *__restrict__ d3;
+    const float4 *__restrict__ qn;
+    const float4 *__restrict__ d;
     __device__ __forceinline__ float4 operator()(int s, bool fx, bool fy) const {
-        const float r = __ldg(qn0 + s) + d0[s];
-        float m = __ldg(qn1 + s) + d1[s];
-        float n = __ldg(qn2 + s) + d2[s];
+        const float4 q = __ldg(qn + s), e = d[s];
+        const float r = q.x + e.x;
+        float m = q.y + e.y;
+        float n = q.z + e.z;
         m = fx ? -m : m;
         n = fy ? -n : n;
         const float ir = Ar<float>::rcp(r);
-        return make_float4(r, m * ir, n * ir, d3[s]);
+        return make_float4(r, m * ir, n * ir, e.w);
     }
 };
 
@@ -169,7 +169,7 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // and rho_ref of the cell.
 template <bool BDF, typename Src>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
-                                            float *const *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
+                                            float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float jw, float je, const Src &src,
                                             float4 &sq) {
     const float div0 = (Fe.x - Fw.x) * a.inv_dx + (Fn.x - Fs.x) * a.inv_dy;
@@ -217,10 +217,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float adt = alpha * dtau;
     const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
     const float coef_p = a.alpha_pi_p_row ? coef : adt;
-    dout[0][g] = e0 + coef * b0;
-    dout[1][g] = e1 + coef * b1;
-    dout[2][g] = e2 + coef * b2;
-    dout[3][g] = p0 + a.beta * coef_p * b3;
+    dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
     if (stage1) {
         const float pb = a.beta * b3;
         sq.x += b0 * b0; sq.y += b1 * b1; sq.z += b2 * b2; sq.w += pb * pb;
@@ -240,7 +237,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 struct DirectSrc {
     static constexpr bool kDxfStaged = false;
     const MixedArgs &a;
-    const float *const *d0;
+    const float4 *d0;
     __device__ __forceinline__ void prefetch(int, int) {}
     __device__ __forceinline__ float jump(int gi, int gj, bool per_x) const {
         float j = 0.0f;
@@ -254,9 +251,9 @@ struct DirectSrc {
     __device__ __forceinline__ void cell(int cell, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
                                          float &q1, float &q2, float &rr) const {
         (void)cell;
-        e0 = d0[0][g]; e1 = d0[1][g]; e2 = d0[2][g]; p0 = d0[3][g];
-        q0 = __ldg(a.qn32[0] + g); q1 = __ldg(a.qn32[1] + g); q2 = __ldg(a.qn32[2] + g);
-        rr = __ldg(a.rho_ref + g);
+        const float4 e = d0[g], q = __ldg(a.qn + g);
+        e0 = e.x; e1 = e.y; e2 = e.z; p0 = e.w;
+        q0 = q.x; q1 = q.y; q2 = q.z; rr = q.w;
     }
 };
 
@@ -266,14 +263,14 @@ struct DirectSrc {
 struct PrefetchSrc {
     static constexpr bool kDxfStaged = true;
     const MixedArgs &a;
-    const float *const *d0;
+    const float4 *d0;
     float v[8];
     __device__ __forceinline__ void prefetch(int gi, int gj) {
         if (gi < a.nx && gj < a.ny) {
             const int g = gj * a.nx + gi;
-            v[0] = d0[0][g]; v[1] = d0[1][g]; v[2] = d0[2][g]; v[3] = d0[3][g];
-            v[4] = __ldg(a.qn32[0] + g); v[5] = __ldg(a.qn32[1] + g); v[6] = __ldg(a.qn32[2] + g);
-            v[7] = __ldg(a.rho_ref + g);
+            const float4 e = d0[g], q = __ldg(a.qn + g);
+            v[0] = e.x; v[1] = e.y; v[2] = e.z; v[3] = e.w;
+            v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
         }
     }
     __device__ __forceinline__ float jump(int, int, bool) const { return 0.0f; }
@@ -295,7 +292,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
     const Ctl *ctl = a.ctl;
     int in, out;
     stage_buffers(ctl->cur, stage, in, out);
-    float *const *dout = a.d[out];
+    float4 *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
@@ -433,8 +430,8 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, stage, in, out);
-    const float *const *din = a.d[in];
-    const float *const *d0 = a.d[cur];
+    const float4 *din = a.d[in];
+    const float4 *d0 = a.d[cur];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
 
     const int nx = a.nx, ny = a.ny;
@@ -442,7 +439,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
     const int x0 = bx * TX, y0 = by * TY;
     // halo entirely inside the domain: no ghost folding for this tile
     const bool interior = (x0 >= 2) && (x0 + TX + 2 <= nx) && (y0 >= 2) && (y0 + TY + 2 <= ny);
-    const CellLoad ld{a.qn32[0], a.qn32[1], a.qn32[2], din[0], din[1], din[2], din[3]};
+    const CellLoad ld{a.qn, din};
     const bool new_gradp = (a.gradp == kGradNew);
     const bool need_rt = new_gradp && a.realtime;
 
@@ -472,10 +469,10 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
                 }
                 float *dst = reinterpret_cast<float *>(&sm.aux[k]);
                 if (need_rt) {
-                    cp_async4(dst, d0[1] + s);
-                    cp_async4(dst + 1, d0[2] + s);
+                    cp_async4(dst, &d0[s].y);
+                    cp_async4(dst + 1, &d0[s].z);
                 }
-                cp_async4(dst + 2, a.rho_ref + s);
+                cp_async4(dst + 2, &a.qn[s].w);
                 dst[3] = __int_as_float(fl);
             }
         }
@@ -498,9 +495,6 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
         }
     }
     if (!PF && new_gradp) {
-        const float *__restrict__ e1 = d0[1];
-        const float *__restrict__ e2 = d0[2];
-        const float *__restrict__ rref = a.rho_ref;
         for (int k = tid; k < GW * GH; k += NT) {
             const int rr = k / GW, cc = k - rr * GW;
             int s, fx = 0, fy = 0;
@@ -516,8 +510,8 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
             }
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                rx = a.B0 * e1[s];     // B0 (Q^{m} - Q^n) of rho u, ...
-                ry = a.B0 * e2[s];
+                rx = a.B0 * d0[s].y;   // B0 (Q^{m} - Q^n) of rho u, ...
+                ry = a.B0 * d0[s].z;
                 if constexpr (BDF) {
                     if (a.order >= 2) {
                         rx -= a.B2 * a.D1[1][s];
@@ -533,7 +527,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
                 rx = fx ? -rx : rx;
                 ry = fy ? -ry : ry;
             }
-            sm.aux[k] = make_float4(rx, ry, __ldg(rref + s), 0.0f);
+            sm.aux[k] = make_float4(rx, ry, __ldg(&a.qn[s].w), 0.0f);
         }
     }
     if constexpr (PF) {
@@ -574,12 +568,12 @@ stage_kernel_mixed(const MixedArgs a) {
 // ---------------------------------------------------------------------------
 struct GlobalSrc {
     const MixedArgs &a;
-    const float *const *d0;
+    const float4 *d0;
     __device__ __forceinline__ void cell(int, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
                                          float &q1, float &q2, float &rr) const {
-        e0 = d0[0][g]; e1 = d0[1][g]; e2 = d0[2][g]; p0 = d0[3][g];
-        q0 = __ldg(a.qn32[0] + g); q1 = __ldg(a.qn32[1] + g); q2 = __ldg(a.qn32[2] + g);
-        rr = __ldg(a.rho_ref + g);
+        const float4 e = d0[g], q = __ldg(a.qn + g);
+        e0 = e.x; e1 = e.y; e2 = e.z; p0 = e.w;
+        q0 = q.x; q1 = q.y; q2 = q.z; rr = q.w;
     }
 };
 
@@ -627,9 +621,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     int in, out;
     const int cur = ctl->cur;
     stage_buffers(cur, stage, in, out);
-    const float *const *din = a.d[in];
-    const float *const *d0 = a.d[cur];
-    float *const *dout = a.d[out];
+    const float4 *din = a.d[in];
+    const float4 *d0 = a.d[cur];
+    float4 *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
     const bool need_rt = a.realtime != 0;
     const bool per_x = (a.bc[0] == kPeriodic);
@@ -641,8 +635,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
 
     // raw inputs of a row, loaded one row ahead of use
     struct Raw {
-        float q0, q1, q2, d0, d1, d2, d3;   // Q^n and dQ^{s-1} (+ p')
-        float e1, e2, rr;                   // ring terms: dQ^{m} of rho u, rho v; rho_ref
+        float4 q;                           // Q^n of rho, rho u, rho v; rho_ref
+        float4 d;                           // dQ^{s-1} of rho, rho u, rho v; p'
+        float e0, e1, e2, p0;               // dQ^{m}, p'^{m} (ONE_TANK; otherwise the ring terms e1, e2 only)
         float jump;                         // reference jump across the east x-face (0 off the tank's rows)
         int fl;                             // fold bits
     };
@@ -672,11 +667,15 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
         }
         const int s = srow * nx + scol;
-        R.q0 = __ldg(a.qn32[0] + s); R.q1 = __ldg(a.qn32[1] + s); R.q2 = __ldg(a.qn32[2] + s);
-        R.d0 = din[0][s]; R.d1 = din[1][s]; R.d2 = din[2][s]; R.d3 = din[3][s];
-        R.e1 = (ONE_TANK || need_rt) ? d0[1][s] : 0.0f;
-        R.e2 = (ONE_TANK || need_rt) ? d0[2][s] : 0.0f;
-        R.rr = __ldg(a.rho_ref + s);
+        R.q = __ldg(a.qn + s);
+        R.d = din[s];
+        if constexpr (ONE_TANK) {
+            const float4 e = d0[s];
+            R.e0 = e.x; R.e1 = e.y; R.e2 = e.z; R.p0 = e.w;
+        } else {
+            R.e1 = need_rt ? d0[s].y : 0.0f;
+            R.e2 = need_rt ? d0[s].z : 0.0f;
+        }
         if constexpr (ONE_TANK) {
             R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.dref + k * nx + jcol) : 0.0f;
         } else {
@@ -687,15 +686,12 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             }
         }
     };
-    // the update's own inputs of a row (ONE_TANK: those the row loads do not hold)
+    // the update's inputs of a row (not used with ONE_TANK: the row loads hold them)
     auto load_upd = [&](int row, HeldSrc &U) {
         const int g = min(max(row, 0), ny - 1) * nx + ucol;
-        U.e0 = d0[0][g]; U.p0 = d0[3][g];
-        if constexpr (!ONE_TANK) {
-            U.e1 = d0[1][g]; U.e2 = d0[2][g];
-            U.q0 = __ldg(a.qn32[0] + g); U.q1 = __ldg(a.qn32[1] + g); U.q2 = __ldg(a.qn32[2] + g);
-            U.rr = __ldg(a.rho_ref + g);
-        }
+        const float4 e = d0[g], q = __ldg(a.qn + g);
+        U.e0 = e.x; U.e1 = e.y; U.e2 = e.z; U.p0 = e.w;
+        U.q0 = q.x; U.q1 = q.y; U.q2 = q.z; U.rr = q.w;
     };
 
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
@@ -708,21 +704,21 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     HeldSrc Uk, Un;                                          // update inputs of rows k-2, k-1
     float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
     load_raw(y0 - 2, Rk, srk);
-    load_upd(y0 - 2, Uk);
+    if constexpr (!ONE_TANK) load_upd(y0 - 2, Uk);
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
         // prefetch: the next row's raw inputs and the next updated row's inputs
         load_raw(k + 1, Rn, srn);
-        load_upd(k - 1, Un);
+        if constexpr (!ONE_TANK) load_upd(k - 1, Un);
         // ---- W = (rho, u, v, p') of Q^{s-1} at row k ----
         float4 W0;
         {
-            const float r = Rk.q0 + Rk.d0;
-            float mm = Rk.q1 + Rk.d1;
-            float nn = Rk.q2 + Rk.d2;
+            const float r = Rk.q.x + Rk.d.x;
+            float mm = Rk.q.y + Rk.d.y;
+            float nn = Rk.q.z + Rk.d.z;
             mm = (Rk.fl & 1) ? -mm : mm;
             nn = (Rk.fl & 2) ? -nn : nn;
             const float ir = Ar<float>::rcp(r);
-            W0 = make_float4(r, mm * ir, nn * ir, Rk.d3);
+            W0 = make_float4(r, mm * ir, nn * ir, Rk.d.w);
         }
         if (k >= y0) {
             // ---- slopes and pressure gradient of row r = k-1 ----
@@ -746,7 +742,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 sg = wall_ghost_sign<float>(c, r, nx, ny, a.bc);
             }
             float hpx, hpy;
-            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.rr, sg, hpx, hpy);
+            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.q.w, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
             // ---- east x-face of row r (between columns c and c + 1) ----
             const float4 &Wn = We;
@@ -769,10 +765,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
-                    if constexpr (ONE_TANK) {
-                        Uk.e1 = Rm2.e1; Uk.e2 = Rm2.e2;
-                        Uk.q0 = Rm2.q0; Uk.q1 = Rm2.q1; Uk.q2 = Rm2.q2; Uk.rr = Rm2.rr;
-                    }
+                    if constexpr (ONE_TANK) Uk = HeldSrc{Rm2.e0, Rm2.e1, Rm2.e2, Rm2.p0, Rm2.q.x, Rm2.q.y, Rm2.q.z, Rm2.q.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
                                            Fy, jw, Jm2, Uk, sq);
@@ -825,13 +818,14 @@ static __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
     pdl_wait();
     const Ctl *ctl = a.ctl;
     if (ctl->done) return;
-    const float *const *d = a.d[ctl->cur];
+    const float4 *d = a.d[ctl->cur];
     const size_t N = (size_t)a.nx * a.ny;
     double mn = INFINITY;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        const float r0 = a.qn32[0][g] + d[0][g];
+        const float4 e = d[g], q = a.qn[g];
+        const float r0 = q.x + e.x;
         const float ir = Ar<float>::rcp(r0);
-        const float u = (a.qn32[1][g] + d[1][g]) * ir, v = (a.qn32[2][g] + d[2][g]) * ir;
+        const float u = (q.y + e.y) * ir, v = (q.z + e.z) * ir;
         const float fb = 4.0f * a.beta * ir;
         const float cx = sqrtf(u * u + fb), cy = sqrtf(v * v + fb);
         const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
@@ -846,13 +840,14 @@ static __global__ void dtau_min_kernel_mixed(const MixedArgs a) {
 // Global real-time step (Sec. 2.2.4) in the mixed form, Q = Q^n + dQ.
 static __global__ void realtime_dt_kernel_mixed(const MixedArgs a, int cur, double cfl_area,
                                                 unsigned long long *out) {
-    const float *const *d = a.d[cur];
+    const float4 *d = a.d[cur];
     const size_t N = (size_t)a.nx * a.ny;
     double mn = INFINITY;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        const double r = double(a.qn32[0][g]) + double(d[0][g]);
-        const double u = (double(a.qn32[1][g]) + double(d[1][g])) / r;
-        const double v = (double(a.qn32[2][g]) + double(d[2][g])) / r;
+        const float4 e = d[g], q4 = a.qn[g];
+        const double r = double(q4.x) + double(e.x);
+        const double u = (double(q4.y) + double(e.y)) / r;
+        const double v = (double(q4.z) + double(e.z)) / r;
         mn = fmin(mn, cfl_area / (fabs(u) * double(a.dy) + fabs(v) * double(a.dx)));
     }
 #pragma unroll
@@ -868,18 +863,24 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
+        const float4 e = a.d[cur][g];
+        float4 q4 = a.qn[g];   // .w (rho_ref) stays
+        const float dqs[3] = {e.x, e.y, e.z};
+        float qs[3];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const float dq = a.d[cur][f][g];
+            const float dq = dqs[f];
             const double q = a.q64[f][g] + double(dq);
             // differences to the older levels, relative to the new Q^n
             if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
             if (a.D1[0]) a.D1[f][g] = dq;
             a.q64[f][g] = q;
-            a.qn32[f][g] = float(q);
-            a.d[cur][f][g] = 0.0f;
+            qs[f] = float(q);
         }
-        a.lev_p[g] = a.d[cur][3][g];
+        q4.x = qs[0]; q4.y = qs[1]; q4.z = qs[2];
+        a.qn[g] = q4;
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, e.w);
+        a.lev_p[g] = e.w;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->iter = 0;
@@ -898,12 +899,8 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
 static __global__ void restore_kernel_mixed(const MixedArgs a) {
     const int cur = a.ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
-    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        a.d[cur][0][g] = 0.0f;
-        a.d[cur][1][g] = 0.0f;
-        a.d[cur][2][g] = 0.0f;
-        a.d[cur][3][g] = a.lev_p[g];
-    }
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, a.lev_p[g]);
 }
 
 }  // namespace acgb
