@@ -103,13 +103,13 @@ batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H, false>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
     } else {
         const BatchTank &t = tanks[k];
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H, false>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
     }
 }
 

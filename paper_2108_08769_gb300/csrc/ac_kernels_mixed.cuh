@@ -588,7 +588,7 @@ __device__ __forceinline__ float4 shfl_up4(const float4 &v, int d) {
 
 constexpr int kStripOut = 28;   // output columns per warp
 
-// The update's inputs of one cell, held in registers (loaded a row ahead).
+// The update's inputs of one cell, held in registers (from the row loads).
 struct HeldSrc {
     float e0, e1, e2, p0, q0, q1, q2, rr;
     __device__ __forceinline__ void cell(int, int, float &a0, float &a1, float &a2, float &a3, float &b0,
@@ -600,17 +600,11 @@ struct HeldSrc {
 // One strip (strip coordinates sx, sy) of stage `stage` (coefficient alpha)
 // of one tank, by one warp; `partial` receives the strip's four residual
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
-// ONE_TANK (the single-tank kernel): the per-column parts of the boundary
-// logic are formed once per strip and interior rows skip the fold, and the
-// update takes Q^n, rho_ref and the ring terms of its row from the row loads
-// of two rows before (an output cell is an interior cell, so they are its
-// own values) instead of loading them again.  Otherwise (the batch kernel)
-// every row forms the boundary logic again and the update loads its inputs.
-// Both give the same values.  The first form holds more values across rows,
-// which pays where the tank's fields are constant-bank operands and not in
-// the batch kernel, whose tank fields are dynamically indexed constant loads
-// and whose registers already spill.
-template <int H, bool ONE_TANK = true>
+// The per-column parts of the boundary logic are formed once per strip and
+// interior rows skip the fold; the update takes its inputs (dQ^{m}, Q^n,
+// rho_ref) from the row loads of two rows before: an output cell is an
+// interior cell, so they are its own values.
+template <int H>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial) {
     const Ctl *ctl = a.ctl;
@@ -631,13 +625,12 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     int nfx, tfx;
     const int scol = fold_axis(c, nx, a.bc[0], a.bc[1], nfx, tfx);
     const bool out_lane = lane >= 2 && lane < 30 && c < nx;
-    const int ucol = min(max(c, 0), nx - 1);   // in-bounds column for the prefetch of non-output lanes
 
     // raw inputs of a row, loaded one row ahead of use
     struct Raw {
         float4 q;                           // Q^n of rho, rho u, rho v; rho_ref
         float4 d;                           // dQ^{s-1} of rho, rho u, rho v; p'
-        float e0, e1, e2, p0;               // dQ^{m}, p'^{m} (ONE_TANK; otherwise the ring terms e1, e2 only)
+        float4 e;                           // dQ^{m}, p'^{m} (the ring terms and the update's base)
         float jump;                         // reference jump across the east x-face (0 off the tank's rows)
         int fl;                             // fold bits
     };
@@ -652,15 +645,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                         (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
                         (is_wall(a.bc[2]) ? 8 : 0) | (is_wall(a.bc[3]) ? 16 : 0);
     auto load_raw = [&](int k, Raw &R, int &srow) {
-        if constexpr (ONE_TANK) {
-            R.fl = colbits & 3;
-            if (k >= 0 && k < ny) {   // the same for the whole warp
-                srow = k;
-            } else {
-                int nfy, tfy;
-                srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
-                R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
-            }
+        R.fl = colbits & 3;
+        if (k >= 0 && k < ny) {   // the same for the whole warp
+            srow = k;
         } else {
             int nfy, tfy;
             srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
@@ -669,29 +656,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         const int s = srow * nx + scol;
         R.q = __ldg(a.qn + s);
         R.d = din[s];
-        if constexpr (ONE_TANK) {
-            const float4 e = d0[s];
-            R.e0 = e.x; R.e1 = e.y; R.e2 = e.z; R.p0 = e.w;
-        } else {
-            R.e1 = need_rt ? d0[s].y : 0.0f;
-            R.e2 = need_rt ? d0[s].z : 0.0f;
-        }
-        if constexpr (ONE_TANK) {
-            R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.dref + k * nx + jcol) : 0.0f;
-        } else {
-            R.jump = 0.0f;
-            if (k >= 0 && k < ny && gi >= 0) {
-                if (gi < nx) R.jump = __ldg(a.dref + k * nx + gi);
-                else if (gi == nx && per_x) R.jump = __ldg(a.dref + k * nx);
-            }
-        }
-    };
-    // the update's inputs of a row (not used with ONE_TANK: the row loads hold them)
-    auto load_upd = [&](int row, HeldSrc &U) {
-        const int g = min(max(row, 0), ny - 1) * nx + ucol;
-        const float4 e = d0[g], q = __ldg(a.qn + g);
-        U.e0 = e.x; U.e1 = e.y; U.e2 = e.z; U.p0 = e.w;
-        U.q0 = q.x; U.q1 = q.y; U.q2 = q.z; U.rr = q.w;
+        R.e = d0[s];
+        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.dref + k * nx + jcol) : 0.0f;
     };
 
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
@@ -701,14 +667,11 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float Jm2 = 0.0f;                                        // east x-face reference jump of row k-2
     Raw Rm2 = {}, Rm1 = {}, Rk, Rn;                          // raw rows k-2, k-1, k, k+1
     int srk, srn;
-    HeldSrc Uk, Un;                                          // update inputs of rows k-2, k-1
     float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
     load_raw(y0 - 2, Rk, srk);
-    if constexpr (!ONE_TANK) load_upd(y0 - 2, Uk);
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
-        // prefetch: the next row's raw inputs and the next updated row's inputs
+        // prefetch: the next row's inputs
         load_raw(k + 1, Rn, srn);
-        if constexpr (!ONE_TANK) load_upd(k - 1, Un);
         // ---- W = (rho, u, v, p') of Q^{s-1} at row k ----
         float4 W0;
         {
@@ -728,19 +691,14 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             limit_slopes(Wm1, We, Ww, W0, Wm2, a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                rx = (a.B0 * Rm1.e1) * inv_dt;
-                ry = (a.B0 * Rm1.e2) * inv_dt;
+                rx = (a.B0 * Rm1.e.y) * inv_dt;
+                ry = (a.B0 * Rm1.e.z) * inv_dt;
                 rx = (Rm1.fl & 1) ? -rx : rx;
                 ry = (Rm1.fl & 2) ? -ry : ry;
             }
             // gravity reversed in wall ghosts (as wall_ghost_sign)
-            float sg;
-            if constexpr (ONE_TANK) {
-                const bool wall_ghost = (colbits & 4) || (r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16));
-                sg = wall_ghost ? -1.0f : 1.0f;
-            } else {
-                sg = wall_ghost_sign<float>(c, r, nx, ny, a.bc);
-            }
+            const bool wall_ghost = (colbits & 4) || (r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16));
+            const float sg = wall_ghost ? -1.0f : 1.0f;
             float hpx, hpy;
             new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.q.w, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
@@ -765,7 +723,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
-                    if constexpr (ONE_TANK) Uk = HeldSrc{Rm2.e0, Rm2.e1, Rm2.e2, Rm2.p0, Rm2.q.x, Rm2.q.y, Rm2.q.z, Rm2.q.w};
+                    const HeldSrc Uk{Rm2.e.x, Rm2.e.y, Rm2.e.z, Rm2.e.w, Rm2.q.x, Rm2.q.y, Rm2.q.z, Rm2.q.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
                                            Fy, jw, Jm2, Uk, sq);
@@ -778,11 +736,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         }
         Wm2 = Wm1;
         Wm1 = W0;
-        if constexpr (ONE_TANK) Rm2 = Rm1;
+        Rm2 = Rm1;
         Rm1 = Rk;
         Rk = Rn;
         srk = srn;
-        Uk = Un;
     }
     if (stage == 1) {
         // per-warp sums in FP32, one FP64 partial per strip
