@@ -588,7 +588,7 @@ __device__ __forceinline__ float4 shfl_up4(const float4 &v, int d) {
 
 constexpr int kStripOut = 28;   // output columns per warp
 
-// The update's inputs of one cell, held in registers (from the row loads).
+// The update's inputs of one cell, held in registers.
 struct HeldSrc {
     float e0, e1, e2, p0, q0, q1, q2, rr;
     __device__ __forceinline__ void cell(int, int, float &a0, float &a1, float &a2, float &a3, float &b0,
@@ -601,9 +601,9 @@ struct HeldSrc {
 // of one tank, by one warp; `partial` receives the strip's four residual
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
 // The per-column parts of the boundary logic are formed once per strip and
-// interior rows skip the fold; the update takes its inputs (dQ^{m}, Q^n,
-// rho_ref) from the row loads of two rows before: an output cell is an
-// interior cell, so they are its own values.
+// interior rows skip the fold; the update loads its two records (dQ^{m},
+// p'^{m}; Q^n, rho_ref) when it runs: the same lane loaded them two rows
+// before, so they come from L1, and nothing more is held across rows.
 template <int H>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial) {
@@ -630,7 +630,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     struct Raw {
         float4 q;                           // Q^n of rho, rho u, rho v; rho_ref
         float4 d;                           // dQ^{s-1} of rho, rho u, rho v; p'
-        float4 e;                           // dQ^{m}, p'^{m} (the ring terms and the update's base)
+        float4 e;                           // dQ^{m}, p'^{m} (the ring terms)
         float jump;                         // reference jump across the east x-face (0 off the tank's rows)
         int fl;                             // fold bits
     };
@@ -665,7 +665,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
     float Jm2 = 0.0f;                                        // east x-face reference jump of row k-2
-    Raw Rm2 = {}, Rm1 = {}, Rk, Rn;                          // raw rows k-2, k-1, k, k+1
+    Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
     int srk, srn;
     float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
     load_raw(y0 - 2, Rk, srk);
@@ -723,7 +723,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
-                    const HeldSrc Uk{Rm2.e.x, Rm2.e.y, Rm2.e.z, Rm2.e.w, Rm2.q.x, Rm2.q.y, Rm2.q.z, Rm2.q.w};
+                    const int gu = (k - 2) * nx + min(max(c, 0), nx - 1);
+                    const float4 ue = d0[gu], uq = __ldg(a.qn + gu);
+                    const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
                                            Fy, jw, Jm2, Uk, sq);
@@ -736,7 +738,6 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         }
         Wm2 = Wm1;
         Wm1 = W0;
-        Rm2 = Rm1;
         Rm1 = Rk;
         Rk = Rn;
         srk = srn;
