@@ -126,9 +126,10 @@ __device__ __forceinline__ double minmod_bits(double a, double b) {
 template <typename T, bool TWICE = false>
 __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR,
                                            T beta, T inv_beta, T F[4]) {
-    const T mL = rL * uL, nL = rL * vL, qL = pL * inv_beta;
-    const T mR = rR * uR, nR = rR * vR, qR = pR * inv_beta;
-    const T dr = rR - rL, dm = mR - mL, dn = nR - nL, dq = qR - qL;
+    const T mL = rL * uL, nL = rL * vL;
+    const T mR = rR * uR, nR = rR * vR;
+    const T dr = rR - rL, dm = mR - mL, dn = nR - nL, dp = pR - pL;
+    const T dq = dp * inv_beta;   // the jump of Q's last component p/beta
     const T four_beta = T(4) * beta;
     // Gauss-Legendre points mapped to [0,1]: (xi + 1)/2, weights w/2
     const T tq[3] = {T(0.11270166537925831148), T(0.5), T(0.88729833462074168852)};
@@ -136,7 +137,8 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     // D = sum_j w_j |A_j| dQ, accumulated as
     //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
     //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
-    // (the weight w_j rides on k = w_j rho / c)
+    // (the weight w_j rides on k = w_j rho / c, and with it the 1/beta of
+    // l a + dq = (l beta a + dp)/beta, a = (dm - u dr)/beta)
     T Sau, Se, Sue, Sve, Sg, Sh;
     // the three densities' reciprocals from one reciprocal of their product
     // (1 reciprocal + 6 products in place of 3 reciprocals)
@@ -165,11 +167,11 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T hu = T(0.5) * u;
         const T l4 = fma(T(0.5), c, hu), l5 = fma(T(-0.5), c, hu);
         const T au = fabs(u);
-        const T a = (dm - u * dr) * inv_beta;
+        const T ba = dm - u * dr;   // beta a
         const T w = wq[j];
-        const T k = (w * r) * ic;
-        const T g4 = (l4 - au) * k * (l4 * a + dq);
-        const T g5 = (l5 + au) * k * (l5 * a + dq);
+        const T k = ((w * inv_beta) * r) * ic;
+        const T g4 = (l4 - au) * k * (l4 * ba + dp);
+        const T g5 = (l5 + au) * k * (l5 * ba + dp);
         const T e = g4 * l4 + g5 * l5;
         const T gs = ir * (g4 + g5), h = ir * (g4 * l5 + g5 * l4);
         if (j == 0) {
