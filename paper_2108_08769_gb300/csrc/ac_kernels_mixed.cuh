@@ -563,20 +563,10 @@ stage_kernel_mixed(const MixedArgs a) {
 // slopes and pressure gradient of row k-1, the x-face fluxes of row k-1 and
 // the y-face flux between rows k-2 and k-1, and it updates row k-2.  Lanes
 // 0, 1, 30, 31 are halo (their slopes or fluxes feed the output lanes'
-// faces).  Every per-cell and per-face value uses the same functions as the
-// tile sweep.
+// faces).  Every per-cell value uses the same functions as the tile sweep;
+// a lane's x- and y-face fluxes go through the face-pair form of the Osher
+// flux (osher_flux_pair).
 // ---------------------------------------------------------------------------
-struct GlobalSrc {
-    const MixedArgs &a;
-    const float4 *d0;
-    __device__ __forceinline__ void cell(int, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
-                                         float &q1, float &q2, float &rr) const {
-        const float4 e = d0[g], q = __ldg(a.qn + g);
-        e0 = e.x; e1 = e.y; e2 = e.z; p0 = e.w;
-        q0 = q.x; q1 = q.y; q2 = q.z; rr = q.w;
-    }
-};
-
 __device__ __forceinline__ float4 shfl_down4(const float4 &v, int d) {
     return make_float4(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
                        __shfl_down_sync(0xffffffffu, v.z, d), __shfl_down_sync(0xffffffffu, v.w, d));
