@@ -482,8 +482,8 @@ MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
 # 2048x8192 tank, profiles/sweep_kernel_mixed_rayleigh_taylor_2048x8192.md):
 # DRAM bytes and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2
 # forms counted as two) per cell of one stage launch
-MIXED_TRAFFIC_PER_CELL_STAGE = 68.2
-MIXED_FP32_OPS_PER_CELL_STAGE = 474.4
+MIXED_TRAFFIC_PER_CELL_STAGE = 68.0
+MIXED_FP32_OPS_PER_CELL_STAGE = 472.1
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
