@@ -293,15 +293,16 @@ stage_kernel(const SweepArgs<T> a) {
         if (a.gradp == kGradNew) {
             // Eq. new_gradp times dx, with dx d_x rho = srx etc.
             const int gi = x0 + li - 1, gj = y0 + lj - 1;
-            const T sg = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc);
             const T rho = R[c], u = U[c], v = V[c];
+            // the body force with gravity reversed in wall ghosts: a sign, not a product
+            const T rho_g = wall_ghost_sign<T>(gi, gj, nx, ny, a.bc) < T(0) ? -rho : rho;
             const T rtx = need_rt ? sm.rt[0][k] : T(0);
             const T rty = need_rt ? sm.rt[1][k] : T(0);
             const T ru = rho * u, rv = rho * v, uv = u * v;
-            spx = -a.dx * rtx - (u * u * srx + T(2) * ru * sux) -
-                  a.dx_over_dy * (uv * sry + ru * svy + rv * suy) + a.dx * rho * a.gx * sg;
-            spy = -a.dy * rty - (v * v * sry + T(2) * rv * svy) -
-                  a.dy_over_dx * (uv * srx + rv * sux + ru * svx) + a.dy * rho * a.gy * sg;
+            spx = a.dx * fma(rho_g, a.gx, -rtx) - (u * u * srx + T(2) * ru * sux) -
+                  a.dx_over_dy * (uv * sry + ru * svy + rv * suy);
+            spy = a.dy * fma(rho_g, a.gy, -rty) - (v * v * sry + T(2) * rv * svy) -
+                  a.dy_over_dx * (uv * srx + rv * sux + ru * svx);
         } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
             // Qian et al. split (Sec. 2.3.2): limit the kinematic part of the
             // one-sided pressure differences, add the cell's hydrostatic
