@@ -462,10 +462,10 @@ def run_batched(args, stream, flush, barrier):
 # counted by ncu on stage_kernel<double,32,14> on this 256x256 tank
 # (profiles/stage_kernel_f64_hydrostatic_256.md), averaged over the three
 # stages of a pseudo-iteration (stage 1 also forms the local dtau and the
-# real-time terms that stages 2 and 3 read back: 764.7, 662.7, 662.7), and
-# the FP64 instructions (DFMA + DADD + DMUL) behind them (537.8, 462.3, 462.3)
-FP64_FLOPS_PER_CELL_STAGE = 696.7
-FP64_INSTR_PER_CELL_STAGE = 487.5
+# real-time terms that stages 2 and 3 read back: 760.9, 658.9, 658.9), and
+# the FP64 instructions (DFMA + DADD + DMUL) behind them (534.0, 458.6, 458.6)
+FP64_FLOPS_PER_CELL_STAGE = 692.9
+FP64_INSTR_PER_CELL_STAGE = 483.7
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
 # the three stages (3.74, 6.36, 6.36 MB read; the output stays in L2)
