@@ -34,6 +34,21 @@ def fd_jacobian(Q, beta, h=1e-6):
     return np.array(cols).T
 
 
+def numpy_osher(QL, QR, beta):
+    """The Osher flux as a path integral built from numpy alone: |A| from
+    np.linalg.eig of the finite-difference Jacobian at the leggauss nodes of the
+    straight path in Q."""
+    x, w = np.polynomial.legendre.leggauss(3)
+    dQ = QR - QL
+    S = np.zeros((5, 5))
+    for xj, wj in zip(x, w):
+        Qj = QL + dQ * 0.5 * (xj + 1.0)
+        J = fd_jacobian(Qj, beta, h=1e-7)
+        ev, V = np.linalg.eig(J)
+        S += wj * (V @ np.diag(np.abs(ev)) @ np.linalg.inv(V)).real
+    return 0.5 * (oracle.flux_x(QL, beta) + oracle.flux_x(QR, beta)) - 0.5 * (0.5 * S @ dQ)
+
+
 # ----------------------------------------------------------------- eigenstructure
 
 def test_golden_tables_match_workloads():
@@ -81,19 +96,10 @@ def test_osher_equals_numpy_path_quadrature():
     |A| from np.linalg.eig of the finite-difference Jacobian, nodes/weights
     from leggauss, straight path in Q.  Catches a wrong 1/2 factor, wrong
     nodes or weights, or a wrong matrix-vector order."""
-    x, w = np.polynomial.legendre.leggauss(3)
     for _ in range(20):
         QL, beta = rand_state()
         QR, _ = rand_state()
-        dQ = QR - QL
-        S = np.zeros((5, 5))
-        for xj, wj in zip(x, w):
-            Qj = QL + dQ * 0.5 * (xj + 1.0)
-            # exact Jacobian from FD with tight step, then |A| by eigen-decomposition
-            J = fd_jacobian(Qj, beta, h=1e-7)
-            ev, V = np.linalg.eig(J)
-            S += wj * (V @ np.diag(np.abs(ev)) @ np.linalg.inv(V)).real
-        expect = 0.5 * (oracle.flux_x(QL, beta) + oracle.flux_x(QR, beta)) - 0.5 * (0.5 * S @ dQ)
+        expect = numpy_osher(QL, QR, beta)
         got = oracle.riemann_flux("osher", QL, QR, beta)
         assert np.allclose(got, expect, rtol=1e-6, atol=1e-6)
 
@@ -346,6 +352,42 @@ def test_point_implicit_iteration_closed_form():
     # and the fixed point is the Backward-Euler step of d(rho u)/dt = rho g
     st, *_ = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=300)
     assert st[1][0, 0] == pytest.approx(c.dt * rho * c.gx, rel=1e-12)
+
+
+def test_residual_norms_of_a_velocity_step():
+    """Alg. 1: the residual of a pseudo-iteration is the root mean square over
+    the cells of the stage-1 bracket, the pressure row in pressure units (beta
+    times the p/beta row).  A periodic box holds two bands of uniform fluid
+    moving at u1 and u2, two cells wide or more: every minmod slope is zero and
+    so is the new pressure gradient (no gravity, no real-time term at the first
+    iteration), so each face carries F(Q) of its uniform side (consistency)
+    except the two faces at the jumps, whose flux comes from numpy_osher.  The
+    bracket is then nonzero only in the four cells beside the jumps.  Catches
+    a residual taken as a sum instead of a mean, without the square root, after
+    the update instead of before it, or a pressure row not scaled by beta."""
+    nx, ny, rho, p, u1, u2 = 8, 3, 1.3, 0.4, 0.6, -0.25
+    c = _uniform_case(nx, ny, 0.0, 0.0)
+    c.beta = 2.5
+    c.dt = 1.0
+    u = np.where(np.arange(nx) < nx // 2, u1, u2)[None, :].repeat(ny, axis=0)
+    c.rho = np.full((ny, nx), rho)
+    c.rhou = rho * u
+    c.rhov = np.zeros((ny, nx))
+    c.p = np.full((ny, nx), p)
+    st, status, its, R, R0 = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=1)
+    assert its == 1
+    Q1 = np.array([rho, rho * u1, 0.0, 0.0, p / c.beta])
+    Q2 = np.array([rho, rho * u2, 0.0, 0.0, p / c.beta])
+    Fa, Fb = numpy_osher(Q1, Q2, c.beta), numpy_osher(Q2, Q1, c.beta)
+    F1, F2 = oracle.flux_x(Q1, c.beta), oracle.flux_x(Q2, c.beta)
+    # cells nx/2-1 and nx/2 beside the face u1|u2, cells nx-1 and 0 beside u2|u1
+    b = np.array([-(Fa - F1), -(F2 - Fa), -(Fb - F2), -(F1 - Fb)]) / c.dx
+    rows = [0, 1, 2, 4]
+    expect = np.sqrt((b[:, rows] ** 2).sum(axis=0) * ny / (nx * ny))
+    expect[3] *= c.beta
+    assert np.allclose(R, expect, rtol=1e-6, atol=1e-12)
+    assert np.allclose(R0, expect, rtol=1e-6, atol=1e-12)
+    assert expect[0] > 0 and expect[1] > 0 and expect[3] > 0
 
 
 def test_dtau_is_the_acoustic_cfl_limit():
