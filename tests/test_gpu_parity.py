@@ -35,7 +35,7 @@ def run_both(case, steps=1, tol=None, max_iters=None):
         got = t.get_state()
         R, R0 = t.residual_norms()
         ref, st, oits, oR, oR0 = oracle.physical_step(case, state, tol=tol, max_iters=max_iters)
-        out.append((got, ref, rc, its, st, oits, R, oR))
+        out.append((got, ref, rc, its, st, oits, R, oR, R0, oR0))
         state = ref
     t.close()
     return out
@@ -54,7 +54,7 @@ def norm_atol(ref, case):
 
 
 def assert_parity(res, tol=TOL, check_iters=True, case=None):
-    for got, ref, rc, its, st, oits, R, oR in res:
+    for got, ref, rc, its, st, oits, R, oR, R0, oR0 in res:
         errs = rel_errors(got, ref)
         assert max(errs) <= tol, errs
         if check_iters:
@@ -62,6 +62,7 @@ def assert_parity(res, tol=TOL, check_iters=True, case=None):
             assert rc == st, (rc, st)
         atol = norm_atol(ref, case) if case is not None else 0.0
         assert np.all(np.abs(R - oR) <= 1e-9 * np.abs(oR) + atol), (R, oR, atol)
+        assert np.all(np.abs(R0 - oR0) <= 1e-9 * np.abs(oR0) + atol), (R0, oR0, atol)
 
 
 def test_riemann_200x4_converged_steps():
@@ -165,7 +166,7 @@ def test_degenerate_grids(nx, ny):
 def test_not_converged_status():
     case = W.riemann_tank()
     res = run_both(case, steps=1, tol=1e-14, max_iters=3)
-    got, ref, rc, its, st, oits, R, oR = res[0]
+    got, ref, rc, its, st, oits, R, oR, R0, oR0 = res[0]
     assert rc == ac.AC_NOT_CONVERGED and its == 3 and st == oracle.NOT_CONVERGED
     assert_parity(res, case=case)
 
