@@ -334,16 +334,18 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
 // turn.  Every operation of the flux is then a packed one (the reciprocal
 // and reciprocal square root excepted) and no lane sums are needed.  Same
 // quadrature and terms as osher_flux, per lane; the weight of a point rides
-// on k = w rho / c.  Inputs are (rho, un, ut, p) per lane, output as
-// osher_flux per lane.
+// on k = w rho / c (1/beta stays on the jump term, where it costs no
+// register held across a caller's loop).  Inputs are (rho, un, ut, p) per
+// lane; returns 2F per lane (the caller's divergence takes the 1/2).
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
 
 __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL, float2 pL, float2 rR, float2 uR,
                                                 float2 vR, float2 pR, float beta, float inv_beta, float2 F[4]) {
     const float2 ib = dup2(inv_beta);
-    const float2 mL = __fmul2_rn(rL, uL), nL = __fmul2_rn(rL, vL), qL = __fmul2_rn(pL, ib);
-    const float2 mR = __fmul2_rn(rR, uR), nR = __fmul2_rn(rR, vR), qR = __fmul2_rn(pR, ib);
-    const float2 dr = sub2(rR, rL), dm = sub2(mR, mL), dn = sub2(nR, nL), dq = sub2(qR, qL);
+    const float2 mL = __fmul2_rn(rL, uL), nL = __fmul2_rn(rL, vL);
+    const float2 mR = __fmul2_rn(rR, uR), nR = __fmul2_rn(rR, vR);
+    const float2 dr = sub2(rR, rL), dm = sub2(mR, mL), dn = sub2(nR, nL), dp = sub2(pR, pL);
+    const float2 dq = __fmul2_rn(dp, ib);   // the jump of Q's last component p/beta
     const float2 ndr = neg2(dr);
     // central parts F(Q_L) + F(Q_R) first, so that the face states die here
     const float2 c0 = __fadd2_rn(mL, mR);
@@ -390,12 +392,11 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
             Sh = __fadd2_rn(Sh, h);
         }
     }
-    const float2 half = dup2(0.5f);
-    // F = 1/2 (F(Q_L) + F(Q_R) - D), D as in osher_flux
-    F[0] = __fmul2_rn(half, sub2(c0, __ffma2_rn(dr, Sau, Se)));
-    F[1] = __fmul2_rn(half, sub2(c1, __ffma2_rn(dup2(beta), Sg, __ffma2_rn(dm, Sau, Sue))));
-    F[2] = __fmul2_rn(half, sub2(c2c, __ffma2_rn(dn, Sau, Sve)));
-    F[3] = __fmul2_rn(half, sub2(c3, sub2(__fmul2_rn(dq, Sau), Sh)));
+    // 2F = F(Q_L) + F(Q_R) - D, D as in osher_flux
+    F[0] = sub2(c0, __ffma2_rn(dr, Sau, Se));
+    F[1] = sub2(c1, __ffma2_rn(dup2(beta), Sg, __ffma2_rn(dm, Sau, Sue)));
+    F[2] = sub2(c2c, __ffma2_rn(dn, Sau, Sve));
+    F[3] = sub2(c3, sub2(__fmul2_rn(dq, Sau), Sh));
 }
 
 // Face flux of the solver RS, chosen at compile time so that a kernel built

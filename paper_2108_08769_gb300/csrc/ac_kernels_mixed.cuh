@@ -164,18 +164,19 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 
 // Divergence, sources and the point-implicit update of one cell (Eqs. RK2,
 // point_implicit): writes dQ^s and p'^s at g and adds the stage-1 squared
-// bracket to sq.  Fw, Fe, Fs, Fn: face fluxes; jw, je: reference jumps of
-// the west and east faces; src.cell(cell, g, ...) gives dQ^{m}, p'^{m}, Q^n
-// and rho_ref of the cell.
+// bracket to sq.  Fw, Fe, Fs, Fn: face fluxes, scaled by s_f (1 or 2), and
+// fdx, fdy = 1/(s_f dx), 1/(s_f dy); jw, je: reference jumps of the west and
+// east faces; src.cell(cell, g, ...) gives dQ^{m}, p'^{m}, Q^n and rho_ref
+// of the cell.
 template <bool BDF, typename Src>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
-                                            const float4 &Fs, const float4 &Fn, float jw, float je, const Src &src,
-                                            float4 &sq) {
-    const float div0 = (Fe.x - Fw.x) * a.inv_dx + (Fn.x - Fs.x) * a.inv_dy;
-    const float div1 = (Fe.y - Fw.y) * a.inv_dx + (Fn.y - Fs.y) * a.inv_dy;
-    const float div2 = (Fe.z - Fw.z) * a.inv_dx + (Fn.z - Fs.z) * a.inv_dy;
-    const float div3 = (Fe.w - Fw.w) * a.inv_dx + (Fn.w - Fs.w) * a.inv_dy;
+                                            const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
+                                            float je, const Src &src, float4 &sq) {
+    const float div0 = (Fe.x - Fw.x) * fdx + (Fn.x - Fs.x) * fdy;
+    const float div1 = (Fe.y - Fw.y) * fdx + (Fn.y - Fs.y) * fdy;
+    const float div2 = (Fe.z - Fw.z) * fdx + (Fn.z - Fs.z) * fdy;
+    const float div3 = (Fe.w - Fw.w) * fdx + (Fn.w - Fs.w) * fdy;
     float e0, e1, e2, p0, q0, q1, q2, rref;
     src.cell(cell, g, e0, e1, e2, p0, q0, q1, q2, rref);
     const float r0 = q0 + e0;
@@ -389,7 +390,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         const int g = gj * nx + gi;
         const int fw = lj * (TX + 1) + li;
         cell_update<BDF>(a, alpha, inv_dt, stage == 1, dout, cell, g, sm.fx[fw], sm.fx[fw + 1], sm.fy[cell],
-                         sm.fy[cell + TX], sm.dxf[fw], sm.dxf[fw + 1], src, sq);
+                         sm.fy[cell + TX], a.inv_dx, a.inv_dy, sm.dxf[fw], sm.dxf[fw + 1], src, sq);
     }
     if (stage == 1) {
         // per-warp sums in FP32, block and grid sums in FP64
@@ -565,7 +566,7 @@ stage_kernel_mixed(const MixedArgs a) {
 // 0, 1, 30, 31 are halo (their slopes or fluxes feed the output lanes'
 // faces).  Every per-cell value uses the same functions as the tile sweep;
 // a lane's x- and y-face fluxes go through the face-pair form of the Osher
-// flux (osher_flux_pair).
+// flux (osher_flux_pair), which returns 2F.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float4 shfl_down4(const float4 &v, int d) {
     return make_float4(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
@@ -615,6 +616,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     int nfx, tfx;
     const int scol = fold_axis(c, nx, a.bc[0], a.bc[1], nfx, tfx);
     const bool out_lane = lane >= 2 && lane < 30 && c < nx;
+    // the face pairs come as 2F: (2Fe - 2Fw) (1/(2 dx)) is (Fe - Fw)/dx exactly
+    const float hidx = 0.5f * a.inv_dx, hidy = 0.5f * a.inv_dy;
 
     // raw inputs of a row, loaded one row ahead of use
     struct Raw {
@@ -718,7 +721,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
-                                           Fy, jw, Jm2, Uk, sq);
+                                           Fy, hidx, hidy, jw, Jm2, Uk, sq);
                 }
                 Fyp = Fy;
             }
