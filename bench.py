@@ -336,7 +336,8 @@ def run_ours(args, ws, rank, local):
         ft.close()
         l_value = ws * lc.cells * sum(l_iters) / (l_ms * 1e-3)
         gbs = MIXED_BYTES_PER_CELL_ITER / 3.0 * lc.cells / l_launch_s / 1e9
-        ops = MIXED_FP32_OPS_PER_CELL_STAGE * lc.cells / l_launch_s / 1e12
+        l_traffic, l_ops = MIXED_COUNTS_BY_VARIANT.get(lv, (None, None))
+        ops = None if l_ops is None else l_ops * lc.cells / l_launch_s / 1e12
         large = {"workload": "Rayleigh-Taylor tank 2048x8192 (1x4 m, rho 3 over 1, cosine interface, slip walls, "
                              "c0=10 m/s, dt=5e-4 s, 1e-8 drop or 500 pseudo-iterations), mixed form",
                  "value": l_value, "unit": UNIT, "steps": lk, "ms_per_step": l_ms / lk,
@@ -347,11 +348,11 @@ def run_ours(args, ws, rank, local):
                                          else f"stage_kernel_mixed<{ltx},{lty},{lnt}>"), "tile_variant": lv,
                               "launch_ms": l_launch_s * 1e3,
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
-                              "traffic": MIXED_TRAFFIC_PER_CELL_STAGE * lc.cells,
-                              "alu_frac": ops / FP32_PEAK_TOPS,
-                              "alu_note": f"{MIXED_FP32_OPS_PER_CELL_STAGE:.0f} FP32 arithmetic operations per "
-                                          f"cell-stage (ncu) against {FP32_PEAK_TOPS:.1f} T/s (128 lanes/SM x 152 SMs "
-                                          "x 2.07 GHz)"},
+                              "traffic": None if l_traffic is None else l_traffic * lc.cells,
+                              "alu_frac": None if ops is None else ops / FP32_PEAK_TOPS,
+                              "alu_note": (f"{l_ops:.0f} FP32 arithmetic operations per cell-stage (ncu) against "
+                                           f"{FP32_PEAK_TOPS:.1f} T/s (128 lanes/SM x 152 SMs x 2.07 GHz)"
+                                           if l_ops is not None else "no ncu count for this variant")},
                  "error_vs_fp64_gpu": field_errors(lm_state, lf_state)}
 
     # ---- many tanks in one batch vs the same tanks run one after another ----
@@ -478,12 +479,16 @@ BYTES_PER_CELL_ITER_F64 = 376.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, sweep_kernel_mixed<256,4>, the tuned kernel on this
-# 2048x8192 tank, profiles/sweep_kernel_mixed_rayleigh_taylor_2048x8192.md):
-# DRAM bytes and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2
-# forms counted as two) per cell of one stage launch
-MIXED_TRAFFIC_PER_CELL_STAGE = 68.0
-MIXED_FP32_OPS_PER_CELL_STAGE = 472.1
+# measured (ncu, one stage-2 launch on this 2048x8192 tank,
+# profiles/sweep_kernel_mixed_rayleigh_taylor_2048x8192.md) for the strip
+# variants the autotuner picks there: DRAM bytes and FP32 arithmetic
+# operations (FFMA, FADD, FMUL; packed FP32x2 forms counted as two) per cell
+# of one stage launch.  64-row strips re-read more halo rows than 256-row
+# ones.  A variant without a capture of its current code reports null.
+MIXED_COUNTS_BY_VARIANT = {
+    16: (71.0, 474.4),   # sweep_kernel_mixed<64,4>
+    18: (68.1, 464.7),   # sweep_kernel_mixed<256,4>
+}
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
