@@ -43,7 +43,8 @@ extern "C" {
 #define AC_ERR_ARG (-1)       /* invalid argument (sizes, kinds, NULL, beta <= 0, ...) */
 #define AC_ERR_CUDA (-2)      /* a CUDA runtime call failed */
 #define AC_ERR_NONFINITE (-3) /* a residual norm or an input became NaN/Inf */
-#define AC_ERR_TIMEOUT (-4)   /* a bounded device wait gave up */
+#define AC_ERR_TIMEOUT (-4)   /* reserved for a bounded device wait that gives up; no kernel here waits
+                                 on another (every CTA is independent), so no call returns it */
 #define AC_ERR_OOM (-5)       /* device allocation failed */
 #define AC_ERR_STATE (-6)     /* call out of order (e.g. a step before ac_set_state) */
 
