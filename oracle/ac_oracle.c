@@ -36,7 +36,9 @@
  *  R8  Residual: RMS over interior cells of the stage-1 bracket (the unsteady
  *      residual at Q^{m}); pressure row in Pa/s (times beta).  Converged when
  *      every field has R_k <= max(tol*R0_k, abs_tol_k), R0 being the first
- *      iteration's norm.  tol < 0 disables the test.         [parity unpinned]
+ *      iteration's norm.  tol < 0 disables the test.  The reading is a
+ *      convention; its implementation here is pinned by closed forms (a
+ *      velocity step's bracket; the uniform gravity box's iteration count).
  *  R9  The stored state holds p; the Riemann solvers use p/beta as the fifth
  *      conserved component (Sec. 2.1.2).
  *  R10 Ghost cells: two layers.  A wall ghost mirrors the interior cell at the

@@ -390,6 +390,54 @@ def test_residual_norms_of_a_velocity_step():
     assert expect[0] > 0 and expect[1] > 0 and expect[3] > 0
 
 
+def _gravity_box_iterates(c, rho, iters):
+    """Momenta x_m of the uniform gravity box after m pseudo-iterations and
+    the residuals R_m of iteration m, from the closed-form recurrence of
+    test_point_implicit_iteration_closed_form (bracket rho g - x_{m-1}/dt at
+    the start of iteration m, taken by the last stage with alpha = 1)."""
+    x = np.zeros(2)
+    g = np.array([c.gx, c.gy])
+    xs, Rs = [], []
+    for _ in range(iters):
+        Rs.append(np.abs(rho * g - x / c.dt))
+        cur = (np.full((4, 4), rho), np.full((4, 4), x[0]), np.full((4, 4), x[1]), np.full((4, 4), 0.25))
+        dtau = oracle.dtau(c, cur)[0, 0]
+        x = x + dtau / (1.0 + dtau / c.dt) * (rho * g - x / c.dt)
+        xs.append(x.copy())
+    return xs, Rs
+
+
+@pytest.mark.parametrize("tol, floor", [(1e-3, 0.0), (1e-12, 0.05)])
+def test_stopping_test_closed_form(tol, floor):
+    """Alg. 1 with the residual reading: the step stops after the first
+    pseudo-iteration m whose residual satisfies R_k <= max(tol R^1_k,
+    abs_tol_k) for every field, R^1 being the first iteration's, and returns
+    the state after that iteration's update.  In the uniform gravity box the
+    density and pressure rows have zero residual and the momentum rows decay
+    by the closed-form recurrence, so m, the state and both norms are known.
+    The second case stops on the absolute floor.  Catches a test against the
+    previous iteration's norm instead of the first, a test taken before the
+    iteration's update, a floor ignored, or R0 not the first iteration's."""
+    c = _uniform_case(4, 4, 0.0, 0.0)
+    c.gx, c.gy = 0.7, -0.3
+    c.dt = 0.05
+    c.options.abs_tol = (0.0, floor, floor, 0.0)
+    rho = 1.7
+    xs, Rs = _gravity_box_iterates(c, rho, 400)
+    thr = np.maximum(tol * Rs[0], floor)
+    m = next(i for i, R in enumerate(Rs) if np.all(R <= thr)) + 1
+    # the count is robust to round-off: no residual sits within 1e-9 of the threshold
+    assert all(np.all(np.abs(R - thr) > 1e-9 * thr) for R in Rs[:m])
+    assert m > 3
+    st, status, its, R, R0 = oracle.physical_step(c, c.state(), tol=tol, max_iters=500)
+    assert (status, its) == (0, m)
+    assert st[1][0, 0] == pytest.approx(xs[m - 1][0], rel=1e-12)
+    assert st[2][0, 0] == pytest.approx(xs[m - 1][1], rel=1e-12)
+    assert np.allclose(R[1:3], Rs[m - 1], rtol=1e-10, atol=0)
+    assert np.allclose(R0[1:3], Rs[0], rtol=1e-12, atol=0)
+    assert R[0] == 0.0 and R[3] == 0.0
+
+
 def test_dtau_is_the_acoustic_cfl_limit():
     """Sec. 2.2.3: the local pseudo-time step makes the fastest x and y waves
     together cross CFL_tau cells, dtau (rho(A_x)/dx + rho(A_y)/dy) = CFL_tau,
