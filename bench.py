@@ -31,6 +31,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -84,7 +85,9 @@ class Clocks:
 
     def __init__(self, index):
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples beside the run (AC_BENCH_CLOCKS_DIR), else in the temporary directory
+        self.path = os.path.join(os.environ.get("AC_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"ac_bench_clocks_{os.getpid()}.csv")
         self.proc = None
 
     def __enter__(self):
@@ -460,8 +463,8 @@ def run_batched(args, stream, flush, barrier):
 
 
 # FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
-# counted by ncu on stage_kernel<double,32,14> on this 256x256 tank
-# (profiles/stage_kernel_f64_hydrostatic_256.md), averaged over the three
+# counted by ncu on stage_kernel<double,32,14> on this 256x256 tank (the
+# summary is under profiles/), averaged over the three
 # stages of a pseudo-iteration (stage 1 also forms the local dtau and the
 # real-time terms that stages 2 and 3 read back: 760.9, 658.9, 658.9), and
 # the FP64 instructions (DFMA + DADD + DMUL) behind them (534.0, 458.6, 458.6)
@@ -479,8 +482,8 @@ BYTES_PER_CELL_ITER_F64 = 376.0
 # mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
 # (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
 MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, one stage-2 launch on this 2048x8192 tank,
-# profiles/sweep_kernel_mixed_rayleigh_taylor_2048x8192.md) for the strip
+# measured (ncu, one stage-2 launch on this 2048x8192 tank, summarised
+# under profiles/) for the strip
 # variants the autotuner picks there: DRAM bytes and FP32 arithmetic
 # operations (FFMA, FADD, FMUL; packed FP32x2 forms counted as two) per cell
 # of one stage launch.  64-row strips re-read more halo rows than 256-row

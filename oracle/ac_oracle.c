@@ -16,7 +16,7 @@
  * matrices R_x and L_x, the face rotation R) the oracle builds that matrix and
  * multiplies by it, even where a cheaper closed form exists.
  *
- * Readings of points the paper leaves open (each is also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  R1  beta is in pressure units (Sec. 2.1.3: c = sqrt(u^2 + 4 beta/rho)).
  *  R2  MUSCL one-sided differences are divided by dx (the printed "dx/2" would
  *      double every slope), and the face sits at x_i +- dx/2 (Eqs. muscl1-2,
