@@ -534,8 +534,9 @@ def run_configs(args, rank, local):
             t.set_stream(stream.cuda_stream)
             t.physical_step(case.dt, -1.0, iters)          # warm-up (tuning)
             t.set_state(*case.state())
-            ms, its, _ = timed_steps(t, case, args.steps, stream, flush, torch.cuda.synchronize, tol=-1.0,
-                                     max_iters=iters)
+            with Clocks(local) as clk:
+                ms, its, _ = timed_steps(t, case, args.steps, stream, flush, torch.cuda.synchronize, tol=-1.0,
+                                         max_iters=iters)
             t.set_state(*case.state())
             t.physical_step(case.dt, -1.0, iters)
             states[prec] = t.get_state()
@@ -543,7 +544,7 @@ def run_configs(args, rank, local):
             t.close()
             val = case.cells * sum(its) / (ms * 1e-3)
             line[prec] = {"value": val, "hbm_frac_of_measured": val * bpc / 1e9 / measured_hbm_gbs(),
-                          "tile": [tx, ty, nt], "tile_variant": v}
+                          "tile": [tx, ty, nt], "tile_variant": v, "clocks": clk.summary()}
         line["mixed"]["speedup_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
         line["mixed"]["error_vs_fp64_gpu"] = field_errors(states["mixed"], states["fp64"])
         oc = sample_fn() if sample_fn else case
