@@ -115,7 +115,9 @@ double ac_beta_from_speed(double c0, double rho_ref);
 /* Create a context for one tank.  grid, bc must be non-NULL; fluids may be
  * NULL (when given, ac_set_state rejects densities outside
  * [rho_light/2, 2 rho_heavy]); opt may be NULL (defaults).  beta > 0 in Pa
- * (Eq. AC_end).  Allocates the device state on the current device.
+ * (Eq. AC_end).  Allocates the device state on the current device.  Cells
+ * are indexed with 32-bit integers on the device: nx*ny may not exceed 2^31
+ * (AC_ERR_ARG).
  * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA.  *out is NULL on error. */
 int ac_create(const ac_grid *grid, const ac_fluids *fluids, double beta, const ac_bc *bc,
               const ac_options *opt, ac_ctx **out);
@@ -204,13 +206,17 @@ int ac_tile_shape(const ac_ctx *ctx, int *tx, int *ty, int *threads, int *varian
  * physical step is one graph launch whose WHILE loop runs until every tank
  * has stopped.  The tile shape (cells per CTA, threads per CTA) is chosen by
  * timing every compiled shape on the batch at its first step.
- * The tanks' own numbers do not depend on the rest of the batch: with the
- * same tile shape they equal a single-tank context's bit for bit. */
+ * The tanks' own numbers do not depend on the rest of the batch.  With the
+ * column-strip sweep they equal a single-tank context's bit for bit; with
+ * the tile sweep (a separately compiled kernel, whose multiply-adds the
+ * compiler may contract differently) they agree with it to round-off. */
 typedef struct ac_batch ac_batch;
 
-/* grids[n], beta[n] (Pa) and bcs[n] describe the tanks; opt (may be NULL)
- * applies to all of them and must select AC_PREC_MIXED and the local
- * pseudo-time step.  Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA. */
+/* grids[n], beta[n] (Pa) and bcs[n] describe the tanks, 1 <= n <= 65535;
+ * opt (may be NULL) applies to all of them and must select AC_PREC_MIXED and
+ * the local pseudo-time step.  The tanks together may hold at most 2^31
+ * cells (each rounded up to its aligned slot).
+ * Errors: AC_ERR_ARG, AC_ERR_OOM, AC_ERR_CUDA. */
 int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc *bcs, const ac_options *opt,
                     ac_batch **out);
 void ac_batch_destroy(ac_batch *b);

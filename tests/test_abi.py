@@ -48,6 +48,7 @@ def test_default_options_and_beta_helper():
     (dict(beta=-1.0), "beta"),
     (dict(bc=("periodic", "slip", "slip", "slip")), "periodic"),
     (dict(lx=0.0), "lx"),
+    (dict(nx=65536, ny=32769), "2^31"),
 ])
 def test_create_rejects_bad_arguments_before_touching_the_gpu(kw, fragment):
     args = dict(nx=8, ny=8, lx=1.0, ly=1.0, gx=0.0, gy=-9.81, beta=1e3, bc=("slip",) * 4)
@@ -64,3 +65,32 @@ def test_create_rejects_bad_options():
     with pytest.raises(ac.ACError) as e:
         ac.Tank(8, 8, 1.0, 1.0, 0.0, -9.81, 1e3, ("slip",) * 4, options=o)
     assert e.value.code == ac.AC_ERR_ARG
+
+
+def _tank_stub(nx=8, ny=8, beta=1e3, bc=("slip",) * 4, **opt):
+    from types import SimpleNamespace
+    from paper_2108_08769_gb300 import workloads as W
+    return SimpleNamespace(nx=nx, ny=ny, lx=1.0, ly=1.0, gx=0.0, gy=-9.81, beta=beta, bc=bc,
+                           options=W.Options(**opt))
+
+
+@pytest.mark.parametrize("cases,fragment", [
+    ([], "1..65535"),
+    ([_tank_stub(), _tank_stub(nx=0)], "tank 1: invalid grid"),
+    ([_tank_stub(beta=0.0)], "beta"),
+    ([_tank_stub(bc=("slip", "slip", "periodic", "slip"))], "periodic"),
+    ([_tank_stub(local_dtau=False)], "local pseudo-time step"),
+    ([_tank_stub(nx=46341, ny=46341)], "2^31"),
+    ([_tank_stub(nx=32768, ny=32768), _tank_stub(nx=32768, ny=32768), _tank_stub()], "2^31"),
+])
+def test_batch_create_rejects_bad_arguments_before_touching_the_gpu(cases, fragment):
+    """ac_batch_create checks every tank and the batch's total size before
+    any device call (no GPU here)."""
+    if not cases:
+        with pytest.raises(ac.ACError) as e:
+            ac._check(ac.load().ac_batch_create(0, None, None, None, None, ac.C.byref(ac.C.c_void_p())))
+    else:
+        with pytest.raises(ac.ACError) as e:
+            ac.Batch(cases)
+    assert e.value.code == ac.AC_ERR_ARG
+    assert fragment in str(e.value)
