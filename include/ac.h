@@ -192,8 +192,10 @@ int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launche
  * (AC_ERR_STATE before it): tile width tx, height ty, threads per CTA and
  * the variant's index in the library's table.  Setting the environment
  * variable AC_TILE (mixed form) or AC_TILE_F64 (FP64) to an index before the
- * first step forces that variant; other solvers than Osher and BDF2/BDF3
- * always run variant 0. */
+ * first step forces that variant.  The Bassi and Roe fluxes always run
+ * variant 0, and so does BDF2/BDF3 in the mixed form; the mixed form's
+ * column-strip variants implement the new pressure gradient only and are
+ * replaced by variant 0 for the others. */
 int ac_tile_shape(const ac_ctx *ctx, int *tx, int *ty, int *threads, int *variant);
 
 /* ---- many tanks at once (mixed form) -------------------------------------
