@@ -402,8 +402,10 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
 // Face flux of the solver RS, chosen at compile time so that a kernel built
 // for one solver carries none of the others' registers.  The FP32 Osher flux
 // of one face is always the packed form above, so every FP32 tile sweep (any
-// tile shape, single tank or batch) computes a face bit for bit the same way;
-// the column-strip sweep takes its faces in pairs (osher_flux_pair).
+// tile shape, single tank or batch) evaluates a face's flux with the same
+// rounded operations (the face states around it are plain arithmetic that
+// the compiler may contract differently in different kernels); the
+// column-strip sweep takes its faces in pairs (osher_flux_pair).
 // With TWICE (FP64 only) every solver returns 2F.
 template <int RS, typename T, bool TWICE = false>
 __device__ __forceinline__ void riemann_flux(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T beta,
