@@ -149,6 +149,38 @@ def cpu_baseline_sample(case, iters=10):
                       f"({dt:.1f} s, FP64 C oracle, 1 thread)"}
 
 
+def _oracle_worker(workload, iters, barrier):
+    """One copy of the oracle in its own process (all-core baseline)."""
+    case, _ = make_case(workload)
+    import oracle
+    oracle.build()
+    state = case.state()
+    barrier.wait()
+    t0 = time.perf_counter()
+    _, _, its, _, _ = oracle.physical_step(case, state, tol=-1.0, max_iters=iters)
+    return t0, time.perf_counter(), case.cells * its
+
+
+def cpu_baseline_all_cores(workload, iters=10):
+    """The same oracle sample run as one copy per host core, in processes
+    started with spawn (no GPU context is inherited): all copies' cell
+    pseudo-iterations over the span from the first start to the last
+    finish."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(n)
+        with ctx.Pool(n) as pool:
+            res = pool.starmap(_oracle_worker, [(workload, iters, barrier)] * n)
+    span = max(r[1] for r in res) - min(r[0] for r in res)
+    work = sum(r[2] for r in res)
+    case, _ = make_case(workload)
+    return {"value": work / span, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} processes, each 1 physical step x {iters} pseudo-iterations on the full "
+                      f"{case.nx}x{case.ny} tank ({span:.1f} s wall, FP64 C oracle, 1 thread each)"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -381,6 +413,7 @@ def run_ours(args, ws, rank, local):
         line["batched"] = batched
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline_sample(case)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
     print(json.dumps(line), flush=True)
 
 

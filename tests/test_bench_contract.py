@@ -61,3 +61,14 @@ def test_reference_arm_under_two_ranks_prints_once():
     lines = json_lines(r.stdout)
     assert len(lines) == 1
     check_line(lines[0], 2)
+
+
+def test_all_core_oracle_baseline():
+    """One oracle copy per host core in spawned processes: the baseline
+    object names the cores used and the sample, and the rate is positive."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_baseline_all_cores("hydrostatic_256", iters=1)
+    assert r["kind"] == "oracle" and r["unit"] == "cell-iter/s"
+    assert r["cores"] == (os.cpu_count() or 1) and r["value"] > 0
+    assert f"{r['cores']} processes" in r["sample"]
