@@ -135,6 +135,21 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def host_cpu():
+    """Host CPU model and core count, as lscpu reports them."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.startswith("Model name:"):
+                model = l.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return f"{model or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} cores)"
+
+
 def cpu_baseline_sample(case, iters=10):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample:
     one physical step of the same tank with a fixed number of iterations."""
@@ -144,7 +159,7 @@ def cpu_baseline_sample(case, iters=10):
     t0 = time.perf_counter()
     _, st, its, _, _ = oracle.physical_step(case, state, tol=-1.0, max_iters=iters)
     dt = time.perf_counter() - t0
-    return {"value": case.cells * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": case.cells * its / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"1 physical step x {its} pseudo-iterations on the full {case.nx}x{case.ny} tank "
                       f"({dt:.1f} s, FP64 C oracle, 1 thread)"}
 
@@ -176,7 +191,7 @@ def cpu_baseline_all_cores(workload, iters=10):
     span = max(r[1] for r in res) - min(r[0] for r in res)
     work = sum(r[2] for r in res)
     case, _ = make_case(workload)
-    return {"value": work / span, "unit": UNIT, "cores": n, "kind": "oracle",
+    return {"value": work / span, "unit": UNIT, "cores": n, "kind": "oracle", "host": host_cpu(),
             "sample": f"{n} processes, each 1 physical step x {iters} pseudo-iterations on the full "
                       f"{case.nx}x{case.ny} tank ({span:.1f} s wall, FP64 C oracle, 1 thread each)"}
 
