@@ -217,7 +217,7 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "cells": case.cells,
                                             "pseudo_iters_per_step": iters},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: 1 physical step x {iters} pseudo-iterations of the full "
                                        f"{case.nx}x{case.ny} tank, FP64 C oracle, 1 thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
