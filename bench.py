@@ -321,12 +321,16 @@ def run_ours(args, ws, rank, local):
     per_launch_s = stage_launch_ms(tank, case, min(args.steps, 3)) * 1e-3
     ftx, fty, _, fv = tank.tile_shape()
     achieved = FP64_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12
+    # the part's FP64 FMA rate measured here (independent FMA chains), as a
+    # check of the nominal peak the fraction is taken against
+    probe = ac.ac_probe_fp64_fma_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FP64_TRAFFIC_PER_CELL_STAGE * case.cells,
                 "kernel": f"stage_kernel<double,{ftx},{fty}>", "tile_variant": fv, "launch_ms": per_launch_s * 1e3,
                 "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
-                "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM), not measured",
+                "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM)",
+                "peak_probe_tflops": probe, "frac_of_probe": achieved / probe,
                 # the same launch counted in FP64 instructions against the pipe's
                 # issue rate (2 per SM per clock): DADD and DMUL take a pipe slot
                 # for one flop, so the flop fraction is at most ~0.71 of this one

@@ -198,6 +198,14 @@ int ac_stage_kernel_time(const ac_ctx *ctx, double *total_ms, long long *launche
  * replaced by variant 0 for the others. */
 int ac_tile_shape(const ac_ctx *ctx, int *tx, int *ty, int *threads, int *variant);
 
+/* Measurement helper, not part of the method: the device's FP64 fused
+ * multiply-add rate in TFLOP/s (an FMA counted as 2 flops), timed with CUDA
+ * events over a kernel of independent FMA chains on the current device
+ * (about 10 ms, default stream; allocates and frees 1.2 MiB).  The FP64
+ * sweep's roofline is checked against it.  Errors: AC_ERR_ARG, AC_ERR_OOM,
+ * AC_ERR_CUDA. */
+int ac_probe_fp64_fma_tflops(double *tflops);
+
 /* ---- many tanks at once (mixed form) -------------------------------------
  * A batch advances n independent tanks of any sizes, densities and beta in
  * the mixed form (FP32 sweep; FP64 time levels, reference pressure and

@@ -36,7 +36,7 @@ EXPORTS = (
     "ac_default_options", "ac_beta_from_speed", "ac_create", "ac_destroy", "ac_set_stream",
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_history",
     "ac_set_history", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
-    "ac_tile_shape",
+    "ac_tile_shape", "ac_probe_fp64_fma_tflops",
     "ac_stage_sweep_noalloc", "ac_realtime_dt", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
     "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
     "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
@@ -107,6 +107,7 @@ def load(build: bool = True):
     L.ac_stage_kernel_time.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong)]
     _IP = C.POINTER(C.c_int)
     L.ac_tile_shape.argtypes = [C.c_void_p, _IP, _IP, _IP, _IP]
+    L.ac_probe_fp64_fma_tflops.argtypes = [_D]
     _PA4 = C.c_void_p * 4
     _PA3 = C.c_void_p * 3
     L.ac_stage_sweep_noalloc.argtypes = [C.POINTER(ac_grid), C.c_double, C.POINTER(ac_bc), C.POINTER(ac_options),
@@ -159,6 +160,13 @@ def ac_default_options() -> ac_options:
     o = ac_options()
     _check(load().ac_default_options(C.byref(o)))
     return o
+
+
+def ac_probe_fp64_fma_tflops() -> float:
+    """The device's FP64 FMA rate (TFLOP/s), measured by the library."""
+    v = C.c_double(0.0)
+    _check(load().ac_probe_fp64_fma_tflops(C.byref(v)))
+    return v.value
 
 
 def ac_beta_from_speed(c0: float, rho_ref: float) -> float:

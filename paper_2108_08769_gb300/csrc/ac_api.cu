@@ -15,6 +15,7 @@
 // interface: FP64 (every step in double precision) and mixed (FP32 sweep,
 // FP64 time level, reference pressure and norms; see ac_kernels_mixed.cuh).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -973,7 +974,7 @@ int ac_get_state(const ac_ctx *c, double *rho, double *rhou, double *rhov, doubl
     return c->be->get_state(c, dst);
 }
 
-int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out) {
+static int physical_step_impl(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out) {
     g_err.clear();
     if (iters_out) *iters_out = 0;
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
@@ -1040,6 +1041,25 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
     return c->hctl->status == 0 ? AC_OK : AC_NOT_CONVERGED;
 }
 
+// The public step: an NVTX range around the whole call, for timeline
+// profilers, and the AC_LOG line (iterations, status, R0 and R per field).
+int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out) {
+    nvtxRangePushA("ac_physical_step");
+    int its = 0;
+    const int rc = physical_step_impl(c, dt, tol, max_iters, &its);
+    nvtxRangePop();
+    if (iters_out) *iters_out = its;
+    if (c && c->hctl && acgb::log_enabled()) {
+        const Ctl &h = *c->hctl;
+        std::fprintf(stderr,
+                     "ac_physical_step: %dx%d %s rc=%d iters=%d R0=(%.3e %.3e %.3e %.3e) "
+                     "R=(%.3e %.3e %.3e %.3e)\n",
+                     c->grid.nx, c->grid.ny, c->opt.precision == AC_PREC_MIXED ? "mixed" : "fp64", rc, its,
+                     h.R0[0], h.R0[1], h.R0[2], h.R0[3], h.R[0], h.R[1], h.R[2], h.R[3]);
+    }
+    return rc;
+}
+
 int ac_residual_norms(const ac_ctx *c, double out[4], double out0[4]) {
     if (!c || !out) return fail(AC_ERR_ARG, "NULL argument");
     for (int k = 0; k < 4; ++k) {
@@ -1100,6 +1120,60 @@ int ac_set_profiling(ac_ctx *c, int on) {
     c->profiling = on != 0;
     c->stage_ms = 0.0;
     c->stage_launches = 0;
+    return AC_OK;
+}
+
+// FP64 FMA rate probe: every thread runs eight independent fused
+// multiply-add chains (x <- x m + c with |m| < 1, so values stay bounded), so
+// the FP64 pipe, not dependency latency, sets the pace.  One double per
+// thread is written, to the grid-sized buffer, so nothing is optimised away.
+static __global__ void fp64_fma_probe_kernel(double *out, int iters) {
+    const double m = 0.9999999, k = 1e-9;
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 1e-3 * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fma(x[j], m, k);
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sum += x[j];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+int ac_probe_fp64_fma_tflops(double *tflops) {
+    g_err.clear();
+    if (!tflops) return fail(AC_ERR_ARG, "tflops is NULL");
+    *tflops = 0.0;
+    int dev = 0, sms = 0;
+    cudaError_t e0_ = cudaGetDevice(&dev);
+    if (e0_ == cudaSuccess) e0_ = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0_ != cudaSuccess) return fail(AC_ERR_CUDA, "FP64 probe: %s", cudaGetErrorString(e0_));
+    const int blocks = 4 * sms, threads = 256, iters = 4096;
+    double *out = nullptr;
+    e0_ = cudaMalloc(&out, (size_t)blocks * threads * sizeof(double));
+    if (e0_ != cudaSuccess)
+        return fail(e0_ == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA, "FP64 probe: %s",
+                    cudaGetErrorString(e0_));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.0f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // the first launch warms up
+        if ((e = cudaEventRecord(e0, 0)) != cudaSuccess) break;
+        fp64_fma_probe_kernel<<<blocks, threads>>>(out, iters);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaEventRecord(e1, 0)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "FP64 probe: %s", cudaGetErrorString(e));
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    *tflops = flops / (ms * 1e-3) / 1e12;
     return AC_OK;
 }
 

@@ -13,9 +13,11 @@
 // to "some tank still iterating".  The whole pseudo-iteration loop of one
 // physical step is one graph launch.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -744,7 +746,7 @@ int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, doub
     return AC_OK;
 }
 
-int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
+static int batch_step_impl(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
                            int *status_out) {
     set_last_error(AC_OK, "%s", "");
     if (!b) return fail(AC_ERR_ARG, "batch is NULL");
@@ -829,6 +831,31 @@ int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_it
     }
     b->nhist = std::min(b->nhist + 1, 2);
     return ret;
+}
+
+// The public batch step: an NVTX range around the call and, with AC_LOG=1,
+// one line per step on stderr (tanks, status, iteration range, how many
+// tanks converged).
+int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
+                           int *status_out) {
+    nvtxRangePushA("ac_batch_physical_step");
+    const bool log = b && acgb::log_enabled();
+    std::vector<int> its_log, st_log;
+    if (log && !iters_out) its_log.assign(b->n, 0), iters_out = its_log.data();
+    if (log && !status_out) st_log.assign(b->n, 0), status_out = st_log.data();
+    const int rc = batch_step_impl(b, dt, tol, max_iters, iters_out, status_out);
+    nvtxRangePop();
+    if (log) {
+        int lo = max_iters, hi = 0, conv = 0;
+        for (int k = 0; k < b->n; ++k) {
+            lo = std::min(lo, iters_out[k]);
+            hi = std::max(hi, iters_out[k]);
+            conv += status_out[k] == AC_OK;
+        }
+        std::fprintf(stderr, "ac_batch_physical_step: %d tanks rc=%d iters=%d..%d converged=%d\n", b->n, rc, lo, hi,
+                     conv);
+    }
+    return rc;
 }
 
 int ac_batch_residual_norms(const ac_batch *b, int k, double out[4], double out0[4]) {

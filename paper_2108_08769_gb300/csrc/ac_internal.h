@@ -27,6 +27,13 @@ inline bool pdl_enabled() {
     return on;
 }
 
+// AC_LOG=1 in the environment: the physical-step calls print one line per
+// step on stderr (read at every call, so a process may switch it).
+inline bool log_enabled() {
+    const char *e = getenv("AC_LOG");
+    return e && e[0] == '1';
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args... args) {

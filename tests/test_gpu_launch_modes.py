@@ -78,3 +78,38 @@ def test_profiling_mode_agrees_with_the_graph(monkeypatch):
     assert i0 == i1 and np.array_equal(r0, r1)
     for x, y in zip(s0, s1):
         assert np.array_equal(x, y)
+
+
+LOG_CHILD = r'''
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2108_08769_gb300 import ac, workloads as W
+case = W.random_two_fluid(16, 8)
+t = ac.Tank.from_case(case)
+t.physical_step(case.dt, -1.0, 3)
+t.physical_step(case.dt, -1.0, 2)
+t.close()
+cases = W.batched_tanks(count=3, nmin=16, nmax=24, seed=3)
+b = ac.Batch.from_cases(cases)
+b.physical_step(1e-3, -1.0, 4)
+b.close()
+'''
+
+
+def test_ac_log_prints_one_line_per_step(tmp_path):
+    """AC_LOG=1: every physical step, single tank or batch, prints one line
+    on stderr with its iterations, status and norms."""
+    script = tmp_path / "log_child.py"
+    script.write_text(LOG_CHILD)
+    r = subprocess.run([sys.executable, str(script), ROOT], env=dict(os.environ, AC_LOG="1"),
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    single = [l for l in r.stderr.splitlines() if l.startswith("ac_physical_step:")]
+    batch = [l for l in r.stderr.splitlines() if l.startswith("ac_batch_physical_step:")]
+    assert len(single) == 2 and len(batch) == 1, r.stderr[-2000:]
+    assert "16x8 fp64 rc=0 iters=3 " in single[0] and "iters=2 " in single[1]
+    assert "R0=(" in single[0] and "R=(" in single[0]
+    assert "3 tanks rc=0 iters=4..4" in batch[0]
+    quiet = subprocess.run([sys.executable, str(script), ROOT], env=dict(os.environ, AC_LOG="0"),
+                           capture_output=True, text=True, timeout=600)
+    assert quiet.returncode == 0 and "ac_physical_step:" not in quiet.stderr

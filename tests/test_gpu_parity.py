@@ -346,3 +346,13 @@ def test_tile_shape_reported_after_the_first_step():
     tx, ty, nt, v = t.tile_shape()
     assert v >= 0 and tx * ty >= nt > 0
     t.close()
+
+
+def test_fp64_fma_probe_is_near_the_nominal_rate():
+    """The FP64 FMA probe measures this part's rate: within a factor of two
+    of the nominal 2 FMA lanes per SM at the current clock."""
+    import torch
+    v = ac.ac_probe_fp64_fma_tflops()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal_at_2ghz = 2 * 2 * sms * 2.0e9 / 1e12
+    assert 0.5 * nominal_at_2ghz < v < 2.0 * nominal_at_2ghz, v
