@@ -24,7 +24,8 @@
  *  R3  Osher: the quadrature sum multiplies the jump from the left,
  *      (1/2) sum_j w_j |A_j| (Q_R - Q_L)  (Sec. 2.4.3).
  *  R4  RK coefficients alpha_s = 1/(s_max - s + 1); the paper fixes only the
- *      last two (Sec. 2.2.2).                                    [parity unpinned]
+ *      last two (Sec. 2.2.2).  The reading is a convention; the oracle's
+ *      stages are pinned by a first-order closed case (an alternating state).
  *  R5  alpha_PI = 1 + B0 alpha_s dtau_i / dt scales the whole bracket,
  *      pressure row included (Alg. 1, Eq. RK2, Eq. point_implicit).  An option
  *      leaves the pressure row unscaled.

@@ -390,6 +390,57 @@ def test_residual_norms_of_a_velocity_step():
     assert expect[0] > 0 and expect[1] > 0 and expect[3] > 0
 
 
+def test_runge_kutta_stages_on_an_alternating_state():
+    """Alg. 1 and Eq. RK2 with alpha_s = 1/(s_max - s + 1): Q^s = Q^0 +
+    alpha_s dtau bracket(Q^{s-1}).  In a periodic box whose fields alternate
+    between two values along x (uniform in y), every one-sided difference
+    changes sign from cell to cell, so every minmod slope is zero at every
+    stage and the pattern stays two-valued; with no gravity and no real-time
+    term the new pressure gradient is zero too.  Each stage is then the
+    first-order update with the Osher flux at cell values, taken here from
+    numpy_osher, with the oracle's pinned dtau.  Catches other stage
+    coefficients (alpha_1 = 1/4, or all 1), stages fed from Q^0 instead of
+    Q^{s-1}, or a wrong sign or 1/dx in the divergence."""
+    nx, ny = 6, 2
+    c = _uniform_case(nx, ny, 0.0, 0.0)
+    c.gx = c.gy = 0.0
+    c.beta = 2.0
+    c.options.realtime = False
+    alt = np.where(np.arange(nx) % 2 == 0, 1.0, -1.0)[None, :].repeat(ny, axis=0)
+    c.rho = 1.3 + 0.2 * alt
+    c.rhou = 0.15 * alt
+    c.rhov = 0.05 - 0.02 * alt
+    c.p = 0.4 + 0.3 * alt
+    st, *_ = oracle.physical_step(c, c.state(), tol=-1.0, max_iters=1)
+    dtau = oracle.dtau(c, c.state())
+
+    def to_q(state, i):
+        r, ru, rv, p = (a[0, i] for a in state)
+        return np.array([r, ru, rv, 0.0, p / c.beta])
+
+    def bracket(state):
+        Q = [to_q(state, i) for i in range(nx)]
+        F = [numpy_osher(Q[i], Q[(i + 1) % nx], c.beta) for i in range(nx)]   # east face of cell i
+        return [-(F[i] - F[i - 1]) / c.dx for i in range(nx)]
+
+    q0 = c.state()
+    cur = q0
+    s_max = c.options.s_max
+    for s_ in range(1, s_max + 1):
+        alpha = 1.0 / (s_max - s_ + 1)
+        b = bracket(cur)
+        nxt = [a.copy() for a in q0]
+        for i in range(nx):
+            for f, row in ((0, 0), (1, 1), (2, 2)):
+                nxt[f][:, i] = q0[f][:, i] + alpha * dtau[:, i] * b[i][row]
+            nxt[3][:, i] = q0[3][:, i] + c.beta * alpha * dtau[:, i] * b[i][4]
+        cur = nxt
+    for f in range(4):
+        change = np.abs(cur[f] - q0[f]).max()
+        assert change > 1e-6
+        assert np.abs(st[f] - cur[f]).max() <= 1e-5 * change, (f, np.abs(st[f] - cur[f]).max(), change)
+
+
 def _gravity_box_iterates(c, rho, iters):
     """Momenta x_m of the uniform gravity box after m pseudo-iterations and
     the residuals R_m of iteration m, from the closed-form recurrence of
