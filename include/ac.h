@@ -130,14 +130,20 @@ void ac_destroy(ac_ctx *ctx);
 int ac_set_stream(ac_ctx *ctx, void *stream);
 
 /* Set the state Q = (rho, rho u, rho v, p) from host arrays (nx*ny doubles
- * each).  Also sets the real-time level Q^n := Q and clears the older
- * levels.  rho must be finite and > 0; all values finite
- * (AC_ERR_NONFINITE otherwise, AC_ERR_ARG for rho <= 0). */
+ * each); the solvers see p as p/beta, the fifth component of the compact
+ * form (Sec. 2.1.2).  Also sets the real-time level Q^n := Q, the
+ * assignment that opens every physical step of Alg. 1, and clears the older
+ * levels (Sec. 2.2.2: the next step starts from Backward-Euler).  rho must
+ * be finite and > 0; all values finite (AC_ERR_NONFINITE otherwise,
+ * AC_ERR_ARG for rho <= 0). */
 int ac_set_state(ac_ctx *ctx, const double *rho, const double *rhou, const double *rhov,
                  const double *p);
 
-/* Copy the current state to host arrays (nx*ny doubles each; any pointer
- * may be NULL to skip that field).  Synchronises the context's stream. */
+/* Copy the current state Q = (rho, rho u, rho v, p) (Sec. 2.1.2, with p in
+ * Pa rather than p/beta) to host arrays (nx*ny doubles each; any pointer may
+ * be NULL to skip that field): after a physical step this is Q^{n+1}, the
+ * converged pseudo-time state of Alg. 1.  Synchronises the context's
+ * stream. */
 int ac_get_state(const ac_ctx *ctx, double *rho, double *rhou, double *rhov, double *p);
 
 /* One real-time step of dual time stepping (Alg. 1): Q^n <- Q, then
@@ -152,8 +158,11 @@ int ac_get_state(const ac_ctx *ctx, double *rho, double *rhou, double *rhov, dou
  * AC_ERR_NONFINITE the state is restored to its value before the call. */
 int ac_physical_step(ac_ctx *ctx, double dt, double tol, int max_iters, int *iters_out);
 
-/* Residual norms of the last physical step: out[4] = final R (rho, rho u,
- * rho v, p), out0[4] (may be NULL) = first-iteration R0. */
+/* Residual norms of the last physical step (Alg. 1's convergence test;
+ * the paper does not define the norm, and this library reads it as the RMS
+ * over cells of the stage-1 bracket of Eq. RK2, pressure row in Pa/s):
+ * out[4] = final R (rho, rho u, rho v, p), out0[4] (may be NULL) =
+ * first-iteration R0. */
 int ac_residual_norms(const ac_ctx *ctx, double out[4], double out0[4]);
 
 /* Global real-time step from a real-time Courant number (Sec. 2.2.4):
@@ -222,7 +231,9 @@ int ac_probe_fp64_fma_tflops(double *tflops);
  * compiler may contract differently) they agree with it to round-off. */
 typedef struct ac_batch ac_batch;
 
-/* grids[n], beta[n] (Pa) and bcs[n] describe the tanks, 1 <= n <= 65535;
+/* Create a batch: each tank is one instance of the problem of ac_create
+ * (Sec. 2.1.1 equations, Sec. 2.5 boundaries, beta of Eq. AC_end).
+ * grids[n], beta[n] (Pa) and bcs[n] describe the tanks, 1 <= n <= 65535;
  * opt (may be NULL) applies to all of them and must select AC_PREC_MIXED and
  * the local pseudo-time step.  The tanks together may hold at most 2^31
  * cells (each rounded up to its aligned slot).
@@ -231,12 +242,17 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
                     ac_batch **out);
 void ac_batch_destroy(ac_batch *b);
 int ac_batch_set_stream(ac_batch *b, void *stream);
-/* State of tank k (0 <= k < n) from host arrays, as ac_set_state. */
+/* State of tank k (0 <= k < n) from host arrays, as ac_set_state (Q^n := Q
+ * of Alg. 1 for that tank). */
 int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou, const double *rhov,
                        const double *p);
+/* State of tank k to host arrays, as ac_get_state (Q^{n+1} of Alg. 1 after
+ * a step). */
 int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, double *rhov, double *p);
-/* One physical step of every tank with its own dt[k]; tol and max_iters as
- * in ac_physical_step.  iters_out[n] and status_out[n] (may be NULL)
+/* One physical step of every tank with its own dt[k]: Alg. 1 per tank
+ * (Q^n <- Q, pseudo-iterations of the Runge-Kutta stages of Eq. RK2 until
+ * that tank's residual test passes); tol and max_iters as in
+ * ac_physical_step.  iters_out[n] and status_out[n] (may be NULL)
  * receive each tank's iterations and status (AC_OK, AC_NOT_CONVERGED,
  * AC_ERR_NONFINITE).  Returns AC_OK when every tank converged (or tol < 0),
  * AC_NOT_CONVERGED when some tank hit max_iters, AC_ERR_NONFINITE when some
@@ -244,6 +260,7 @@ int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, doub
  * the step, the others advanced). */
 int ac_batch_physical_step(ac_batch *b, const double *dt, double tol, int max_iters, int *iters_out,
                            int *status_out);
+/* Residual norms of tank k's last step, as ac_residual_norms (Alg. 1). */
 int ac_batch_residual_norms(const ac_batch *b, int k, double out[4], double out0[4]);
 /* The tile shape the autotuner chose (AC_ERR_STATE before the first step). */
 int ac_batch_tile_shape(const ac_batch *b, int *tx, int *ty, int *threads);
@@ -279,9 +296,12 @@ long long ac_batch_kernel_launches(const ac_batch *b);
  * Every GPU that loads the library holds that 1 MiB until the process
  * exits.  All calls share the array: calls whose work overlaps on the GPU
  * (other streams, other host threads) race and must be serialised by the
- * caller.  The first call on each device looks up the array's device
- * address and sets the kernel's shared-memory limit; make that first call
- * before any stream capture. */
+ * caller.  Every call looks up the array's address on the current device
+ * and sets the kernel's shared-memory limit (host-side calls that allocate
+ * nothing, so the address stays valid across a device reset); the first
+ * call on a device may also load the library's kernels, so make that first
+ * call before any stream capture.  The grid size is checked before any
+ * field pointer is looked at. */
 int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac_bc *bc, const ac_options *opt,
                            int stage, double dt, const double *const q_prev[4], const double *const q0[4],
                            const double *const qn[3], double *const q_out[4], double *norms, void *stream);

@@ -11,15 +11,15 @@
 // The scratch array is a file-scope __device__ variable: every GPU that
 // loads the library holds it (1 MiB) until the process exits.  Host code
 // must not pass the array's name to a kernel (on the host it is only a
-// stand-in); its device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// stand-in); its device address is looked up with cudaGetSymbolAddress on
+// the current device at every call (a host-side lookup that allocates
+// nothing), so no address outlives a device reset.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/ac.h"
 #include "ac_internal.h"
@@ -38,28 +38,23 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 #define fail acgb::set_last_error
 
-// per-device set-up: device address of the scratch array, shared-memory limit
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-int setup_device(int dev, unsigned char **scratch) {
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (dev < 0 || dev >= kMaxDevices) return fail(AC_ERR_ARG, "device %d out of range", dev);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        const int smem = (int)sizeof(StageSmem<double, kTX, kTY>);
-        e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kOsher>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kBassi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kRoe>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *scratch = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+// Set-up on the current device, at every call: the scratch array's device
+// address and the sweep kernels' shared-memory limit.  Both are host-side
+// calls that allocate nothing; on a device's first call they may load the
+// library's kernels, which is why that first call should come before any
+// stream capture.
+int setup_device(unsigned char **scratch) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    const int smem = (int)sizeof(StageSmem<double, kTX, kTY>);
+    e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kOsher>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kBassi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_kernel<double, kTX, kTY, kRoe>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    *scratch = static_cast<unsigned char *>(p);
     return AC_OK;
 }
 
@@ -110,6 +105,16 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
     if ((bc->xlo == AC_BC_PERIODIC) != (bc->xhi == AC_BC_PERIODIC) ||
         (bc->ylo == AC_BC_PERIODIC) != (bc->yhi == AC_BC_PERIODIC))
         return fail(AC_ERR_ARG, "periodic boundaries must be set on both sides of an axis");
+    // the grid must fit the fixed scratch; checked before anything else is
+    // looked at, so an oversized grid never reaches a launch
+    const dim3 g((grid->nx + kTX - 1) / kTX, (grid->ny + kTY - 1) / kTY);
+    const size_t tiles = (size_t)g.x * g.y;
+    if (tiles > kMaxTiles)
+        return fail(AC_ERR_ARG,
+                    "grid %dx%d needs %zu tiles of %dx%d cells; the no-allocation scratch holds at most %zu "
+                    "(about %zu cells)",
+                    grid->nx, grid->ny, tiles, kTX, kTY, kMaxTiles, kMaxTiles * kTX * kTY);
+
     if (opt->precision != AC_PREC_FP64) return fail(AC_ERR_ARG, "only the FP64 sweep has a no-allocation variant");
     if (opt->rk_stages < 1 || opt->rk_stages > 4) return fail(AC_ERR_ARG, "rk_stages must be 1..4");
     if (stage < 1 || stage > opt->rk_stages) return fail(AC_ERR_ARG, "stage must be 1..rk_stages (got %d)", stage);
@@ -124,19 +129,9 @@ extern "C" int ac_stage_sweep_noalloc(const ac_grid *grid, double beta, const ac
     for (int f = 0; f < 4; ++f)
         if (!q0[f] || !q_out[f] || (stage > 1 && !q_prev[f]))
             return fail(AC_ERR_ARG, "field pointer %d is NULL", f);
-    const dim3 g((grid->nx + kTX - 1) / kTX, (grid->ny + kTY - 1) / kTY);
-    const size_t tiles = (size_t)g.x * g.y;
-    if (tiles > kMaxTiles)
-        return fail(AC_ERR_ARG,
-                    "grid %dx%d needs %zu tiles of %dx%d cells; the no-allocation scratch holds at most %zu "
-                    "(about %zu cells)",
-                    grid->nx, grid->ny, tiles, kTX, kTY, kMaxTiles, kMaxTiles * kTX * kTY);
-
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    cudaError_t e;
     unsigned char *scratch = nullptr;
-    int rc = setup_device(dev, &scratch);
+    int rc = setup_device(&scratch);
     if (rc != AC_OK) return rc;
     Ctl *ctl = reinterpret_cast<Ctl *>(scratch);
     double *partials = reinterpret_cast<double *>(scratch + kCtlBytes);
