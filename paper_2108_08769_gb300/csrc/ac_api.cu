@@ -138,6 +138,11 @@ struct Backend {
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
     virtual int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) = 0;
+    // kernels enqueued after the end of each pseudo-iteration (mixed form:
+    // the pressure rebase), and whether the end sets the rebase flag
+    virtual int after_iteration(ac_ctx *c, cudaStream_t s) { (void)c; (void)s; return AC_OK; }
+    virtual int kernels_after_iteration() const { return 0; }
+    virtual bool rebases() const { return false; }
     // chosen variant (-1 before tuning) and its tile shape
     virtual int shape(int &tx, int &ty, int &nt) const = 0;
 };
@@ -438,13 +443,14 @@ std::vector<std::pair<TuneKey, int>> g_tuned;
 
 struct MixedBackend : Backend {
     int variant = -1;
-    float4 *d[3] = {};   // per cell (dQ of rho, rho u, rho v; p'), three rotating buffers
+    float4 *d[3] = {};   // per cell (dQ of rho, rho u, rho v; dp or p), three rotating buffers
     float4 *qn = nullptr;  // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    float *dref = nullptr, *lev_p = nullptr;
+    float *jx = nullptr, *jy = nullptr, *lev_p = nullptr;
     float *D1[3] = {}, *D2[3] = {};   // Q^n - Q^{n-1}, Q^n - Q^{n-2} (BDF2, BDF3)
-    double *q64[3] = {};
-    std::vector<double> p_ref;   // FP64 reference pressure (host copy)
-    bool use_ref = false;
+    double *q64[4] = {};   // FP64 levels of rho, rho u, rho v, p
+    double *p64_step = nullptr;   // FP64 pressure level at the start of the step
+    double *pref64 = nullptr;   // FP64 reference pressure (with a reference)
+    bool use_ref = false, plevel = false;
 
     int shape(int &tx, int &ty, int &nt) const override {
         const MixedVariant &m = kMixedVariants[variant < 0 ? 0 : variant];
@@ -568,10 +574,13 @@ struct MixedBackend : Backend {
         a.beta = float(c->beta); a.inv_beta = float(1.0 / c->beta);
         a.gx = float(c->grid.gx); a.gy = float(c->grid.gy);
         a.cfl_area = float(c->opt.cfl_tau * dx * dy);
+        a.plevel = plevel ? 1 : 0;
         for (int b = 0; b < 3; ++b) a.d[b] = d[b];
         a.qn = qn;
-        for (int f = 0; f < 3; ++f) a.q64[f] = q64[f];
-        a.dref = dref; a.lev_p = lev_p;
+        for (int f = 0; f < 4; ++f) a.q64[f] = q64[f];
+        a.p64_step = p64_step;
+        a.pref64 = pref64;
+        a.jx = jx; a.jy = jy; a.lev_p = lev_p;
         for (int f = 0; f < 3; ++f) { a.D1[f] = D1[f]; a.D2[f] = D2[f]; }
         a.order = c->order_now;
         a.B0 = float(kBDF[c->order_now][0]);
@@ -583,10 +592,17 @@ struct MixedBackend : Backend {
     }
     int alloc(ac_ctx *c) override {
         const size_t fb = c->N * sizeof(float), db = c->N * sizeof(double), f4 = c->N * sizeof(float4);
+        // the reference applies when both y sides are walls and the pressure
+        // gradient comes from Eq. new_gradp; the pressure level with Eq. new_gradp
+        use_ref = mixed_uses_reference(c->bc, c->opt.gradp);
+        plevel = mixed_uses_level(c->opt.gradp);
         for (int b = 0; b < 3; ++b) CK(cudaMalloc(&d[b], f4));
         CK(cudaMalloc(&qn, f4));
-        for (int f = 0; f < 3; ++f) CK(cudaMalloc(&q64[f], db));
-        CK(cudaMalloc(&dref, fb));
+        for (int f = 0; f < 4; ++f) CK(cudaMalloc(&q64[f], db));
+        if (plevel) CK(cudaMalloc(&p64_step, db));
+        if (use_ref) CK(cudaMalloc(&pref64, db));
+        CK(cudaMalloc(&jx, fb));
+        CK(cudaMalloc(&jy, fb));
         CK(cudaMalloc(&lev_p, fb));
         for (int f = 0; f < 3; ++f) {
             if (c->opt.bdf_order >= 2) CK(cudaMalloc(&D1[f], fb));
@@ -614,16 +630,16 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));
         set_variant(c, 0);
         variant = -1;   // tuned at the first physical step
-        // the reference applies when both y sides are walls and the pressure
-        // gradient comes from Eq. new_gradp
-        use_ref = mixed_uses_reference(c->bc, c->opt.gradp);
         return AC_OK;
     }
     void release() override {
         for (int b = 0; b < 3; ++b) cudaFree(d[b]);
         cudaFree(qn);
-        for (int f = 0; f < 3; ++f) cudaFree(q64[f]);
-        cudaFree(dref);
+        for (int f = 0; f < 4; ++f) cudaFree(q64[f]);
+        cudaFree(p64_step);
+        cudaFree(pref64);
+        cudaFree(jx);
+        cudaFree(jy);
         cudaFree(lev_p);
         for (int f = 0; f < 3; ++f) { cudaFree(D1[f]); cudaFree(D2[f]); }
     }
@@ -634,21 +650,21 @@ struct MixedBackend : Backend {
             if (D2[q]) CK(cudaMemsetAsync(D2[q], 0, N * sizeof(float), c->stream));
         }
         MixedReference ref;
-        build_mixed_reference(c->grid.nx, c->grid.ny, c->dy, c->grid.gy, c->bc, use_ref, f, ref);
-        p_ref = ref.p_ref;
+        build_mixed_reference(c->grid.nx, c->grid.ny, c->dy, c->grid.gy, use_ref, plevel, f, ref);
         cudaStream_t s = c->stream;
-        const size_t fb = N * sizeof(float);
-        // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, p')
+        const size_t fb = N * sizeof(float), db = N * sizeof(double);
+        // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, dp = 0 or p)
         std::vector<float4> hq(N), hd(N);
         for (size_t q = 0; q < N; ++q) {
             hq[q] = make_float4(float(f[0][q]), float(f[1][q]), float(f[2][q]), ref.rho_ref[q]);
-            hd[q] = make_float4(0.0f, 0.0f, 0.0f, ref.p_prime[q]);
+            hd[q] = make_float4(0.0f, 0.0f, 0.0f, ref.p_record[q]);
         }
-        for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(q64[k], f[k], N * sizeof(double), cudaMemcpyHostToDevice, s));
+        for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(q64[k], f[k], db, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(q64[3], ref.p_level.data(), db, cudaMemcpyHostToDevice, s));
+        if (pref64) CK(cudaMemcpyAsync(pref64, ref.p_ref.data(), db, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(qn, hq.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d[0], hd.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(lev_p, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(dref, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(lev_p, ref.p_record.data(), fb, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         return AC_OK;
     }
@@ -657,13 +673,14 @@ struct MixedBackend : Backend {
         std::vector<float4> h(N);
         const int cur = c->cur_host;
         CK(cudaMemcpyAsync(h.data(), d[cur], N * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (out[k]) CK(cudaMemcpyAsync(out[k], q64[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        // state = FP64 level + FP32 increment
         if (out[0]) for (size_t q = 0; q < N; ++q) out[0][q] += double(h[q].x);
         if (out[1]) for (size_t q = 0; q < N; ++q) out[1][q] += double(h[q].y);
         if (out[2]) for (size_t q = 0; q < N; ++q) out[2][q] += double(h[q].z);
-        if (out[3]) for (size_t q = 0; q < N; ++q) out[3][q] = p_ref[q] + double(h[q].w);
+        if (out[3]) for (size_t q = 0; q < N; ++q) out[3][q] += double(h[q].w);
         return AC_OK;
     }
     // Between steps, history 1 is the FP64 level q64 and history 2 is
@@ -720,6 +737,9 @@ struct MixedBackend : Backend {
     int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) override {
         begin_step_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters);
         CK(cudaGetLastError());
+        level_jumps_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
+        CK(cudaGetLastError());
+        c->launches += 1;
         return AC_OK;
     }
     int dtau_min(ac_ctx *c, cudaStream_t s) override {
@@ -740,8 +760,19 @@ struct MixedBackend : Backend {
     int restore(ac_ctx *c, cudaStream_t s) override {
         restore_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
         CK(cudaGetLastError());
+        level_jumps_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
+        CK(cudaGetLastError());
         return AC_OK;
     }
+    int after_iteration(ac_ctx *c, cudaStream_t s) override {
+        if (!plevel) return AC_OK;
+        const dim3 g(grid_stride_blocks(c->N));
+        CK(launch_pdl(c->pdl, rebase_shift_kernel_mixed, g, dim3(256), 0, s, args(c, 0)));
+        CK(launch_pdl(c->pdl, rebase_jumps_kernel_mixed, g, dim3(256), 0, s, args(c, 0)));
+        return AC_OK;
+    }
+    int kernels_after_iteration() const override { return plevel ? 2 : 0; }
+    bool rebases() const override { return plevel; }
 };
 
 // ------------------------------------------------------------------ loop
@@ -751,6 +782,7 @@ struct MixedBackend : Backend {
 int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false) {
     int rc;
     IterEnd e{};
+    e.rebase_pow2 = c->be->rebases() ? 1 : 0;
     e.nparts = c->be->nblocks;
     e.s_max = c->opt.rk_stages;
     e.use_cond = use_cond;
@@ -763,10 +795,12 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
     CK(launch_pdl(c->pdl, end_iteration_kernel, dim3(1), dim3(kEndLanes), 0, s, c->ctl, c->partials, e));
-    return AC_OK;
+    return c->be->after_iteration(c, s);
 }
 
-int kernels_per_iteration(const ac_ctx *c) { return c->opt.rk_stages + 1 + (c->opt.local_dtau ? 0 : 1); }
+int kernels_per_iteration(const ac_ctx *c) {
+    return c->opt.rk_stages + 1 + (c->opt.local_dtau ? 0 : 1) + c->be->kernels_after_iteration();
+}
 
 int build_graph(ac_ctx *c) {
     if (c->exec && c->graph_order == c->order_now) return AC_OK;

@@ -123,25 +123,8 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
     Ctl *ctl = a.ctl;
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
-    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        const float4 e = a.d[cur][g];
-        float4 q4 = a.qn[g];   // .w (rho_ref) stays
-        const float dqs[3] = {e.x, e.y, e.z};
-        float qs[3];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const float dq = dqs[f];
-            const double q = a.q64[f][g] + double(dq);
-            if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
-            if (a.D1[0]) a.D1[f][g] = dq;
-            a.q64[f][g] = q;
-            qs[f] = float(q);
-        }
-        q4.x = qs[0]; q4.y = qs[1]; q4.z = qs[2];
-        a.qn[g] = q4;
-        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, e.w);
-        a.lev_p[g] = e.w;
-    }
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_shift(a, cur, g);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double h = dt[blockIdx.y];
         ctl->iter = 0;
@@ -153,11 +136,44 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
         ctl->dt = h;
         ctl->inv_dt = 1.0 / h;
         ctl->dtau_bits = 0x7ff0000000000000ull;
+        ctl->rebase = 0;
         if (blockIdx.y == 0) {
             sync->arrive = 0;
             sync->still_active = 0;
         }
     }
+}
+
+// Level jumps of every tank (blockIdx.y = tank), after the level shift.
+__global__ void batch_jumps_kernel(const BatchTank *tanks) {
+    const MixedArgs &a = tanks[blockIdx.y].a;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_jumps(a, g);
+}
+
+// Pressure rebase within a step (see mixed_rebase_shift), every tank whose
+// end of iteration asked for one (blockIdx.y = tank); the jumps follow in a
+// second launch.
+__global__ void batch_rebase_shift_kernel(const BatchTank *tanks) {
+    pdl_trigger();
+    pdl_wait();
+    const MixedArgs &a = tanks[blockIdx.y].a;
+    if (!a.ctl->rebase) return;
+    const int cur = a.ctl->cur;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_rebase_shift(a, cur, g);
+}
+
+__global__ void batch_rebase_jumps_kernel(const BatchTank *tanks) {
+    pdl_trigger();
+    pdl_wait();
+    const MixedArgs &a = tanks[blockIdx.y].a;
+    if (!a.ctl->rebase) return;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_jumps(a, g);
 }
 
 // End of a pseudo-iteration for every tank (blockIdx.x = tank): its norms
@@ -196,6 +212,8 @@ batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long lo
             else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
             else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
             ctl->done = done;
+            // pressure rebase after iterations 1, 2, 4, 8, ... (see mixed_rebase_shift)
+            ctl->rebase = (t.a.plevel && !done && (it & (it - 1)) == 0) ? 1 : 0;
             active = !done;
         }
         if (active) atomicAdd(&sync->still_active, 1u);
@@ -218,7 +236,7 @@ __global__ void batch_restore_kernel(BatchTank *tanks) {
     const int cur = a.ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
-        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, a.lev_p[g]);
+        mixed_restore(a, cur, g);
 }
 
 struct Variant {
@@ -301,11 +319,13 @@ struct ac_batch {
     std::vector<size_t> off;            // first cell of each tank in the pooled arrays
     size_t total;                       // pooled cells (with alignment padding)
     // pooled device arrays
-    float4 *d[3];                       // per cell (dQ of rho, rho u, rho v; p'), three rotating pools
+    float4 *d[3];                       // per cell (dQ of rho, rho u, rho v; dp or p), three rotating pools
     float4 *qn;                         // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    float *dref, *lev_p;
+    float *jx, *jy, *lev_p;             // level jumps, restore copy of p (without a level)
     float *D1[3], *D2[3];               // BDF2/BDF3 level differences (pools)
-    double *q64[3];
+    double *q64[4];                     // FP64 levels of rho, rho u, rho v, p
+    double *p64_step;                   // FP64 pressure levels at the start of the step
+    double *pref64;                     // FP64 reference pressures (tanks with a reference)
     double *partials;
     Ctl *ctl;
     BatchSync *sync;
@@ -315,8 +335,9 @@ struct ac_batch {
     std::vector<BatchTank> tanks_host;
     int slot0;                          // first constant-table slot, -1: descriptors in global memory
     bool pdl;                           // launch the loop's kernels with programmatic dependencies
-    std::vector<std::vector<double>> p_ref;
     std::vector<char> use_ref;
+    bool plevel;                        // pressure carried over an FP64 level (every tank)
+    dim3 rebase_grid;                   // per-cell kernels over all tanks: (blocks per tank, tanks)
     Ctl *hctl;                          // pinned mirror of all control blocks
     int variant;
     int ntiles;
@@ -465,6 +486,10 @@ int enqueue_iteration(ac_batch *b, cudaStream_t s, unsigned long long cond, int 
     CK(launch_pdl(b->pdl, batch_end_kernel<256>, dim3(b->n), dim3(256), 0, s, b->tanks_dev, b->sync, b->n, cond,
                   use_cond));
     CK(cudaGetLastError());
+    if (b->plevel) {
+        CK(launch_pdl(b->pdl, batch_rebase_shift_kernel, b->rebase_grid, dim3(256), 0, s, b->tanks_dev));
+        CK(launch_pdl(b->pdl, batch_rebase_jumps_kernel, b->rebase_grid, dim3(256), 0, s, b->tanks_dev));
+    }
     return AC_OK;
 }
 
@@ -516,8 +541,12 @@ void ac_batch_destroy(ac_batch *b) {
     if (b->cap) cudaStreamDestroy(b->cap);
     for (int x = 0; x < 3; ++x) cudaFree(b->d[x]);
     cudaFree(b->qn);
-    for (int f = 0; f < 3; ++f) { cudaFree(b->q64[f]); cudaFree(b->D1[f]); cudaFree(b->D2[f]); }
-    cudaFree(b->dref);
+    for (int f = 0; f < 3; ++f) { cudaFree(b->D1[f]); cudaFree(b->D2[f]); }
+    for (int f = 0; f < 4; ++f) cudaFree(b->q64[f]);
+    cudaFree(b->p64_step);
+    cudaFree(b->pref64);
+    cudaFree(b->jx);
+    cudaFree(b->jy);
     cudaFree(b->lev_p);
     cudaFree(b->partials);
     cudaFree(b->ctl);
@@ -578,8 +607,10 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     b->order_now = 1;
     b->slot0 = acquire_slots(n);
     b->off.resize(n);
-    b->p_ref.resize(n);
     b->use_ref.resize(n);
+    b->plevel = mixed_uses_level(o.gradp);
+    bool any_ref = false;
+    for (int k = 0; k < n; ++k) any_ref = any_ref || mixed_uses_reference(bcs[k], o.gradp);
     b->tanks_host.resize(n);
 #define CKB(call)                                                                                        \
     do {                                                                                                 \
@@ -594,8 +625,11 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     const size_t fb = total * sizeof(float), db = total * sizeof(double), f4 = total * sizeof(float4);
     for (int x = 0; x < 3; ++x) CKB(cudaMalloc(&b->d[x], f4));
     CKB(cudaMalloc(&b->qn, f4));
-    for (int f = 0; f < 3; ++f) CKB(cudaMalloc(&b->q64[f], db));
-    CKB(cudaMalloc(&b->dref, fb));
+    for (int f = 0; f < 4; ++f) CKB(cudaMalloc(&b->q64[f], db));
+    if (b->plevel) CKB(cudaMalloc(&b->p64_step, db));
+    if (any_ref) CKB(cudaMalloc(&b->pref64, db));
+    CKB(cudaMalloc(&b->jx, fb));
+    CKB(cudaMalloc(&b->jy, fb));
     CKB(cudaMalloc(&b->lev_p, fb));
     for (int f = 0; f < 3; ++f) {
         if (o.bdf_order >= 2) CKB(cudaMalloc(&b->D1[f], fb));
@@ -647,10 +681,15 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.beta = float(beta[k]); a.inv_beta = float(1.0 / beta[k]);
         a.gx = float(g.gx); a.gy = float(g.gy);
         a.cfl_area = float(o.cfl_tau * dx * dy);
+        a.plevel = b->plevel ? 1 : 0;
+        b->use_ref[k] = mixed_uses_reference(bcs[k], o.gradp);
         for (int x = 0; x < 3; ++x) a.d[x] = b->d[x] + pos;
         a.qn = b->qn + pos;
-        for (int f = 0; f < 3; ++f) a.q64[f] = b->q64[f] + pos;
-        a.dref = b->dref + pos;
+        for (int f = 0; f < 4; ++f) a.q64[f] = b->q64[f] + pos;
+        a.p64_step = b->p64_step ? b->p64_step + pos : nullptr;
+        a.pref64 = b->use_ref[k] ? b->pref64 + pos : nullptr;
+        a.jx = b->jx + pos;
+        a.jy = b->jy + pos;
         a.lev_p = b->lev_p + pos;
         for (int f = 0; f < 3; ++f) {
             a.D1[f] = b->D1[f] ? b->D1[f] + pos : nullptr;
@@ -660,13 +699,15 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.B0 = 1.0f;
         a.partials = b->partials + tpos * 4;
         a.ctl = b->ctl + k;
-        b->use_ref[k] = mixed_uses_reference(bcs[k], o.gradp);
         for (int q = 0; q < 4; ++q) b->hctl[k].abs_tol[q] = o.abs_tol[q];
         b->hctl[k].done = 1;
         pos += ((size_t)g.nx * g.ny + kAlign - 1) / kAlign * kAlign;
         tpos += (size_t)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
     }
     CKB(cudaMemcpy(b->ctl, b->hctl, n * sizeof(Ctl), cudaMemcpyHostToDevice));
+    size_t maxN = 0;
+    for (int k = 0; k < n; ++k) maxN = std::max(maxN, (size_t)grids[k].nx * grids[k].ny);
+    b->rebase_grid = dim3((unsigned)std::min<size_t>((maxN + 255) / 256, 64), n);
     if (int rc = build_tiles(b, 0)) { ac_batch_destroy(b); return rc; }
     b->variant = -1;
 #undef CKB
@@ -694,8 +735,7 @@ int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou
     const double *f[4] = {rho, rhou, rhov, p};
     const ac_grid &g = b->grids[k];
     MixedReference ref;
-    build_mixed_reference(g.nx, g.ny, g.ly / g.ny, g.gy, b->bcs[k], b->use_ref[k] != 0, f, ref);
-    b->p_ref[k] = ref.p_ref;
+    build_mixed_reference(g.nx, g.ny, g.ly / g.ny, g.gy, b->use_ref[k] != 0, b->plevel, f, ref);
     cudaStream_t s = b->stream;
     CK(cudaStreamSynchronize(s));
     // the tank's control block: buffer 0 holds its state from now on
@@ -704,22 +744,23 @@ int ac_batch_set_state(ac_batch *b, int k, const double *rho, const double *rhou
     hc.cur = 0;
     hc.done = 1;
     hc.iter = 0;
-    const size_t o = b->off[k], fb = N * sizeof(float);
-    // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, p')
+    const size_t o = b->off[k], fb = N * sizeof(float), db = N * sizeof(double);
+    // the two per-cell records: (Q^n in FP32, rho_ref) and (dQ = 0, dp = 0 or p)
     std::vector<float4> hq(N), hd(N);
     for (size_t i = 0; i < N; ++i) {
         hq[i] = make_float4(float(f[0][i]), float(f[1][i]), float(f[2][i]), ref.rho_ref[i]);
-        hd[i] = make_float4(0.0f, 0.0f, 0.0f, ref.p_prime[i]);
+        hd[i] = make_float4(0.0f, 0.0f, 0.0f, ref.p_record[i]);
     }
-    for (int q = 0; q < 3; ++q) CK(cudaMemcpyAsync(b->q64[q] + o, f[q], N * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int q = 0; q < 3; ++q) CK(cudaMemcpyAsync(b->q64[q] + o, f[q], db, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->q64[3] + o, ref.p_level.data(), db, cudaMemcpyHostToDevice, s));
+    if (b->use_ref[k]) CK(cudaMemcpyAsync(b->pref64 + o, ref.p_ref.data(), db, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->qn + o, hq.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->d[0] + o, hd.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s));
     for (int q = 0; q < 3; ++q) {
         if (b->D1[q]) CK(cudaMemsetAsync(b->D1[q] + o, 0, fb, s));
         if (b->D2[q]) CK(cudaMemsetAsync(b->D2[q] + o, 0, fb, s));
     }
-    CK(cudaMemcpyAsync(b->lev_p + o, ref.p_prime.data(), fb, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(b->dref + o, ref.dref.data(), fb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b->lev_p + o, ref.p_record.data(), fb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->ctl + k, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     b->hctl[k] = hc;
@@ -736,13 +777,14 @@ int ac_batch_get_state(const ac_batch *b, int k, double *rho, double *rhou, doub
     double *out[4] = {rho, rhou, rhov, p};
     std::vector<float4> h(N);
     CK(cudaMemcpyAsync(h.data(), b->d[cur] + o, N * sizeof(float4), cudaMemcpyDeviceToHost, b->stream));
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 4; ++q)
         if (out[q]) CK(cudaMemcpyAsync(out[q], b->q64[q] + o, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    // state = FP64 level + FP32 increment
     if (rho) for (size_t i = 0; i < N; ++i) rho[i] += double(h[i].x);
     if (rhou) for (size_t i = 0; i < N; ++i) rhou[i] += double(h[i].y);
     if (rhov) for (size_t i = 0; i < N; ++i) rhov[i] += double(h[i].z);
-    if (p) for (size_t i = 0; i < N; ++i) p[i] = b->p_ref[k][i] + double(h[i].w);
+    if (p) for (size_t i = 0; i < N; ++i) p[i] += double(h[i].w);
     return AC_OK;
 }
 
@@ -783,7 +825,9 @@ static int batch_step_impl(ac_batch *b, const double *dt, double tol, int max_it
     const dim3 bg((unsigned)std::min<size_t>((maxN + 255) / 256, 64), b->n);
     batch_begin_kernel<<<bg, 256, 0, s>>>(b->tanks_dev, b->sync, b->dt_dev, tol, max_iters);
     CK(cudaGetLastError());
-    b->launches += 1;
+    batch_jumps_kernel<<<bg, 256, 0, s>>>(b->tanks_dev);
+    CK(cudaGetLastError());
+    b->launches += 2;
     b->pdl = false;   // the tuner times launches one after another
     int rc = tune(b, s);
     if (rc != AC_OK) return rc;
@@ -812,7 +856,7 @@ static int batch_step_impl(ac_batch *b, const double *dt, double tol, int max_it
         CK(cudaStreamSynchronize(s));
         for (int k = 0; k < b->n; ++k) iters_run = std::max<long long>(iters_run, b->hctl[k].iter);
     }
-    b->launches += iters_run * (b->opt.rk_stages + 1);
+    b->launches += iters_run * (b->opt.rk_stages + 1 + (b->plevel ? 2 : 0));
     int ret = AC_OK;
     bool any_nonfinite = false;
     for (int k = 0; k < b->n; ++k) {
@@ -824,6 +868,8 @@ static int batch_step_impl(ac_batch *b, const double *dt, double tol, int max_it
     }
     if (any_nonfinite) {
         batch_restore_kernel<<<dim3(bg.x, b->n), 256, 0, s>>>(b->tanks_dev);
+        CK(cudaGetLastError());
+        batch_jumps_kernel<<<bg, 256, 0, s>>>(b->tanks_dev);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
         b->nhist = 0;

@@ -34,10 +34,12 @@ struct Ctl {
     double R[4], R0[4];
     double abs_tol[4];
     unsigned long long dtau_bits;  // global pseudo-time step (bit pattern of a positive double)
+    int rebase;      // mixed form: fold the pressure increment into its FP64 level before the next iteration
 };
 
 // What the end of a pseudo-iteration needs (see end_iteration).
 struct IterEnd {
+    int rebase_pow2;           // mixed form with a pressure level: rebase after iterations 1, 2, 4, 8, ...
     int nparts;                // residual partial slots written by stage 1
     int s_max;
     int use_cond;              // set the graph's while-condition
@@ -154,6 +156,7 @@ __device__ __forceinline__ void end_iteration(Ctl *ctl, const double *partials, 
         else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
         else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
         ctl->done = done;
+        ctl->rebase = (e.rebase_pow2 && !done && (it & (it - 1)) == 0) ? 1 : 0;
         ctl->dtau_bits = 0x7ff0000000000000ull;
         if (e.use_cond) cudaGraphSetConditional(e.cond, done ? 0u : 1u);
     }

@@ -1,16 +1,20 @@
 // ac_kernels_mixed.cuh -- the fused stage sweep in the mixed form:
-// FP32 flux, reconstruction and update arithmetic; FP64 real-time level,
+// FP32 flux, reconstruction and update arithmetic; FP64 real-time levels,
 // hydrostatic reference pressure and residual sums.
 //
 // Storage (per cell; the two 16-byte records are read with one vector load):
 //   qn        (FP32 copy of the real-time level Q^n = (rho, rho u, rho v),
-//             reference density rho_ref); p_ref (FP64, host side) is the
-//             discrete hydrostatic column integral of rho_ref along y
+//             reference density rho_ref)
 //   d[b]      three rotating buffers of (dQ = Q - Q^n for rho, rho u, rho v,
-//             p' = p - p_ref), FP32
-//   dref      FP32 jump p_ref(i) - p_ref(i-1) across the west x-face
-//   q64[3]    FP64 real-time level, advanced once per physical step
+//             dp = p - p^n), FP32: every field is an increment over its
+//             level, small within a physical step
+//   q64[4]    FP64 levels Q^n and p^n, advanced once per physical step
 //             (Q^{n+1} = Q^n + dQ in FP64: the level accumulation)
+//   pref64    FP64 static reference pressure: the discrete hydrostatic
+//             column of rho_ref (none: zero)
+//   jx, jy    FP32 jumps of the level across each cell's west and south
+//             faces: jx = p^n(i) - p^n(i-1), jy = q^n(j) - q^n(j-1) with
+//             q^n = p^n - p_ref, formed in FP64 at the start of each step
 //
 // Why this is exact algebra and not an approximation of the scheme:
 //   * The real-time term of Eq. bdf is (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} +
@@ -21,18 +25,21 @@
 //   * Every Riemann flux here is affine in a pressure offset common to the
 //     two face states (|A| does not depend on p), so each face may be solved
 //     with p'' = p - P_f for any face constant P_f, adding P_f back to the
-//     normal momentum flux.  On y-faces P_f is the hydrostatic face value of
-//     the reference, which the cells on both sides agree on (wall ghosts
-//     mirror p_ref and reverse gravity, Sec. 2.5); the divergence of those
-//     face values is exactly -rho_ref g_y, which cancels the reference part
-//     of the body force, leaving (rho - rho_ref) g_y.  On x-faces P_f is the
-//     mean of the two cells' references and the jump dref enters the face
-//     states; the divergence of the means is -(dref_e + dref_w)/(2 dx).
+//     normal momentum flux.  On x-faces P_f is the mean of the two cells'
+//     levels p^n; the states then carry dp -+ jx/2 and the divergence of
+//     the means is -(jx_e + jx_w)/(2 dx).  On y-faces P_f is the reference's
+//     hydrostatic face value, which the cells on both sides agree on (wall
+//     ghosts mirror p_ref and reverse gravity, Sec. 2.5) and whose divergence
+//     is exactly -rho_ref g_y, cancelling the reference part of the body
+//     force and leaving (rho - rho_ref) g_y, plus the mean of the two cells'
+//     q^n, whose divergence is -(jy_n + jy_s)/(2 dy).
 //   * The new pressure gradient (Eq. new_gradp) does not depend on p; only
 //     its gravity term changes to (rho - rho_ref) g_y once the reference
 //     slope rho_ref g_y is moved into P_f.
-// With zero rho_ref and dref (used when the y sides are not both walls or
-// the pressure gradient is limited from p) this is the plain FP32 sweep.
+// FP32 then holds only increments and cell-to-cell jumps, never a pressure
+// of the size of the tank's hydrostatic head.  With a limited pressure
+// gradient (Sec. 2.3.1-2.3.2) the slopes need pressure differences, so there
+// the FP32 record holds p itself (plevel = 0: no level, zero jumps).
 #pragma once
 
 #include "ac_kernels.cuh"
@@ -49,16 +56,25 @@ struct MixedArgs {
     float dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
     float beta, inv_beta, gx, gy;
     float cfl_area;
-    float4 *d[3];          // per cell (dQ of rho, rho u, rho v; p'), three rotating buffers
+    int plevel;            // 1: pressure as dp over the FP64 level p^n; 0: the record holds p
+    float4 *d[3];          // per cell (dQ of rho, rho u, rho v; dp or p), three rotating buffers
     float4 *qn;            // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    const float *dref;     // reference jump across the west x-face
-    float *lev_p;          // p' at the start of the physical step
+    float *jx, *jy;        // level jumps across the west and south faces
+    float *lev_p;          // p at the start of the physical step (plevel = 0, for a restore)
     float *D1[3], *D2[3];  // Q^n - Q^{n-1}, Q^n - Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
     int order;             // backward-difference order used in this step (1..3)
     float B0, B2, B3;      // its coefficients (Table BDF); B1 = -(B0 + B2 + B3)
-    double *q64[3];        // FP64 real-time level
+    double *q64[4];        // FP64 real-time levels of rho, rho u, rho v and p (p: zero when plevel = 0)
+    double *p64_step;      // FP64 pressure level at the start of the physical step (for a restore)
+    const double *pref64;  // FP64 reference pressure (null: none)
     double *partials;
     Ctl *ctl;
+};
+
+// Residual partial sums: each cell's stage-1 bracket is squared exactly in
+// FP64 (an FP32 value squared fits a double's mantissa) and summed in FP64.
+struct Sq64 {
+    double x, y, z, w;
 };
 
 template <int TX, int TY>
@@ -69,7 +85,7 @@ struct MixedSmem {
     static constexpr int NYF = TX * (TY + 1);
     // one 16-byte vector per cell or face: a face or a cell reads all four
     // components with one shared-memory instruction
-    float4 w[RW * RH];       // (rho, u, v, p') of the tile + two-cell halo
+    float4 w[RW * RH];       // (rho, u, v, dp) of the tile + two-cell halo
     union {                  // aux is dead once the slopes exist; fx reuses it
         float4 aux[GW * GH]; // (RT of rho u, RT of rho v, rho_ref, -) on the ring
         float4 fx[NXF];      // x-face fluxes: (mass, x-mom, y-mom, p/beta)
@@ -77,11 +93,12 @@ struct MixedSmem {
     float4 gx[GW * GH];      // half slopes along x: (rho, u, v, p)
     float4 gy[GW * GH];      // half slopes along y: (rho, u, v, p - p_ref)
     float4 fy[NYF];          // y-face fluxes
-    float dxf[NXF];          // reference jump on each x-face
+    float dxf[NXF];          // level jump on each x-face
+    float dyf[NYF];          // level jump on each y-face
     double red[4][32];
 };
 
-// Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell as W = (rho, u, v, p').
+// Gather Q^{s-1} = Q^n + dQ^{s-1} of one cell as W = (rho, u, v, dp).
 struct CellLoad {
     const float4 *__restrict__ qn;
     const float4 *__restrict__ d;
@@ -122,7 +139,7 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
 // column-strip sweep, so that both compute every value the same way.
 // ---------------------------------------------------------------------------
 
-// Half slope of p' from the new pressure gradient (Eq. new_gradp) at a cell
+// Half slope of p from the new pressure gradient (Eq. new_gradp) at a cell
 // with W = Wc, the half slopes of rho, u, v, the frozen real-time terms of
 // rho u, rho v (rtx, rty), the reference density and the ghost gravity sign.
 __device__ __forceinline__ void new_gradp_half_slopes(const MixedArgs &a, const float4 &Wc, float hrx, float hry,
@@ -139,8 +156,8 @@ __device__ __forceinline__ void new_gradp_half_slopes(const MixedArgs &a, const 
 
 // Face states between cells A (left/below) and B with half slopes SA, SB
 // along the face normal: density, normal and tangential velocity (rotation,
-// Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure; jump = reference
-// jump across an x-face.
+// Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure relative to the
+// face constant; jump = level jump across the face.
 struct FaceStates {
     float rL, nL, tL, pL, rR, nR, tR, pR;
 };
@@ -150,9 +167,9 @@ __device__ __forceinline__ void x_face_states(const float4 &A, const float4 &B, 
     f.rR = B.x - SB.x; f.nR = B.y - SB.y; f.tR = B.z - SB.z; f.pR = B.w - SB.w + 0.5f * jump;
 }
 __device__ __forceinline__ void y_face_states(const float4 &A, const float4 &B, const float4 &SA, const float4 &SB,
-                                              FaceStates &f) {
-    f.rL = A.x + SA.x; f.nL = A.z + SA.z; f.tL = A.y + SA.y; f.pL = A.w + SA.w;
-    f.rR = B.x - SB.x; f.nR = B.z - SB.z; f.tR = B.y - SB.y; f.pR = B.w - SB.w;
+                                              float jump, FaceStates &f) {
+    f.rL = A.x + SA.x; f.nL = A.z + SA.z; f.tL = A.y + SA.y; f.pL = A.w + SA.w - 0.5f * jump;
+    f.rR = B.x - SB.x; f.nR = B.z - SB.z; f.tR = B.y - SB.y; f.pR = B.w - SB.w + 0.5f * jump;
 }
 // The face flux from its states: (mass, x-momentum, y-momentum, p/beta).
 template <int RS>
@@ -163,16 +180,16 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 }
 
 // Divergence, sources and the point-implicit update of one cell (Eqs. RK2,
-// point_implicit): writes dQ^s and p'^s at g and adds the stage-1 squared
+// point_implicit): writes dQ^s and dp^s at g and adds the stage-1 squared
 // bracket to sq.  Fw, Fe, Fs, Fn: face fluxes, scaled by s_f (1 or 2), and
-// fdx, fdy = 1/(s_f dx), 1/(s_f dy); jw, je: reference jumps of the west and
-// east faces; src.cell(cell, g, ...) gives dQ^{m}, p'^{m}, Q^n and rho_ref
-// of the cell.
+// fdx, fdy = 1/(s_f dx), 1/(s_f dy); jw, je, js, jn: level jumps of the
+// west, east, south and north faces; src.cell(cell, g, ...) gives dQ^{m},
+// dp^{m}, Q^n and rho_ref of the cell.
 template <bool BDF, typename Src>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
-                                            float je, const Src &src, float4 &sq) {
+                                            float je, float js, float jn, const Src &src, Sq64 &sq) {
     const float div0 = (Fe.x - Fw.x) * fdx + (Fn.x - Fs.x) * fdy;
     const float div1 = (Fe.y - Fw.y) * fdx + (Fn.y - Fs.y) * fdy;
     const float div2 = (Fe.z - Fw.z) * fdx + (Fn.z - Fs.z) * fdy;
@@ -198,11 +215,12 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     rt0 *= inv_dt;
     rt1 *= inv_dt;
     rt2 *= inv_dt;
-    // reference force: -(divergence of the x-face reference means)
-    const float sref = -0.5f * (je + jw) * a.inv_dx;
+    // level force: -(divergence of the face constants' level parts)
+    const float sx = -0.5f * (je + jw) * a.inv_dx;
+    const float sy = -0.5f * (jn + js) * a.inv_dy;
     const float b0 = -div0 - rt0;
-    const float b1 = -div1 - rt1 + r0 * a.gx + sref;
-    const float b2 = -div2 - rt2 + (r0 - rref) * a.gy;
+    const float b1 = -div1 - rt1 + r0 * a.gx + sx;
+    const float b2 = -div2 - rt2 + (r0 - rref) * a.gy + sy;
     const float b3 = -div3;
     float dtau;
     if (a.local_dtau) {
@@ -220,8 +238,11 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float coef_p = a.alpha_pi_p_row ? coef : adt;
     dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
     if (stage1) {
-        const float pb = a.beta * b3;
-        sq.x += b0 * b0; sq.y += b1 * b1; sq.z += b2 * b2; sq.w += pb * pb;
+        const double d0 = b0, d1 = b1, d2 = b2, d3 = double(a.beta) * double(b3);
+        sq.x = fma(d0, d0, sq.x);
+        sq.y = fma(d1, d1, sq.y);
+        sq.z = fma(d2, d2, sq.z);
+        sq.w = fma(d3, d3, sq.w);
     }
 }
 
@@ -234,21 +255,34 @@ __device__ __forceinline__ void cp_async4(void *smem, const float *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Level jump of the x-face west of cell (gi, gj) (gi = nx: the east face of
+// the last column) and of the y-face south of it (gj = ny: the north face
+// of the top row); zero on faces that are not the domain's, and on
+// boundary faces unless the axis is periodic.
+__device__ __forceinline__ float x_face_jump(const MixedArgs &a, int gi, int gj, bool per_x) {
+    float j = 0.0f;
+    if (gj < a.ny) {
+        if (gi < a.nx) j = __ldg(a.jx + gj * a.nx + gi);
+        else if (gi == a.nx && per_x) j = __ldg(a.jx + gj * a.nx);
+    }
+    return j;
+}
+__device__ __forceinline__ float y_face_jump(const MixedArgs &a, int gi, int gj, bool per_y) {
+    float j = 0.0f;
+    if (gi < a.nx) {
+        if (gj < a.ny) j = __ldg(a.jy + gj * a.nx + gi);
+        else if (gj == a.ny && per_y) j = __ldg(a.jy + gi);
+    }
+    return j;
+}
+
 // Inputs of phases 3-4 read straight from global memory when used.
 struct DirectSrc {
-    static constexpr bool kDxfStaged = false;
+    static constexpr bool kJumpsStaged = false;
     const MixedArgs &a;
     const float4 *d0;
     __device__ __forceinline__ void prefetch(int, int) {}
-    __device__ __forceinline__ float jump(int gi, int gj, bool per_x) const {
-        float j = 0.0f;
-        if (gj < a.ny) {
-            if (gi < a.nx) j = __ldg(a.dref + gj * a.nx + gi);
-            else if (gi == a.nx && per_x) j = __ldg(a.dref + gj * a.nx);
-        }
-        return j;
-    }
-    // (dQ^{m} of rho, rho u, rho v, p'^{m}; Q^n of rho, rho u, rho v; rho_ref) of cell g
+    // (dQ^{m} of rho, rho u, rho v, dp^{m}; Q^n of rho, rho u, rho v; rho_ref) of cell g
     __device__ __forceinline__ void cell(int cell, int g, float &e0, float &e1, float &e2, float &p0, float &q0,
                                          float &q1, float &q2, float &rr) const {
         (void)cell;
@@ -259,10 +293,10 @@ struct DirectSrc {
 };
 
 // Inputs of phase 4 loaded into registers at the start of phase 3, so that
-// their latency overlaps the face fluxes (one cell per thread); the x-face
-// reference jumps are already in shared memory (staged with cp.async).
+// their latency overlaps the face fluxes (one cell per thread); the face
+// level jumps are already in shared memory (staged with cp.async).
 struct PrefetchSrc {
-    static constexpr bool kDxfStaged = true;
+    static constexpr bool kJumpsStaged = true;
     const MixedArgs &a;
     const float4 *d0;
     float v[8];
@@ -274,7 +308,6 @@ struct PrefetchSrc {
             v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
         }
     }
-    __device__ __forceinline__ float jump(int, int, bool) const { return 0.0f; }
     __device__ __forceinline__ void cell(int, int, float &e0, float &e1, float &e2, float &p0, float &q0,
                                          float &q1, float &q2, float &rr) const {
         e0 = v[0]; e1 = v[1]; e2 = v[2]; p0 = v[3]; q0 = v[4]; q1 = v[5]; q2 = v[6]; rr = v[7];
@@ -330,7 +363,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
             }
             new_gradp_half_slopes(a, Wc, hrx, hry, hux, huy, hvx, hvy, ax.x, ax.y, ax.z, sg, hpx, hpy);
         } else if (a.gradp == kGradSplitMinmod || a.gradp == kGradSplitSuperbee) {
-            // Qian et al. split (Sec. 2.3.2); p' = p here (no reference)
+            // Qian et al. split (Sec. 2.3.2); the record holds p here (no level)
             float sg = 1.0f;
             if (!interior) sg = wall_ghost_sign<float>(x0 + li - 1, y0 + lj - 1, nx, ny, a.bc);
             const float gxs = a.gx * sg, gys = a.gy * sg;
@@ -348,7 +381,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
     __syncthreads();
 
     // ---- 3. face states and Osher fluxes (pressures relative to P_f) ----
-    const bool per_x = (a.bc[0] == kPeriodic);
+    const bool per_x = (a.bc[0] == kPeriodic), per_y = (a.bc[2] == kPeriodic);
     src.prefetch(x0 + tid % TX, y0 + tid / TX);
     for (int k = tid; k < S::NXF + S::NYF; k += NT) {
         const bool isx = k < S::NXF;
@@ -357,10 +390,10 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         if (isx) {
             const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
             float jump;
-            if constexpr (Src::kDxfStaged) {
+            if constexpr (Src::kJumpsStaged) {
                 jump = sm.dxf[k];
             } else {
-                jump = src.jump(x0 + fi, y0 + fj, per_x);
+                jump = x_face_jump(a, x0 + fi, y0 + fj, per_x);
                 sm.dxf[k] = jump;
             }
             const int ga = (fj + 1) * GW + fi;
@@ -370,9 +403,16 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         } else {
             const int kk = k - S::NXF;
             const int fj = kk / TX, fi = kk - fj * TX;
+            float jump;
+            if constexpr (Src::kJumpsStaged) {
+                jump = sm.dyf[kk];
+            } else {
+                jump = y_face_jump(a, x0 + fi, y0 + fj, per_y);
+                sm.dyf[kk] = jump;
+            }
             const int ga = fj * GW + fi + 1;
             const int ca = (fj + 1) * RW + fi + 2;
-            y_face_states(sm.w[ca], sm.w[ca + RW], sm.gy[ga], sm.gy[ga + GW], f);
+            y_face_states(sm.w[ca], sm.w[ca + RW], sm.gy[ga], sm.gy[ga + GW], jump, f);
             dst = &sm.fy[kk];
         }
         // one flux call for both kinds: no divergence where a warp holds both
@@ -380,8 +420,8 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
     }
     __syncthreads();
 
-    // ---- 4. divergence + sources + point-implicit update of dQ and p' ----
-    float4 sq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // ---- 4. divergence + sources + point-implicit update of dQ and dp ----
+    Sq64 sq = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int cell = tid; cell < TX * TY; cell += NT) {
         const int lj = cell / TX, li = cell - lj * TX;
@@ -390,16 +430,17 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         const int g = gj * nx + gi;
         const int fw = lj * (TX + 1) + li;
         cell_update<BDF>(a, alpha, inv_dt, stage == 1, dout, cell, g, sm.fx[fw], sm.fx[fw + 1], sm.fy[cell],
-                         sm.fy[cell + TX], a.inv_dx, a.inv_dy, sm.dxf[fw], sm.dxf[fw + 1], src, sq);
+                         sm.fy[cell + TX], a.inv_dx, a.inv_dy, sm.dxf[fw], sm.dxf[fw + 1], sm.dyf[cell],
+                         sm.dyf[cell + TX], src, sq);
     }
     if (stage == 1) {
-        // per-warp sums in FP32, block and grid sums in FP64
+        // warp, block and grid sums in FP64
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            float v = f == 0 ? sq.x : f == 1 ? sq.y : f == 2 ? sq.z : sq.w;
+            double v = f == 0 ? sq.x : f == 1 ? sq.y : f == 2 ? sq.z : sq.w;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if ((tid & 31) == 0) sm.red[f][tid >> 5] = double(v);
+            if ((tid & 31) == 0) sm.red[f][tid >> 5] = v;
         }
         __syncthreads();
         if (tid < 4) {
@@ -445,14 +486,21 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
     const bool need_rt = new_gradp && a.realtime;
 
     if constexpr (PF) {
-        // x-face reference jumps (zero outside the domain)
-        const bool per_x = (a.bc[0] == kPeriodic);
+        // face level jumps (zero outside the domain, as x_face_jump, y_face_jump)
+        const bool per_x = (a.bc[0] == kPeriodic), per_y = (a.bc[2] == kPeriodic);
         for (int k = tid; k < S::NXF; k += NT) {
             const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
             const int gi = x0 + fi, gj = y0 + fj;
-            if (gj < ny && gi < nx) cp_async4(&sm.dxf[k], a.dref + gj * nx + gi);
-            else if (gj < ny && gi == nx && per_x) cp_async4(&sm.dxf[k], a.dref + gj * nx);
+            if (gj < ny && gi < nx) cp_async4(&sm.dxf[k], a.jx + gj * nx + gi);
+            else if (gj < ny && gi == nx && per_x) cp_async4(&sm.dxf[k], a.jx + gj * nx);
             else sm.dxf[k] = 0.0f;
+        }
+        for (int k = tid; k < S::NYF; k += NT) {
+            const int fj = k / TX, fi = k - fj * TX;
+            const int gi = x0 + fi, gj = y0 + fj;
+            if (gi < nx && gj < ny) cp_async4(&sm.dyf[k], a.jy + gj * nx + gi);
+            else if (gi < nx && gj == ny && per_y) cp_async4(&sm.dyf[k], a.jy + gi);
+            else sm.dyf[k] = 0.0f;
         }
         // ring: (dQ of rho u, dQ of rho v, rho_ref, fold bits)
         if (new_gradp) {
@@ -479,7 +527,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
         }
     }
 
-    // ---- 1. stage Q^{s-1} = Q^n + dQ^{s-1} (+ halo) as W = (rho, u, v, p') ----
+    // ---- 1. stage Q^{s-1} = Q^n + dQ^{s-1} (+ halo) as W = (rho, u, v, dp) ----
     if (interior) {
         const int base = (y0 - 2) * nx + (x0 - 2);
         for (int k = tid; k < RW * RH; k += NT) {
@@ -593,7 +641,7 @@ struct HeldSrc {
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
 // The per-column parts of the boundary logic are formed once per strip and
 // interior rows skip the fold; the update loads its two records (dQ^{m},
-// p'^{m}; Q^n, rho_ref) when it runs: the same lane loaded them two rows
+// dp^{m}; Q^n, rho_ref) when it runs: the same lane loaded them two rows
 // before, so they come from L1, and nothing more is held across rows.
 template <int H>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
@@ -622,9 +670,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     // raw inputs of a row, loaded one row ahead of use
     struct Raw {
         float4 q;                           // Q^n of rho, rho u, rho v; rho_ref
-        float4 d;                           // dQ^{s-1} of rho, rho u, rho v; p'
-        float4 e;                           // dQ^{m}, p'^{m} (the ring terms)
-        float jump;                         // reference jump across the east x-face (0 off the tank's rows)
+        float4 d;                           // dQ^{s-1} of rho, rho u, rho v; dp
+        float4 e;                           // dQ^{m}, dp^{m} (the ring terms)
+        float jump;                         // level jump across the east x-face (0 off the tank's rows)
+        float jy;                           // level jump across the south y-face (0 off the tank's faces)
         int fl;                             // fold bits
     };
     // Per-column parts of the boundary logic, fixed for the whole strip, in
@@ -634,6 +683,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     // (-1: none).
     const int gi = c + 1;   // the east x-face's column
     const int jcol = (gi >= 0 && gi < nx) ? gi : ((gi == nx && per_x) ? 0 : -1);
+    const bool own_col = c >= 0 && c < nx;   // the south y-face of this column is the tank's
+    const bool per_y = (a.bc[2] == kPeriodic);
     const int colbits = (nfx & 1) | ((tfx & 1) << 1) |
                         (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
                         (is_wall(a.bc[2]) ? 8 : 0) | (is_wall(a.bc[3]) ? 16 : 0);
@@ -650,22 +701,26 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         R.q = __ldg(a.qn + s);
         R.d = din[s];
         R.e = d0[s];
-        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.dref + k * nx + jcol) : 0.0f;
+        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.jx + k * nx + jcol) : 0.0f;
+        // row ny: the north face of the top row (periodic: the south face of row 0)
+        R.jy = (own_col && k >= 0 && (k < ny || (k == ny && per_y))) ? __ldg(a.jy + (k < ny ? k : 0) * nx + c)
+                                                                       : 0.0f;
     };
 
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
     float4 Sym2 = Wm2;                                       // y half slopes of row k-2
     float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
-    float Jm2 = 0.0f;                                        // east x-face reference jump of row k-2
+    float Jm2 = 0.0f;                                        // east x-face level jump of row k-2
+    float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
     Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
     int srk, srn;
-    float4 sq = make_float4(0.f, 0.f, 0.f, 0.f);
+    Sq64 sq = {0.0, 0.0, 0.0, 0.0};
     load_raw(y0 - 2, Rk, srk);
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
         // prefetch: the next row's inputs
         load_raw(k + 1, Rn, srn);
-        // ---- W = (rho, u, v, p') of Q^{s-1} at row k ----
+        // ---- W = (rho, u, v, dp) of Q^{s-1} at row k ----
         float4 W0;
         {
             const float r = Rk.q.x + Rk.d.x;
@@ -703,7 +758,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             // harmless, on the first row): both fluxes as one packed pair ----
             FaceStates f, fy;
             x_face_states(Wm1, Wn, Sx, Sn, jump, f);
-            y_face_states(Wm2, Wm1, Sym2, Sy, fy);
+            y_face_states(Wm2, Wm1, Sym2, Sy, Rm1.jy, fy);
             float2 Fp[4];
             osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
                             make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
@@ -721,9 +776,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
-                                           Fy, hidx, hidy, jw, Jm2, Uk, sq);
+                                           Fy, hidx, hidy, jw, Jm2, Jyp, Rm1.jy, Uk, sq);
                 }
                 Fyp = Fy;
+                Jyp = Rm1.jy;
             }
             Fxm2 = Fx;
             Jm2 = jump;
@@ -736,8 +792,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         srk = srn;
     }
     if (stage == 1) {
-        // per-warp sums in FP32, one FP64 partial per strip
-        float v0 = sq.x, v1 = sq.y, v2 = sq.z, v3 = sq.w;
+        // the strip's sums, in FP64 throughout
+        double v0 = sq.x, v1 = sq.y, v2 = sq.z, v3 = sq.w;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             v0 += __shfl_down_sync(0xffffffffu, v0, o);
@@ -806,33 +862,66 @@ static __global__ void realtime_dt_kernel_mixed(const MixedArgs a, int cur, doub
     if ((threadIdx.x & 31) == 0) atomicMin(out, (unsigned long long)__double_as_longlong(mn));
 }
 
-// Start of a physical step in the mixed form: the FP64 level absorbs the
-// increments (Q^n <- Q^n + dQ, Alg. 1), its FP32 copy is refreshed, the
-// increments restart from zero, and p' is kept for a restore.
+// Start of a physical step in the mixed form, one cell: the FP64 levels
+// absorb the increments (Q^n <- Q^n + dQ, p^n <- p^n + dp, Alg. 1), the FP32
+// copy of Q^n is refreshed and the increments restart from zero.  Without a
+// pressure level the record keeps p, and p is kept for a restore.
+__device__ __forceinline__ void mixed_level_shift(const MixedArgs &a, int cur, size_t g) {
+    const float4 e = a.d[cur][g];
+    float4 q4 = a.qn[g];   // .w (rho_ref) stays
+    const float dqs[3] = {e.x, e.y, e.z};
+    float qs[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float dq = dqs[f];
+        const double q = a.q64[f][g] + double(dq);
+        // differences to the older levels, relative to the new Q^n
+        if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
+        if (a.D1[0]) a.D1[f][g] = dq;
+        a.q64[f][g] = q;
+        qs[f] = float(q);
+    }
+    q4.x = qs[0]; q4.y = qs[1]; q4.z = qs[2];
+    a.qn[g] = q4;
+    if (a.plevel) {
+        const double p = a.q64[3][g] + double(e.w);
+        a.q64[3][g] = p;
+        a.p64_step[g] = p;
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, e.w);
+        a.lev_p[g] = e.w;
+    }
+}
+
+// Jumps of the pressure level across the west and south faces of cell g,
+// differenced in FP64 and rounded once: jx = p^n(i) - p^n(i-1),
+// jy = q^n(j) - q^n(j-1), q^n = p^n - p_ref.  Boundary faces carry zero (a
+// wall or transmissive ghost repeats its cell's level) unless the axis is
+// periodic.  Without a pressure level p^n is zero and so are the jumps.
+__device__ __forceinline__ void mixed_level_jumps(const MixedArgs &a, size_t g) {
+    const int nx = a.nx, ny = a.ny;
+    const int j = (int)(g / nx), i = (int)(g - (size_t)j * nx);
+    const double *P = a.q64[3], *R = a.pref64;
+    const double p = P[g];
+    float jx = 0.0f, jy = 0.0f;
+    if (i > 0) jx = float(p - P[g - 1]);
+    else if (a.bc[0] == kPeriodic) jx = float(p - P[g + nx - 1]);
+    size_t s = g;   // the cell below across the south face
+    bool has_s = false;
+    if (j > 0) { s = g - nx; has_s = true; }
+    else if (a.bc[2] == kPeriodic) { s = g + (size_t)(ny - 1) * nx; has_s = true; }
+    if (has_s) jy = R ? float((p - R[g]) - (P[s] - R[s])) : float(p - P[s]);
+    a.jx[g] = jx;
+    a.jy[g] = jy;
+}
+
 static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters) {
     Ctl *ctl = a.ctl;
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
-    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x) {
-        const float4 e = a.d[cur][g];
-        float4 q4 = a.qn[g];   // .w (rho_ref) stays
-        const float dqs[3] = {e.x, e.y, e.z};
-        float qs[3];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            const float dq = dqs[f];
-            const double q = a.q64[f][g] + double(dq);
-            // differences to the older levels, relative to the new Q^n
-            if (a.D2[0]) a.D2[f][g] = float(double(a.D1[f][g]) + double(dq));
-            if (a.D1[0]) a.D1[f][g] = dq;
-            a.q64[f][g] = q;
-            qs[f] = float(q);
-        }
-        q4.x = qs[0]; q4.y = qs[1]; q4.z = qs[2];
-        a.qn[g] = q4;
-        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, e.w);
-        a.lev_p[g] = e.w;
-    }
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_shift(a, cur, g);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->iter = 0;
         ctl->done = 0;
@@ -843,15 +932,66 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
         ctl->dt = dt;
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;
+        ctl->rebase = 0;
     }
 }
 
-// After a non-finite residual: back to the state at the start of the step.
+// After the level shift (a separate launch: it reads the neighbours' new
+// levels).
+static __global__ void level_jumps_kernel_mixed(const MixedArgs a) {
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_jumps(a, g);
+}
+
+// Back to the state at the start of the step, one cell (after a
+// non-finite residual): the levels hold it, the pressure level as it was
+// before any rebase of the step (the jumps are formed again afterwards).
+__device__ __forceinline__ void mixed_restore(const MixedArgs &a, int cur, size_t g) {
+    if (a.plevel) a.q64[3][g] = a.p64_step[g];
+    a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, a.plevel ? 0.0f : a.lev_p[g]);
+}
+
+// Rebase of the pressure within a physical step, one cell: the FP64 level
+// absorbs the current increment, which restarts from zero (the pressure has
+// no real-time term, so its level may move at any time; the sum is exact up
+// to one FP64 rounding).  FP32 then holds only the change since the rebase:
+// in the first iterations of a step that starts from an unbalanced state
+// (a collapsing column) the pressure moves by as much as the hydrostatic
+// head.  The jumps are formed again by a second launch (mixed_level_jumps).
+__device__ __forceinline__ void mixed_rebase_shift(const MixedArgs &a, int cur, size_t g) {
+    float4 *r = a.d[cur] + g;
+    a.q64[3][g] += double(r->w);
+    r->w = 0.0f;
+}
+
+// The end of iteration m sets ctl->rebase after m = 1, 2, 4, 8, ... (not on
+// the last iteration); otherwise these return at once.
+static __global__ void rebase_shift_kernel_mixed(const MixedArgs a) {
+    pdl_trigger();
+    pdl_wait();
+    const Ctl *ctl = a.ctl;
+    if (!ctl->rebase) return;
+    const int cur = ctl->cur;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_rebase_shift(a, cur, g);
+}
+
+static __global__ void rebase_jumps_kernel_mixed(const MixedArgs a) {
+    pdl_trigger();
+    pdl_wait();
+    if (!a.ctl->rebase) return;
+    const size_t N = (size_t)a.nx * a.ny;
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
+        mixed_level_jumps(a, g);
+}
+
 static __global__ void restore_kernel_mixed(const MixedArgs a) {
     const int cur = a.ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
     for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < N; g += (size_t)gridDim.x * blockDim.x)
-        a.d[cur][g] = make_float4(0.0f, 0.0f, 0.0f, a.lev_p[g]);
+        mixed_restore(a, cur, g);
 }
 
 }  // namespace acgb

@@ -17,24 +17,29 @@ inline bool mixed_uses_reference(const ac_bc &bc, int gradp) {
     return is_wall_side(bc.ylo) && is_wall_side(bc.yhi) && gradp == AC_GRADP_NEW;
 }
 
+// The pressure is carried as an FP32 increment over an FP64 level when the
+// pressure gradient comes from the rearranged momentum equation; a limited
+// pressure gradient needs pressure differences, so there the FP32 record
+// holds p itself.
+inline bool mixed_uses_level(int gradp) { return gradp == AC_GRADP_NEW; }
+
 // From host fields f = (rho, rho u, rho v, p) of an nx x ny grid: the FP32
 // reference density, its FP64 discrete hydrostatic columns p_ref (anchored at
-// each column's top cell), the FP32 jump of p_ref across each cell's west
-// x-face, and p' = p - p_ref in FP32.  Without a reference all are zero and
-// p' = p.
+// each column's top cell; empty without a reference), and the initial
+// pressure record and level: (FP32 dp = 0, FP64 p^n = p) with a pressure
+// level, (FP32 p, 0) without.
 struct MixedReference {
-    std::vector<float> rho_ref, dref, p_prime;
-    std::vector<double> p_ref;
+    std::vector<float> rho_ref, p_record;
+    std::vector<double> p_ref, p_level;
 };
 
-inline void build_mixed_reference(int nx, int ny, double dy, double gy, const ac_bc &bc, bool use_ref,
+inline void build_mixed_reference(int nx, int ny, double dy, double gy, bool use_ref, bool plevel,
                                   const double *const f[4], MixedReference &r) {
     const size_t N = (size_t)nx * ny;
     r.rho_ref.assign(N, 0.0f);
-    r.dref.assign(N, 0.0f);
-    r.p_prime.resize(N);
-    r.p_ref.assign(N, 0.0);
+    r.p_ref.clear();
     if (use_ref) {
+        r.p_ref.assign(N, 0.0);
         for (size_t k = 0; k < N; ++k) r.rho_ref[k] = float(f[0][k]);
         for (int i = 0; i < nx; ++i) {
             const size_t top = (size_t)(ny - 1) * nx + i;
@@ -44,15 +49,13 @@ inline void build_mixed_reference(int nx, int ny, double dy, double gy, const ac
                 r.p_ref[k] = r.p_ref[k + nx] - (double(r.rho_ref[k]) + double(r.rho_ref[k + nx])) * gy * dy / 2.0;
             }
         }
-        const bool per_x = bc.xlo == AC_BC_PERIODIC;
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                const size_t k = (size_t)j * nx + i;
-                if (i > 0) r.dref[k] = float(r.p_ref[k] - r.p_ref[k - 1]);
-                else if (per_x) r.dref[k] = float(r.p_ref[k] - r.p_ref[k + nx - 1]);
-            }
     }
-    for (size_t k = 0; k < N; ++k) r.p_prime[k] = float(f[3][k] - r.p_ref[k]);
+    r.p_record.resize(N);
+    r.p_level.resize(N);
+    for (size_t k = 0; k < N; ++k) {
+        r.p_record[k] = plevel ? 0.0f : float(f[3][k]);
+        r.p_level[k] = plevel ? f[3][k] : 0.0;
+    }
 }
 
 }  // namespace acgb

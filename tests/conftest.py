@@ -25,22 +25,28 @@ def load_golden(name):
     return rows
 
 
-def field_scales(state):
-    """Per-field scale for relative errors.  rho and p: max |field|.  The
-    momentum is a vector: both components are measured against the largest
-    momentum magnitude max |rho u|, floored at max(rho) * 1e-3 m/s so that a
+MOMENTUM_FLOOR = 1e-3   # m/s: momentum scales are at least max(rho) times this
+
+
+def field_scales(state, floor=True):
+    """Per-field scale for relative errors: every field, each momentum
+    component included, against its own largest magnitude.  With `floor`,
+    the momentum scales are at least max(rho) * MOMENTUM_FLOOR, so that a
     fluid at rest (round-off momenta) is compared against a physical scale
-    rather than noise."""
+    rather than noise; without it only a zero field is replaced by 1e-300."""
     import numpy as np
-    rho = np.abs(state[0]).max()
-    mom = float(np.sqrt(np.asarray(state[1]) ** 2 + np.asarray(state[2]) ** 2).max())
-    mom = max(mom, 1e-3 * rho)
-    return [float(rho), mom, mom, max(float(np.abs(state[3]).max()), 1e-12)]
+    rho = float(np.abs(state[0]).max())
+    mom = [float(np.abs(state[k]).max()) for k in (1, 2)]
+    if floor:
+        mom = [max(m, MOMENTUM_FLOOR * rho) for m in mom]
+    else:
+        mom = [max(m, 1e-300) for m in mom]
+    return [rho, mom[0], mom[1], max(float(np.abs(state[3]).max()), 1e-12)]
 
 
-def rel_errors(got, ref):
+def rel_errors(got, ref, floor=True):
     import numpy as np
-    sc = field_scales(ref)
+    sc = field_scales(ref, floor)
     return [float(np.abs(np.asarray(g) - np.asarray(r)).max() / s) for g, r, s in zip(got, ref, sc)]
 
 

@@ -1,9 +1,10 @@
 """GPU FP64 sweep vs the FP64 oracle, element by element, through the C ABI.
 
 Bar: relative L-infinity error <= 1e-11 per field after one physical step
-from an identical input state (momentum components scaled by the largest
-momentum magnitude, at least max(rho) * 1e-3 m/s), and identical pseudo-iteration counts when the stopping test ends
-the step.  Sizes span several 32x8 tiles with ragged tails; options cover
+from an identical input state (every field, each momentum component
+separately, against its own largest magnitude; momentum scales at least
+max(rho) * 1e-3 m/s), and identical pseudo-iteration counts when the
+stopping test ends the step.  Sizes span several 32x8 tiles with ragged tails; options cover
 every boundary kind, pressure-gradient method, limiter, stage count and
 pseudo-time-step mode.
 """
