@@ -445,7 +445,8 @@ struct MixedBackend : Backend {
     int variant = -1;
     float4 *d[3] = {};   // per cell (dQ of rho, rho u, rho v; dp or p), three rotating buffers
     float4 *qn = nullptr;  // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    float *jx = nullptr, *jy = nullptr, *lev_p = nullptr;
+    float2 *jmp = nullptr;   // per cell level jumps (west face, south face)
+    float *lev_p = nullptr;
     float *D1[3] = {}, *D2[3] = {};   // Q^n - Q^{n-1}, Q^n - Q^{n-2} (BDF2, BDF3)
     double *q64[4] = {};   // FP64 levels of rho, rho u, rho v, p
     double *p64_step = nullptr;   // FP64 pressure level at the start of the step
@@ -580,7 +581,7 @@ struct MixedBackend : Backend {
         for (int f = 0; f < 4; ++f) a.q64[f] = q64[f];
         a.p64_step = p64_step;
         a.pref64 = pref64;
-        a.jx = jx; a.jy = jy; a.lev_p = lev_p;
+        a.jmp = jmp; a.lev_p = lev_p;
         for (int f = 0; f < 3; ++f) { a.D1[f] = D1[f]; a.D2[f] = D2[f]; }
         a.order = c->order_now;
         a.B0 = float(kBDF[c->order_now][0]);
@@ -601,8 +602,7 @@ struct MixedBackend : Backend {
         for (int f = 0; f < 4; ++f) CK(cudaMalloc(&q64[f], db));
         if (plevel) CK(cudaMalloc(&p64_step, db));
         if (use_ref) CK(cudaMalloc(&pref64, db));
-        CK(cudaMalloc(&jx, fb));
-        CK(cudaMalloc(&jy, fb));
+        CK(cudaMalloc(&jmp, c->N * sizeof(float2)));
         CK(cudaMalloc(&lev_p, fb));
         for (int f = 0; f < 3; ++f) {
             if (c->opt.bdf_order >= 2) CK(cudaMalloc(&D1[f], fb));
@@ -638,8 +638,7 @@ struct MixedBackend : Backend {
         for (int f = 0; f < 4; ++f) cudaFree(q64[f]);
         cudaFree(p64_step);
         cudaFree(pref64);
-        cudaFree(jx);
-        cudaFree(jy);
+        cudaFree(jmp);
         cudaFree(lev_p);
         for (int f = 0; f < 3; ++f) { cudaFree(D1[f]); cudaFree(D2[f]); }
     }

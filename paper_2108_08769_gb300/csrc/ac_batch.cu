@@ -321,7 +321,8 @@ struct ac_batch {
     // pooled device arrays
     float4 *d[3];                       // per cell (dQ of rho, rho u, rho v; dp or p), three rotating pools
     float4 *qn;                         // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    float *jx, *jy, *lev_p;             // level jumps, restore copy of p (without a level)
+    float2 *jmp;                        // per cell level jumps (west face, south face)
+    float *lev_p;                       // restore copy of p (without a level)
     float *D1[3], *D2[3];               // BDF2/BDF3 level differences (pools)
     double *q64[4];                     // FP64 levels of rho, rho u, rho v, p
     double *p64_step;                   // FP64 pressure levels at the start of the step
@@ -545,8 +546,7 @@ void ac_batch_destroy(ac_batch *b) {
     for (int f = 0; f < 4; ++f) cudaFree(b->q64[f]);
     cudaFree(b->p64_step);
     cudaFree(b->pref64);
-    cudaFree(b->jx);
-    cudaFree(b->jy);
+    cudaFree(b->jmp);
     cudaFree(b->lev_p);
     cudaFree(b->partials);
     cudaFree(b->ctl);
@@ -628,8 +628,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     for (int f = 0; f < 4; ++f) CKB(cudaMalloc(&b->q64[f], db));
     if (b->plevel) CKB(cudaMalloc(&b->p64_step, db));
     if (any_ref) CKB(cudaMalloc(&b->pref64, db));
-    CKB(cudaMalloc(&b->jx, fb));
-    CKB(cudaMalloc(&b->jy, fb));
+    CKB(cudaMalloc(&b->jmp, total * sizeof(float2)));
     CKB(cudaMalloc(&b->lev_p, fb));
     for (int f = 0; f < 3; ++f) {
         if (o.bdf_order >= 2) CKB(cudaMalloc(&b->D1[f], fb));
@@ -688,8 +687,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         for (int f = 0; f < 4; ++f) a.q64[f] = b->q64[f] + pos;
         a.p64_step = b->p64_step ? b->p64_step + pos : nullptr;
         a.pref64 = b->use_ref[k] ? b->pref64 + pos : nullptr;
-        a.jx = b->jx + pos;
-        a.jy = b->jy + pos;
+        a.jmp = b->jmp + pos;
         a.lev_p = b->lev_p + pos;
         for (int f = 0; f < 3; ++f) {
             a.D1[f] = b->D1[f] ? b->D1[f] + pos : nullptr;

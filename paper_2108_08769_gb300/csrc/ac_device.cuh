@@ -6,6 +6,7 @@
 // memory, no library calls.
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -337,7 +338,17 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
 // on k = w rho / c (1/beta stays on the jump term, where it costs no
 // register held across a caller's loop).  Inputs are (rho, un, ut, p) per
 // lane; returns 2F per lane (the caller's divergence takes the 1/2).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+// a - b as one packed FP32x2 subtraction (the same value as a + (-b),
+// without separate sign flips of b's halves)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
 
 __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL, float2 pL, float2 rR, float2 uR,
                                                 float2 vR, float2 pR, float beta, float inv_beta, float2 F[4]) {
@@ -346,7 +357,7 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
     const float2 mR = __fmul2_rn(rR, uR), nR = __fmul2_rn(rR, vR);
     const float2 dr = sub2(rR, rL), dm = sub2(mR, mL), dn = sub2(nR, nL), dp = sub2(pR, pL);
     const float2 dq = __fmul2_rn(dp, ib);   // the jump of Q's last component p/beta
-    const float2 ndr = neg2(dr);
+    const float2 ndr = sub2(rL, rR);        // -dr, exactly
     // central parts F(Q_L) + F(Q_R) first, so that the face states die here
     const float2 c0 = __fadd2_rn(mL, mR);
     const float2 c1 = __fadd2_rn(__ffma2_rn(mR, uR, __ffma2_rn(mL, uL, pL)), pR);
@@ -368,10 +379,10 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
         // l4 = u/2 + c/2, l5 = u/2 - c/2 (c/2 is exact, so one rounding each)
         const float2 hu = __fmul2_rn(dup2(0.5f), u);
         const float2 l4 = __ffma2_rn(dup2(0.5f), c, hu), l5 = __ffma2_rn(dup2(-0.5f), c, hu);
-        const float2 au = make_float2(fabsf(u.x), fabsf(u.y)), nau = make_float2(-au.x, -au.y);
+        const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
         const float2 a = __fmul2_rn(__ffma2_rn(u, ndr, dm), ib);
         const float2 k = __fmul2_rn(__fmul2_rn(w, r), ic);
-        const float2 g4 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l4, nau), k), __ffma2_rn(l4, a, dq));
+        const float2 g4 = __fmul2_rn(__fmul2_rn(sub2(l4, au), k), __ffma2_rn(l4, a, dq));
         const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dq));
         const float2 e = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
         const float2 gs = __fmul2_rn(ir, __fadd2_rn(g4, g5));

@@ -12,9 +12,10 @@
 //             (Q^{n+1} = Q^n + dQ in FP64: the level accumulation)
 //   pref64    FP64 static reference pressure: the discrete hydrostatic
 //             column of rho_ref (none: zero)
-//   jx, jy    FP32 jumps of the level across each cell's west and south
-//             faces: jx = p^n(i) - p^n(i-1), jy = q^n(j) - q^n(j-1) with
-//             q^n = p^n - p_ref, formed in FP64 at the start of each step
+//   jmp       FP32 jumps of the level across each cell's west and south
+//             faces, (jx, jy) in one 8-byte record: jx = p^n(i) - p^n(i-1),
+//             jy = q^n(j) - q^n(j-1) with q^n = p^n - p_ref, formed in FP64
+//             at the start of each step (and at each rebase)
 //
 // Why this is exact algebra and not an approximation of the scheme:
 //   * The real-time term of Eq. bdf is (B0 Q^{m} + B1 Q^n + B2 Q^{n-1} +
@@ -59,7 +60,7 @@ struct MixedArgs {
     int plevel;            // 1: pressure as dp over the FP64 level p^n; 0: the record holds p
     float4 *d[3];          // per cell (dQ of rho, rho u, rho v; dp or p), three rotating buffers
     float4 *qn;            // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
-    float *jx, *jy;        // level jumps across the west and south faces
+    float2 *jmp;           // per cell (level jump across the west face, across the south face)
     float *lev_p;          // p at the start of the physical step (plevel = 0, for a restore)
     float *D1[3], *D2[3];  // Q^n - Q^{n-1}, Q^n - Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
     int order;             // backward-difference order used in this step (1..3)
@@ -71,10 +72,41 @@ struct MixedArgs {
     Ctl *ctl;
 };
 
-// Residual partial sums: each cell's stage-1 bracket is squared exactly in
-// FP64 (an FP32 value squared fits a double's mantissa) and summed in FP64.
+// Residual partial sums of the tile sweep (one or two cells per thread):
+// each cell's stage-1 bracket is squared exactly in FP64 (an FP32 value
+// squared fits a double's mantissa) and summed in FP64.
 struct Sq64 {
     double x, y, z, w;
+    __device__ __forceinline__ void add(float b0, float b1, float b2, float b3) {
+        const double d0 = b0, d1 = b1, d2 = b2, d3 = b3;
+        x = fma(d0, d0, x);
+        y = fma(d1, d1, y);
+        z = fma(d2, d2, z);
+        w = fma(d3, d3, w);
+    }
+};
+
+// Residual partial sums of the column-strip sweep, where one lane adds the
+// squares of up to 256 cells: compensated (Kahan) FP32 summation per lane,
+// whose error stays within about two FP32 roundings of the lane's total
+// whatever the number of cells (a plain FP32 sum of n squares can be off by
+// n roundings), and FP64 for every sum across lanes, strips and the grid
+// (lane_sum()).  On GB300 the FP64 unit runs at 1/64 of the FP32 rate; one
+// FP64 accumulation per cell cost 18 % of a stage-1 strip launch.
+struct SqKahan {
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    __device__ __forceinline__ void add(float b0, float b1, float b2, float b3) {
+        const float q[4] = {b0 * b0, b1 * b1, b2 * b2, b3 * b3};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float y = __fsub_rn(q[f], c[f]);
+            const float t = __fadd_rn(s[f], y);
+            c[f] = __fsub_rn(__fsub_rn(t, s[f]), y);
+            s[f] = t;
+        }
+    }
+    // the lane's sum of field f, the compensation folded in FP64
+    __device__ __forceinline__ double lane_sum(int f) const { return double(s[f]) - double(c[f]); }
 };
 
 template <int TX, int TY>
@@ -185,11 +217,11 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // fdx, fdy = 1/(s_f dx), 1/(s_f dy); jw, je, js, jn: level jumps of the
 // west, east, south and north faces; src.cell(cell, g, ...) gives dQ^{m},
 // dp^{m}, Q^n and rho_ref of the cell.
-template <bool BDF, typename Src>
+template <bool BDF, typename Src, typename Sq>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
-                                            float je, float js, float jn, const Src &src, Sq64 &sq) {
+                                            float je, float js, float jn, const Src &src, Sq &sq) {
     const float div0 = (Fe.x - Fw.x) * fdx + (Fn.x - Fs.x) * fdy;
     const float div1 = (Fe.y - Fw.y) * fdx + (Fn.y - Fs.y) * fdy;
     const float div2 = (Fe.z - Fw.z) * fdx + (Fn.z - Fs.z) * fdy;
@@ -237,13 +269,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
     const float coef_p = a.alpha_pi_p_row ? coef : adt;
     dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
-    if (stage1) {
-        const double d0 = b0, d1 = b1, d2 = b2, d3 = double(a.beta) * double(b3);
-        sq.x = fma(d0, d0, sq.x);
-        sq.y = fma(d1, d1, sq.y);
-        sq.z = fma(d2, d2, sq.z);
-        sq.w = fma(d3, d3, sq.w);
-    }
+    if (stage1) sq.add(b0, b1, b2, a.beta * b3);   // the p row in pressure units
 }
 
 // 4-byte global -> shared copy that completes asynchronously (cp.async);
@@ -262,16 +288,16 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float x_face_jump(const MixedArgs &a, int gi, int gj, bool per_x) {
     float j = 0.0f;
     if (gj < a.ny) {
-        if (gi < a.nx) j = __ldg(a.jx + gj * a.nx + gi);
-        else if (gi == a.nx && per_x) j = __ldg(a.jx + gj * a.nx);
+        if (gi < a.nx) j = __ldg(&a.jmp[gj * a.nx + gi].x);
+        else if (gi == a.nx && per_x) j = __ldg(&a.jmp[gj * a.nx].x);
     }
     return j;
 }
 __device__ __forceinline__ float y_face_jump(const MixedArgs &a, int gi, int gj, bool per_y) {
     float j = 0.0f;
     if (gi < a.nx) {
-        if (gj < a.ny) j = __ldg(a.jy + gj * a.nx + gi);
-        else if (gj == a.ny && per_y) j = __ldg(a.jy + gi);
+        if (gj < a.ny) j = __ldg(&a.jmp[gj * a.nx + gi].y);
+        else if (gj == a.ny && per_y) j = __ldg(&a.jmp[gi].y);
     }
     return j;
 }
@@ -491,15 +517,15 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs &a, int stage, float 
         for (int k = tid; k < S::NXF; k += NT) {
             const int fj = k / (TX + 1), fi = k - fj * (TX + 1);
             const int gi = x0 + fi, gj = y0 + fj;
-            if (gj < ny && gi < nx) cp_async4(&sm.dxf[k], a.jx + gj * nx + gi);
-            else if (gj < ny && gi == nx && per_x) cp_async4(&sm.dxf[k], a.jx + gj * nx);
+            if (gj < ny && gi < nx) cp_async4(&sm.dxf[k], &a.jmp[gj * nx + gi].x);
+            else if (gj < ny && gi == nx && per_x) cp_async4(&sm.dxf[k], &a.jmp[gj * nx].x);
             else sm.dxf[k] = 0.0f;
         }
         for (int k = tid; k < S::NYF; k += NT) {
             const int fj = k / TX, fi = k - fj * TX;
             const int gi = x0 + fi, gj = y0 + fj;
-            if (gi < nx && gj < ny) cp_async4(&sm.dyf[k], a.jy + gj * nx + gi);
-            else if (gi < nx && gj == ny && per_y) cp_async4(&sm.dyf[k], a.jy + gi);
+            if (gi < nx && gj < ny) cp_async4(&sm.dyf[k], &a.jmp[gj * nx + gi].y);
+            else if (gi < nx && gj == ny && per_y) cp_async4(&sm.dyf[k], &a.jmp[gi].y);
             else sm.dyf[k] = 0.0f;
         }
         // ring: (dQ of rho u, dQ of rho v, rho_ref, fold bits)
@@ -701,9 +727,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         R.q = __ldg(a.qn + s);
         R.d = din[s];
         R.e = d0[s];
-        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(a.jx + k * nx + jcol) : 0.0f;
+        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(&a.jmp[k * nx + jcol].x) : 0.0f;
         // row ny: the north face of the top row (periodic: the south face of row 0)
-        R.jy = (own_col && k >= 0 && (k < ny || (k == ny && per_y))) ? __ldg(a.jy + (k < ny ? k : 0) * nx + c)
+        R.jy = (own_col && k >= 0 && (k < ny || (k == ny && per_y))) ? __ldg(&a.jmp[(k < ny ? k : 0) * nx + c].y)
                                                                        : 0.0f;
     };
 
@@ -715,7 +741,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
     Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
     int srk, srn;
-    Sq64 sq = {0.0, 0.0, 0.0, 0.0};
+    SqKahan sq;
     load_raw(y0 - 2, Rk, srk);
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
         // prefetch: the next row's inputs
@@ -792,8 +818,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         srk = srn;
     }
     if (stage == 1) {
-        // the strip's sums, in FP64 throughout
-        double v0 = sq.x, v1 = sq.y, v2 = sq.z, v3 = sq.w;
+        // the strip's sums across lanes, in FP64
+        double v0 = sq.lane_sum(0), v1 = sq.lane_sum(1), v2 = sq.lane_sum(2), v3 = sq.lane_sum(3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             v0 += __shfl_down_sync(0xffffffffu, v0, o);
@@ -912,8 +938,7 @@ __device__ __forceinline__ void mixed_level_jumps(const MixedArgs &a, size_t g) 
     if (j > 0) { s = g - nx; has_s = true; }
     else if (a.bc[2] == kPeriodic) { s = g + (size_t)(ny - 1) * nx; has_s = true; }
     if (has_s) jy = R ? float((p - R[g]) - (P[s] - R[s])) : float(p - P[s]);
-    a.jx[g] = jx;
-    a.jy[g] = jy;
+    a.jmp[g] = make_float2(jx, jy);
 }
 
 static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters) {

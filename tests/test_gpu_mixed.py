@@ -253,23 +253,24 @@ def test_every_tile_variant_against_oracle(monkeypatch, v, bc):
     check(got, oracle_run(case, iters=6))
 
 
-STRIP_VARIANT = 16   # column-strip sweep, 64-row strips
+STRIP_VARIANTS = [16, 18]   # column-strip sweeps, 64- and 256-row strips
 
 
+@pytest.mark.parametrize("v", STRIP_VARIANTS, ids=["strips_64", "strips_256"])
 @pytest.mark.parametrize("opts", [dict(limiter_k=2), dict(realtime=False, cfl_tau=0.3), dict(local_dtau=False),
                                   dict(alpha_pi_p_row=False), dict(s_max=2), dict(s_max=4)],
                          ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
-def test_strip_sweep_options_against_oracle(monkeypatch, opts):
-    """The column-strip form under every option it implements (it covers
-    the new pressure gradient and Backward-Euler), forced on a ragged grid
-    whose strips have ghost columns on both sides."""
-    monkeypatch.setenv("AC_TILE", str(STRIP_VARIANT))
+def test_strip_sweep_options_against_oracle(monkeypatch, opts, v):
+    """The column-strip sweep under every option it implements (the new
+    pressure gradient and Backward-Euler), forced on a ragged grid whose
+    strips have ghost columns on both sides."""
+    monkeypatch.setenv("AC_TILE", str(v))
     case = W.random_two_fluid(61, 83, ratio=300.0, c0=10.0, bc=("slip", "noslip", "slip", "transmissive"))
-    for k, v in opts.items():
-        setattr(case.options, k, v)
+    for name, value in opts.items():
+        setattr(case.options, name, value)
     t = ac.Tank.from_case(case, precision="mixed")
     t.physical_step(case.dt, -1.0, 6)
-    assert t.tile_shape()[3] == STRIP_VARIANT
+    assert t.tile_shape()[3] == v
     got = t.get_state()
     t.close()
     check(got, oracle_run(case, iters=6))
