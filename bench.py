@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048x8192 mixed-form leg")
     ap.add_argument("--configs", action="store_true",
-                    help="instead of the benchmark line: one line per test configuration (FP64, mixed, oracle)")
+                    help="instead of the benchmark line: one line per test configuration at its stated length "
+                         "(FP64, mixed, errors, the configuration's own checks)")
+    ap.add_argument("--config4-steps", type=int, default=20,
+                    help="physical steps of the 2048x8192 Rayleigh-Taylor configuration in --configs (stated: 200)")
     return ap.parse_args()
 
 
@@ -216,7 +219,10 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "cells": case.cells,
-                                            "pseudo_iters_per_step": iters},
+                                            "pseudo_iters_per_step": iters,
+                                            "note": f"each timed step is one physical step of {iters} pseudo-iterations "
+                                                    "of the full tank (the GPU arm's steps run to the stopping test, "
+                                                    "500 here); the metric is a rate, so the two compare"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: 1 physical step x {iters} pseudo-iterations of the full "
                                        f"{case.nx}x{case.ny} tank, FP64 C oracle, 1 thread"},
@@ -326,23 +332,33 @@ def run_ours(args, ws, rank, local):
            "h2d_bytes_per_step": 4 * case.cells * 8, "d2h_bytes_per_step": 4 * case.cells * 8}
 
     # ---- roofline of the FP64 stage sweep ----
+    # the stage launch's duration inside the timed steps: each step's time
+    # over its stage launches (the end-of-iteration kernel's few per cent
+    # included, so the rate is a lower bound); the same launch timed alone
+    # with events on either side is reported beside it
+    s_max = case.options.s_max
+    per_launch_s = dev_ms * 1e-3 / (s_max * sum(iters))
     tank.set_state(*case.state())
-    per_launch_s = stage_launch_ms(tank, case, min(args.steps, 3)) * 1e-3
+    isolated_s = stage_launch_ms(tank, case, min(args.steps, 3)) * 1e-3
     ftx, fty, _, fv = tank.tile_shape()
-    achieved = FP64_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12
+    achieved = FP64_ALG_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12
     # the part's FP64 FMA rate measured here (independent FMA chains), as a
     # check of the nominal peak the fraction is taken against
     probe = ac.ac_probe_fp64_fma_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FP64_TRAFFIC_PER_CELL_STAGE * case.cells,
-                "kernel": f"stage_kernel<double,{ftx},{fty}>", "tile_variant": fv, "launch_ms": per_launch_s * 1e3,
-                "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE,
+                "kernel": f"stage_kernel<double,{ftx},{fty}>", "tile_variant": fv,
+                "launch_ms": per_launch_s * 1e3, "launch_ms_timed_alone": isolated_s * 1e3,
+                "flops_per_cell_stage": FP64_ALG_FLOPS_PER_CELL_STAGE,
+                "flops_note": "algorithmic FP64 flops of one stage per cell, fixed (derivation in the design notes)",
+                "executed_flops_per_cell_stage": FP64_EXEC_FLOPS_PER_CELL_STAGE,
+                "executed_frac": FP64_EXEC_FLOPS_PER_CELL_STAGE * case.cells / per_launch_s / 1e12 / FP64_PEAK_TFLOPS,
                 "peak_source": "nominal FP64 rate of the part (profiling recipe: 2 FP64 FMA lanes/SM)",
                 "peak_probe_tflops": probe, "frac_of_probe": achieved / probe,
                 # the same launch counted in FP64 instructions against the pipe's
                 # issue rate (2 per SM per clock): DADD and DMUL take a pipe slot
-                # for one flop, so the flop fraction is at most ~0.71 of this one
+                # for one flop
                 "dp_instructions_per_cell_stage": FP64_INSTR_PER_CELL_STAGE,
                 "dp_pipe_frac": FP64_INSTR_PER_CELL_STAGE * case.cells / per_launch_s / FP64_PIPE_INSTR_PER_S,
                 "hbm_frac_of_measured": BYTES_PER_CELL_ITER_F64 / 3.0 * case.cells / per_launch_s / 1e9
@@ -411,6 +427,7 @@ def run_ours(args, ws, rank, local):
                               "kernel": (f"sweep_kernel_mixed<{lty},{lnt // 32}> (28-column strips)" if ltx == 28
                                          else f"stage_kernel_mixed<{ltx},{lty},{lnt}>"), "tile_variant": lv,
                               "launch_ms": l_launch_s * 1e3,
+                              "launch_ms_in_step": l_ms * 1e-3 / (3 * sum(l_iters)) * 1e3,
                               "bytes_per_cell_iter": MIXED_BYTES_PER_CELL_ITER,
                               "traffic": None if l_traffic is None else l_traffic * lc.cells,
                               "alu_frac": None if ops is None else ops / FP32_PEAK_TOPS,
@@ -524,13 +541,22 @@ def run_batched(args, stream, flush, barrier):
                                           "unit": "GB/s", "frac": gbs / measured_hbm_gbs()}}
 
 
-# FP64 flops of one stage sweep per cell: executed DFMA x 2 + DADD + DMUL
-# counted by ncu on stage_kernel<double,32,14> on this 256x256 tank (the
-# summary is under profiles/), averaged over the three
-# stages of a pseudo-iteration (stage 1 also forms the local dtau and the
-# real-time terms that stages 2 and 3 read back: 760.9, 658.9, 658.9), and
-# the FP64 instructions (DFMA + DADD + DMUL) behind them (534.0, 458.6, 458.6)
-FP64_FLOPS_PER_CELL_STAGE = 692.9
+# FP64 flops of one stage per cell that the method itself needs (the
+# rank-2 Osher flux of one x- and one y-face, 187 flops each; W, the limited
+# slopes' differences, the pressure gradient of Eq. new_gradp, the face
+# states, the divergence, sources and the point-implicit update; the
+# real-time terms, local dtau and residual squares of stage 1 averaged over
+# the three stages), counted with an FMA as 2 flops and a reciprocal, square
+# root or reciprocal square root as 1; limiting, comparisons and sign
+# handling count 0.  The derivation is tabulated with the design notes.  It
+# is fixed: it does not move when the kernel executes fewer or more
+# operations.
+FP64_ALG_FLOPS_PER_CELL_STAGE = 501.0
+# what stage_kernel<double,32,14> executes on this 256x256 tank (ncu: DFMA x 2
+# + DADD + DMUL, mean of stages 1-3: 760.9, 658.9, 658.9; the tile's ring
+# recomputes slopes and pressure gradients, and stage 1 forms the values
+# stages 2 and 3 read back), and the FP64 instructions behind them
+FP64_EXEC_FLOPS_PER_CELL_STAGE = 692.9
 FP64_INSTR_PER_CELL_STAGE = 483.7
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
@@ -541,19 +567,16 @@ FP64_TRAFFIC_PER_CELL_STAGE = 83.7
 # per-cell values kept for the later stages (32 B); stages 2 and 3 read
 # Q^{s-1}, Q^{m} and those values and write Q^s (4 x 32 B each)
 BYTES_PER_CELL_ITER_F64 = 376.0
-# mixed form: stage 1 reads Q^n (3 x 4 B) + dQ^{m} (4 x 4 B) + rho_ref, dref
-# (2 x 4 B) and writes 4 x 4 B; later stages also read dQ^{s-1} (4 x 4 B)
-MIXED_BYTES_PER_CELL_ITER = 52.0 + 2 * 68.0
-# measured (ncu, one stage-2 launch on this 2048x8192 tank, summarised
-# under profiles/) for the strip
-# variants the autotuner picks there: DRAM bytes and FP32 arithmetic
-# operations (FFMA, FADD, FMUL; packed FP32x2 forms counted as two) per cell
-# of one stage launch.  64-row strips re-read more halo rows than 256-row
-# ones.  A variant without a capture of its current code reports null.
-MIXED_COUNTS_BY_VARIANT = {
-    16: (71.0, 474.4),   # sweep_kernel_mixed<64,4>
-    18: (68.1, 464.7),   # sweep_kernel_mixed<256,4>
-}
+# mixed form: stage 1 reads the (Q^n, rho_ref) and (dQ^{m}, dp^{m}) records
+# (2 x 16 B) and the level-jump record (8 B) and writes 16 B; stages 2 and 3
+# also read the (dQ^{s-1}, dp^{s-1}) record (16 B)
+MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
+# measured (ncu, one stage-2 launch on a 2048x8192 tank, summarised under
+# profiles/) for the strip variants the autotuner picks there: DRAM bytes
+# and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2 forms
+# counted as two) per cell of one stage launch.  A variant without a capture
+# of its current code reports null.
+MIXED_COUNTS_BY_VARIANT = {}
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
@@ -565,12 +588,15 @@ def measured_hbm_gbs():
 
 
 def run_configs(args, rank, local):
-    """Every single-tank configuration of the test set in both forms: a
-    fixed number of pseudo-iterations per physical step (the same work in
-    both forms), CUDA events around K steps, the mixed form's error against
-    the FP64 GPU run from the same state, the HBM fraction from the
-    algorithmic bytes, and the FP64 oracle's rate on 2 pseudo-iterations of
-    the same tank (of a 512x2048 tank for the 2048x8192 one)."""
+    """Every single-tank configuration of the test set at its stated length,
+    in both forms, one JSON line each: throughput (CUDA events around every
+    physical step, the stopping test on: 1e-8 residual drop or 500
+    pseudo-iterations), the HBM fraction from the algorithmic bytes, per-field
+    relative L-inf and L1 errors (mixed against FP64; for the Riemann tank
+    both against the FP64 oracle), the configuration's own checks, and the
+    clocks seen.  The Rayleigh-Taylor tank runs --config4-steps of its 200
+    physical steps (the FP64 form alone takes ~23 s per step there)."""
+    import numpy as np
     import torch
     import oracle
     from paper_2108_08769_gb300 import ac, workloads as W
@@ -581,39 +607,91 @@ def run_configs(args, rank, local):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     oracle.build()
-    configs = [("riemann_200x4", W.riemann_tank, 500, None),
-               ("hydrostatic_256", lambda: W.hydrostatic_tank(256), 500, None),
-               ("water_column_1024x512", lambda: W.water_column(1024, 512), 200, None),
-               ("rayleigh_taylor_2048x8192", lambda: W.rayleigh_taylor(2048, 8192), 50,
-                lambda: W.rayleigh_taylor(512, 2048))]
-    for name, fn, iters, sample_fn in configs:
+
+    def run(case, prec, steps):
+        t = ac.Tank.from_case(case, precision=prec)
+        t.set_stream(stream.cuda_stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        its, rcs = [], []
+        with Clocks(local) as clk:
+            for k in range(steps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                rc, n = t.physical_step(case.dt, case.tol, case.max_iters)
+                evs[k][1].record(stream)
+                its.append(n)
+                rcs.append(rc)
+            torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        state = t.get_state()
+        tx, ty, nt, v = t.tile_shape()
+        t.close()
+        val = case.cells * sum(its) / (ms * 1e-3)
+        bpc = BYTES_PER_CELL_ITER_F64 if prec == "fp64" else MIXED_BYTES_PER_CELL_ITER
+        return state, {"value": val, "unit": UNIT, "ms_per_step": ms / steps,
+                       "hbm_frac_of_measured": val * bpc / 1e9 / measured_hbm_gbs(),
+                       "pseudo_iters": {"min": min(its), "max": max(its), "total": sum(its)},
+                       "converged_steps": sum(1 for r in rcs if r == ac.AC_OK),
+                       "tile": [tx, ty, nt], "tile_variant": v, "clocks": clk.summary()}
+
+    configs = [("riemann_200x4", W.riemann_tank, None), ("hydrostatic_256", lambda: W.hydrostatic_tank(256), None),
+               ("water_column_1024x512", lambda: W.water_column(1024, 512), None),
+               ("rayleigh_taylor_2048x8192", lambda: W.rayleigh_taylor(2048, 8192), args.config4_steps)]
+    for name, fn, nsteps in configs:
         case = fn()
-        line = {"config": name, "cells": case.cells, "pseudo_iters_per_step": iters, "steps": args.steps,
-                "unit": UNIT}
-        states = {}
-        for prec, bpc in (("fp64", BYTES_PER_CELL_ITER_F64), ("mixed", MIXED_BYTES_PER_CELL_ITER)):
-            t = ac.Tank.from_case(case, precision=prec)
-            t.set_stream(stream.cuda_stream)
-            t.physical_step(case.dt, -1.0, iters)          # warm-up (tuning)
-            t.set_state(*case.state())
-            with Clocks(local) as clk:
-                ms, its, _ = timed_steps(t, case, args.steps, stream, flush, torch.cuda.synchronize, tol=-1.0,
-                                         max_iters=iters)
-            t.set_state(*case.state())
-            t.physical_step(case.dt, -1.0, iters)
-            states[prec] = t.get_state()
-            tx, ty, nt, v = t.tile_shape()
-            t.close()
-            val = case.cells * sum(its) / (ms * 1e-3)
-            line[prec] = {"value": val, "hbm_frac_of_measured": val * bpc / 1e9 / measured_hbm_gbs(),
-                          "tile": [tx, ty, nt], "tile_variant": v, "clocks": clk.summary()}
+        steps = nsteps or case.steps
+        line = {"config": name, "cells": case.cells, "physical_steps": steps, "of_stated": case.steps,
+                "dt": case.dt, "t_end": steps * case.dt, "tol": case.tol, "max_iters": case.max_iters}
+        f64, line["fp64"] = run(case, "fp64", steps)
+        mixed, line["mixed"] = run(case, "mixed", steps)
         line["mixed"]["speedup_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
-        line["mixed"]["error_vs_fp64_gpu"] = field_errors(states["mixed"], states["fp64"])
-        oc = sample_fn() if sample_fn else case
-        t0 = time.perf_counter()
-        _, _, oits, _, _ = oracle.physical_step(oc, oc.state(), tol=-1.0, max_iters=2)
-        line["oracle_1_core"] = {"value": oc.cells * oits / (time.perf_counter() - t0),
-                                 "sample": f"2 pseudo-iterations of a {oc.nx}x{oc.ny} tank"}
+        line["mixed"]["error_vs_fp64_gpu"] = field_errors(mixed, f64)
+        if name == "riemann_200x4":
+            # the FP64 oracle over the same 20 physical steps, field by field
+            st = case.state()
+            t0 = time.perf_counter()
+            oits = []
+            for _ in range(steps):
+                st, _, n, _, _ = oracle.physical_step(case, st)
+                oits.append(n)
+            line["oracle_1_core"] = {"value": case.cells * sum(oits) / (time.perf_counter() - t0), "unit": UNIT,
+                                     "pseudo_iters_total": sum(oits)}
+            line["fp64"]["error_vs_oracle"] = field_errors(f64, st)
+            line["mixed"]["error_vs_oracle"] = field_errors(mixed, st)
+            # Sec. 2.4.1's wave relations: the same tank in pure pseudo-time
+            # (real-time term off, global pseudo-time step, minmod on p as in
+            # Sec. 3.1) to tau = 1e-3 s, before the fastest wave (~316 m/s in
+            # the air) reaches the ends, against the exact solution at x/tau
+            rel = {}
+            for prec in ("fp64", "mixed"):
+                rp = W.riemann_tank()
+                rp.options.realtime, rp.options.local_dtau, rp.options.gradp = False, False, "minmod"
+                tau = 1e-3
+                t = ac.Tank.from_case(rp, precision=prec)
+                rc, n = t.pseudo_time_run(tau)
+                q = t.get_state()
+                t.close()
+                xs = (np.arange(rp.nx) + 0.5) * (rp.lx / rp.nx) - 0.5
+                ex = np.array([oracle.bassi_sample([1000.0, 0.0, 0.0, 1e5], [1.0, 0.0, 0.0, 0.0], rp.beta, x / tau)
+                               for x in xs])
+                sc = np.abs(ex).max(axis=0)
+                rel[prec] = {"pseudo_iters": n,
+                             "l1_rel_rho": float(np.abs(q[0][0] - ex[:, 0]).mean() / sc[0]),
+                             "l1_rel_u": float(np.abs(q[1][0] / q[0][0] - ex[:, 1]).mean() / sc[1]),
+                             "l1_rel_p": float(np.abs(q[3][0] - ex[:, 3]).mean() / sc[3])}
+            rel["exact_star_state"] = dict(zip(("S_L", "S_R", "u_star", "p_star", "rho_star_L", "rho_star_R"),
+                                               [float(v) for v in oracle.bassi_star(
+                                                   [1000.0, 0.0, 0.0, 1e5], [1.0, 0.0, 0.0, 0.0], rp.beta)]))
+            line["riemann_relations_tau_1e-3"] = rel
+        if name == "hydrostatic_256":
+            # at rest to 1e-10, the pressure kink held: slope ratio water/air = density ratio
+            u = np.abs(f64[1] / f64[0]).max()
+            v = np.abs(f64[2] / f64[0]).max()
+            col = f64[3][:, case.nx // 2]
+            sl = np.diff(col) / case.dy
+            line["fp64"]["max_velocity"] = float(max(u, v))
+            line["fp64"]["kink_slope_ratio"] = float(sl[case.ny // 4] / sl[3 * case.ny // 4])
+            line["mixed"]["max_velocity"] = float(max(np.abs(mixed[1] / mixed[0]).max(), np.abs(mixed[2] / mixed[0]).max()))
         print(json.dumps(line), flush=True)
 
 

@@ -158,6 +158,17 @@ int ac_get_state(const ac_ctx *ctx, double *rho, double *rhou, double *rhov, dou
  * AC_ERR_NONFINITE the state is restored to its value before the call. */
 int ac_physical_step(ac_ctx *ctx, double dt, double tol, int max_iters, int *iters_out);
 
+/* Pure pseudo-time evolution (the set-up of the Riemann problems of Sec.
+ * 3.1): with the real-time term off and the global pseudo-time step
+ * (options realtime = 0, local_dtau = 0), run pseudo-iterations of s_max
+ * Runge-Kutta stages (Eq. RK2) from the current state until the pseudo-time
+ * reaches tau_end, the last step shortened to land on it, or max_iters
+ * iterations have run.  The state is advanced in place (no stopping test).
+ * Returns AC_OK when tau_end was reached, AC_NOT_CONVERGED when max_iters
+ * came first, AC_ERR_ARG for other options or tau_end not finite and > 0;
+ * *iters_out (may be NULL) receives the iterations run. */
+int ac_pseudo_time_run(ac_ctx *ctx, double tau_end, int max_iters, int *iters_out);
+
 /* Residual norms of the last physical step (Alg. 1's convergence test;
  * the paper does not define the norm, and this library reads it as the RMS
  * over cells of the stage-1 bracket of Eq. RK2, pressure row in Pa/s):

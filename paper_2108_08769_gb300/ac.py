@@ -37,7 +37,7 @@ EXPORTS = (
     "ac_set_state", "ac_get_state", "ac_physical_step", "ac_residual_norms", "ac_get_history",
     "ac_set_history", "ac_kernel_launches", "ac_last_error", "ac_set_profiling", "ac_stage_kernel_time",
     "ac_tile_shape", "ac_probe_fp64_fma_tflops",
-    "ac_stage_sweep_noalloc", "ac_realtime_dt", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
+    "ac_stage_sweep_noalloc", "ac_realtime_dt", "ac_pseudo_time_run", "ac_batch_create", "ac_batch_destroy", "ac_batch_set_stream",
     "ac_batch_set_state", "ac_batch_get_state", "ac_batch_physical_step", "ac_batch_residual_norms",
     "ac_batch_tile_shape", "ac_batch_set_profiling", "ac_batch_stage_kernel_time", "ac_batch_kernel_launches",
 )
@@ -97,6 +97,7 @@ def load(build: bool = True):
     L.ac_set_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
     L.ac_get_state.argtypes = [C.c_void_p, _D, _D, _D, _D]
     L.ac_physical_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
+    L.ac_pseudo_time_run.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.ac_residual_norms.argtypes = [C.c_void_p, _D, _D]
     L.ac_realtime_dt.argtypes = [C.c_void_p, C.c_double, _D]
     L.ac_get_history.argtypes = [C.c_void_p, C.c_int, _D, _D, _D]
@@ -266,6 +267,12 @@ class Tank:
     def physical_step(self, dt: float, tol: float, max_iters: int) -> Tuple[int, int]:
         its = C.c_int(0)
         rc = load().ac_physical_step(self._h, dt, tol, max_iters, C.byref(its))
+        _check(rc, (AC_OK, AC_NOT_CONVERGED))
+        return rc, its.value
+
+    def pseudo_time_run(self, tau_end: float, max_iters: int = 1000000) -> Tuple[int, int]:
+        its = C.c_int(0)
+        rc = load().ac_pseudo_time_run(self._h, tau_end, max_iters, C.byref(its))
         _check(rc, (AC_OK, AC_NOT_CONVERGED))
         return rc, its.value
 

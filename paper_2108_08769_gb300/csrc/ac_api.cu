@@ -133,7 +133,7 @@ struct Backend {
     virtual int get_state(const ac_ctx *c, double *const out[4]) = 0;
     virtual int get_history(const ac_ctx *c, int k, double *const out[3]) = 0;
     virtual int set_history(ac_ctx *c, int k, const double *const in[3]) = 0;
-    virtual int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) = 0;
+    virtual int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters, double tau_end) = 0;
     virtual int dtau_min(ac_ctx *c, cudaStream_t s) = 0;
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
@@ -365,8 +365,9 @@ struct F64Backend : Backend {
         CK(cudaStreamSynchronize(c->stream));
         return AC_OK;
     }
-    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) override {
-        begin_step_kernel<double><<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters);
+    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters, double tau_end) override {
+        begin_step_kernel<double><<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters,
+                                                                            tau_end);
         CK(cudaGetLastError());
         return AC_OK;
     }
@@ -733,8 +734,8 @@ struct MixedBackend : Backend {
         }
         return AC_OK;
     }
-    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters) override {
-        begin_step_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters);
+    int begin(ac_ctx *c, cudaStream_t s, double dt, double tol, int max_iters, double tau_end) override {
+        begin_step_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0), dt, tol, max_iters, tau_end);
         CK(cudaGetLastError());
         level_jumps_kernel_mixed<<<grid_stride_blocks(c->N), 256, 0, s>>>(args(c, 0));
         CK(cudaGetLastError());
@@ -1007,7 +1008,10 @@ int ac_get_state(const ac_ctx *c, double *rho, double *rhou, double *rhov, doubl
     return c->be->get_state(c, dst);
 }
 
-static int physical_step_impl(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out) {
+// One physical step (Alg. 1), or with a finite tau_end a pure pseudo-time
+// run that stops when the pseudo-time reaches tau_end.
+static int physical_step_impl(ac_ctx *c, double dt, double tol, int max_iters, int *iters_out,
+                              double tau_end = INFINITY) {
     g_err.clear();
     if (iters_out) *iters_out = 0;
     if (!c) return fail(AC_ERR_ARG, "ctx is NULL");
@@ -1021,7 +1025,7 @@ static int physical_step_impl(ac_ctx *c, double dt, double tol, int max_iters, i
     // the first real-time step can only be Backward-Euler, the second at
     // most BDF2, and so on (Sec. 2.2.2)
     c->order_now = c->opt.realtime ? std::min(c->opt.bdf_order, c->nhist + 1) : 1;
-    if ((rc = c->be->begin(c, s, dt, tol, max_iters)) != AC_OK) return rc;
+    if ((rc = c->be->begin(c, s, dt, tol, max_iters, tau_end)) != AC_OK) return rc;
     c->launches += 1;
     c->pdl = false;   // the tuner times launches one after another
     if ((rc = c->be->tune(c, s)) != AC_OK) return rc;
@@ -1090,6 +1094,18 @@ int ac_physical_step(ac_ctx *c, double dt, double tol, int max_iters, int *iters
                      c->grid.nx, c->grid.ny, c->opt.precision == AC_PREC_MIXED ? "mixed" : "fp64", rc, its,
                      h.R0[0], h.R0[1], h.R0[2], h.R0[3], h.R[0], h.R[1], h.R[2], h.R[3]);
     }
+    return rc;
+}
+
+int ac_pseudo_time_run(ac_ctx *c, double tau_end, int max_iters, int *iters_out) {
+    nvtxRangePushA("ac_pseudo_time_run");
+    int rc;
+    if (!c) rc = fail(AC_ERR_ARG, "ctx is NULL");
+    else if (c->opt.realtime || c->opt.local_dtau)
+        rc = fail(AC_ERR_ARG, "a pure pseudo-time run needs the real-time term off and the global pseudo-time step");
+    else if (!(tau_end > 0.0) || !std::isfinite(tau_end)) rc = fail(AC_ERR_ARG, "tau_end must be finite and > 0");
+    else rc = physical_step_impl(c, 1.0, -1.0, max_iters, iters_out, tau_end);
+    nvtxRangePop();
     return rc;
 }
 

@@ -137,6 +137,8 @@ __global__ void batch_begin_kernel(BatchTank *tanks, BatchSync *sync, const doub
         ctl->inv_dt = 1.0 / h;
         ctl->dtau_bits = 0x7ff0000000000000ull;
         ctl->rebase = 0;
+        ctl->tau = 0.0;
+        ctl->tau_end = INFINITY;
         if (blockIdx.y == 0) {
             sync->arrive = 0;
             sync->still_active = 0;

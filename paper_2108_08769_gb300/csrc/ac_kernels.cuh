@@ -35,7 +35,14 @@ struct Ctl {
     double abs_tol[4];
     unsigned long long dtau_bits;  // global pseudo-time step (bit pattern of a positive double)
     int rebase;      // mixed form: fold the pressure increment into its FP64 level before the next iteration
+    double tau, tau_end;  // pure pseudo-time run: pseudo-time reached and its end (+inf in a physical step)
 };
+
+// The global pseudo-time step of the current iteration, shortened so that a
+// pure pseudo-time run lands on its end (tau_end is +inf otherwise).
+__device__ __forceinline__ double global_dtau(const Ctl *ctl) {
+    return fmin(__longlong_as_double((long long)ctl->dtau_bits), ctl->tau_end - ctl->tau);
+}
 
 // What the end of a pseudo-iteration needs (see end_iteration).
 struct IterEnd {
@@ -151,10 +158,20 @@ __device__ __forceinline__ void end_iteration(Ctl *ctl, const double *partials, 
             if (!(R <= thr)) conv = false;
         }
         ctl->cur = final_buffer(ctl->cur, e.s_max);
+        bool reached = false;   // a pure pseudo-time run reached its end
+        if (ctl->tau_end < INFINITY) {
+            ctl->tau += global_dtau(ctl);
+            reached = ctl->tau >= ctl->tau_end;
+        }
         int done = 0;
         if (!finite) { ctl->status = -3; done = 1; }
+        else if (reached) { ctl->status = 0; done = 1; }
         else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
-        else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
+        else if (it >= ctl->max_iters) {
+            // a fixed iteration count is complete; a pseudo-time run short of its end is not
+            ctl->status = (ctl->fixed && !(ctl->tau_end < INFINITY)) ? 0 : 1;
+            done = 1;
+        }
         ctl->done = done;
         ctl->rebase = (e.rebase_pow2 && !done && (it & (it - 1)) == 0) ? 1 : 0;
         ctl->dtau_bits = 0x7ff0000000000000ull;
@@ -435,7 +452,7 @@ stage_kernel(const SweepArgs<T> a) {
             dtau = a.cfl_area * Ar<T>::rcp(den);
             if (a.reuse) a.aux[0][g] = dtau;
         } else {
-            dtau = T(__longlong_as_double((long long)ctl->dtau_bits));
+            dtau = T(global_dtau(ctl));
         }
         const T api = T(1) + a.B[0] * a.alpha * dtau * inv_dt;   // Eq. point_implicit
         const T coef = (a.alpha * dtau) * Ar<T>::rcp(api);
@@ -515,7 +532,7 @@ __global__ void realtime_dt_kernel(const SweepArgs<T> a, int cur, double cfl_are
 
 // Start of a physical step: Q^n <- Q (Alg. 1) and reset of the control block.
 template <typename T>
-__global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, int max_iters) {
+__global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, int max_iters, double tau_end) {
     Ctl *ctl = a.ctl;
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
@@ -540,6 +557,8 @@ __global__ void begin_step_kernel(const SweepArgs<T> a, double dt, double tol, i
         ctl->dt = dt;
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;  // +inf
+        ctl->tau = 0.0;
+        ctl->tau_end = tau_end;
     }
 }
 

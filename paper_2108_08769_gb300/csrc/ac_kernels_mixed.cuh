@@ -263,7 +263,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
         const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
         dtau = __fdividef(a.cfl_area, den);
     } else {
-        dtau = float(__longlong_as_double((long long)a.ctl->dtau_bits));
+        dtau = float(global_dtau(a.ctl));
     }
     const float adt = alpha * dtau;
     const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
@@ -941,7 +941,8 @@ __device__ __forceinline__ void mixed_level_jumps(const MixedArgs &a, size_t g) 
     a.jmp[g] = make_float2(jx, jy);
 }
 
-static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters) {
+static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, double tol, int max_iters,
+                                               double tau_end) {
     Ctl *ctl = a.ctl;
     const int cur = ctl->cur;
     const size_t N = (size_t)a.nx * a.ny;
@@ -958,6 +959,8 @@ static __global__ void begin_step_kernel_mixed(const MixedArgs a, double dt, dou
         ctl->inv_dt = 1.0 / dt;
         ctl->dtau_bits = 0x7ff0000000000000ull;
         ctl->rebase = 0;
+        ctl->tau = 0.0;
+        ctl->tau_end = tau_end;
     }
 }
 

@@ -68,6 +68,8 @@ __global__ void noalloc_init_kernel(Ctl *ctl, double inv_dt) {
     ctl->inv_dt = inv_dt;
     ctl->dt = inv_dt > 0.0 ? 1.0 / inv_dt : 0.0;
     ctl->dtau_bits = 0x7ff0000000000000ull;
+    ctl->tau = 0.0;
+    ctl->tau_end = INFINITY;
 }
 
 // R_k = sqrt(sum of the tiles' partial sums / cells), summed in a fixed order.
