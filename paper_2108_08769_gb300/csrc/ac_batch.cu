@@ -250,6 +250,8 @@ constexpr Variant kVariants[] = {
     {32, 8, 256},  {32, 16, 256}, {32, 16, 512}, {64, 8, 256},        {64, 8, 512},
     {64, 16, 512}, {16, 16, 256}, {32, 8, 256, true}, {16, 16, 256, true},
     {28, 32, 128, false, true}, {28, 64, 128, false, true}, {28, 128, 128, false, true},
+    // the same strips held to 3 CTAs per SM (room for the descriptor reads without spills)
+    {28, 32, 128, false, true}, {28, 64, 128, false, true}, {28, 128, 128, false, true},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -403,9 +405,9 @@ struct StageLaunch {
     cudaError_t go(cudaStream_t s) const {
         return launch_stage<TX, TY, NT, RS, BDF, PF>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
     }
-    template <int H>
+    template <int H, int MINB = 4>
     cudaError_t strips(cudaStream_t s) const {
-        return launch_sweep<H, 4, 4>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
+        return launch_sweep<H, 4, MINB>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
     }
 };
 
@@ -429,7 +431,10 @@ int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
         case 8: e = L.go<16, 16, 256, kOsher, false, true>(s); break;
         case 9: e = L.strips<32>(s); break;
         case 10: e = L.strips<64>(s); break;
-        default: e = L.strips<128>(s); break;
+        case 11: e = L.strips<128>(s); break;
+        case 12: e = L.strips<32, 3>(s); break;
+        case 13: e = L.strips<64, 3>(s); break;
+        default: e = L.strips<128, 3>(s); break;
     }
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "batch stage launch failed: %s", cudaGetErrorString(e));
     return AC_OK;

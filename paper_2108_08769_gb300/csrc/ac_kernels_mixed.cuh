@@ -72,17 +72,32 @@ struct MixedArgs {
     Ctl *ctl;
 };
 
+// Exact FP32 -> FP64 conversion with integer instructions (exponent rebias,
+// mantissa shift), off GB300's FP64 unit, which runs at 1/64 of the FP32
+// rate.  FP32 subnormals (below 1.2e-38) become 0; infinities and NaNs stay
+// what they are, so a non-finite residual is still seen.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long ex = e == 0u ? 0ull : (e == 255u ? 0x7ffull : (unsigned long long)(e + 896u));
+    return __longlong_as_double((long long)(sgn | (ex << 52) | (e == 0u ? 0ull : m)));
+}
+
 // Residual partial sums of the tile sweep (one or two cells per thread):
-// each cell's stage-1 bracket is squared exactly in FP64 (an FP32 value
-// squared fits a double's mantissa) and summed in FP64.
-struct Sq64 {
-    double x, y, z, w;
+// each cell's stage-1 squares in FP32, and every sum from the warp's up in
+// FP64 (the thread's values converted exactly).
+struct SqTile {
+    float x = 0.0f, y = 0.0f, z = 0.0f, w = 0.0f;
     __device__ __forceinline__ void add(float b0, float b1, float b2, float b3) {
-        const double d0 = b0, d1 = b1, d2 = b2, d3 = b3;
-        x = fma(d0, d0, x);
-        y = fma(d1, d1, y);
-        z = fma(d2, d2, z);
-        w = fma(d3, d3, w);
+        x = fmaf(b0, b0, x);
+        y = fmaf(b1, b1, y);
+        z = fmaf(b2, b2, z);
+        w = fmaf(b3, b3, w);
+    }
+    __device__ __forceinline__ double get(int f) const {
+        return f32_to_f64_exact(f == 0 ? x : f == 1 ? y : f == 2 ? z : w);
     }
 };
 
@@ -447,7 +462,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
     __syncthreads();
 
     // ---- 4. divergence + sources + point-implicit update of dQ and dp ----
-    Sq64 sq = {0.0, 0.0, 0.0, 0.0};
+    SqTile sq;
 #pragma unroll
     for (int cell = tid; cell < TX * TY; cell += NT) {
         const int lj = cell / TX, li = cell - lj * TX;
@@ -463,7 +478,7 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         // warp, block and grid sums in FP64
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            double v = f == 0 ? sq.x : f == 1 ? sq.y : f == 2 ? sq.z : sq.w;
+            double v = sq.get(f);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if ((tid & 31) == 0) sm.red[f][tid >> 5] = v;

@@ -99,7 +99,7 @@ def test_tank_does_not_depend_on_the_rest_of_the_batch(monkeypatch, v):
     full.close()
 
 
-N_BATCH_VARIANTS = 12
+N_BATCH_VARIANTS = 15
 
 
 @pytest.mark.parametrize("v", range(N_BATCH_VARIANTS))
