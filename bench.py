@@ -571,12 +571,15 @@ BYTES_PER_CELL_ITER_F64 = 376.0
 # (2 x 16 B) and the level-jump record (8 B) and writes 16 B; stages 2 and 3
 # also read the (dQ^{s-1}, dp^{s-1}) record (16 B)
 MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
-# measured (ncu, one stage-2 launch on a 2048x8192 tank, summarised under
-# profiles/) for the strip variants the autotuner picks there: DRAM bytes
-# and FP32 arithmetic operations (FFMA, FADD, FMUL; packed FP32x2 forms
-# counted as two) per cell of one stage launch.  A variant without a capture
-# of its current code reports null.
-MIXED_COUNTS_BY_VARIANT = {}
+# measured (ncu, stages 1 and 2 of a pseudo-iteration on this 2048x8192
+# tank, summarised under profiles/) for the strip variant the autotuner
+# picks there: DRAM bytes and FP32 arithmetic operations (FFMA, FADD, FMUL;
+# packed FP32x2 forms counted as two) per cell of one stage launch, the
+# mean over the three stages (stage 3 as stage 2).  A variant without a
+# capture of its current code reports null.
+MIXED_COUNTS_BY_VARIANT = {
+    16: ((57.7 + 2 * 75.4) / 3, (504.3 + 2 * 483.3) / 3),   # sweep_kernel_mixed<64,4>
+}
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
 
