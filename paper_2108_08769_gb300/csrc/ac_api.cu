@@ -138,8 +138,9 @@ struct Backend {
     virtual int stage(ac_ctx *c, cudaStream_t s, int st) = 0;
     virtual int restore(ac_ctx *c, cudaStream_t s) = 0;
     virtual int realtime_dt(ac_ctx *c, double cfl_area, unsigned long long *out) = 0;
-    // kernels enqueued after the end of each pseudo-iteration (mixed form:
-    // the pressure rebase), and whether the end sets the rebase flag
+    // kernels enqueued after the end of a pseudo-iteration (mixed form: the
+    // pressure rebase, which runs when the end of the iteration asks for it),
+    // and whether the end sets the rebase flag
     virtual int after_iteration(ac_ctx *c, cudaStream_t s) { (void)c; (void)s; return AC_OK; }
     virtual int kernels_after_iteration() const { return 0; }
     virtual bool rebases() const { return false; }
@@ -778,8 +779,10 @@ struct MixedBackend : Backend {
 // ------------------------------------------------------------------ loop
 
 // Enqueue one pseudo-iteration on stream s (events around the stage sweeps
-// when `timed`).
-int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false) {
+// when `timed`); `after` adds the kernels that follow the end of an
+// iteration (they act only when its end asks for them).
+int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int use_cond, bool timed = false,
+                      bool after = true) {
     int rc;
     IterEnd e{};
     e.rebase_pow2 = c->be->rebases() ? 1 : 0;
@@ -795,7 +798,15 @@ int enqueue_iteration(ac_ctx *c, cudaStream_t s, unsigned long long cond, int us
         if (timed) CK(cudaEventRecord(c->ev[st], s));
     }
     CK(launch_pdl(c->pdl, end_iteration_kernel, dim3(1), dim3(kEndLanes), 0, s, c->ctl, c->partials, e));
-    return c->be->after_iteration(c, s);
+    return after ? c->be->after_iteration(c, s) : AC_OK;
+}
+
+// Pressure rebases in a physical step of `iters` pseudo-iterations (those
+// after iterations 1, 2, 4, 8 that are not the last).
+long long rebases_in(int iters) {
+    long long n = 0;
+    for (int m = 1; m < iters; ++m) n += rebase_after(m);
+    return n;
 }
 
 int kernels_per_iteration(const ac_ctx *c) {
@@ -814,6 +825,29 @@ int build_graph(ac_ctx *c) {
     CK(cudaGraphCreate(&c->graph, 0));
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
+    // With a pressure rebase (mixed form) the first kRebaseLast pseudo-iterations
+    // run in line ahead of the loop, the rebase kernels after iterations 1, 2,
+    // 4, 8 only, so that the loop body itself carries no per-iteration node
+    // for them.  Each of these iterations sets the loop's condition; once
+    // the step is done their kernels return at once.
+    std::vector<cudaGraphNode_t> pro;
+    if (c->be->rebases()) {
+        CK(cudaStreamBeginCaptureToGraph(c->cap, c->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = AC_OK;
+        for (int m = 1; m <= kRebaseLast && rc == AC_OK; ++m)
+            rc = enqueue_iteration(c, c->cap, (unsigned long long)h, 1, false, rebase_after(m));
+        cudaStreamCaptureStatus st;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &st, nullptr, &g, &deps, nullptr, &nd);
+        if (e == cudaSuccess) pro.assign(deps, deps + nd);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &captured);
+        if (rc != AC_OK) return rc;
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(AC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
     // (the params union has no usable default constructor: zero raw storage)
     alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
     memset(cp_raw, 0, sizeof cp_raw);
@@ -823,10 +857,10 @@ int build_graph(ac_ctx *c) {
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp));
+    CK(cudaGraphAddNode(&node, c->graph, pro.empty() ? nullptr : pro.data(), nullptr, pro.size(), &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_iteration(c, c->cap, (unsigned long long)h, 1);
+    int rc = enqueue_iteration(c, c->cap, (unsigned long long)h, 1, false, false);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &captured);
     if (rc != AC_OK) return rc;
@@ -1063,7 +1097,15 @@ static int physical_step_impl(ac_ctx *c, double dt, double tol, int max_iters, i
         CK(cudaGraphLaunch(c->exec, s));
         CK(cudaMemcpyAsync(c->hctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        c->launches += (long long)c->hctl->iter * kernels_per_iteration(c);
+        // with a rebase the graph's in-line prologue always launches its
+        // kRebaseLast iterations and four rebase pairs (returning at once
+        // once the step is done); the loop runs the rest
+        const int ka = c->be->kernels_after_iteration();
+        if (c->be->rebases())
+            c->launches += (long long)std::max(c->hctl->iter, kRebaseLast) * (kernels_per_iteration(c) - ka) +
+                           rebases_in(kRebaseLast + 1) * ka;
+        else
+            c->launches += (long long)c->hctl->iter * kernels_per_iteration(c);
     }
     if (iters_out) *iters_out = c->hctl->iter;
     if (c->hctl->status == -3) {

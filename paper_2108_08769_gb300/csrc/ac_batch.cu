@@ -214,8 +214,8 @@ batch_end_kernel(BatchTank *tanks, BatchSync *sync, int ntanks, unsigned long lo
             else if (!ctl->fixed && conv) { ctl->status = 0; done = 1; }
             else if (it >= ctl->max_iters) { ctl->status = ctl->fixed ? 0 : 1; done = 1; }
             ctl->done = done;
-            // pressure rebase after iterations 1, 2, 4, 8, ... (see mixed_rebase_shift)
-            ctl->rebase = (t.a.plevel && !done && (it & (it - 1)) == 0) ? 1 : 0;
+            // pressure rebase after iterations 1, 2, 4, 8 (see mixed_rebase_shift)
+            ctl->rebase = (t.a.plevel && !done && rebase_after(it)) ? 1 : 0;
             active = !done;
         }
         if (active) atomicAdd(&sync->still_active, 1u);

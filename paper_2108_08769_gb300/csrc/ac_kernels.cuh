@@ -45,8 +45,14 @@ __device__ __forceinline__ double global_dtau(const Ctl *ctl) {
 }
 
 // What the end of a pseudo-iteration needs (see end_iteration).
+// The mixed form rebases its pressure level after these pseudo-iterations of
+// a step (1, 2, 4, ..., kRebaseLast): the first ones are where a step that
+// starts from an unbalanced state moves the pressure the most.
+constexpr int kRebaseLast = 8;
+__host__ __device__ __forceinline__ bool rebase_after(int it) { return it <= kRebaseLast && (it & (it - 1)) == 0; }
+
 struct IterEnd {
-    int rebase_pow2;           // mixed form with a pressure level: rebase after iterations 1, 2, 4, 8, ...
+    int rebase_pow2;           // mixed form with a pressure level: rebase after iterations 1, 2, 4, 8
     int nparts;                // residual partial slots written by stage 1
     int s_max;
     int use_cond;              // set the graph's while-condition
@@ -173,7 +179,7 @@ __device__ __forceinline__ void end_iteration(Ctl *ctl, const double *partials, 
             done = 1;
         }
         ctl->done = done;
-        ctl->rebase = (e.rebase_pow2 && !done && (it & (it - 1)) == 0) ? 1 : 0;
+        ctl->rebase = (e.rebase_pow2 && !done && rebase_after(it)) ? 1 : 0;
         ctl->dtau_bits = 0x7ff0000000000000ull;
         if (e.use_cond) cudaGraphSetConditional(e.cond, done ? 0u : 1u);
     }

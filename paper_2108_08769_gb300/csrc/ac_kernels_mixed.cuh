@@ -1008,8 +1008,8 @@ __device__ __forceinline__ void mixed_rebase_shift(const MixedArgs &a, int cur, 
     r->w = 0.0f;
 }
 
-// The end of iteration m sets ctl->rebase after m = 1, 2, 4, 8, ... (not on
-// the last iteration); otherwise these return at once.
+// The end of iteration m sets ctl->rebase after m = 1, 2, 4, 8 (not on the
+// last iteration); otherwise these return at once.
 static __global__ void rebase_shift_kernel_mixed(const MixedArgs a) {
     pdl_trigger();
     pdl_wait();
