@@ -542,22 +542,23 @@ def run_batched(args, stream, flush, barrier):
 
 
 # FP64 flops of one stage per cell that the method itself needs (the
-# rank-2 Osher flux of one x- and one y-face, 187 flops each; W, the limited
-# slopes' differences, the pressure gradient of Eq. new_gradp, the face
-# states, the divergence, sources and the point-implicit update; the
-# real-time terms, local dtau and residual squares of stage 1 averaged over
-# the three stages), counted with an FMA as 2 flops and a reciprocal, square
-# root or reciprocal square root as 1; limiting, comparisons and sign
-# handling count 0.  The derivation is tabulated with the design notes.  It
-# is fixed: it does not move when the kernel executes fewer or more
-# operations.
-FP64_ALG_FLOPS_PER_CELL_STAGE = 501.0
+# rank-2 Osher flux of one x- and one y-face, 178 flops each, in the form
+# whose acoustic terms carry no density; W, the limited slopes'
+# differences, the pressure gradient of Eq. new_gradp, the face states, the
+# divergence, sources and the point-implicit update; the real-time terms,
+# local dtau and residual squares of stage 1 averaged over the three
+# stages), counted with an FMA as 2 flops and a reciprocal, square root or
+# reciprocal square root as 1; limiting, comparisons and sign handling
+# count 0.  The derivation is tabulated with the design notes.  It does not
+# move when the kernel executes fewer or more operations (recomputation on
+# a tile's ring, stage-1 values read back), only with the formulation.
+FP64_ALG_FLOPS_PER_CELL_STAGE = 483.0
 # what stage_kernel<double,32,14> executes on this 256x256 tank (ncu: DFMA x 2
-# + DADD + DMUL, mean of stages 1-3: 760.9, 658.9, 658.9; the tile's ring
+# + DADD + DMUL, mean of stages 1-3: 741.3, 639.2, 639.2; the tile's ring
 # recomputes slopes and pressure gradients, and stage 1 forms the values
 # stages 2 and 3 read back), and the FP64 instructions behind them
-FP64_EXEC_FLOPS_PER_CELL_STAGE = 692.9
-FP64_INSTR_PER_CELL_STAGE = 483.7
+FP64_EXEC_FLOPS_PER_CELL_STAGE = 673.2
+FP64_INSTR_PER_CELL_STAGE = 468.4
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
 # the three stages (3.74, 6.36, 6.36 MB read; the output stays in L2)
@@ -578,7 +579,7 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.7 + 2 * 75.4) / 3, (504.3 + 2 * 483.3) / 3),   # sweep_kernel_mixed<64,4>
+    16: ((57.7 + 2 * 75.4) / 3, (490.0 + 2 * 469.0) / 3),   # sweep_kernel_mixed<64,4>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 

@@ -138,8 +138,11 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     // D = sum_j w_j |A_j| dQ, accumulated as
     //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
     //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
-    // (the weight w_j rides on k = w_j rho / c, and with it the 1/beta of
-    // l a + dq = (l beta a + dp)/beta, a = (dm - u dr)/beta)
+    // with, at point j, g4 = (l4 - |u|) k (l4 beta a + dp), g5 = (l5 + |u|) k
+    // (l5 beta a + dp), k = w_j / (beta c): e = rho (g4 l4 + g5 l5) enters Se
+    // and, times u and v, Sue and Sve (rho u = m, rho v = n), and Sg, Sh take
+    // g4 + g5 and g4 l5 + g5 l4 (the acoustic terms of |A| dQ over rho times
+    // rho: the density cancels)
     T Sau, Se, Sue, Sve, Sg, Sh;
     // the three densities' reciprocals from one reciprocal of their product
     // (1 reciprocal + 6 products in place of 3 reciprocals)
@@ -160,7 +163,7 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T m = mL + tq[j] * dm;
         const T n = nL + tq[j] * dn;
         const T ir = irq[j];
-        const T u = m * ir, v = n * ir;
+        const T u = m * ir;
         const T c2 = u * u + four_beta * ir;
         T c, ic;
         Ar<T>::sqrt_rsqrt(c2, c, ic);
@@ -170,15 +173,15 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T au = fabs(u);
         const T ba = dm - u * dr;   // beta a
         const T w = wq[j];
-        const T k = ((w * inv_beta) * r) * ic;
+        const T k = (w * inv_beta) * ic;
         const T g4 = (l4 - au) * k * (l4 * ba + dp);
         const T g5 = (l5 + au) * k * (l5 * ba + dp);
-        const T e = g4 * l4 + g5 * l5;
-        const T gs = ir * (g4 + g5), h = ir * (g4 * l5 + g5 * l4);
+        const T E = g4 * l4 + g5 * l5;   // e / rho
+        const T gs = g4 + g5, h = g4 * l5 + g5 * l4;
         if (j == 0) {
-            Sau = w * au; Se = e; Sue = u * e; Sve = v * e; Sg = gs; Sh = h;
+            Sau = w * au; Se = r * E; Sue = m * E; Sve = n * E; Sg = gs; Sh = h;
         } else {
-            Sau += w * au; Se += e; Sue += u * e; Sve += v * e; Sg += gs; Sh += h;
+            Sau += w * au; Se += r * E; Sue += m * E; Sve += n * E; Sg += gs; Sh += h;
         }
     }
     // central part 1/2 (F(Q_L) + F(Q_R)); dissipation 1/2 * D (D already
@@ -268,6 +271,17 @@ __device__ __forceinline__ void bassi_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
 // osher_flux; only the order of the three point sums differs.
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// a - b as one packed FP32x2 subtraction (the same value as a + (-b),
+// without separate sign flips of b's halves)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
 
 __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, float pL, float rR, float uR,
                                               float vR, float pR, float beta, float inv_beta, float F[4]) {
@@ -282,46 +296,44 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
     const float2 mm = __ffma2_rn(t, dup2(dm), dup2(mL));
     const float2 nn = __ffma2_rn(t, dup2(dn), dup2(nL));
     const float2 ir = make_float2(Ar<float>::rcp(r.x), Ar<float>::rcp(r.y));
-    const float2 u = __fmul2_rn(mm, ir), v = __fmul2_rn(nn, ir);
+    const float2 u = __fmul2_rn(mm, ir);
     const float2 c2 = __ffma2_rn(u, u, __fmul2_rn(dup2(four_beta), ir));
     const float2 ic = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
     const float2 c = __fmul2_rn(c2, ic);
     const float2 hu = __fmul2_rn(dup2(0.5f), u), hc = __fmul2_rn(dup2(0.5f), c);
-    const float2 l4 = __fadd2_rn(hu, hc), l5 = __fadd2_rn(hu, neg2(hc));
+    const float2 l4 = __fadd2_rn(hu, hc), l5 = sub2(hu, hc);
     const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
     const float2 a = __fmul2_rn(__ffma2_rn(neg2(u), dup2(dr), dup2(dm)), dup2(inv_beta));
-    const float2 k = __fmul2_rn(r, ic);
-    const float2 g4 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l4, neg2(au)), k), __ffma2_rn(l4, a, dup2(dq)));
-    const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dup2(dq)));
-    const float2 e = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
+    // k = 1/c: the density cancels as in osher_flux (e = rho E, e/rho terms from E)
+    const float2 g4 = __fmul2_rn(__fmul2_rn(sub2(l4, au), ic), __ffma2_rn(l4, a, dup2(dq)));
+    const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), ic), __ffma2_rn(l5, a, dup2(dq)));
+    const float2 E = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
     const float2 gs = __fadd2_rn(g4, g5);
     const float2 h = __ffma2_rn(g5, l4, __fmul2_rn(g4, l5));
-    // lane sums of (|u|, e, u e, v e, ir (g4 + g5), ir (g4 l5 + g5 l4)), times w13
-    const float2 ue = __fmul2_rn(u, e), ve = __fmul2_rn(v, e);
-    const float2 ig = __fmul2_rn(ir, gs), ih = __fmul2_rn(ir, h);
-    float Sau = w13 * (au.x + au.y), Se = w13 * (e.x + e.y), Sue = w13 * (ue.x + ue.y);
-    float Sve = w13 * (ve.x + ve.y), Sg = w13 * (ig.x + ig.y), Sh = w13 * (ih.x + ih.y);
+    // lane sums of (|u|, rho E, m E, n E, g4 + g5, g4 l5 + g5 l4), times w13
+    const float2 re = __fmul2_rn(r, E), me = __fmul2_rn(mm, E), ne = __fmul2_rn(nn, E);
+    float Sau = w13 * (au.x + au.y), Se = w13 * (re.x + re.y), Sue = w13 * (me.x + me.y);
+    float Sve = w13 * (ne.x + ne.y), Sg = w13 * (gs.x + gs.y), Sh = w13 * (h.x + h.y);
     // ---- point 2 ----
     {
         const float r2 = rL + 0.5f * dr, m2 = mL + 0.5f * dm, n2 = nL + 0.5f * dn;
         const float ir2 = Ar<float>::rcp(r2);
-        const float u2 = m2 * ir2, v2 = n2 * ir2;
+        const float u2 = m2 * ir2;
         const float c22 = u2 * u2 + four_beta * ir2;
         const float ic2 = rsqrtf(c22), cc = c22 * ic2;
         const float hu2 = 0.5f * u2, hc2 = 0.5f * cc;
         const float l42 = hu2 + hc2, l52 = hu2 - hc2;
         const float au2 = fabsf(u2);
         const float a2 = (dm - u2 * dr) * inv_beta;
-        const float k2 = r2 * ic2;
-        const float g42 = (l42 - au2) * k2 * (l42 * a2 + dq);
-        const float g52 = (l52 + au2) * k2 * (l52 * a2 + dq);
-        const float e2 = g42 * l42 + g52 * l52;
+        const float g42 = (l42 - au2) * ic2 * (l42 * a2 + dq);
+        const float g52 = (l52 + au2) * ic2 * (l52 * a2 + dq);
+        const float E2 = g42 * l42 + g52 * l52;
         Sau += w2 * au2;
-        Se += w2 * e2;
-        Sue += w2 * (u2 * e2);
-        Sve += w2 * (v2 * e2);
-        Sg += w2 * (ir2 * (g42 + g52));
-        Sh += w2 * (ir2 * (g42 * l52 + g52 * l42));
+        Se += w2 * (r2 * E2);
+        Sue += w2 * (m2 * E2);
+        Sve += w2 * (n2 * E2);
+        Sg += w2 * (g42 + g52);
+        Sh += w2 * (g42 * l52 + g52 * l42);
     }
     F[0] = 0.5f * ((mL + mR) - (dr * Sau + Se));
     F[1] = 0.5f * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
@@ -335,21 +347,9 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
 // turn.  Every operation of the flux is then a packed one (the reciprocal
 // and reciprocal square root excepted) and no lane sums are needed.  Same
 // quadrature and terms as osher_flux, per lane; the weight of a point rides
-// on k = w rho / c (1/beta stays on the jump term, where it costs no
-// register held across a caller's loop).  Inputs are (rho, un, ut, p) per
+// on k = w / c (1/beta stays on the jump term, where it costs no register
+// held across a caller's loop).  Inputs are (rho, un, ut, p) per
 // lane; returns 2F per lane (the caller's divergence takes the 1/2).
-// a - b as one packed FP32x2 subtraction (the same value as a + (-b),
-// without separate sign flips of b's halves)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    unsigned long long ra, rb, rd;
-    memcpy(&ra, &a, 8);
-    memcpy(&rb, &b, 8);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    float2 d;
-    memcpy(&d, &rd, 8);
-    return d;
-}
-
 __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL, float2 pL, float2 rR, float2 uR,
                                                 float2 vR, float2 pR, float beta, float inv_beta, float2 F[4]) {
     const float2 ib = dup2(inv_beta);
@@ -372,7 +372,7 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
         const float2 t = dup2(tq[j]), w = dup2(wq[j]);
         const float2 r = __ffma2_rn(t, dr, rL), m = __ffma2_rn(t, dm, mL), n = __ffma2_rn(t, dn, nL);
         const float2 ir = make_float2(Ar<float>::rcp(r.x), Ar<float>::rcp(r.y));
-        const float2 u = __fmul2_rn(m, ir), v = __fmul2_rn(n, ir);
+        const float2 u = __fmul2_rn(m, ir);
         const float2 c2 = __ffma2_rn(u, u, __fmul2_rn(fb, ir));
         const float2 ic = make_float2(rsqrtf(c2.x), rsqrtf(c2.y));
         const float2 c = __fmul2_rn(c2, ic);
@@ -381,24 +381,25 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
         const float2 l4 = __ffma2_rn(dup2(0.5f), c, hu), l5 = __ffma2_rn(dup2(-0.5f), c, hu);
         const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
         const float2 a = __fmul2_rn(__ffma2_rn(u, ndr, dm), ib);
-        const float2 k = __fmul2_rn(__fmul2_rn(w, r), ic);
+        // k = w / c: the density cancels as in osher_flux (e = rho E)
+        const float2 k = __fmul2_rn(w, ic);
         const float2 g4 = __fmul2_rn(__fmul2_rn(sub2(l4, au), k), __ffma2_rn(l4, a, dq));
         const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dq));
-        const float2 e = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
-        const float2 gs = __fmul2_rn(ir, __fadd2_rn(g4, g5));
-        const float2 h = __fmul2_rn(ir, __ffma2_rn(g5, l4, __fmul2_rn(g4, l5)));
+        const float2 E = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
+        const float2 gs = __fadd2_rn(g4, g5);
+        const float2 h = __ffma2_rn(g5, l4, __fmul2_rn(g4, l5));
         if (j == 0) {
             Sau = __fmul2_rn(w, au);
-            Se = e;
-            Sue = __fmul2_rn(u, e);
-            Sve = __fmul2_rn(v, e);
+            Se = __fmul2_rn(r, E);
+            Sue = __fmul2_rn(m, E);
+            Sve = __fmul2_rn(n, E);
             Sg = gs;
             Sh = h;
         } else {
             Sau = __ffma2_rn(w, au, Sau);
-            Se = __fadd2_rn(Se, e);
-            Sue = __ffma2_rn(u, e, Sue);
-            Sve = __ffma2_rn(v, e, Sve);
+            Se = __ffma2_rn(r, E, Se);
+            Sue = __ffma2_rn(m, E, Sue);
+            Sve = __ffma2_rn(n, E, Sve);
             Sg = __fadd2_rn(Sg, gs);
             Sh = __fadd2_rn(Sh, h);
         }
