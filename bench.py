@@ -579,7 +579,7 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.7 + 2 * 75.4) / 3, (490.0 + 2 * 469.0) / 3),   # sweep_kernel_mixed<64,4>
+    16: ((57.8 + 2 * 75.4) / 3, (474.2 + 2 * 453.2) / 3),   # sweep_kernel_mixed<64,4>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 

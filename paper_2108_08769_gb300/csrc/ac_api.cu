@@ -573,6 +573,7 @@ struct MixedBackend : Backend {
         const double dx = c->dx, dy = c->dy;
         a.dx = float(dx); a.dy = float(dy); a.half_dx = float(0.5 * dx); a.half_dy = float(0.5 * dy);
         a.inv_dx = float(1.0 / dx); a.inv_dy = float(1.0 / dy);
+        a.nh_inv_dx = float(-0.5 / dx); a.nh_inv_dy = float(-0.5 / dy);
         a.dx_over_dy = float(dx / dy); a.dy_over_dx = float(dy / dx);
         a.beta = float(c->beta); a.inv_beta = float(1.0 / c->beta);
         a.gx = float(c->grid.gx); a.gy = float(c->grid.gy);

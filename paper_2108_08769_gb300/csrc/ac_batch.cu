@@ -683,6 +683,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         const double dx = g.lx / g.nx, dy = g.ly / g.ny;
         a.dx = float(dx); a.dy = float(dy); a.half_dx = float(0.5 * dx); a.half_dy = float(0.5 * dy);
         a.inv_dx = float(1.0 / dx); a.inv_dy = float(1.0 / dy);
+        a.nh_inv_dx = float(-0.5 / dx); a.nh_inv_dy = float(-0.5 / dy);
         a.dx_over_dy = float(dx / dy); a.dy_over_dx = float(dy / dx);
         a.beta = float(beta[k]); a.inv_beta = float(1.0 / beta[k]);
         a.gx = float(g.gx); a.gy = float(g.gy);

@@ -55,6 +55,7 @@ struct MixedArgs {
     int stage, s_max;
     float alpha;
     float dx, dy, half_dx, half_dy, inv_dx, inv_dy, dx_over_dy, dy_over_dx;
+    float nh_inv_dx, nh_inv_dy;   // -1/(2 dx), -1/(2 dy)
     float beta, inv_beta, gx, gy;
     float cfl_area;
     int plevel;            // 1: pressure as dp over the FP64 level p^n; 0: the record holds p
@@ -233,7 +234,7 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // west, east, south and north faces; src.cell(cell, g, ...) gives dQ^{m},
 // dp^{m}, Q^n and rho_ref of the cell.
 template <bool BDF, typename Src, typename Sq>
-__device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, bool stage1,
+__device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, float b0dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
                                             float je, float js, float jn, const Src &src, Sq &sq) {
@@ -246,8 +247,12 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float r0 = q0 + e0;
     const float m0 = q1 + e1;
     const float n0 = q2 + e2;
-    float rt0 = a.B0 * e0, rt1 = a.B0 * e1, rt2 = a.B0 * e2;
+    // real-time terms (B0 Q^{m} - ...)/dt, for Backward-Euler B0/dt (b0dt) times Q^{m} - Q^n
+    float rt0, rt1, rt2;
     if constexpr (BDF) {
+        rt0 = a.B0 * e0;
+        rt1 = a.B0 * e1;
+        rt2 = a.B0 * e2;
         if (a.order >= 2) {
             rt0 -= a.B2 * a.D1[0][g];
             rt1 -= a.B2 * a.D1[1][g];
@@ -258,16 +263,19 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
             rt1 -= a.B3 * a.D2[1][g];
             rt2 -= a.B3 * a.D2[2][g];
         }
+        rt0 *= inv_dt;
+        rt1 *= inv_dt;
+        rt2 *= inv_dt;
+    } else {
+        rt0 = b0dt * e0;
+        rt1 = b0dt * e1;
+        rt2 = b0dt * e2;
     }
-    rt0 *= inv_dt;
-    rt1 *= inv_dt;
-    rt2 *= inv_dt;
-    // level force: -(divergence of the face constants' level parts)
-    const float sx = -0.5f * (je + jw) * a.inv_dx;
-    const float sy = -0.5f * (jn + js) * a.inv_dy;
+    // with the level force -(divergence of the face constants' level parts),
+    // -(je + jw)/(2 dx) and -(jn + js)/(2 dy)
     const float b0 = -div0 - rt0;
-    const float b1 = -div1 - rt1 + r0 * a.gx + sx;
-    const float b2 = -div2 - rt2 + (r0 - rref) * a.gy + sy;
+    const float b1 = fmaf(je + jw, a.nh_inv_dx, fmaf(r0, a.gx, -div1 - rt1));
+    const float b2 = fmaf(jn + js, a.nh_inv_dy, fmaf(r0 - rref, a.gy, -div2 - rt2));
     const float b3 = -div3;
     float dtau;
     if (a.local_dtau) {
@@ -281,7 +289,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
         dtau = float(global_dtau(a.ctl));
     }
     const float adt = alpha * dtau;
-    const float coef = __fdividef(adt, 1.0f + a.B0 * adt * inv_dt);   // Eq. point_implicit
+    const float coef = __fdividef(adt, fmaf(adt, b0dt, 1.0f));   // Eq. point_implicit
     const float coef_p = a.alpha_pi_p_row ? coef : adt;
     dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
     if (stage1) sq.add(b0, b1, b2, a.beta * b3);   // the p row in pressure units
@@ -470,8 +478,8 @@ __device__ __forceinline__ void mixed_tile_compute(const MixedArgs &a, int stage
         if (gi >= nx || gj >= ny) continue;
         const int g = gj * nx + gi;
         const int fw = lj * (TX + 1) + li;
-        cell_update<BDF>(a, alpha, inv_dt, stage == 1, dout, cell, g, sm.fx[fw], sm.fx[fw + 1], sm.fy[cell],
-                         sm.fy[cell + TX], a.inv_dx, a.inv_dy, sm.dxf[fw], sm.dxf[fw + 1], sm.dyf[cell],
+        cell_update<BDF>(a, alpha, inv_dt, a.B0 * inv_dt, stage == 1, dout, cell, g, sm.fx[fw], sm.fx[fw + 1],
+                         sm.fy[cell], sm.fy[cell + TX], a.inv_dx, a.inv_dy, sm.dxf[fw], sm.dxf[fw + 1], sm.dyf[cell],
                          sm.dyf[cell + TX], src, sq);
     }
     if (stage == 1) {
@@ -699,6 +707,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     const float4 *d0 = a.d[cur];
     float4 *dout = a.d[out];
     const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
+    const float b0dt = a.B0 * inv_dt;
     const bool need_rt = a.realtime != 0;
     const bool per_x = (a.bc[0] == kPeriodic);
     // the column's source (ghost columns fold onto interior ones)
@@ -780,8 +789,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             limit_slopes(Wm1, We, Ww, W0, Wm2, a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                rx = (a.B0 * Rm1.e.y) * inv_dt;
-                ry = (a.B0 * Rm1.e.z) * inv_dt;
+                rx = b0dt * Rm1.e.y;
+                ry = b0dt * Rm1.e.z;
                 rx = (Rm1.fl & 1) ? -rx : rx;
                 ry = (Rm1.fl & 2) ? -ry : ry;
             }
@@ -816,8 +825,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     const float4 ue = d0[gu], uq = __ldg(a.qn + gu);
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
                     if (out_lane)
-                        cell_update<false>(a, alpha, inv_dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
-                                           Fy, hidx, hidy, jw, Jm2, Jyp, Rm1.jy, Uk, sq);
+                        cell_update<false>(a, alpha, inv_dt, b0dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2,
+                                           Fyp, Fy, hidx, hidy, jw, Jm2, Jyp, Rm1.jy, Uk, sq);
                 }
                 Fyp = Fy;
                 Jyp = Rm1.jy;
