@@ -558,7 +558,7 @@ FP64_ALG_FLOPS_PER_CELL_STAGE = 483.0
 # recomputes slopes and pressure gradients, and stage 1 forms the values
 # stages 2 and 3 read back), and the FP64 instructions behind them
 FP64_EXEC_FLOPS_PER_CELL_STAGE = 673.2
-FP64_INSTR_PER_CELL_STAGE = 468.4
+FP64_INSTR_PER_CELL_STAGE = 459.7
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
 # the three stages (3.74, 6.36, 6.36 MB read; the output stays in L2)
@@ -579,7 +579,7 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.8 + 2 * 75.4) / 3, (474.2 + 2 * 453.2) / 3),   # sweep_kernel_mixed<64,4>
+    16: ((57.8 + 2 * 75.4) / 3, (467.0 + 2 * 446.0) / 3),   # sweep_kernel_mixed<64,4>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 

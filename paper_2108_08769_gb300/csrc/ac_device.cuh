@@ -138,11 +138,12 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
     // D = sum_j w_j |A_j| dQ, accumulated as
     //   D0 = dr Sau + Se,  D1 = dm Sau + Sue + beta Sg,
     //   D2 = dn Sau + Sve, D3 = dq Sau - Sh
-    // with, at point j, g4 = (l4 - |u|) k (l4 beta a + dp), g5 = (l5 + |u|) k
-    // (l5 beta a + dp), k = w_j / (beta c): e = rho (g4 l4 + g5 l5) enters Se
-    // and, times u and v, Sue and Sve (rho u = m, rho v = n), and Sg, Sh take
-    // g4 + g5 and g4 l5 + g5 l4 (the acoustic terms of |A| dQ over rho times
-    // rho: the density cancels)
+    // with, at point j, G4 = (l4 - |u|) (l4 beta a + dp), G5 = (l5 + |u|)
+    // (l5 beta a + dp) and k = w_j / (beta c): e = rho k (G4 l4 + G5 l5)
+    // enters Se and, times u and v, Sue and Sve (rho u = m, rho v = n), and
+    // Sg, Sh take k (G4 + G5) and k (G4 l5 + G5 l4) (the acoustic terms of
+    // |A| dQ over rho times rho: the density cancels).  Since l4 + l5 = u,
+    // G4 l5 + G5 l4 = (G4 + G5) u - (G4 l4 + G5 l5).
     T Sau, Se, Sue, Sve, Sg, Sh;
     // the three densities' reciprocals from one reciprocal of their product
     // (1 reciprocal + 6 products in place of 3 reciprocals)
@@ -174,14 +175,16 @@ __device__ __forceinline__ void osher_flux(T rL, T uL, T vL, T pL, T rR, T uR, T
         const T ba = dm - u * dr;   // beta a
         const T w = wq[j];
         const T k = (w * inv_beta) * ic;
-        const T g4 = (l4 - au) * k * (l4 * ba + dp);
-        const T g5 = (l5 + au) * k * (l5 * ba + dp);
-        const T E = g4 * l4 + g5 * l5;   // e / rho
-        const T gs = g4 + g5, h = g4 * l5 + g5 * l4;
+        const T G4 = (l4 - au) * (l4 * ba + dp);
+        const T G5 = (l5 + au) * (l5 * ba + dp);
+        const T Gs = G4 + G5;
+        const T Ep = G4 * l4 + G5 * l5;
+        const T Hp = Gs * u - Ep;        // G4 l5 + G5 l4
+        const T E = k * Ep;              // e / rho
         if (j == 0) {
-            Sau = w * au; Se = r * E; Sue = m * E; Sve = n * E; Sg = gs; Sh = h;
+            Sau = w * au; Se = r * E; Sue = m * E; Sve = n * E; Sg = k * Gs; Sh = k * Hp;
         } else {
-            Sau += w * au; Se += r * E; Sue += m * E; Sve += n * E; Sg += gs; Sh += h;
+            Sau += w * au; Se += r * E; Sue += m * E; Sve += n * E; Sg += k * Gs; Sh += k * Hp;
         }
     }
     // central part 1/2 (F(Q_L) + F(Q_R)); dissipation 1/2 * D (D already
@@ -304,13 +307,15 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
     const float2 l4 = __fadd2_rn(hu, hc), l5 = sub2(hu, hc);
     const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
     const float2 a = __fmul2_rn(__ffma2_rn(neg2(u), dup2(dr), dup2(dm)), dup2(inv_beta));
-    // k = 1/c: the density cancels as in osher_flux (e = rho E, e/rho terms from E)
-    const float2 g4 = __fmul2_rn(__fmul2_rn(sub2(l4, au), ic), __ffma2_rn(l4, a, dup2(dq)));
-    const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), ic), __ffma2_rn(l5, a, dup2(dq)));
-    const float2 E = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
-    const float2 gs = __fadd2_rn(g4, g5);
-    const float2 h = __ffma2_rn(g5, l4, __fmul2_rn(g4, l5));
-    // lane sums of (|u|, rho E, m E, n E, g4 + g5, g4 l5 + g5 l4), times w13
+    // k = 1/c, taken out of G4, G5 as in osher_flux (the density cancels)
+    const float2 G4 = __fmul2_rn(sub2(l4, au), __ffma2_rn(l4, a, dup2(dq)));
+    const float2 G5 = __fmul2_rn(__fadd2_rn(l5, au), __ffma2_rn(l5, a, dup2(dq)));
+    const float2 Gs = __fadd2_rn(G4, G5);
+    const float2 Ep = __ffma2_rn(G5, l5, __fmul2_rn(G4, l4));
+    const float2 E = __fmul2_rn(ic, Ep);
+    const float2 gs = __fmul2_rn(ic, Gs);
+    const float2 h = __fmul2_rn(ic, sub2(__fmul2_rn(Gs, u), Ep));   // G4 l5 + G5 l4, times k
+    // lane sums of (|u|, rho E, m E, n E, k (G4 + G5), k (G4 l5 + G5 l4)), times w13
     const float2 re = __fmul2_rn(r, E), me = __fmul2_rn(mm, E), ne = __fmul2_rn(nn, E);
     float Sau = w13 * (au.x + au.y), Se = w13 * (re.x + re.y), Sue = w13 * (me.x + me.y);
     float Sve = w13 * (ne.x + ne.y), Sg = w13 * (gs.x + gs.y), Sh = w13 * (h.x + h.y);
@@ -325,15 +330,18 @@ __device__ __forceinline__ void osher_flux_x2(float rL, float uL, float vL, floa
         const float l42 = hu2 + hc2, l52 = hu2 - hc2;
         const float au2 = fabsf(u2);
         const float a2 = (dm - u2 * dr) * inv_beta;
-        const float g42 = (l42 - au2) * ic2 * (l42 * a2 + dq);
-        const float g52 = (l52 + au2) * ic2 * (l52 * a2 + dq);
-        const float E2 = g42 * l42 + g52 * l52;
+        const float G42 = (l42 - au2) * (l42 * a2 + dq);
+        const float G52 = (l52 + au2) * (l52 * a2 + dq);
+        const float Gs2 = G42 + G52;
+        const float Ep2 = G42 * l42 + G52 * l52;
+        const float k2 = w2 * ic2;
+        const float E2 = k2 * Ep2;
         Sau += w2 * au2;
-        Se += w2 * (r2 * E2);
-        Sue += w2 * (m2 * E2);
-        Sve += w2 * (n2 * E2);
-        Sg += w2 * (g42 + g52);
-        Sh += w2 * (g42 * l52 + g52 * l42);
+        Se += r2 * E2;
+        Sue += m2 * E2;
+        Sve += n2 * E2;
+        Sg += k2 * Gs2;
+        Sh += k2 * (Gs2 * u2 - Ep2);   // G42 l52 + G52 l42
     }
     F[0] = 0.5f * ((mL + mR) - (dr * Sau + Se));
     F[1] = 0.5f * ((mL * uL + pL + mR * uR + pR) - (dm * Sau + Sue + beta * Sg));
@@ -366,7 +374,7 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
     const float2 fb = dup2(4.0f * beta);
     const float tq[3] = {0.11270166537925831148f, 0.5f, 0.88729833462074168852f};
     const float wq[3] = {5.0f / 18.0f, 8.0f / 18.0f, 5.0f / 18.0f};
-    float2 Sau, Se, Sue, Sve, Sg, Sh;
+    float2 Sau, Se, Sue, Sve, Sg, Sh, SE;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float2 t = dup2(tq[j]), w = dup2(wq[j]);
@@ -381,33 +389,37 @@ __device__ __forceinline__ void osher_flux_pair(float2 rL, float2 uL, float2 vL,
         const float2 l4 = __ffma2_rn(dup2(0.5f), c, hu), l5 = __ffma2_rn(dup2(-0.5f), c, hu);
         const float2 au = make_float2(fabsf(u.x), fabsf(u.y));
         const float2 a = __fmul2_rn(__ffma2_rn(u, ndr, dm), ib);
-        // k = w / c: the density cancels as in osher_flux (e = rho E)
+        // k = w / c, taken out of G4, G5 as in osher_flux (the density cancels)
         const float2 k = __fmul2_rn(w, ic);
-        const float2 g4 = __fmul2_rn(__fmul2_rn(sub2(l4, au), k), __ffma2_rn(l4, a, dq));
-        const float2 g5 = __fmul2_rn(__fmul2_rn(__fadd2_rn(l5, au), k), __ffma2_rn(l5, a, dq));
-        const float2 E = __ffma2_rn(g5, l5, __fmul2_rn(g4, l4));
-        const float2 gs = __fadd2_rn(g4, g5);
-        const float2 h = __ffma2_rn(g5, l4, __fmul2_rn(g4, l5));
+        const float2 G4 = __fmul2_rn(sub2(l4, au), __ffma2_rn(l4, a, dq));
+        const float2 G5 = __fmul2_rn(__fadd2_rn(l5, au), __ffma2_rn(l5, a, dq));
+        const float2 KG = __fmul2_rn(k, __fadd2_rn(G4, G5));
+        const float2 E = __fmul2_rn(k, __ffma2_rn(G5, l5, __fmul2_rn(G4, l4)));
+        // k (G4 l5 + G5 l4) = k (G4 + G5) u - E: Sh takes KG u and, after the
+        // loop, minus the sum of E (there is no packed negation)
         if (j == 0) {
             Sau = __fmul2_rn(w, au);
             Se = __fmul2_rn(r, E);
             Sue = __fmul2_rn(m, E);
             Sve = __fmul2_rn(n, E);
-            Sg = gs;
-            Sh = h;
+            Sg = KG;
+            Sh = __fmul2_rn(KG, u);
+            SE = E;
         } else {
             Sau = __ffma2_rn(w, au, Sau);
             Se = __ffma2_rn(r, E, Se);
             Sue = __ffma2_rn(m, E, Sue);
             Sve = __ffma2_rn(n, E, Sve);
-            Sg = __fadd2_rn(Sg, gs);
-            Sh = __fadd2_rn(Sh, h);
+            Sg = __fadd2_rn(Sg, KG);
+            Sh = __ffma2_rn(KG, u, Sh);
+            SE = __fadd2_rn(SE, E);
         }
     }
     // 2F = F(Q_L) + F(Q_R) - D, D as in osher_flux
     F[0] = sub2(c0, __ffma2_rn(dr, Sau, Se));
     F[1] = sub2(c1, __ffma2_rn(dup2(beta), Sg, __ffma2_rn(dm, Sau, Sue)));
     F[2] = sub2(c2c, __ffma2_rn(dn, Sau, Sve));
+    Sh = sub2(Sh, SE);
     F[3] = sub2(c3, sub2(__fmul2_rn(dq, Sau), Sh));
 }
 
