@@ -430,7 +430,7 @@ template <int H, int WPC, int MINB>
 int launch_sweep(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
     const int nstrips = (int)(g.x * g.y);
     const cudaError_t e = launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB>, dim3((nstrips + WPC - 1) / WPC),
-                                     dim3(WPC * 32), 0, s, a, (int)g.x, nstrips);
+                                     dim3(WPC * 32), WPC * sizeof(StripRing), s, a, (int)g.x, nstrips);
     return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
@@ -634,6 +634,9 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<16, 16, 256, 5, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 14, 448, 1, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 14, 448, 1>()));
+        // the 8-warp strip CTA holds 8 row rings (56 KB)
+        CK(cudaFuncSetAttribute(sweep_kernel_mixed<64, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(8 * sizeof(StripRing))));
         CK((allow_mixed_smem<32, 8, 256, 6, kBassi, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kRoe, true>()));
         CK((allow_mixed_smem<32, 8, 256, 6, kOsher, true>()));

@@ -95,6 +95,8 @@ template <int H, int WPC, int MINB, bool CD>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ strip_tank, int nstrips, int stage,
                    float alpha, int slot0) {
+    extern __shared__ __align__(16) unsigned char strip_smem[];
+    StripRing *ring = reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5);
     pdl_trigger();
     pdl_wait();
     const int w = blockIdx.x * WPC + (threadIdx.x >> 5);
@@ -105,13 +107,13 @@ batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
     } else {
         const BatchTank &t = tanks[k];
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4);
+        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
     }
 }
 
@@ -269,10 +271,11 @@ template <int H, int WPC, int MINB>
 cudaError_t launch_sweep(const BatchTank *tanks, const int *map, int nstrips, int stage, float alpha, int slot0,
                          bool pdl, cudaStream_t s) {
     const dim3 g((nstrips + WPC - 1) / WPC);
+    const size_t smem = WPC * sizeof(StripRing);
     if (slot0 >= 0)
-        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true>, g, dim3(WPC * 32), 0, s, tanks, map, nstrips,
-                          stage, alpha, slot0);
-    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false>, g, dim3(WPC * 32), 0, s, tanks, map, nstrips,
+        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true>, g, dim3(WPC * 32), smem, s, tanks, map,
+                          nstrips, stage, alpha, slot0);
+    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false>, g, dim3(WPC * 32), smem, s, tanks, map, nstrips,
                       stage, alpha, 0);
 }
 

@@ -656,7 +656,8 @@ stage_kernel_mixed(const MixedArgs a) {
 // pressure gradient; either limiter).  Each warp owns 32 adjacent columns, of which the middle 28 are
 // output, and walks up a strip of H rows with a rolling window in registers:
 // the y-direction stencil lives in each lane's registers, x-neighbours come
-// from warp shuffles, so there is no shared memory and no block barrier.  At
+// from warp shuffles, and each lane's row records arrive through its own
+// slots of a shared-memory ring (StripRing), so there is no block barrier.  At
 // the row it ingests, k, the warp forms W(k); with W(k-2..k) it forms the
 // slopes and pressure gradient of row k-1, the x-face fluxes of row k-1 and
 // the y-face flux between rows k-2 and k-1, and it updates row k-2.  Lanes
@@ -676,6 +677,26 @@ __device__ __forceinline__ float4 shfl_up4(const float4 &v, int d) {
 
 constexpr int kStripOut = 28;   // output columns per warp
 
+// One warp's rows in flight: each lane's records of four rows (slot k & 3
+// holds row k), copied from global memory by cp.async one row ahead of use
+// and read back by the same lane, so that no register holds a row before it
+// is needed and none is copied from row to row.
+struct StripRing {
+    float4 q[4][32];   // Q^n of rho, rho u, rho v; rho_ref
+    float4 d[4][32];   // dQ^{s-1} of rho, rho u, rho v; dp
+    float4 e[4][32];   // dQ^{m}, dp^{m} (the ring terms)
+    float jx[4][32];   // level jump across the east x-face (0 off the tank's rows)
+    float jy[4][32];   // level jump across the south y-face (0 off the tank's faces)
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the most recent group of this thread's copies have landed
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // The update's inputs of one cell, held in registers.
 struct HeldSrc {
     float e0, e1, e2, p0, q0, q1, q2, rr;
@@ -689,12 +710,14 @@ struct HeldSrc {
 // of one tank, by one warp; `partial` receives the strip's four residual
 // partial sums at stage 1.  Shared by the single-tank and batched kernels.
 // The per-column parts of the boundary logic are formed once per strip and
-// interior rows skip the fold; the update loads its two records (dQ^{m},
-// dp^{m}; Q^n, rho_ref) when it runs: the same lane loaded them two rows
-// before, so they come from L1, and nothing more is held across rows.
+// interior rows skip the fold.  Every row's records go through the warp's
+// ring (StripRing): row k + 1 is copied in while row k is worked on, and
+// the later uses of a row (its ring terms, reference density and level
+// jumps one row on, the update's records two rows on) read it back from
+// shared memory.
 template <int H>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
-                                            double *partial) {
+                                            double *partial, StripRing *ring) {
     const Ctl *ctl = a.ctl;
     const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
@@ -717,15 +740,6 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     // the face pairs come as 2F: (2Fe - 2Fw) (1/(2 dx)) is (Fe - Fw)/dx exactly
     const float hidx = 0.5f * a.inv_dx, hidy = 0.5f * a.inv_dy;
 
-    // raw inputs of a row, loaded one row ahead of use
-    struct Raw {
-        float4 q;                           // Q^n of rho, rho u, rho v; rho_ref
-        float4 d;                           // dQ^{s-1} of rho, rho u, rho v; dp
-        float4 e;                           // dQ^{m}, dp^{m} (the ring terms)
-        float jump;                         // level jump across the east x-face (0 off the tank's rows)
-        float jy;                           // level jump across the south y-face (0 off the tank's faces)
-        int fl;                             // fold bits
-    };
     // Per-column parts of the boundary logic, fixed for the whole strip, in
     // one word: the fold bits of an interior row (bits 0-1), whether the
     // column is a wall ghost (bit 2), whether the low and high y sides are
@@ -738,23 +752,31 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     const int colbits = (nfx & 1) | ((tfx & 1) << 1) |
                         (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
                         (is_wall(a.bc[2]) ? 8 : 0) | (is_wall(a.bc[3]) ? 16 : 0);
-    auto load_raw = [&](int k, Raw &R, int &srow) {
-        R.fl = colbits & 3;
-        if (k >= 0 && k < ny) {   // the same for the whole warp
-            srow = k;
-        } else {
-            int nfy, tfy;
-            srow = fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
-            R.fl = ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
-        }
-        const int s = srow * nx + scol;
-        R.q = __ldg(a.qn + s);
-        R.d = din[s];
-        R.e = d0[s];
-        R.jump = (k >= 0 && k < ny && jcol >= 0) ? __ldg(&a.jmp[k * nx + jcol].x) : 0.0f;
+    // fold bits of row k in this column (ghost rows fold onto tank rows)
+    auto row_flags = [&](int k) {
+        if (k >= 0 && k < ny) return colbits & 3;   // the same for the whole warp
+        int nfy, tfy;
+        fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+        return ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
+    };
+    // copies of row k's records into ring slot k & 3, as one group
+    auto stage_row = [&](int k) {
+        int nfy, tfy;
+        const int srow = (k >= 0 && k < ny) ? k : fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+        const int s = srow * nx + scol, sl = k & 3;
+        cp_async16(&ring->q[sl][lane], a.qn + s);
+        cp_async16(&ring->d[sl][lane], din + s);
+        cp_async16(&ring->e[sl][lane], d0 + s);
+        if (k >= 0 && k < ny && jcol >= 0)
+            cp_async4(&ring->jx[sl][lane], &a.jmp[k * nx + jcol].x);
+        else
+            ring->jx[sl][lane] = 0.0f;
         // row ny: the north face of the top row (periodic: the south face of row 0)
-        R.jy = (own_col && k >= 0 && (k < ny || (k == ny && per_y))) ? __ldg(&a.jmp[(k < ny ? k : 0) * nx + c].y)
-                                                                       : 0.0f;
+        if (own_col && k >= 0 && (k < ny || (k == ny && per_y)))
+            cp_async4(&ring->jy[sl][lane], &a.jmp[(k < ny ? k : 0) * nx + c].y);
+        else
+            ring->jy[sl][lane] = 0.0f;
+        cp_async_commit();
     };
 
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
@@ -763,23 +785,25 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
     float Jm2 = 0.0f;                                        // east x-face level jump of row k-2
     float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
-    Raw Rm1 = {}, Rk, Rn;                                    // raw rows k-1, k, k+1
-    int srk, srn;
     SqKahan sq;
-    load_raw(y0 - 2, Rk, srk);
+    stage_row(y0 - 2);
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
-        // prefetch: the next row's inputs
-        load_raw(k + 1, Rn, srn);
+        // prefetch: the next row's records; then row k's own copies have landed
+        stage_row(k + 1);
+        cp_async_wait_1();
+        const int sk = k & 3, s1 = (k - 1) & 3, s2 = (k - 2) & 3;
         // ---- W = (rho, u, v, dp) of Q^{s-1} at row k ----
         float4 W0;
         {
-            const float r = Rk.q.x + Rk.d.x;
-            float mm = Rk.q.y + Rk.d.y;
-            float nn = Rk.q.z + Rk.d.z;
-            mm = (Rk.fl & 1) ? -mm : mm;
-            nn = (Rk.fl & 2) ? -nn : nn;
+            const float4 q = ring->q[sk][lane], d = ring->d[sk][lane];
+            const int fl = row_flags(k);
+            const float r = q.x + d.x;
+            float mm = q.y + d.y;
+            float nn = q.z + d.z;
+            mm = (fl & 1) ? -mm : mm;
+            nn = (fl & 2) ? -nn : nn;
             const float ir = Ar<float>::rcp(r);
-            W0 = make_float4(r, mm * ir, nn * ir, Rk.d.w);
+            W0 = make_float4(r, mm * ir, nn * ir, d.w);
         }
         if (k >= y0) {
             // ---- slopes and pressure gradient of row r = k-1 ----
@@ -789,26 +813,29 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             limit_slopes(Wm1, We, Ww, W0, Wm2, a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                rx = b0dt * Rm1.e.y;
-                ry = b0dt * Rm1.e.z;
-                rx = (Rm1.fl & 1) ? -rx : rx;
-                ry = (Rm1.fl & 2) ? -ry : ry;
+                const float4 e1 = ring->e[s1][lane];
+                const int fl = row_flags(r);
+                rx = b0dt * e1.y;
+                ry = b0dt * e1.z;
+                rx = (fl & 1) ? -rx : rx;
+                ry = (fl & 2) ? -ry : ry;
             }
             // gravity reversed in wall ghosts (as wall_ghost_sign)
             const bool wall_ghost = (colbits & 4) || (r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16));
             const float sg = wall_ghost ? -1.0f : 1.0f;
             float hpx, hpy;
-            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, Rm1.q.w, sg, hpx, hpy);
+            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, ring->q[s1][lane].w, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
             // ---- east x-face of row r (between columns c and c + 1) ----
             const float4 &Wn = We;
             const float4 Sn = shfl_down4(Sx, 1);
-            const float jump = Rm1.jump;
+            const float jump = ring->jx[s1][lane];
+            const float jy1 = ring->jy[s1][lane];   // below row r
             // ---- and the y-face between rows r - 1 and r (not needed, but
             // harmless, on the first row): both fluxes as one packed pair ----
             FaceStates f, fy;
             x_face_states(Wm1, Wn, Sx, Sn, jump, f);
-            y_face_states(Wm2, Wm1, Sym2, Sy, Rm1.jy, fy);
+            y_face_states(Wm2, Wm1, Sym2, Sy, jy1, fy);
             float2 Fp[4];
             osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
                             make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
@@ -821,15 +848,15 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
-                    const int gu = (k - 2) * nx + min(max(c, 0), nx - 1);
-                    const float4 ue = d0[gu], uq = __ldg(a.qn + gu);
+                    // row k - 2 is a tank row, so its slot holds this column's records
+                    const float4 ue = ring->e[s2][lane], uq = ring->q[s2][lane];
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
                     if (out_lane)
                         cell_update<false>(a, alpha, inv_dt, b0dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2,
-                                           Fyp, Fy, hidx, hidy, jw, Jm2, Jyp, Rm1.jy, Uk, sq);
+                                           Fyp, Fy, hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq);
                 }
                 Fyp = Fy;
-                Jyp = Rm1.jy;
+                Jyp = jy1;
             }
             Fxm2 = Fx;
             Jm2 = jump;
@@ -837,10 +864,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         }
         Wm2 = Wm1;
         Wm1 = W0;
-        Rm1 = Rk;
-        Rk = Rn;
-        srk = srn;
     }
+    cp_async_wait_all();   // the copies past the strip's last row
     if (stage == 1) {
         // the strip's sums across lanes, in FP64
         double v0 = sq.lane_sum(0), v1 = sq.lane_sum(1), v2 = sq.lane_sum(2), v3 = sq.lane_sum(3);
@@ -863,10 +888,12 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     pdl_trigger();
     pdl_wait();
     if (a.ctl->done) return;
+    extern __shared__ __align__(16) unsigned char strip_smem[];
     const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
     if (warp >= nstrips) return;   // whole warps only
     const int sy = warp / strips_x, sx = warp - sy * strips_x;
-    mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4);
+    mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
+                   reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5));
 }
 
 // Global pseudo-time step option for the mixed form.
