@@ -714,8 +714,9 @@ struct HeldSrc {
 // ring (StripRing): row k + 1 is copied in while row k is worked on, and
 // the later uses of a row (its ring terms, reference density and level
 // jumps one row on, the update's records two rows on) read it back from
-// shared memory.
-template <int H>
+// shared memory.  UNROLL: row-loop unrolling (2 lets the compiler keep the
+// rolling rows' registers in place instead of moving them each row).
+template <int H, int UNROLL = 1>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial, StripRing *ring) {
     const Ctl *ctl = a.ctl;
@@ -787,6 +788,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
     SqKahan sq;
     stage_row(y0 - 2);
+#pragma unroll UNROLL
     for (int k = y0 - 2; k <= y1 + 1; ++k) {
         // prefetch: the next row's records; then row k's own copies have landed
         stage_row(k + 1);
@@ -892,8 +894,8 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
     if (warp >= nstrips) return;   // whole warps only
     const int sy = warp / strips_x, sx = warp - sy * strips_x;
-    mixed_strip<H>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
-                   reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5));
+    mixed_strip<H, 2>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
+                      reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5));
 }
 
 // Global pseudo-time step option for the mixed form.
