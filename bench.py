@@ -579,7 +579,7 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.8 + 2 * 75.4) / 3, (467.0 + 2 * 446.0) / 3),   # sweep_kernel_mixed<64,4>
+    16: ((57.8 + 2 * 75.4) / 3, (465.9 + 2 * 444.9) / 3),   # sweep_kernel_mixed<64,4>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
