@@ -90,8 +90,9 @@ batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
 }
 
 // Column-strip form over the flattened strips of all tanks: warp w takes
-// strip w (see mixed_strip); CD as above.
-template <int H, int WPC, int MINB, bool CD>
+// strip w (see mixed_strip); CD as above; SK: 1 for stage 1, 2 for the
+// later stages.
+template <int H, int WPC, int MINB, bool CD, int SK>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ strip_tank, int nstrips, int stage,
                    float alpha, int slot0) {
@@ -107,13 +108,13 @@ batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
+        mixed_strip<H, 1, SK>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
     } else {
         const BatchTank &t = tanks[k];
         if (t.a.ctl->done) return;
         const int local = w - t.tile0;
         const int sy = local / t.tiles_x, sx = local - sy * t.tiles_x;
-        mixed_strip<H>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
+        mixed_strip<H, 1, SK>(t.a, stage, alpha, sx, sy, t.a.partials + (size_t)local * 4, ring);
     }
 }
 
@@ -272,11 +273,19 @@ cudaError_t launch_sweep(const BatchTank *tanks, const int *map, int nstrips, in
                          bool pdl, cudaStream_t s) {
     const dim3 g((nstrips + WPC - 1) / WPC);
     const size_t smem = WPC * sizeof(StripRing);
+    const dim3 b(WPC * 32);
+    if (stage == 1) {
+        if (slot0 >= 0)
+            return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true, 1>, g, b, smem, s, tanks, map, nstrips,
+                              stage, alpha, slot0);
+        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false, 1>, g, b, smem, s, tanks, map, nstrips, stage,
+                          alpha, 0);
+    }
     if (slot0 >= 0)
-        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true>, g, dim3(WPC * 32), smem, s, tanks, map,
-                          nstrips, stage, alpha, slot0);
-    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false>, g, dim3(WPC * 32), smem, s, tanks, map, nstrips,
-                      stage, alpha, 0);
+        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true, 2>, g, b, smem, s, tanks, map, nstrips, stage,
+                          alpha, slot0);
+    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false, 2>, g, b, smem, s, tanks, map, nstrips, stage,
+                      alpha, 0);
 }
 
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>

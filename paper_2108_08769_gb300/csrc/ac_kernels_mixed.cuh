@@ -182,6 +182,23 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
     }
 }
 
+// The same limiter from the differences themselves: east/west along x,
+// north/south along y (the column-strip sweep forms each difference once and
+// passes it on to the neighbour that needs it as its other side).
+__device__ __forceinline__ void limit_diffs(float er, float wr, float nr, float sr, float eu, float wu, float nu,
+                                            float su, float ev, float wv, float nv, float sv, int k, float klim,
+                                            float &hrx, float &hry, float &hux, float &huy, float &hvx, float &hvy) {
+    if (k == 1) {
+        hrx = half_minmod(er, wr); hry = half_minmod(nr, sr);
+        hux = half_minmod(eu, wu); huy = half_minmod(nu, su);
+        hvx = half_minmod(ev, wv); hvy = half_minmod(nv, sv);
+    } else {
+        hrx = 0.5f * limiter(er, wr, klim); hry = 0.5f * limiter(nr, sr, klim);
+        hux = 0.5f * limiter(eu, wu, klim); huy = 0.5f * limiter(nu, su, klim);
+        hvx = 0.5f * limiter(ev, wv, klim); hvy = 0.5f * limiter(nv, sv, klim);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Per-cell and per-face arithmetic shared by the tile sweep and the
 // column-strip sweep, so that both compute every value the same way.
@@ -232,12 +249,15 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // bracket to sq.  Fw, Fe, Fs, Fn: face fluxes, scaled by s_f (1 or 2), and
 // fdx, fdy = 1/(s_f dx), 1/(s_f dy); jw, je, js, jn: level jumps of the
 // west, east, south and north faces; src.cell(cell, g, ...) gives dQ^{m},
-// dp^{m}, Q^n and rho_ref of the cell.
+// dp^{m}, Q^n and rho_ref of the cell.  live = false: the arithmetic runs
+// (a halo lane of the column-strip sweep, on a real cell's values) but
+// nothing is stored or summed.
 template <bool BDF, typename Src, typename Sq>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, float b0dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
-                                            float je, float js, float jn, const Src &src, Sq &sq) {
+                                            float je, float js, float jn, const Src &src, Sq &sq,
+                                            bool live = true) {
     const float div0 = (Fe.x - Fw.x) * fdx + (Fn.x - Fs.x) * fdy;
     const float div1 = (Fe.y - Fw.y) * fdx + (Fn.y - Fs.y) * fdy;
     const float div2 = (Fe.z - Fw.z) * fdx + (Fn.z - Fs.z) * fdy;
@@ -291,8 +311,10 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float adt = alpha * dtau;
     const float coef = __fdividef(adt, fmaf(adt, b0dt, 1.0f));   // Eq. point_implicit
     const float coef_p = a.alpha_pi_p_row ? coef : adt;
-    dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
-    if (stage1) sq.add(b0, b1, b2, a.beta * b3);   // the p row in pressure units
+    if (live) dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
+    if (stage1) {
+        if (live) sq.add(b0, b1, b2, a.beta * b3);   // the p row in pressure units
+    }
 }
 
 // 4-byte global -> shared copy that completes asynchronously (cp.async);
@@ -662,7 +684,8 @@ stage_kernel_mixed(const MixedArgs a) {
 // slopes and pressure gradient of row k-1, the x-face fluxes of row k-1 and
 // the y-face flux between rows k-2 and k-1, and it updates row k-2.  Lanes
 // 0, 1, 30, 31 are halo (their slopes or fluxes feed the output lanes'
-// faces).  Every per-cell value uses the same functions as the tile sweep;
+// faces; they run the update's arithmetic too, storing nothing, so that the
+// warp does not branch around it).  Every per-cell value uses the same functions as the tile sweep;
 // a lane's x- and y-face fluxes go through the face-pair form of the Osher
 // flux (osher_flux_pair), which returns 2F.
 // ---------------------------------------------------------------------------
@@ -715,10 +738,14 @@ struct HeldSrc {
 // the later uses of a row (its ring terms, reference density and level
 // jumps one row on, the update's records two rows on) read it back from
 // shared memory.  UNROLL: row-loop unrolling (2 lets the compiler keep the
-// rolling rows' registers in place instead of moving them each row).
-template <int H, int UNROLL = 1>
+// rolling rows' registers in place instead of moving them each row).  SK: 1
+// compiles stage 1 only (its input Q^{s-1} is Q^{m}, so one record serves
+// both and the ring's e slots stay unused), 2 the later stages only (no
+// residual sums), 0 either, chosen by `stage`.
+template <int H, int UNROLL = 1, int SK = 0>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial, StripRing *ring) {
+    const bool st1 = SK == 0 ? (stage == 1) : (SK == 1);
     const Ctl *ctl = a.ctl;
     const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
@@ -767,7 +794,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         const int s = srow * nx + scol, sl = k & 3;
         cp_async16(&ring->q[sl][lane], a.qn + s);
         cp_async16(&ring->d[sl][lane], din + s);
-        cp_async16(&ring->e[sl][lane], d0 + s);
+        if (SK != 1) cp_async16(&ring->e[sl][lane], d0 + s);
         if (k >= 0 && k < ny && jcol >= 0)
             cp_async4(&ring->jx[sl][lane], &a.jmp[k * nx + jcol].x);
         else
@@ -780,7 +807,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         cp_async_commit();
     };
 
+    // the ring terms (dQ^{m}, dp^{m}) of the row in slot sl
+    auto ering = [&](int sl) -> float4 { return SK == 1 ? ring->d[sl][lane] : ring->e[sl][lane]; };
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
+    float4 Dp = Wm2;                                         // W(k-1) - W(k-2) (rho, u, v)
     float4 Sym2 = Wm2;                                       // y half slopes of row k-2
     float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
@@ -810,12 +840,19 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         if (k >= y0) {
             // ---- slopes and pressure gradient of row r = k-1 ----
             const int r = k - 1;
-            const float4 We = shfl_down4(Wm1, 1), Ww = shfl_up4(Wm1, 1);
+            // differences of rho, u, v across the east face (the west one is
+            // the west neighbour's east difference) and the north face (the
+            // south one was the north difference of the row before)
+            const float4 We = shfl_down4(Wm1, 1);
+            const float exr = We.x - Wm1.x, exu = We.y - Wm1.y, exv = We.z - Wm1.z;
+            const float wxr = __shfl_up_sync(0xffffffffu, exr, 1), wxu = __shfl_up_sync(0xffffffffu, exu, 1),
+                        wxv = __shfl_up_sync(0xffffffffu, exv, 1);
             float hrx, hry, hux, huy, hvx, hvy;
-            limit_slopes(Wm1, We, Ww, W0, Wm2, a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
+            limit_diffs(exr, wxr, W0.x - Wm1.x, Dp.x, exu, wxu, W0.y - Wm1.y, Dp.y, exv, wxv, W0.z - Wm1.z, Dp.z,
+                        a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
-                const float4 e1 = ring->e[s1][lane];
+                const float4 e1 = ering(s1);
                 const int fl = row_flags(r);
                 rx = b0dt * e1.y;
                 ry = b0dt * e1.z;
@@ -828,22 +865,23 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             float hpx, hpy;
             new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, ring->q[s1][lane].w, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
-            // ---- east x-face of row r (between columns c and c + 1) ----
-            const float4 &Wn = We;
-            const float4 Sn = shfl_down4(Sx, 1);
-            const float jump = ring->jx[s1][lane];
-            const float jy1 = ring->jy[s1][lane];   // below row r
-            // ---- and the y-face between rows r - 1 and r (not needed, but
-            // harmless, on the first row): both fluxes as one packed pair ----
-            FaceStates f, fy;
-            x_face_states(Wm1, Wn, Sx, Sn, jump, f);
-            y_face_states(Wm2, Wm1, Sym2, Sy, jy1, fy);
-            float2 Fp[4];
-            osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
-                            make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
-                            make_float2(f.tR, fy.tR), make_float2(f.pR, fy.pR), a.beta, a.inv_beta, Fp);
-            const float4 Fx = make_float4(Fp[0].x, Fp[1].x, Fp[2].x, Fp[3].x);
+            // (on the strip's first slope row, r = y0 - 1, neither face is
+            // needed: only its y slopes are, by the y-face above it)
             if (k >= y0 + 1) {
+                // ---- east x-face of row r (between columns c and c + 1) ----
+                const float4 &Wn = We;
+                const float4 Sn = shfl_down4(Sx, 1);
+                const float jump = ring->jx[s1][lane];
+                const float jy1 = ring->jy[s1][lane];   // below row r
+                // ---- and the y-face between rows r - 1 and r: both fluxes as one packed pair ----
+                FaceStates f, fy;
+                x_face_states(Wm1, Wn, Sx, Sn, jump, f);
+                y_face_states(Wm2, Wm1, Sym2, Sy, jy1, fy);
+                float2 Fp[4];
+                osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
+                                make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
+                                make_float2(f.tR, fy.tR), make_float2(f.pR, fy.pR), a.beta, a.inv_beta, Fp);
+                const float4 Fx = make_float4(Fp[0].x, Fp[1].x, Fp[2].x, Fp[3].x);
                 // the y-face's normal momentum is rho v
                 const float4 Fy = make_float4(Fp[0].y, Fp[2].y, Fp[1].y, Fp[3].y);
                 if (k >= y0 + 2) {
@@ -851,24 +889,24 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
                     // row k - 2 is a tank row, so its slot holds this column's records
-                    const float4 ue = ring->e[s2][lane], uq = ring->q[s2][lane];
+                    const float4 ue = ering(s2), uq = ring->q[s2][lane];
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
-                    if (out_lane)
-                        cell_update<false>(a, alpha, inv_dt, b0dt, stage == 1, dout, 0, (k - 2) * nx + c, Fw, Fxm2,
-                                           Fyp, Fy, hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq);
+                    cell_update<false>(a, alpha, inv_dt, b0dt, st1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp, Fy,
+                                       hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq, out_lane);
                 }
                 Fyp = Fy;
                 Jyp = jy1;
+                Fxm2 = Fx;
+                Jm2 = jump;
             }
-            Fxm2 = Fx;
-            Jm2 = jump;
             Sym2 = Sy;
         }
+        Dp = make_float4(W0.x - Wm1.x, W0.y - Wm1.y, W0.z - Wm1.z, 0.0f);
         Wm2 = Wm1;
         Wm1 = W0;
     }
     cp_async_wait_all();   // the copies past the strip's last row
-    if (stage == 1) {
+    if (st1) {
         // the strip's sums across lanes, in FP64
         double v0 = sq.lane_sum(0), v1 = sq.lane_sum(1), v2 = sq.lane_sum(2), v3 = sq.lane_sum(3);
 #pragma unroll
@@ -884,7 +922,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     }
 }
 
-template <int H, int WPC, int MINB>
+// SK: 1 for stage 1, 2 for the later stages (see mixed_strip).
+template <int H, int WPC, int MINB, int SK>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     pdl_trigger();
@@ -894,7 +933,7 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
     if (warp >= nstrips) return;   // whole warps only
     const int sy = warp / strips_x, sx = warp - sy * strips_x;
-    mixed_strip<H, 2>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
+    mixed_strip<H, 2, SK>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
                       reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5));
 }
 
