@@ -429,12 +429,15 @@ int launch_mixed(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
 template <int H, int WPC, int MINB>
 int launch_sweep(const MixedArgs &a, dim3 g, bool pdl, cudaStream_t s) {
     const int nstrips = (int)(g.x * g.y);
-    // stage 1 (residual sums; its input is Q^{m} itself) and the later stages are separate instances
+    // the default options have instances of their own for stage 1 (residual sums; its input is Q^{m}
+    // itself) and for the later stages; other options run the general instance
     const dim3 grid((nstrips + WPC - 1) / WPC), block(WPC * 32);
     const size_t smem = WPC * sizeof(StripRing);
-    const cudaError_t e = a.stage == 1
-                              ? launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB, 1>, grid, block, smem, s, a, (int)g.x, nstrips)
-                              : launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB, 2>, grid, block, smem, s, a, (int)g.x, nstrips);
+    const bool fast = a.limiter_k == 1 && a.realtime && a.local_dtau && a.alpha_pi_p_row;
+    const cudaError_t e =
+        !fast           ? launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB, 0>, grid, block, smem, s, a, (int)g.x, nstrips)
+        : a.stage == 1 ? launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB, 1>, grid, block, smem, s, a, (int)g.x, nstrips)
+                       : launch_pdl(pdl, sweep_kernel_mixed<H, WPC, MINB, 2>, grid, block, smem, s, a, (int)g.x, nstrips);
     return e == cudaSuccess ? AC_OK : AC_ERR_CUDA;
 }
 
@@ -639,6 +642,8 @@ struct MixedBackend : Backend {
         CK((allow_mixed_smem<32, 14, 448, 1, kOsher, false, true>()));
         CK((allow_mixed_smem<32, 14, 448, 1>()));
         // the 8-warp strip CTA holds 8 row rings (56 KB)
+        CK(cudaFuncSetAttribute(sweep_kernel_mixed<64, 8, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(8 * sizeof(StripRing))));
         CK(cudaFuncSetAttribute(sweep_kernel_mixed<64, 8, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(8 * sizeof(StripRing))));
         CK(cudaFuncSetAttribute(sweep_kernel_mixed<64, 8, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -90,8 +90,8 @@ batch_stage_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ 
 }
 
 // Column-strip form over the flattened strips of all tanks: warp w takes
-// strip w (see mixed_strip); CD as above; SK: 1 for stage 1, 2 for the
-// later stages.
+// strip w (see mixed_strip); CD as above; SK: 0 for any stage and options,
+// 1 and 2 for stage 1 and the later stages with the default options.
 template <int H, int WPC, int MINB, bool CD, int SK>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 batch_sweep_kernel(const BatchTank *__restrict__ tanks, const int *__restrict__ strip_tank, int nstrips, int stage,
@@ -268,24 +268,25 @@ cudaError_t allow_smem() {
 }
 
 // slot0 < 0: descriptors in global memory
-template <int H, int WPC, int MINB>
-cudaError_t launch_sweep(const BatchTank *tanks, const int *map, int nstrips, int stage, float alpha, int slot0,
-                         bool pdl, cudaStream_t s) {
+template <int H, int WPC, int MINB, int SK>
+cudaError_t launch_sweep_sk(const BatchTank *tanks, const int *map, int nstrips, int stage, float alpha, int slot0,
+                            bool pdl, cudaStream_t s) {
     const dim3 g((nstrips + WPC - 1) / WPC);
     const size_t smem = WPC * sizeof(StripRing);
     const dim3 b(WPC * 32);
-    if (stage == 1) {
-        if (slot0 >= 0)
-            return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true, 1>, g, b, smem, s, tanks, map, nstrips,
-                              stage, alpha, slot0);
-        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false, 1>, g, b, smem, s, tanks, map, nstrips, stage,
-                          alpha, 0);
-    }
     if (slot0 >= 0)
-        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true, 2>, g, b, smem, s, tanks, map, nstrips, stage,
+        return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, true, SK>, g, b, smem, s, tanks, map, nstrips, stage,
                           alpha, slot0);
-    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false, 2>, g, b, smem, s, tanks, map, nstrips, stage,
+    return launch_pdl(pdl, batch_sweep_kernel<H, WPC, MINB, false, SK>, g, b, smem, s, tanks, map, nstrips, stage,
                       alpha, 0);
+}
+// fast: the batch runs the default options (see mixed_strip)
+template <int H, int WPC, int MINB>
+cudaError_t launch_sweep(const BatchTank *tanks, const int *map, int nstrips, int stage, float alpha, int slot0,
+                         bool fast, bool pdl, cudaStream_t s) {
+    if (!fast) return launch_sweep_sk<H, WPC, MINB, 0>(tanks, map, nstrips, stage, alpha, slot0, pdl, s);
+    if (stage == 1) return launch_sweep_sk<H, WPC, MINB, 1>(tanks, map, nstrips, stage, alpha, slot0, pdl, s);
+    return launch_sweep_sk<H, WPC, MINB, 2>(tanks, map, nstrips, stage, alpha, slot0, pdl, s);
 }
 
 template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
@@ -412,21 +413,23 @@ struct StageLaunch {
     int ntiles, stage;
     float alpha;
     int slot0;
-    bool pdl;
+    bool fast, pdl;
     template <int TX, int TY, int NT, int RS = kOsher, bool BDF = false, bool PF = false>
     cudaError_t go(cudaStream_t s) const {
         return launch_stage<TX, TY, NT, RS, BDF, PF>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
     }
     template <int H, int MINB = 4>
     cudaError_t strips(cudaStream_t s) const {
-        return launch_sweep<H, 4, MINB>(tanks, map, ntiles, stage, alpha, slot0, pdl, s);
+        return launch_sweep<H, 4, MINB>(tanks, map, ntiles, stage, alpha, slot0, fast, pdl, s);
     }
 };
 
 int stage_launch(ac_batch *b, cudaStream_t s, int stage, int v) {
     cudaError_t e;
     const float alpha = float(1.0 / double(b->opt.rk_stages - stage + 1));   // alpha_s
-    const StageLaunch L{b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, b->pdl};
+    // the batch's tanks all use the pseudo-time step of their own cells
+    const bool fast = b->opt.limiter_k == 1 && b->opt.realtime && b->opt.alpha_pi_p_row;
+    const StageLaunch L{b->tanks_dev, b->tile_map, b->ntiles, stage, alpha, b->slot0, fast, b->pdl};
     // the Bassi and Roe fluxes are compiled for the first tile shape only
     if (b->opt.riemann == AC_RIEMANN_BASSI) e = L.go<32, 8, 256, kBassi, true>(s);
     else if (b->opt.riemann == AC_RIEMANN_ROE) e = L.go<32, 8, 256, kRoe, true>(s);

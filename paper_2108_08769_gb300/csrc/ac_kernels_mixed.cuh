@@ -251,8 +251,9 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // west, east, south and north faces; src.cell(cell, g, ...) gives dQ^{m},
 // dp^{m}, Q^n and rho_ref of the cell.  live = false: the arithmetic runs
 // (a halo lane of the column-strip sweep, on a real cell's values) but
-// nothing is stored or summed.
-template <bool BDF, typename Src, typename Sq>
+// nothing is stored or summed.  FAST: the default options (local pseudo-time
+// step, alpha_PI on the p row) are compiled in rather than read.
+template <bool BDF, bool FAST = false, typename Src, typename Sq>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, float b0dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
@@ -298,7 +299,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float b2 = fmaf(jn + js, a.nh_inv_dy, fmaf(r0 - rref, a.gy, -div2 - rt2));
     const float b3 = -div3;
     float dtau;
-    if (a.local_dtau) {
+    if (FAST || a.local_dtau) {
         const float ir = Ar<float>::rcp(r0);
         const float u = m0 * ir, v = n0 * ir, fb = 4.0f * a.beta * ir;
         const float u2 = u * u + fb, v2 = v * v + fb;
@@ -310,7 +311,7 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     }
     const float adt = alpha * dtau;
     const float coef = __fdividef(adt, fmaf(adt, b0dt, 1.0f));   // Eq. point_implicit
-    const float coef_p = a.alpha_pi_p_row ? coef : adt;
+    const float coef_p = (FAST || a.alpha_pi_p_row) ? coef : adt;
     if (live) dout[g] = make_float4(e0 + coef * b0, e1 + coef * b1, e2 + coef * b2, p0 + a.beta * coef_p * b3);
     if (stage1) {
         if (live) sq.add(b0, b1, b2, a.beta * b3);   // the p row in pressure units
@@ -738,13 +739,18 @@ struct HeldSrc {
 // the later uses of a row (its ring terms, reference density and level
 // jumps one row on, the update's records two rows on) read it back from
 // shared memory.  UNROLL: row-loop unrolling (2 lets the compiler keep the
-// rolling rows' registers in place instead of moving them each row).  SK: 1
-// compiles stage 1 only (its input Q^{s-1} is Q^{m}, so one record serves
-// both and the ring's e slots stay unused), 2 the later stages only (no
-// residual sums), 0 either, chosen by `stage`.
+// rolling rows' registers in place instead of moving them each row).  SK = 0
+// compiles any stage and any of the sweep's options, read at run time; SK =
+// 1 and 2 compile the default options (minmod limiter, real-time term,
+// local pseudo-time step, alpha_PI on the p row) in, for stage 1 (whose
+// input Q^{s-1} is Q^{m}, so one record serves both and the ring's e slots
+// stay unused) and for the later stages (no residual sums).  The first four
+// rows (y0 - 2 .. y0 + 1) run in a loop of their own, where part of the row's
+// work is not needed yet; the main loop then has no test of the row number.
 template <int H, int UNROLL = 1, int SK = 0>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial, StripRing *ring) {
+    constexpr bool FAST = SK != 0;
     const bool st1 = SK == 0 ? (stage == 1) : (SK == 1);
     const Ctl *ctl = a.ctl;
     const int lane = threadIdx.x & 31;
@@ -757,9 +763,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     const float4 *din = a.d[in];
     const float4 *d0 = a.d[cur];
     float4 *dout = a.d[out];
-    const float inv_dt = a.realtime ? float(ctl->inv_dt) : 0.0f;
+    const bool need_rt = FAST || a.realtime != 0;
+    const float inv_dt = need_rt ? float(ctl->inv_dt) : 0.0f;
     const float b0dt = a.B0 * inv_dt;
-    const bool need_rt = a.realtime != 0;
+    const int klim = FAST ? 1 : a.limiter_k;
     const bool per_x = (a.bc[0] == kPeriodic);
     // the column's source (ghost columns fold onto interior ones)
     int nfx, tfx;
@@ -818,8 +825,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
     SqKahan sq;
     stage_row(y0 - 2);
-#pragma unroll UNROLL
-    for (int k = y0 - 2; k <= y1 + 1; ++k) {
+    // row k of the sweep; with FIRST, one of the strip's first four rows
+    auto row = [&](int k, auto first) {
+        constexpr bool FIRST = decltype(first)::value;
         // prefetch: the next row's records; then row k's own copies have landed
         stage_row(k + 1);
         cp_async_wait_1();
@@ -837,7 +845,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             const float ir = Ar<float>::rcp(r);
             W0 = make_float4(r, mm * ir, nn * ir, d.w);
         }
-        if (k >= y0) {
+        if (!FIRST || k >= y0) {
             // ---- slopes and pressure gradient of row r = k-1 ----
             const int r = k - 1;
             // differences of rho, u, v across the east face (the west one is
@@ -849,7 +857,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                         wxv = __shfl_up_sync(0xffffffffu, exv, 1);
             float hrx, hry, hux, huy, hvx, hvy;
             limit_diffs(exr, wxr, W0.x - Wm1.x, Dp.x, exu, wxu, W0.y - Wm1.y, Dp.y, exv, wxv, W0.z - Wm1.z, Dp.z,
-                        a.limiter_k, float(a.limiter_k), hrx, hry, hux, huy, hvx, hvy);
+                        klim, float(klim), hrx, hry, hux, huy, hvx, hvy);
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
                 const float4 e1 = ering(s1);
@@ -867,7 +875,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
             // (on the strip's first slope row, r = y0 - 1, neither face is
             // needed: only its y slopes are, by the y-face above it)
-            if (k >= y0 + 1) {
+            if (!FIRST || k >= y0 + 1) {
                 // ---- east x-face of row r (between columns c and c + 1) ----
                 const float4 &Wn = We;
                 const float4 Sn = shfl_down4(Sx, 1);
@@ -884,15 +892,15 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 const float4 Fx = make_float4(Fp[0].x, Fp[1].x, Fp[2].x, Fp[3].x);
                 // the y-face's normal momentum is rho v
                 const float4 Fy = make_float4(Fp[0].y, Fp[2].y, Fp[1].y, Fp[3].y);
-                if (k >= y0 + 2) {
+                if (!FIRST || k >= y0 + 2) {
                     // ---- update of row k - 2 ----
                     const float4 Fw = shfl_up4(Fxm2, 1);
                     const float jw = __shfl_up_sync(0xffffffffu, Jm2, 1);
                     // row k - 2 is a tank row, so its slot holds this column's records
                     const float4 ue = ering(s2), uq = ring->q[s2][lane];
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
-                    cell_update<false>(a, alpha, inv_dt, b0dt, st1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp, Fy,
-                                       hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq, out_lane);
+                    cell_update<false, FAST>(a, alpha, inv_dt, b0dt, st1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
+                                             Fy, hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq, out_lane);
                 }
                 Fyp = Fy;
                 Jyp = jy1;
@@ -904,7 +912,12 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         Dp = make_float4(W0.x - Wm1.x, W0.y - Wm1.y, W0.z - Wm1.z, 0.0f);
         Wm2 = Wm1;
         Wm1 = W0;
-    }
+    };
+    int k = y0 - 2;
+#pragma unroll 1
+    for (; k < y0 + 2; ++k) row(k, std::true_type{});
+#pragma unroll UNROLL
+    for (; k <= y1 + 1; ++k) row(k, std::false_type{});
     cp_async_wait_all();   // the copies past the strip's last row
     if (st1) {
         // the strip's sums across lanes, in FP64
@@ -922,7 +935,10 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     }
 }
 
-// SK: 1 for stage 1, 2 for the later stages (see mixed_strip).
+// SK: 0 for any stage and options, 1 and 2 for stage 1 and the later stages
+// with the default options (see mixed_strip); the general form unrolls its
+// row loop by 2, the default-option forms by 1 (unrolled, their stage-1
+// instance spills).
 template <int H, int WPC, int MINB, int SK>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
@@ -933,7 +949,7 @@ sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
     const int warp = blockIdx.x * WPC + (threadIdx.x >> 5);
     if (warp >= nstrips) return;   // whole warps only
     const int sy = warp / strips_x, sx = warp - sy * strips_x;
-    mixed_strip<H, 2, SK>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
+    mixed_strip<H, SK == 0 ? 2 : 1, SK>(a, a.stage, a.alpha, sx, sy, a.partials + (size_t)warp * 4,
                       reinterpret_cast<StripRing *>(strip_smem) + (threadIdx.x >> 5));
 }
 
