@@ -746,7 +746,9 @@ struct HeldSrc {
 // input Q^{s-1} is Q^{m}, so one record serves both and the ring's e slots
 // stay unused) and for the later stages (no residual sums).  The first four
 // rows (y0 - 2 .. y0 + 1) run in a loop of their own, where part of the row's
-// work is not needed yet; the main loop then has no test of the row number.
+// work is not needed yet, and so do the rows near the tank's top, whose
+// windows reach ghost rows; the main loop then tests neither the row number
+// nor the fold of ghost rows.
 template <int H, int UNROLL = 1, int SK = 0>
 __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float alpha, int sx, int sy,
                                             double *partial, StripRing *ring) {
@@ -787,28 +789,31 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     const int colbits = (nfx & 1) | ((tfx & 1) << 1) |
                         (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
                         (is_wall(a.bc[2]) ? 8 : 0) | (is_wall(a.bc[3]) ? 16 : 0);
-    // fold bits of row k in this column (ghost rows fold onto tank rows)
-    auto row_flags = [&](int k) {
-        if (k >= 0 && k < ny) return colbits & 3;   // the same for the whole warp
+    // fold bits of row k in this column (ghost rows fold onto tank rows); the
+    // edge flag (a std::bool_constant) is false where k is known to be a tank row
+    auto row_flags = [&](int k, auto edge) {
+        if (!decltype(edge)::value || (k >= 0 && k < ny)) return colbits & 3;   // the same for the whole warp
         int nfy, tfy;
         fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
         return ((nfx + tfy) & 1) | (((nfy + tfx) & 1) << 1);
     };
-    // copies of row k's records into ring slot k & 3, as one group
-    auto stage_row = [&](int k) {
+    // copies of row k's records into ring slot k & 3, as one group (edge as
+    // above)
+    auto stage_row = [&](int k, auto edge) {
+        constexpr bool E = decltype(edge)::value;
         int nfy, tfy;
-        const int srow = (k >= 0 && k < ny) ? k : fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
+        const int srow = (!E || (k >= 0 && k < ny)) ? k : fold_axis(k, ny, a.bc[2], a.bc[3], nfy, tfy);
         const int s = srow * nx + scol, sl = k & 3;
         cp_async16(&ring->q[sl][lane], a.qn + s);
         cp_async16(&ring->d[sl][lane], din + s);
         if (SK != 1) cp_async16(&ring->e[sl][lane], d0 + s);
-        if (k >= 0 && k < ny && jcol >= 0)
+        if ((!E || (k >= 0 && k < ny)) && jcol >= 0)
             cp_async4(&ring->jx[sl][lane], &a.jmp[k * nx + jcol].x);
         else
             ring->jx[sl][lane] = 0.0f;
         // row ny: the north face of the top row (periodic: the south face of row 0)
-        if (own_col && k >= 0 && (k < ny || (k == ny && per_y)))
-            cp_async4(&ring->jy[sl][lane], &a.jmp[(k < ny ? k : 0) * nx + c].y);
+        if (own_col && (!E || (k >= 0 && (k < ny || (k == ny && per_y)))))
+            cp_async4(&ring->jy[sl][lane], &a.jmp[((!E || k < ny) ? k : 0) * nx + c].y);
         else
             ring->jy[sl][lane] = 0.0f;
         cp_async_commit();
@@ -824,19 +829,20 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     float Jm2 = 0.0f;                                        // east x-face level jump of row k-2
     float Jyp = 0.0f;                                        // level jump of the y-face below row k-2
     SqKahan sq;
-    stage_row(y0 - 2);
-    // row k of the sweep; with FIRST, one of the strip's first four rows
-    auto row = [&](int k, auto first) {
-        constexpr bool FIRST = decltype(first)::value;
+    stage_row(y0 - 2, std::true_type{});
+    // row k of the sweep; first: one of the strip's first four rows; edge:
+    // rows k - 2 .. k + 1 may include ghost rows
+    auto row = [&](int k, auto first, auto edge) {
+        constexpr bool FIRST = decltype(first)::value, EDGE = decltype(edge)::value;
         // prefetch: the next row's records; then row k's own copies have landed
-        stage_row(k + 1);
+        stage_row(k + 1, edge);
         cp_async_wait_1();
         const int sk = k & 3, s1 = (k - 1) & 3, s2 = (k - 2) & 3;
         // ---- W = (rho, u, v, dp) of Q^{s-1} at row k ----
         float4 W0;
         {
             const float4 q = ring->q[sk][lane], d = ring->d[sk][lane];
-            const int fl = row_flags(k);
+            const int fl = row_flags(k, edge);
             const float r = q.x + d.x;
             float mm = q.y + d.y;
             float nn = q.z + d.z;
@@ -861,14 +867,15 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
             float rx = 0.0f, ry = 0.0f;
             if (need_rt) {
                 const float4 e1 = ering(s1);
-                const int fl = row_flags(r);
+                const int fl = row_flags(r, edge);
                 rx = b0dt * e1.y;
                 ry = b0dt * e1.z;
                 rx = (fl & 1) ? -rx : rx;
                 ry = (fl & 2) ? -ry : ry;
             }
             // gravity reversed in wall ghosts (as wall_ghost_sign)
-            const bool wall_ghost = (colbits & 4) || (r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16));
+            const bool wall_ghost =
+                (colbits & 4) || (EDGE && ((r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16))));
             const float sg = wall_ghost ? -1.0f : 1.0f;
             float hpx, hpy;
             new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, ring->q[s1][lane].w, sg, hpx, hpy);
@@ -913,11 +920,16 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         Wm2 = Wm1;
         Wm1 = W0;
     };
+    // the strip's first four rows, the rows whose window holds tank rows only
+    // (row k + 1 is copied ahead, so k <= ny - 2), and the top strip's last rows
     int k = y0 - 2;
 #pragma unroll 1
-    for (; k < y0 + 2; ++k) row(k, std::true_type{});
+    for (; k < y0 + 2; ++k) row(k, std::true_type{}, std::true_type{});
+    const int kin = min(y1 + 1, ny - 2);
 #pragma unroll UNROLL
-    for (; k <= y1 + 1; ++k) row(k, std::false_type{});
+    for (; k <= kin; ++k) row(k, std::false_type{}, std::false_type{});
+#pragma unroll 1
+    for (; k <= y1 + 1; ++k) row(k, std::false_type{}, std::true_type{});
     cp_async_wait_all();   // the copies past the strip's last row
     if (st1) {
         // the strip's sums across lanes, in FP64
