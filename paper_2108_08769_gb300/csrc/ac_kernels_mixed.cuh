@@ -717,6 +717,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// The same 4-byte copy of n = 4 or 0 source bytes (0: the slot is filled with
+// zero; the source address must still be valid).
+__device__ __forceinline__ void cp_async4_zf(void *smem, const float *gmem, unsigned n) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // all but the most recent group of this thread's copies have landed
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -785,6 +791,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     const int gi = c + 1;   // the east x-face's column
     const int jcol = (gi >= 0 && gi < nx) ? gi : ((gi == nx && per_x) ? 0 : -1);
     const bool own_col = c >= 0 && c < nx;   // the south y-face of this column is the tank's
+    // a tank row's jump copies: source columns (clamped into the tank) and byte counts
+    const int jxc = jcol >= 0 ? jcol : 0, jyc = own_col ? c : 0;
+    const unsigned jxn = jcol >= 0 ? 4u : 0u, jyn = own_col ? 4u : 0u;
     const bool per_y = (a.bc[2] == kPeriodic);
     const int colbits = (nfx & 1) | ((tfx & 1) << 1) |
                         (((c < 0 && is_wall(a.bc[0])) || (c >= nx && is_wall(a.bc[1]))) ? 4 : 0) |
@@ -807,15 +816,22 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         cp_async16(&ring->q[sl][lane], a.qn + s);
         cp_async16(&ring->d[sl][lane], din + s);
         if (SK != 1) cp_async16(&ring->e[sl][lane], d0 + s);
-        if ((!E || (k >= 0 && k < ny)) && jcol >= 0)
-            cp_async4(&ring->jx[sl][lane], &a.jmp[k * nx + jcol].x);
-        else
-            ring->jx[sl][lane] = 0.0f;
-        // row ny: the north face of the top row (periodic: the south face of row 0)
-        if (own_col && (!E || (k >= 0 && (k < ny || (k == ny && per_y)))))
-            cp_async4(&ring->jy[sl][lane], &a.jmp[((!E || k < ny) ? k : 0) * nx + c].y);
-        else
-            ring->jy[sl][lane] = 0.0f;
+        if (!E) {
+            // a tank row: whether its faces are the tank's depends on the lane
+            // only, so every lane copies (a zero where the face is not the tank's)
+            cp_async4_zf(&ring->jx[sl][lane], &a.jmp[k * nx + jxc].x, jxn);
+            cp_async4_zf(&ring->jy[sl][lane], &a.jmp[k * nx + jyc].y, jyn);
+        } else {
+            if (k >= 0 && k < ny && jcol >= 0)
+                cp_async4(&ring->jx[sl][lane], &a.jmp[k * nx + jcol].x);
+            else
+                ring->jx[sl][lane] = 0.0f;
+            // row ny: the north face of the top row (periodic: the south face of row 0)
+            if (own_col && k >= 0 && (k < ny || (k == ny && per_y)))
+                cp_async4(&ring->jy[sl][lane], &a.jmp[(k < ny ? k : 0) * nx + c].y);
+            else
+                ring->jy[sl][lane] = 0.0f;
+        }
         cp_async_commit();
     };
 
