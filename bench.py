@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", default="hydrostatic_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048x8192 mixed-form leg")
+    ap.add_argument("--no-checks", action="store_true",
+                    help="skip the configurations' own checks (GPU against GPU, outside the timed region)")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the benchmark line: one line per test configuration at its stated length "
                          "(FP64, mixed, errors, the configuration's own checks)")
@@ -440,6 +442,9 @@ def run_ours(args, ws, rank, local):
     batched = None
     if not args.no_large:
         batched = run_batched(args, stream, flush, barrier)
+    checks = None
+    if not args.no_checks and rank == 0:
+        checks = run_checks(stream)
 
     if rank != 0:
         return
@@ -457,6 +462,8 @@ def run_ours(args, ws, rank, local):
         line["mixed_large"] = large
     if batched is not None:
         line["batched"] = batched
+    if checks is not None:
+        line["checks"] = checks
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline_sample(case)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
@@ -464,6 +471,65 @@ def run_ours(args, ws, rank, local):
 
 
 BATCH_ABS_TOL = (0.03, 0.3, 0.3, 100.0)
+
+
+def run_checks(stream):
+    """The single-tank configurations' own checks, GPU against GPU, after the
+    timed legs: the hydrostatic tank 256x256 at its stated 100 physical steps in
+    both forms (at rest to 1e-10 m/s, the pressure kink held: slope ratio water
+    / air = 1000); the collapsing water column 1024x512 while it moves, mixed
+    against FP64 after 10 physical steps of 100 pseudo-iterations, every field
+    and momentum component against its own maximum (the regime where the
+    pressure increment is largest); and the Riemann tank 200x4 at its stated 20
+    physical steps, mixed against FP64.  The stopping test is on (1e-8 drop or
+    500 pseudo-iterations) except for the fixed-length water column."""
+    import numpy as np
+    from paper_2108_08769_gb300 import ac, workloads as W
+
+    def run(case, prec, steps, tol, iters):
+        t = ac.Tank.from_case(case, precision=prec)
+        t.set_stream(stream.cuda_stream)
+        its = []
+        for _ in range(steps):
+            its.append(t.physical_step(case.dt, tol, iters)[1])
+        state = t.get_state()
+        t.close()
+        return state, {"pseudo_iters_min": min(its), "pseudo_iters_max": max(its)}
+
+    def max_velocity(q):
+        return float(max(np.abs(q[1] / q[0]).max(), np.abs(q[2] / q[0]).max()))
+
+    t0 = time.perf_counter()
+    out = {}
+    hc = W.hydrostatic_tank(256)
+    f64, f_it = run(hc, "fp64", hc.steps, hc.tol, hc.max_iters)
+    mx, m_it = run(hc, "mixed", hc.steps, hc.tol, hc.max_iters)
+    col = f64[3][:, hc.nx // 2]
+    sl = np.diff(col) / hc.dy
+    out["hydrostatic_256_100_steps"] = {
+        "fp64": {"max_velocity": max_velocity(f64), "kink_slope_ratio": float(sl[hc.ny // 4] / sl[3 * hc.ny // 4]),
+                 **f_it},
+        "mixed": {"max_velocity": max_velocity(mx), **m_it, "error_vs_fp64": field_errors(mx, f64)},
+        "pass": bool(max_velocity(f64) < 1e-10 and max_velocity(mx) < 1e-10
+                     and abs(sl[hc.ny // 4] / sl[3 * hc.ny // 4] - 1000.0) < 1e-6)}
+    wc = W.water_column(1024, 512)
+    f64, _ = run(wc, "fp64", 10, -1.0, 100)
+    mx, _ = run(wc, "mixed", 10, -1.0, 100)
+    err = field_errors(mx, f64)
+    out["water_column_1024x512_10x100"] = {
+        "max_velocity_fp64": max_velocity(f64), "error_vs_fp64": err,
+        "pass": bool(max(err["rho_unfloored"], err["rhou_unfloored"], err["rhov_unfloored"], err["p_unfloored"])
+                     <= 1e-5)}
+    rc = W.riemann_tank()
+    f64, f_it = run(rc, "fp64", rc.steps, rc.tol, rc.max_iters)
+    mx, m_it = run(rc, "mixed", rc.steps, rc.tol, rc.max_iters)
+    err = field_errors(mx, f64)
+    out["riemann_200x4_20_steps"] = {"fp64": f_it, "mixed": {**m_it, "error_vs_fp64": err},
+                                     "pass": bool(max(err["rho"], err["rhou"], err["rhov"], err["p"]) <= 1e-5)}
+    out["wall_s"] = time.perf_counter() - t0
+    out["note"] = ("FP64 against the FP64 oracle (1e-11 per physical step) and the Riemann tank against the exact "
+                   "solution are the GPU tests' (tests/test_gpu_configs.py, tests/test_gpu_riemann.py)")
+    return out
 
 
 def run_batched(args, stream, flush, barrier):
@@ -579,7 +645,8 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.8 + 2 * 75.4) / 3, (465.9 + 2 * 444.9) / 3),   # sweep_kernel_mixed<64,4>
+    16: ((57.8 + 2 * 75.4) / 3, (464.5 + 2 * 437.6) / 3),   # sweep_kernel_mixed<64,4,4,1>, <64,4,4,2>
+    17: ((56.3 + 2 * 73.3) / 3, (460.9 + 2 * 434.1) / 3),   # sweep_kernel_mixed<128,4,4,1>, <128,4,4,2>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
@@ -596,13 +663,14 @@ def run_configs(args, rank, local):
     in both forms, one JSON line each: throughput (CUDA events around every
     physical step, the stopping test on: 1e-8 residual drop or 500
     pseudo-iterations), the HBM fraction from the algorithmic bytes, per-field
-    relative L-inf and L1 errors (mixed against FP64; for the Riemann tank
-    both against the FP64 oracle), the configuration's own checks, and the
-    clocks seen.  The Rayleigh-Taylor tank runs --config4-steps of its 200
-    physical steps (the FP64 form alone takes ~23 s per step there)."""
+    relative L-inf and L1 errors of the mixed form against FP64, the
+    configuration's own checks, and the clocks seen.  The Rayleigh-Taylor tank
+    runs --config4-steps of its 200 physical steps (the FP64 form alone takes
+    ~23 s per step there).  The Riemann tank against the FP64 oracle over its
+    20 steps and against the exact solution are GPU tests
+    (tests/test_gpu_configs.py, tests/test_gpu_riemann.py)."""
     import numpy as np
     import torch
-    import oracle
     from paper_2108_08769_gb300 import ac, workloads as W
     if rank != 0:
         return
@@ -610,7 +678,6 @@ def run_configs(args, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    oracle.build()
 
     def run(case, prec, steps):
         t = ac.Tank.from_case(case, precision=prec)
@@ -650,43 +717,6 @@ def run_configs(args, rank, local):
         mixed, line["mixed"] = run(case, "mixed", steps)
         line["mixed"]["speedup_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
         line["mixed"]["error_vs_fp64_gpu"] = field_errors(mixed, f64)
-        if name == "riemann_200x4":
-            # the FP64 oracle over the same 20 physical steps, field by field
-            st = case.state()
-            t0 = time.perf_counter()
-            oits = []
-            for _ in range(steps):
-                st, _, n, _, _ = oracle.physical_step(case, st)
-                oits.append(n)
-            line["oracle_1_core"] = {"value": case.cells * sum(oits) / (time.perf_counter() - t0), "unit": UNIT,
-                                     "pseudo_iters_total": sum(oits)}
-            line["fp64"]["error_vs_oracle"] = field_errors(f64, st)
-            line["mixed"]["error_vs_oracle"] = field_errors(mixed, st)
-            # Sec. 2.4.1's wave relations: the same tank in pure pseudo-time
-            # (real-time term off, global pseudo-time step, minmod on p as in
-            # Sec. 3.1) to tau = 1e-3 s, before the fastest wave (~316 m/s in
-            # the air) reaches the ends, against the exact solution at x/tau
-            rel = {}
-            for prec in ("fp64", "mixed"):
-                rp = W.riemann_tank()
-                rp.options.realtime, rp.options.local_dtau, rp.options.gradp = False, False, "minmod"
-                tau = 1e-3
-                t = ac.Tank.from_case(rp, precision=prec)
-                rc, n = t.pseudo_time_run(tau)
-                q = t.get_state()
-                t.close()
-                xs = (np.arange(rp.nx) + 0.5) * (rp.lx / rp.nx) - 0.5
-                ex = np.array([oracle.bassi_sample([1000.0, 0.0, 0.0, 1e5], [1.0, 0.0, 0.0, 0.0], rp.beta, x / tau)
-                               for x in xs])
-                sc = np.abs(ex).max(axis=0)
-                rel[prec] = {"pseudo_iters": n,
-                             "l1_rel_rho": float(np.abs(q[0][0] - ex[:, 0]).mean() / sc[0]),
-                             "l1_rel_u": float(np.abs(q[1][0] / q[0][0] - ex[:, 1]).mean() / sc[1]),
-                             "l1_rel_p": float(np.abs(q[3][0] - ex[:, 3]).mean() / sc[3])}
-            rel["exact_star_state"] = dict(zip(("S_L", "S_R", "u_star", "p_star", "rho_star_L", "rho_star_R"),
-                                               [float(v) for v in oracle.bassi_star(
-                                                   [1000.0, 0.0, 0.0, 1e5], [1.0, 0.0, 0.0, 0.0], rp.beta)]))
-            line["riemann_relations_tau_1e-3"] = rel
         if name == "hydrostatic_256":
             # at rest to 1e-10, the pressure kink held: slope ratio water/air = density ratio
             u = np.abs(f64[1] / f64[0]).max()
