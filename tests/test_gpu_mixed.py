@@ -274,3 +274,34 @@ def test_strip_sweep_options_against_oracle(monkeypatch, opts, v):
     got = t.get_state()
     t.close()
     check(got, oracle_run(case, iters=6))
+
+
+EDGE_GRIDS = [(61, 83, ("slip", "slip", "periodic", "periodic"), 0.0),
+              (45, 70, ("periodic", "periodic", "slip", "noslip"), -9.81),
+              (29, 3, ("slip", "noslip", "slip", "slip"), -9.81),
+              (33, 1, ("transmissive", "slip", "slip", "slip"), -9.81),
+              (2, 2, ("slip", "slip", "slip", "slip"), -9.81)]
+
+
+@pytest.mark.parametrize("v", [15, 16], ids=["strips_32", "strips_64"])
+@pytest.mark.parametrize("grid", EDGE_GRIDS, ids=["61x83_periodic_y", "45x70_walls_y", "29x3", "33x1", "2x2"])
+@pytest.mark.parametrize("opts", [dict(), dict(limiter_k=2)], ids=["default_options", "limiter_k=2"])
+def test_strip_sweep_edge_rows_against_oracle(monkeypatch, v, grid, opts):
+    """The column-strip sweep's three row loops (a strip's first four rows,
+    the rows whose window holds tank rows only, the top strip's last rows) on
+    grids where they meet the tank's edges: periodic y (ghost rows fold onto
+    the other end, the top face's jump is the bottom one's), a ragged top
+    strip (70 rows in 32-row strips), and tanks of 3, 1 and 2 rows, where the
+    main loop has no row at all; with the default options (the instances that
+    compile them in) and with another limiter (the general instance)."""
+    nx, ny, bc, gy = grid
+    monkeypatch.setenv("AC_TILE", str(v))
+    case = W.random_two_fluid(nx, ny, ratio=300.0, c0=10.0, bc=bc, gy=gy)
+    for name, value in opts.items():
+        setattr(case.options, name, value)
+    t = ac.Tank.from_case(case, precision="mixed")
+    t.physical_step(case.dt, -1.0, 6)
+    assert t.tile_shape()[3] == v
+    got = t.get_state()
+    t.close()
+    check(got, oracle_run(case, iters=6))
