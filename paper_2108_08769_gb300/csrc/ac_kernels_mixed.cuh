@@ -182,20 +182,29 @@ __device__ __forceinline__ void limit_slopes(const float4 &c, const float4 &e, c
     }
 }
 
-// The same limiter from the differences themselves: east/west along x,
-// north/south along y (the column-strip sweep forms each difference once and
-// passes it on to the neighbour that needs it as its other side).
+// minmod(a, b) as the median of a, b and 0: zero where the signs differ,
+// else the argument of smaller magnitude; min and max only (the ALU pipe, not
+// the FMA pipe).
+__device__ __forceinline__ float minmod_median(float a, float b) {
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+}
+
+// The column-strip sweep's limiter on whole slopes (the face states take
+// half of a slope in one FMA; halving is exact, so the states equal those
+// from half slopes), from the differences themselves: east/west along x,
+// north/south along y (the sweep forms each difference once and passes it on
+// to the neighbour that needs it as its other side).
 __device__ __forceinline__ void limit_diffs(float er, float wr, float nr, float sr, float eu, float wu, float nu,
                                             float su, float ev, float wv, float nv, float sv, int k, float klim,
-                                            float &hrx, float &hry, float &hux, float &huy, float &hvx, float &hvy) {
+                                            float &srx, float &sry, float &sux, float &suy, float &svx, float &svy) {
     if (k == 1) {
-        hrx = half_minmod(er, wr); hry = half_minmod(nr, sr);
-        hux = half_minmod(eu, wu); huy = half_minmod(nu, su);
-        hvx = half_minmod(ev, wv); hvy = half_minmod(nv, sv);
+        srx = minmod_median(er, wr); sry = minmod_median(nr, sr);
+        sux = minmod_median(eu, wu); suy = minmod_median(nu, su);
+        svx = minmod_median(ev, wv); svy = minmod_median(nv, sv);
     } else {
-        hrx = 0.5f * limiter(er, wr, klim); hry = 0.5f * limiter(nr, sr, klim);
-        hux = 0.5f * limiter(eu, wu, klim); huy = 0.5f * limiter(nu, su, klim);
-        hvx = 0.5f * limiter(ev, wv, klim); hvy = 0.5f * limiter(nv, sv, klim);
+        srx = limiter(er, wr, klim); sry = limiter(nr, sr, klim);
+        sux = limiter(eu, wu, klim); suy = limiter(nu, su, klim);
+        svx = limiter(ev, wv, klim); svy = limiter(nv, sv, klim);
     }
 }
 
@@ -219,6 +228,19 @@ __device__ __forceinline__ void new_gradp_half_slopes(const MixedArgs &a, const 
           a.dy_over_dx * (uv * hrx + rv * hux + ru * hvx) + a.half_dy * (rho - rref) * a.gy * sg;
 }
 
+// The same, whole slope of p - p_ref (twice the above, exactly: every term is
+// scaled by 2, with dx = 2 half_dx), from whole slopes of rho, u, v.
+__device__ __forceinline__ void new_gradp_whole_slopes(const MixedArgs &a, const float4 &Wc, float srx, float sry,
+                                                       float sux, float suy, float svx, float svy, float rtx,
+                                                       float rty, float rref, float sg, float &spx, float &spy) {
+    const float rho = Wc.x, u = Wc.y, v = Wc.z;
+    const float ru = rho * u, rv = rho * v, uv = u * v;
+    spx = -a.dx * rtx - (u * u * srx + 2.0f * ru * sux) -
+          a.dx_over_dy * (uv * sry + ru * svy + rv * suy) + a.dx * rho * a.gx * sg;
+    spy = -a.dy * rty - (v * v * sry + 2.0f * rv * svy) -
+          a.dy_over_dx * (uv * srx + rv * sux + ru * svx) + a.dy * (rho - rref) * a.gy * sg;
+}
+
 // Face states between cells A (left/below) and B with half slopes SA, SB
 // along the face normal: density, normal and tangential velocity (rotation,
 // Alg. 2: (u, v) on x-faces, (v, u) on y-faces), pressure relative to the
@@ -236,6 +258,22 @@ __device__ __forceinline__ void y_face_states(const float4 &A, const float4 &B, 
     f.rL = A.x + SA.x; f.nL = A.z + SA.z; f.tL = A.y + SA.y; f.pL = A.w + SA.w - 0.5f * jump;
     f.rR = B.x - SB.x; f.nR = B.z - SB.z; f.tR = B.y - SB.y; f.pR = B.w - SB.w + 0.5f * jump;
 }
+// The same from whole slopes SA, SB (half of each taken in one FMA).
+__device__ __forceinline__ void x_face_states_whole(const float4 &A, const float4 &B, const float4 &SA,
+                                                    const float4 &SB, float jump, FaceStates &f) {
+    f.rL = fmaf(0.5f, SA.x, A.x); f.nL = fmaf(0.5f, SA.y, A.y); f.tL = fmaf(0.5f, SA.z, A.z);
+    f.pL = fmaf(0.5f, SA.w, A.w) - 0.5f * jump;
+    f.rR = fmaf(-0.5f, SB.x, B.x); f.nR = fmaf(-0.5f, SB.y, B.y); f.tR = fmaf(-0.5f, SB.z, B.z);
+    f.pR = fmaf(-0.5f, SB.w, B.w) + 0.5f * jump;
+}
+__device__ __forceinline__ void y_face_states_whole(const float4 &A, const float4 &B, const float4 &SA,
+                                                    const float4 &SB, float jump, FaceStates &f) {
+    f.rL = fmaf(0.5f, SA.x, A.x); f.nL = fmaf(0.5f, SA.z, A.z); f.tL = fmaf(0.5f, SA.y, A.y);
+    f.pL = fmaf(0.5f, SA.w, A.w) - 0.5f * jump;
+    f.rR = fmaf(-0.5f, SB.x, B.x); f.nR = fmaf(-0.5f, SB.z, B.z); f.tR = fmaf(-0.5f, SB.y, B.y);
+    f.pR = fmaf(-0.5f, SB.w, B.w) + 0.5f * jump;
+}
+
 // The face flux from its states: (mass, x-momentum, y-momentum, p/beta).
 template <int RS>
 __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const FaceStates &f) {
@@ -839,7 +877,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
     auto ering = [&](int sl) -> float4 { return SK == 1 ? ring->d[sl][lane] : ring->e[sl][lane]; };
     float4 Wm2 = make_float4(0.f, 0.f, 0.f, 0.f), Wm1 = Wm2;   // W at rows k-2, k-1
     float4 Dp = Wm2;                                         // W(k-1) - W(k-2) (rho, u, v)
-    float4 Sym2 = Wm2;                                       // y half slopes of row k-2
+    float4 Sym2 = Wm2;                                       // whole y slopes of row k-2
     float4 Fxm2 = Wm2;                                       // east x-face flux of row k-2
     float4 Fyp = Wm2;                                        // y-face flux between rows k-3 and k-2
     float Jm2 = 0.0f;                                        // east x-face level jump of row k-2
@@ -894,7 +932,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 (colbits & 4) || (EDGE && ((r < 0 && (colbits & 8)) || (r >= ny && (colbits & 16))));
             const float sg = wall_ghost ? -1.0f : 1.0f;
             float hpx, hpy;
-            new_gradp_half_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, ring->q[s1][lane].w, sg, hpx, hpy);
+            new_gradp_whole_slopes(a, Wm1, hrx, hry, hux, huy, hvx, hvy, rx, ry, ring->q[s1][lane].w, sg, hpx, hpy);
             const float4 Sx = make_float4(hrx, hux, hvx, hpx), Sy = make_float4(hry, huy, hvy, hpy);
             // (on the strip's first slope row, r = y0 - 1, neither face is
             // needed: only its y slopes are, by the y-face above it)
@@ -906,8 +944,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                 const float jy1 = ring->jy[s1][lane];   // below row r
                 // ---- and the y-face between rows r - 1 and r: both fluxes as one packed pair ----
                 FaceStates f, fy;
-                x_face_states(Wm1, Wn, Sx, Sn, jump, f);
-                y_face_states(Wm2, Wm1, Sym2, Sy, jy1, fy);
+                x_face_states_whole(Wm1, Wn, Sx, Sn, jump, f);
+                y_face_states_whole(Wm2, Wm1, Sym2, Sy, jy1, fy);
                 float2 Fp[4];
                 osher_flux_pair(make_float2(f.rL, fy.rL), make_float2(f.nL, fy.nL), make_float2(f.tL, fy.tL),
                                 make_float2(f.pL, fy.pL), make_float2(f.rR, fy.rR), make_float2(f.nR, fy.nR),
