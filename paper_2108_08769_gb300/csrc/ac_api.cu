@@ -458,6 +458,7 @@ struct MixedBackend : Backend {
     float4 *d[3] = {};   // per cell (dQ of rho, rho u, rho v; dp or p), three rotating buffers
     float4 *qn = nullptr;  // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
     float2 *jmp = nullptr;   // per cell level jumps (west face, south face)
+    float *dtau = nullptr;   // per cell local pseudo-time step (column-strip sweep, default options)
     float *lev_p = nullptr;
     float *D1[3] = {}, *D2[3] = {};   // Q^n - Q^{n-1}, Q^n - Q^{n-2} (BDF2, BDF3)
     double *q64[4] = {};   // FP64 levels of rho, rho u, rho v, p
@@ -597,7 +598,7 @@ struct MixedBackend : Backend {
         for (int f = 0; f < 4; ++f) a.q64[f] = q64[f];
         a.p64_step = p64_step;
         a.pref64 = pref64;
-        a.jmp = jmp; a.lev_p = lev_p;
+        a.jmp = jmp; a.lev_p = lev_p; a.dtau = dtau;
         for (int f = 0; f < 3; ++f) { a.D1[f] = D1[f]; a.D2[f] = D2[f]; }
         a.order = c->order_now;
         a.B0 = float(kBDF[c->order_now][0]);
@@ -620,6 +621,7 @@ struct MixedBackend : Backend {
         if (use_ref) CK(cudaMalloc(&pref64, db));
         CK(cudaMalloc(&jmp, c->N * sizeof(float2)));
         CK(cudaMalloc(&lev_p, fb));
+        CK(cudaMalloc(&dtau, fb));
         for (int f = 0; f < 3; ++f) {
             if (c->opt.bdf_order >= 2) CK(cudaMalloc(&D1[f], fb));
             if (c->opt.bdf_order >= 3) CK(cudaMalloc(&D2[f], fb));
@@ -663,6 +665,7 @@ struct MixedBackend : Backend {
         cudaFree(pref64);
         cudaFree(jmp);
         cudaFree(lev_p);
+        cudaFree(dtau);
         for (int f = 0; f < 3; ++f) { cudaFree(D1[f]); cudaFree(D2[f]); }
     }
     int set_state(ac_ctx *c, const double *const f[4]) override {

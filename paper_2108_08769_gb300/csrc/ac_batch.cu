@@ -340,6 +340,7 @@ struct ac_batch {
     float4 *qn;                         // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
     float2 *jmp;                        // per cell level jumps (west face, south face)
     float *lev_p;                       // restore copy of p (without a level)
+    float *dtau;                        // local pseudo-time steps (column-strip sweep, default options)
     float *D1[3], *D2[3];               // BDF2/BDF3 level differences (pools)
     double *q64[4];                     // FP64 levels of rho, rho u, rho v, p
     double *p64_step;                   // FP64 pressure levels at the start of the step
@@ -572,6 +573,7 @@ void ac_batch_destroy(ac_batch *b) {
     cudaFree(b->pref64);
     cudaFree(b->jmp);
     cudaFree(b->lev_p);
+    cudaFree(b->dtau);
     cudaFree(b->partials);
     cudaFree(b->ctl);
     cudaFree(b->sync);
@@ -654,6 +656,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
     if (any_ref) CKB(cudaMalloc(&b->pref64, db));
     CKB(cudaMalloc(&b->jmp, total * sizeof(float2)));
     CKB(cudaMalloc(&b->lev_p, fb));
+    CKB(cudaMalloc(&b->dtau, fb));
     for (int f = 0; f < 3; ++f) {
         if (o.bdf_order >= 2) CKB(cudaMalloc(&b->D1[f], fb));
         if (o.bdf_order >= 3) CKB(cudaMalloc(&b->D2[f], fb));
@@ -713,6 +716,7 @@ int ac_batch_create(int n, const ac_grid *grids, const double *beta, const ac_bc
         a.p64_step = b->p64_step ? b->p64_step + pos : nullptr;
         a.pref64 = b->use_ref[k] ? b->pref64 + pos : nullptr;
         a.jmp = b->jmp + pos;
+        a.dtau = b->dtau + pos;
         a.lev_p = b->lev_p + pos;
         for (int f = 0; f < 3; ++f) {
             a.D1[f] = b->D1[f] ? b->D1[f] + pos : nullptr;

@@ -63,6 +63,8 @@ struct MixedArgs {
     float4 *qn;            // per cell (FP32 Q^n of rho, rho u, rho v; rho_ref)
     float2 *jmp;           // per cell (level jump across the west face, across the south face)
     float *lev_p;          // p at the start of the physical step (plevel = 0, for a restore)
+    float *dtau;           // per cell local pseudo-time step of the pseudo-iteration: written by stage 1 of
+                           // the column-strip sweep with the default options, read by its later stages
     float *D1[3], *D2[3];  // Q^n - Q^{n-1}, Q^n - Q^{n-2} (rho, rho u, rho v) for BDF2/BDF3
     int order;             // backward-difference order used in this step (1..3)
     float B0, B2, B3;      // its coefficients (Table BDF); B1 = -(B0 + B2 + B3)
@@ -290,13 +292,16 @@ __device__ __forceinline__ float4 face_flux(const MixedArgs &a, bool isx, const 
 // dp^{m}, Q^n and rho_ref of the cell.  live = false: the arithmetic runs
 // (a halo lane of the column-strip sweep, on a real cell's values) but
 // nothing is stored or summed.  FAST: the default options (local pseudo-time
-// step, alpha_PI on the p row) are compiled in rather than read.
-template <bool BDF, bool FAST = false, typename Src, typename Sq>
+// step, alpha_PI on the p row) are compiled in rather than read.  DTM: 0
+// forms the local pseudo-time step from Q^{m}; 1 forms it and stores it in
+// a.dtau (stage 1); 2 takes it from dt_in, as stage 1 stored it (the later
+// stages: Q^{m} is the same for every stage of a pseudo-iteration).
+template <bool BDF, bool FAST = false, int DTM = 0, typename Src, typename Sq>
 __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, float inv_dt, float b0dt, bool stage1,
                                             float4 *dout, int cell, int g, const float4 &Fw, const float4 &Fe,
                                             const float4 &Fs, const float4 &Fn, float fdx, float fdy, float jw,
                                             float je, float js, float jn, const Src &src, Sq &sq,
-                                            bool live = true) {
+                                            bool live = true, float dt_in = 0.0f) {
     const float div0 = (Fe.x - Fw.x) * fdx + (Fn.x - Fs.x) * fdy;
     const float div1 = (Fe.y - Fw.y) * fdx + (Fn.y - Fs.y) * fdy;
     const float div2 = (Fe.z - Fw.z) * fdx + (Fn.z - Fs.z) * fdy;
@@ -337,13 +342,18 @@ __device__ __forceinline__ void cell_update(const MixedArgs &a, float alpha, flo
     const float b2 = fmaf(jn + js, a.nh_inv_dy, fmaf(r0 - rref, a.gy, -div2 - rt2));
     const float b3 = -div3;
     float dtau;
-    if (FAST || a.local_dtau) {
+    if constexpr (DTM == 2) {
+        dtau = dt_in;
+    } else if (FAST || a.local_dtau) {
         const float ir = Ar<float>::rcp(r0);
         const float u = m0 * ir, v = n0 * ir, fb = 4.0f * a.beta * ir;
         const float u2 = u * u + fb, v2 = v * v + fb;
         const float cx = u2 * rsqrtf(u2), cy = v2 * rsqrtf(v2);
         const float den = 0.5f * (fabsf(u) + cx) * a.dy + 0.5f * (fabsf(v) + cy) * a.dx;
         dtau = __fdividef(a.cfl_area, den);
+        if constexpr (DTM == 1) {
+            if (live) a.dtau[g] = dtau;
+        }
     } else {
         dtau = float(global_dtau(a.ctl));
     }
@@ -749,6 +759,7 @@ struct StripRing {
     float4 e[4][32];   // dQ^{m}, dp^{m} (the ring terms)
     float jx[4][32];   // level jump across the east x-face (0 off the tank's rows)
     float jy[4][32];   // level jump across the south y-face (0 off the tank's faces)
+    float dt[4][32];   // local pseudo-time step that stage 1 stored (later stages, default options)
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -854,6 +865,7 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
         cp_async16(&ring->q[sl][lane], a.qn + s);
         cp_async16(&ring->d[sl][lane], din + s);
         if (SK != 1) cp_async16(&ring->e[sl][lane], d0 + s);
+        if (SK == 2) cp_async4(&ring->dt[sl][lane], a.dtau + s);
         if (!E) {
             // a tank row: whether its faces are the tank's depends on the lane
             // only, so every lane copies (a zero where the face is not the tank's)
@@ -960,8 +972,9 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
                     // row k - 2 is a tank row, so its slot holds this column's records
                     const float4 ue = ering(s2), uq = ring->q[s2][lane];
                     const HeldSrc Uk{ue.x, ue.y, ue.z, ue.w, uq.x, uq.y, uq.z, uq.w};
-                    cell_update<false, FAST>(a, alpha, inv_dt, b0dt, st1, dout, 0, (k - 2) * nx + c, Fw, Fxm2, Fyp,
-                                             Fy, hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq, out_lane);
+                    cell_update<false, FAST, SK>(a, alpha, inv_dt, b0dt, st1, dout, 0, (k - 2) * nx + c, Fw, Fxm2,
+                                                 Fyp, Fy, hidx, hidy, jw, Jm2, Jyp, jy1, Uk, sq, out_lane,
+                                                 SK == 2 ? ring->dt[s2][lane] : 0.0f);
                 }
                 Fyp = Fy;
                 Jyp = jy1;
