@@ -636,7 +636,9 @@ FP64_TRAFFIC_PER_CELL_STAGE = 83.7
 BYTES_PER_CELL_ITER_F64 = 376.0
 # mixed form: stage 1 reads the (Q^n, rho_ref) and (dQ^{m}, dp^{m}) records
 # (2 x 16 B) and the level-jump record (8 B) and writes 16 B; stages 2 and 3
-# also read the (dQ^{s-1}, dp^{s-1}) record (16 B)
+# also read the (dQ^{s-1}, dp^{s-1}) record (16 B).  The column-strip sweep
+# moves 4 B per cell and stage more (stage 1 stores the local pseudo-time
+# step, stages 2 and 3 read it): 212 B, a choice of the kernel, not counted here
 MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # measured (ncu, stages 1 and 2 of a pseudo-iteration on this 2048x8192
 # tank, summarised under profiles/) for the strip variant the autotuner
@@ -645,8 +647,8 @@ MIXED_BYTES_PER_CELL_ITER = 56.0 + 2 * 72.0
 # mean over the three stages (stage 3 as stage 2).  A variant without a
 # capture of its current code reports null.
 MIXED_COUNTS_BY_VARIANT = {
-    16: ((57.8 + 2 * 75.4) / 3, (464.5 + 2 * 438.2) / 3),   # sweep_kernel_mixed<64,4,4,1>, <64,4,4,2>
-    17: ((56.3 + 2 * 73.3) / 3, (460.9 + 2 * 434.6) / 3),   # sweep_kernel_mixed<128,4,4,1>, <128,4,4,2>
+    16: ((61.5 + 2 * 79.7) / 3, (449.7 + 2 * 405.6) / 3),   # sweep_kernel_mixed<64,4,4,1>, <64,4,4,2>
+    17: ((60.0 + 2 * 77.5) / 3, (446.5 + 2 * 402.4) / 3),   # sweep_kernel_mixed<128,4,4,1>, <128,4,4,2>
 }
 FP32_PEAK_TOPS = 128 * 152 * 2.07e9 / 1e12
 
