@@ -1016,8 +1016,8 @@ __device__ __forceinline__ void mixed_strip(const MixedArgs &a, int stage, float
 
 // SK: 0 for any stage and options, 1 and 2 for stage 1 and the later stages
 // with the default options (see mixed_strip); the stage-1 instance runs its
-// row loop plain (unrolled by 2 it spills 150 bytes), the others unroll it
-// by 2 (the later-stage instance spills 24 bytes and still gains ~1 %).
+// row loop plain (unrolled by 2 it spills and gains nothing measurable), the
+// others unroll it by 2, which keeps the rolling rows' registers in place.
 template <int H, int WPC, int MINB, int SK>
 __global__ void __launch_bounds__(WPC * 32, MINB)
 sweep_kernel_mixed(const MixedArgs a, int strips_x, int nstrips) {
