@@ -206,6 +206,7 @@ struct StageSmem {
     static constexpr int NXF = (TX + 1) * TY;        // x-faces
     static constexpr int NYF = TX * (TY + 1);        // y-faces
     T w[4][RW * RH];      // rho, u, v, p
+    T wir[RW * RH];       // 1/rho of w (stage 1's local pseudo-time step takes it, with u and v)
     T rt[2][GW * GH];     // frozen real-time term of rho u, rho v on the ring
     T gx[4][GW * GH];     // half slopes along x: rho, u, v, p (times dx/2 for p)
     T gy[4][GW * GH];     // half slopes along y
@@ -260,6 +261,7 @@ stage_kernel(const SweepArgs<T> a) {
         sm.w[1][k] = m * ir;
         sm.w[2][k] = n * ir;
         sm.w[3][k] = qin[3][s];
+        sm.wir[k] = ir;
     }
     // ---- frozen real-time term of the momenta on the ring (Eq. bdf, BE) ----
     const bool need_rt = (a.gradp == kGradNew) && a.realtime;
@@ -421,6 +423,12 @@ stage_kernel(const SweepArgs<T> a) {
         for (int f = 0; f < 4; ++f)
             div[f] = (sm.fx[f][fe] - sm.fx[f][fw]) * hidx + (sm.fy[f][fn] - sm.fy[f][fs]) * hidy;
         const T r0 = q0[0][g], m0 = q0[1][g], n0 = q0[2][g], p0 = q0[3][g];
+        // At stage 1 the input Q^{s-1} is Q^{m} itself, so the cell's W (never
+        // a folded ghost here) holds the 1/rho, u and v of Q^{m}, and the ring
+        // already holds its momenta's real-time terms: taken as they are, the
+        // same values to the last bit.
+        const bool from_tile = a.stage == 1;
+        const int ct = (lj + 2) * RW + (li + 2), cr = (lj + 1) * GW + (li + 1);
         T rt0 = T(0), rt1 = T(0), rt2 = T(0);
         if (a.realtime) {
             if (reuse_now) {
@@ -429,8 +437,13 @@ stage_kernel(const SweepArgs<T> a) {
                 rt2 = a.aux[3][g];
             } else {
                 rt0 = realtime_term(a, r0, 0, g, inv_dt);
-                rt1 = realtime_term(a, m0, 1, g, inv_dt);
-                rt2 = realtime_term(a, n0, 2, g, inv_dt);
+                if (from_tile && need_rt) {
+                    rt1 = sm.rt[0][cr];
+                    rt2 = sm.rt[1][cr];
+                } else {
+                    rt1 = realtime_term(a, m0, 1, g, inv_dt);
+                    rt2 = realtime_term(a, n0, 2, g, inv_dt);
+                }
                 if (a.reuse) {
                     a.aux[1][g] = rt0;
                     a.aux[2][g] = rt1;
@@ -447,8 +460,17 @@ stage_kernel(const SweepArgs<T> a) {
         if (a.local_dtau && reuse_now) {
             dtau = a.aux[0][g];
         } else if (a.local_dtau) {
-            const T ir = Ar<T>::rcp(r0);
-            const T u = m0 * ir, v = n0 * ir, fb = T(4) * a.beta * ir;
+            T ir, u, v;
+            if (from_tile) {
+                ir = sm.wir[ct];
+                u = sm.w[1][ct];
+                v = sm.w[2][ct];
+            } else {
+                ir = Ar<T>::rcp(r0);
+                u = m0 * ir;
+                v = n0 * ir;
+            }
+            const T fb = T(4) * a.beta * ir;
             // square roots as x / sqrt(x) and quotients as products with a
             // rounded reciprocal: a few ulps, far inside the 1e-11 bar
             T cx, cy, unused;
