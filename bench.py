@@ -620,11 +620,11 @@ def run_batched(args, stream, flush, barrier):
 # a tile's ring, stage-1 values read back), only with the formulation.
 FP64_ALG_FLOPS_PER_CELL_STAGE = 483.0
 # what stage_kernel<double,32,14> executes on this 256x256 tank (ncu: DFMA x 2
-# + DADD + DMUL, mean of stages 1-3: 741.3, 639.2, 639.2; the tile's ring
+# + DADD + DMUL, mean of stages 1-3: 721.2, 639.2, 639.2; the tile's ring
 # recomputes slopes and pressure gradients, and stage 1 forms the values
 # stages 2 and 3 read back), and the FP64 instructions behind them
-FP64_EXEC_FLOPS_PER_CELL_STAGE = 673.2
-FP64_INSTR_PER_CELL_STAGE = 459.7
+FP64_EXEC_FLOPS_PER_CELL_STAGE = 666.5
+FP64_INSTR_PER_CELL_STAGE = 455.3
 FP64_PIPE_INSTR_PER_S = 2 * 152 * 2.07e9
 # DRAM bytes per cell of one FP64 stage launch, same capture, averaged over
 # the three stages (3.74, 6.36, 6.36 MB read; the output stays in L2)
