@@ -208,8 +208,8 @@ struct StageSmem {
     T w[4][RW * RH];      // rho, u, v, p
     T wir[RW * RH];       // 1/rho of w (stage 1's local pseudo-time step takes it, with u and v)
     T rt[2][GW * GH];     // frozen real-time term of rho u, rho v on the ring
-    T gx[4][GW * GH];     // half slopes along x: rho, u, v, p (times dx/2 for p)
-    T gy[4][GW * GH];     // half slopes along y
+    T gx[4][GW * GH];     // whole slopes along x: rho, u, v, p (the face states take half of each)
+    T gy[4][GW * GH];     // whole slopes along y
     T fx[4][NXF];         // x-face fluxes: mass, x-mom, y-mom, p/beta
     T fy[4][NYF];         // y-face fluxes
     double red[4][TX * TY / 32];
